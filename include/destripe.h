@@ -1,0 +1,202 @@
+/*
+ * destripe.h -- C ABI of the GB300 destriper.
+ *
+ * Maximum-likelihood destriping of polarimeter / radiometer timelines
+ * (Zonca, Williams, Meinhold & Lubin 2013, "Destriping Cosmic Microwave
+ * Background Polarimeter data", Sect. 3).  The data model is
+ *
+ *     y = A_p m + F~ a + w                       (Eqs. destmodel and noise)
+ *
+ * with A_p the pointing-and-rotation operator (one pixel per sample, rows
+ * w_o(t) per output kind), F~ the baseline matrix (each of the n_b baselines of
+ * an output repeated over its L samples) and w white noise.  The baselines solve
+ *
+ *     [F~^T Z F~] a = F~^T Z y,   Z = V - V A_p M^-1 A_p^T V   (destriping equation)
+ *
+ * where V holds the 0/1 sample weights and M_p = sum_t v w w^T is the per-pixel
+ * normal matrix (h_p times the identity for a q+u polarimeter, Sect. 3).
+ *
+ * Conventions shared by every call:
+ *  - All d_* arguments are DEVICE pointers on the current CUDA device.  The
+ *    caller owns them; a plan keeps the pointing pointers passed to
+ *    destripe_plan (pixels are copied, cos/sin are referenced) until
+ *    destripe_destroy, and keeps no other caller pointer past a call.
+ *  - Arrays are dense and contiguous.  Timelines are output-major
+ *    [n_outputs][n_samples]; baselines are output-major
+ *    [n_outputs][n_baselines]; maps are component-major [n_comp][n_pix] with
+ *    components (I), (Q, U) or (I, Q, U) -- I when any output carries I, Q and U
+ *    when any output carries polarisation.  d_cos2psi and d_sin2psi must be
+ *    16-byte aligned.
+ *  - Work is enqueued on desc->stream (a cudaStream_t; NULL = legacy default
+ *    stream).  Calls return once the work is enqueued, except destripe_plan,
+ *    destripe_solve and destripe_run_host, which synchronise the stream because
+ *    they return host-side results.
+ *  - Errors are reported as ds_status codes only; nothing aborts or throws
+ *    across the ABI.  destripe_strerror gives a static message.
+ *  - A plan is not thread-safe; distinct plans are independent.
+ *  - Precision: DS_PREC_FP64 computes every step in float64 and takes float64
+ *    timelines y.  DS_PREC_MIXED takes float32 timelines y; the per-sample work
+ *    of the CG iterations (expand, bin, rescan, baseline sums) runs in float32
+ *    with float64 accumulation of partial sums, while pixel matrices, their
+ *    inverses and rcond cut, the right-hand side, the CG scalars, the residual
+ *    updates that keep the iteration honest, and the final maps use float64.
+ */
+#ifndef DESTRIPE_H
+#define DESTRIPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ds_plan_s* ds_plan_t;
+
+typedef enum {
+  DS_OK = 0,
+  DS_EINVAL = 1,    /* bad descriptor or argument (sizes, kinds, alignment, NULL) */
+  DS_ENOMEM = 2,    /* device allocation failed */
+  DS_ECUDA = 3,     /* a CUDA runtime call failed */
+  DS_ENOCONV = 4,   /* CG reached max_iter; the best iterate is still written */
+  DS_ETIMEOUT = 5,  /* a bounded device wait gave up */
+  DS_ENAN = 6,      /* non-finite value met in the data or the iteration */
+  DS_EPIX = 7,      /* a pixel index outside [0, 12 nside^2) */
+  DS_ESTATE = 8     /* call not valid for this plan (e.g. precision mismatch) */
+} ds_status;
+
+/* Output kinds and their rows w_o(t), c = cos 2psi, s = sin 2psi (Sect. 3). */
+typedef enum {
+  DS_KIND_I = 0,   /* (1)            on I                  */
+  DS_KIND_Q = 1,   /* ( c, s)        on (Q, U): q channel   */
+  DS_KIND_U = 2,   /* (-s, c)        on (Q, U): u channel   */
+  DS_KIND_IQU = 3  /* (1, c, s)      on (I, Q, U): radiometer */
+} ds_kind;
+
+typedef enum { DS_PREC_FP64 = 0, DS_PREC_MIXED = 1 } ds_prec;
+
+#define DS_MAX_OUTPUTS 4
+
+typedef struct {
+  int64_t n_samples;              /* n_t >= 1, < 2^31 */
+  int32_t nside;                  /* HEALPix resolution, power of two, 1..8192 */
+  int32_t n_outputs;              /* 1..DS_MAX_OUTPUTS outputs sharing the pointing */
+  int32_t kinds[DS_MAX_OUTPUTS];  /* ds_kind of each output */
+  int64_t baseline_len;           /* L >= 1 samples per baseline; the last one may be short */
+  int32_t precision;              /* ds_prec */
+  int32_t reserved;               /* must be 0 */
+  double rcond_min;               /* pixel cut on lambda_min/lambda_max of M_p; <= 0 means 1e-3 */
+  void* stream;                   /* cudaStream_t */
+} ds_desc;
+
+typedef struct {
+  int64_t n_samples;
+  int64_t n_baselines;   /* per output: ceil(n_t / L) */
+  int64_t n_unknowns;    /* n_outputs * n_baselines */
+  int64_t n_pix;         /* 12 nside^2 */
+  int64_t n_good_pix;    /* pixels kept by the cut */
+  int64_t n_valid;       /* samples with weight 1 after flags and the cut */
+  int32_t n_outputs;
+  int32_t n_comp;        /* 1, 2 or 3 */
+  int64_t device_bytes;  /* bytes the plan holds on the device */
+} ds_info;
+
+/* Build a plan: hits, per-pixel normal matrices M_p, their inverses and the
+ * rcond cut (Sect. 3: hitmap h = P^T P and the QU / IQU weighting).
+ *   d_pix      int32 [n_t]  HEALPix RING pixel of each sample (copied)
+ *   d_cos2psi  float [n_t]  cos 2psi (referenced until destroy; 16-B aligned)
+ *   d_sin2psi  float [n_t]  sin 2psi (referenced until destroy; 16-B aligned)
+ *   d_valid    uint8 [n_t]  1 = good sample, 0 = flagged; NULL = all good.  A flag
+ *                           applies to every output of the sample.
+ * Samples on cut pixels get weight 0 in every later call.  Returns DS_EPIX if a
+ * valid sample has a pixel outside the map.  Synchronises desc->stream. */
+ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* d_cos2psi,
+                        const float* d_sin2psi, const uint8_t* d_valid, ds_plan_t* out);
+
+ds_status destripe_plan_info(ds_plan_t plan, ds_info* info);
+
+/* Binned map m = M^-1 sum_t sum_o v w_o(t) (y_o(t) - a_o[t / L]) (Eqs. mapQ/mapU
+ * with the general pixel weight), 0 on cut pixels.
+ *   d_y    [n_o][n_t] float64 (FP64 plan) or float32 (MIXED plan)
+ *   d_a    float64 [n_o][n_b] baselines to subtract, or NULL for none
+ *   d_map  float64 [n_c][n_pix] output
+ *   d_hits int32 [n_pix] output (valid samples per pixel, before the cut), or NULL
+ *   d_mask uint8 [n_pix] output (1 = pixel kept), or NULL
+ * Always accumulated in float64. */
+ds_status destripe_bin(ds_plan_t plan, const void* d_y, const double* d_a, double* d_map,
+                       int32_t* d_hits, uint8_t* d_mask);
+
+/* Left-hand operator of the destriping equation, d_Ax = F~^T Z F~ d_x
+ * (Sect. 3: expand, bin, per-pixel solve, rescan, per-baseline sum).
+ *   d_x, d_Ax  float64 [n_o][n_b]; must not alias.
+ * Uses the plan's precision for the per-sample work. */
+ds_status destripe_apply_A(ds_plan_t plan, const double* d_x, double* d_Ax);
+
+/* Right-hand side d_b = F~^T Z y (float64 accumulation). */
+ds_status destripe_rhs(ds_plan_t plan, const void* d_y, double* d_b);
+
+/* Solve the destriping equation by conjugate gradient (Sect. 3 names CG; the
+ * operator is symmetric positive semi-definite).
+ *   d_y        timelines as for destripe_bin
+ *   d_a        float64 [n_o][n_b]: in = starting guess if warm_start, out = baselines,
+ *              gauge-fixed (outputs carrying I get zero mean over baselines with data;
+ *              baselines without data are 0)
+ *   tol        stop when ||b - A a|| / ||b|| < tol (recursive residual, confirmed by a
+ *              float64 residual in MIXED mode)
+ *   max_iter   iteration cap (<= 0 means 10000)
+ *   iters, rel_resid  host outputs (may be NULL): iterations run and the float64
+ *              relative residual at exit
+ * Returns DS_ENOCONV (with the best iterate written) if max_iter is reached.
+ * Synchronises desc->stream. */
+ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double tol,
+                         int32_t max_iter, int32_t warm_start, int32_t* iters,
+                         double* rel_resid);
+
+/* Destriped map m(y - F~ a) plus hits and mask (the outputs of Sect. 4). */
+ds_status destripe_map(ds_plan_t plan, const void* d_y, const double* d_a, double* d_map,
+                       int32_t* d_hits, uint8_t* d_mask);
+
+/* Remove the I null mode from d_a in place (see destripe_solve). */
+ds_status destripe_gauge(ds_plan_t plan, double* d_a);
+
+void destripe_destroy(ds_plan_t plan);
+
+const char* destripe_strerror(ds_status status);
+
+/* Whole job from HOST buffers: copy the pointing and timelines to the device,
+ * plan, solve, build the destriped map, copy a, the map, hits and mask back.
+ * Host arrays may be pageable or pinned.  h_valid may be NULL.  Outputs
+ * h_a [n_o][n_b], h_map [n_c][n_pix], h_hits [n_pix], h_mask [n_pix] may each
+ * be NULL to skip the copy.  h_y is float64 for FP64, float32 for MIXED.
+ * Synchronises desc->stream. */
+ds_status destripe_run_host(const ds_desc* desc, const int32_t* h_pix, const float* h_cos2psi,
+                            const float* h_sin2psi, const uint8_t* h_valid, const void* h_y,
+                            double tol, int32_t max_iter, double* h_a, double* h_map,
+                            int32_t* h_hits, uint8_t* h_mask, int32_t* iters,
+                            double* rel_resid);
+
+/* Kernel timing and launch counts of a plan (no counterpart in the paper; it
+ * exists to measure the kernels against the HBM roofline).  While profiling is
+ * enabled, the captured CG graph records CUDA events around the binning and
+ * rescan kernels of every iteration; destripe_solve accumulates their elapsed
+ * times over the iterations that actually ran.  Launch counting is always on.
+ *   enable  1 = enable and reset the counters, 0 = disable, -1 = leave as is
+ *   out     may be NULL; filled with the counters since the last reset */
+typedef struct {
+  int64_t kernel_launches;  /* kernels this plan launched (graph nodes counted per replay) */
+  int64_t graph_launches;   /* replays of the captured CG graph */
+  int64_t iterations;       /* CG iterations that ran */
+  int64_t timed_iterations; /* iterations with event timings (profiling enabled) */
+  double bin_ms;            /* sum over timed iterations: binning kernel of A p */
+  double rescan_ms;         /* sum: rescan + per-baseline-sum kernel of A p */
+  double solve_ms;          /* sum: per-pixel solve kernel of A p */
+  double iteration_ms;      /* sum: whole iteration, first kernel start to last kernel end */
+} ds_profile;
+
+ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DESTRIPE_H */

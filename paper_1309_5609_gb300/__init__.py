@@ -1,0 +1,341 @@
+"""GB300 destriper: Python binding of the C ABI in include/destripe.h.
+
+Maximum-likelihood destriping of CMB polarimeter timelines (Zonca et al. 2013,
+Sect. 3): the baselines a solve [F~^T Z F~] a = F~^T Z y by conjugate gradient,
+every step running in the CUDA kernels of libdestripe.so (built for sm_103a).
+
+This module only marshals arguments: torch tensors supply device memory and
+the current CUDA stream, and each function calls the C entry point of the same
+name.  There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+__all__ = [
+    "DS_OK", "DS_ENOCONV", "DestripeError", "Plan", "KIND_CODE", "lib_path", "load_library",
+    "destripe_plan", "destripe_plan_info", "destripe_bin", "destripe_apply_A", "destripe_rhs",
+    "destripe_solve", "destripe_map", "destripe_gauge", "destripe_destroy", "destripe_strerror",
+    "destripe_run_host", "destripe_profile", "components",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+DS_OK, DS_EINVAL, DS_ENOMEM, DS_ECUDA, DS_ENOCONV, DS_ETIMEOUT, DS_ENAN, DS_EPIX, DS_ESTATE = range(9)
+DS_PREC_FP64, DS_PREC_MIXED = 0, 1
+KIND_CODE = {"I": 0, "q": 1, "u": 2, "iqu": 3}
+PRECISION = {"fp64": DS_PREC_FP64, "mixed": DS_PREC_MIXED}
+
+
+class ds_desc(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int64), ("nside", ctypes.c_int32),
+                ("n_outputs", ctypes.c_int32), ("kinds", ctypes.c_int32 * 4),
+                ("baseline_len", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rcond_min", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class ds_info(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int64), ("n_baselines", ctypes.c_int64),
+                ("n_unknowns", ctypes.c_int64), ("n_pix", ctypes.c_int64),
+                ("n_good_pix", ctypes.c_int64), ("n_valid", ctypes.c_int64),
+                ("n_outputs", ctypes.c_int32), ("n_comp", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class ds_profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("timed_iterations", ctypes.c_int64),
+                ("bin_ms", ctypes.c_double), ("rescan_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("iteration_ms", ctypes.c_double)]
+
+
+class DestripeError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {destripe_strerror(status)} (status {status})")
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "destripe_plan": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "destripe_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ds_info)]),
+    "destripe_bin": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "destripe_apply_A": (ctypes.c_int, [_P, _P, _P]),
+    "destripe_rhs": (ctypes.c_int, [_P, _P, _P]),
+    "destripe_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "destripe_map": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "destripe_gauge": (ctypes.c_int, [_P, _P]),
+    "destripe_destroy": (None, [_P]),
+    "destripe_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ds_profile)]),
+    "destripe_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "destripe_run_host": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P,
+                                         ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P,
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def lib_path() -> str:
+    return os.path.join(HERE, "libdestripe.so")
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libdestripe.so (building it with nvcc if it is missing or stale)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        if build_if_missing:
+            from . import build as _build
+            _build.build()
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"destriper library not built: {path} is missing")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+        return lib
+
+
+def destripe_strerror(status: int) -> str:
+    try:
+        return load_library(build_if_missing=False).destripe_strerror(int(status)).decode()
+    except Exception:
+        return f"status {status}"
+
+
+def components(kinds: Sequence[str]) -> tuple:
+    has_i = any(k in ("I", "iqu") for k in kinds)
+    has_p = any(k in ("q", "u", "iqu") for k in kinds)
+    return ("I", "Q", "U") if has_i and has_p else (("Q", "U") if has_p else ("I",))
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _check(t, dtype, numel, name, device=None):
+    import torch
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, plan is on {device}")
+    return t
+
+
+class Plan:
+    """Handle of a C plan plus the tensors it references (kept alive here)."""
+
+    def __init__(self, handle, desc: ds_desc, kinds, nside, refs, device):
+        self.handle = handle
+        self.desc = desc
+        self.kinds = tuple(kinds)
+        self.nside = nside
+        self._refs = refs
+        self.device = device
+        info = destripe_plan_info(self)
+        self.n_t = info["n_samples"]
+        self.n_b = info["n_baselines"]
+        self.n_u = info["n_unknowns"]
+        self.npix = info["n_pix"]
+        self.n_c = info["n_comp"]
+        self.n_o = info["n_outputs"]
+        self.info = info
+
+    @property
+    def precision(self) -> str:
+        return "fp64" if self.desc.precision == DS_PREC_FP64 else "mixed"
+
+    @property
+    def y_dtype(self):
+        import torch
+        return torch.float64 if self.desc.precision == DS_PREC_FP64 else torch.float32
+
+    def close(self):
+        if self.handle:
+            load_library().destripe_destroy(self.handle)
+            self.handle = None
+            self._refs = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _make_desc(n_t, nside, kinds, baseline_len, precision, rcond_min, stream) -> ds_desc:
+    d = ds_desc()
+    d.n_samples = int(n_t)
+    d.nside = int(nside)
+    d.n_outputs = len(kinds)
+    if not 1 <= len(kinds) <= 4:
+        raise ValueError("1 to 4 outputs")
+    for i, k in enumerate(kinds):
+        d.kinds[i] = KIND_CODE[k]
+    d.baseline_len = int(baseline_len)
+    d.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    d.reserved = 0
+    d.rcond_min = float(rcond_min)
+    d.stream = stream
+    return d
+
+
+def destripe_plan(pix, cos2psi, sin2psi, valid=None, *, nside: int, kinds=("q", "u"),
+                  baseline_len: int, precision="mixed", rcond_min: float = 1e-3,
+                  stream=None) -> Plan:
+    """Plan on the pointing (device tensors): int32 pix, float32 cos/sin 2psi, uint8 valid."""
+    import torch
+    lib = load_library()
+    n_t = pix.numel()
+    dev = pix.device
+    _check(pix, torch.int32, n_t, "pix")
+    _check(cos2psi, torch.float32, n_t, "cos2psi", dev)
+    _check(sin2psi, torch.float32, n_t, "sin2psi", dev)
+    if valid is not None:
+        _check(valid, torch.uint8, n_t, "valid", dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    desc = _make_desc(n_t, nside, kinds, baseline_len, precision, rcond_min, stream)
+    h = _P()
+    st = lib.destripe_plan(ctypes.byref(desc), _ptr(pix), _ptr(cos2psi), _ptr(sin2psi),
+                           _ptr(valid), ctypes.byref(h))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_plan")
+    return Plan(h, desc, kinds, nside, (cos2psi, sin2psi), dev)
+
+
+def destripe_plan_info(plan: Plan) -> dict:
+    info = ds_info()
+    st = load_library().destripe_plan_info(plan.handle, ctypes.byref(info))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_plan_info")
+    return {f: getattr(info, f) for f, _ in ds_info._fields_}
+
+
+def destripe_bin(plan: Plan, y, a, map_out, hits_out=None, mask_out=None):
+    import torch
+    _check(y, plan.y_dtype, plan.n_o * plan.n_t, "y", plan.device)
+    if a is not None:
+        _check(a, torch.float64, plan.n_u, "a", plan.device)
+    _check(map_out, torch.float64, plan.n_c * plan.npix, "map", plan.device)
+    if hits_out is not None:
+        _check(hits_out, torch.int32, plan.npix, "hits", plan.device)
+    if mask_out is not None:
+        _check(mask_out, torch.uint8, plan.npix, "mask", plan.device)
+    st = load_library().destripe_bin(plan.handle, _ptr(y), _ptr(a), _ptr(map_out),
+                                     _ptr(hits_out), _ptr(mask_out))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_bin")
+
+
+def destripe_map(plan: Plan, y, a, map_out, hits_out=None, mask_out=None):
+    import torch
+    _check(y, plan.y_dtype, plan.n_o * plan.n_t, "y", plan.device)
+    _check(a, torch.float64, plan.n_u, "a", plan.device)
+    _check(map_out, torch.float64, plan.n_c * plan.npix, "map", plan.device)
+    st = load_library().destripe_map(plan.handle, _ptr(y), _ptr(a), _ptr(map_out),
+                                     _ptr(hits_out), _ptr(mask_out))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_map")
+
+
+def destripe_apply_A(plan: Plan, x, Ax):
+    import torch
+    _check(x, torch.float64, plan.n_u, "x", plan.device)
+    _check(Ax, torch.float64, plan.n_u, "Ax", plan.device)
+    st = load_library().destripe_apply_A(plan.handle, _ptr(x), _ptr(Ax))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_apply_A")
+
+
+def destripe_rhs(plan: Plan, y, b):
+    import torch
+    _check(y, plan.y_dtype, plan.n_o * plan.n_t, "y", plan.device)
+    _check(b, torch.float64, plan.n_u, "b", plan.device)
+    st = load_library().destripe_rhs(plan.handle, _ptr(y), _ptr(b))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_rhs")
+
+
+def destripe_solve(plan: Plan, y, a, tol: float = 1e-10, max_iter: int = 10000,
+                   warm_start: bool = False):
+    """Returns (status, iterations, float64 relative residual); raises on errors
+    other than DS_ENOCONV."""
+    import torch
+    _check(y, plan.y_dtype, plan.n_o * plan.n_t, "y", plan.device)
+    _check(a, torch.float64, plan.n_u, "a", plan.device)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    st = load_library().destripe_solve(plan.handle, _ptr(y), _ptr(a), float(tol), int(max_iter),
+                                       1 if warm_start else 0, ctypes.byref(it), ctypes.byref(rr))
+    if st not in (DS_OK, DS_ENOCONV):
+        raise DestripeError(st, "destripe_solve")
+    return st, it.value, rr.value
+
+
+def destripe_gauge(plan: Plan, a):
+    import torch
+    _check(a, torch.float64, plan.n_u, "a", plan.device)
+    st = load_library().destripe_gauge(plan.handle, _ptr(a))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_gauge")
+
+
+def destripe_destroy(plan: Plan):
+    plan.close()
+
+
+def destripe_profile(plan: Plan, enable: int = -1) -> dict:
+    """enable: 1 = on (resets counters), 0 = off, -1 = unchanged; returns the counters."""
+    prof = ds_profile()
+    st = load_library().destripe_profile(plan.handle, int(enable), ctypes.byref(prof))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_profile")
+    return {f: getattr(prof, f) for f, _ in ds_profile._fields_}
+
+
+def destripe_run_host(pix, cos2psi, sin2psi, valid, y, *, nside: int, kinds, baseline_len: int,
+                      precision="mixed", tol: float = 1e-10, max_iter: int = 10000,
+                      rcond_min: float = 1e-3, stream=None, out_a=None, out_map=None,
+                      out_hits=None, out_mask=None):
+    """Whole job from host (CPU) tensors; outputs are written into the given CPU
+    tensors.  Returns (status, iterations, relative residual)."""
+    import torch
+    lib = load_library()
+    for t, name in ((pix, "pix"), (cos2psi, "cos2psi"), (sin2psi, "sin2psi"), (y, "y")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    desc = _make_desc(pix.numel(), nside, kinds, baseline_len, precision, rcond_min, stream)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    st = lib.destripe_run_host(ctypes.byref(desc), _ptr(pix), _ptr(cos2psi), _ptr(sin2psi),
+                               _ptr(valid), _ptr(y), float(tol), int(max_iter), _ptr(out_a),
+                               _ptr(out_map), _ptr(out_hits), _ptr(out_mask), ctypes.byref(it),
+                               ctypes.byref(rr))
+    if st not in (DS_OK, DS_ENOCONV):
+        raise DestripeError(st, "destripe_run_host")
+    return st, it.value, rr.value

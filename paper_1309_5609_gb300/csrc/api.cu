@@ -1,0 +1,446 @@
+// C ABI entry points (include/destripe.h).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace ds {
+void enqueue_dot(const Plan& P, cudaStream_t st, const double* a, const double* b, int64_t n,
+                 double* out);
+void enqueue_gauge(const Plan& P, cudaStream_t st, double* a);
+void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev);
+void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, double delta,
+                      int warm);
+}  // namespace ds
+
+using namespace ds;
+
+namespace {
+
+constexpr int kGraphIters = 16;        // CG iterations per captured graph launch
+constexpr double kReliableDelta = 1e-3;  // float64 residual after every 1e3 drop in ||r||
+
+int n_comp_of(const int* kinds, int n_o, int* has_i_out) {
+  bool I = false, P = false;
+  int hi = 0;
+  for (int o = 0; o < n_o; ++o) {
+    if (kinds[o] == DS_KIND_I || kinds[o] == DS_KIND_IQU) { I = true; hi = 1; }
+    if (kinds[o] == DS_KIND_Q || kinds[o] == DS_KIND_U || kinds[o] == DS_KIND_IQU) P = true;
+  }
+  *has_i_out = hi;
+  return (I && P) ? 3 : (P ? 2 : 1);
+}
+
+int kindset_of(const int* k, int n_o, int n_c) {
+  if (n_o == 2 && k[0] == DS_KIND_Q && k[1] == DS_KIND_U) return KS_QU;
+  if (n_o == 3 && k[0] == DS_KIND_I && k[1] == DS_KIND_Q && k[2] == DS_KIND_U) return KS_IQU3;
+  if (n_o == 1 && k[0] == DS_KIND_IQU) return KS_IQU1;
+  if (n_o == 1 && k[0] == DS_KIND_I) return KS_I;
+  return n_c == 1 ? KS_GEN1 : (n_c == 2 ? KS_GEN2 : KS_GEN3);
+}
+
+template <typename T>
+cudaError_t dalloc(Plan& P, T** ptr, int64_t count) {
+  const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+  P.device_bytes += (int64_t)bytes;
+  return cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+}
+
+void plan_free(Plan* P) {
+  if (P == nullptr) return;
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+  if (P->ev) {
+    for (int i = 0; i < P->graph_iters * 5; ++i) cudaEventDestroy(P->ev[i]);
+    delete[] P->ev;
+  }
+  void* dev[] = {P->pix, P->hits, P->mask, P->minv, P->bins, P->map32, P->map64, P->nvalid,
+                 P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->red,   P->counters,
+                 P->state, P->err, P->scal};
+  for (void* d : dev)
+    if (d) cudaFree(d);
+  if (P->h_state) cudaFreeHost(P->h_state);
+  if (P->h_err) cudaFreeHost(P->h_err);
+  if (P->h_scal) cudaFreeHost(P->h_scal);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  delete P;
+}
+
+ds_status check_desc(const ds_desc* d) {
+  if (d == nullptr) return DS_EINVAL;
+  if (d->n_samples < 1 || d->n_samples >= (int64_t(1) << 31)) return DS_EINVAL;
+  if (d->nside < 1 || d->nside > 8192 || (d->nside & (d->nside - 1)) != 0) return DS_EINVAL;
+  if (d->n_outputs < 1 || d->n_outputs > DS_MAX_OUTPUTS) return DS_EINVAL;
+  for (int o = 0; o < d->n_outputs; ++o)
+    if (d->kinds[o] < DS_KIND_I || d->kinds[o] > DS_KIND_IQU) return DS_EINVAL;
+  if (d->baseline_len < 1 || d->baseline_len > d->n_samples * 1 + (int64_t(1) << 30)) return DS_EINVAL;
+  if (d->precision != DS_PREC_FP64 && d->precision != DS_PREC_MIXED) return DS_EINVAL;
+  if (d->reserved != 0) return DS_EINVAL;
+  return DS_OK;
+}
+
+ds_status launch_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DS_OK : DS_ECUDA;
+}
+
+ds_status build_graph(Plan& P) {
+  if (P.graph_exec && P.graph_profiled == P.profiling) return DS_OK;
+  if (P.graph_exec) {
+    cudaGraphExecDestroy(P.graph_exec);
+    P.graph_exec = nullptr;
+  }
+  if (P.profiling && P.ev == nullptr) {
+    P.ev = new (std::nothrow) cudaEvent_t[kGraphIters * 5];
+    if (P.ev == nullptr) return DS_ENOMEM;
+    for (int i = 0; i < kGraphIters * 5; ++i) DS_CUDA_TRY(cudaEventCreate(&P.ev[i]));
+  }
+  P.graph_iters = kGraphIters;
+  cudaGraph_t graph = nullptr;
+  DS_CUDA_TRY(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < kGraphIters; ++k)
+    enqueue_iteration(P, P.cap_stream, P.profiling ? P.ev + 5 * k : nullptr);
+  cudaError_t e = cudaStreamEndCapture(P.cap_stream, &graph);
+  if (e != cudaSuccess) return DS_ECUDA;
+  e = cudaGraphInstantiate(&P.graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    P.graph_exec = nullptr;
+    return DS_ECUDA;
+  }
+  P.graph_profiled = P.profiling;
+  return DS_OK;
+}
+
+// Adds the event timings of the first n_ran iterations of the last graph replay.
+void collect_times(Plan& P, int n_ran) {
+  if (!P.graph_profiled || P.ev == nullptr) return;
+  for (int k = 0; k < n_ran && k < P.graph_iters; ++k) {
+    cudaEvent_t* e = P.ev + 5 * k;
+    float t01 = 0.f, t12 = 0.f, t23 = 0.f, t04 = 0.f;
+    if (cudaEventElapsedTime(&t01, e[0], e[1]) != cudaSuccess) return;
+    cudaEventElapsedTime(&t12, e[1], e[2]);
+    cudaEventElapsedTime(&t23, e[2], e[3]);
+    cudaEventElapsedTime(&t04, e[0], e[4]);
+    P.t_bin += t01;
+    P.t_solve += t12;
+    P.t_rescan += t23;
+    P.t_iter += t04;
+    P.timed_iterations += 1;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* destripe_strerror(ds_status s) {
+  switch (s) {
+    case DS_OK: return "ok";
+    case DS_EINVAL: return "invalid argument";
+    case DS_ENOMEM: return "device allocation failed";
+    case DS_ECUDA: return "CUDA runtime error";
+    case DS_ENOCONV: return "conjugate gradient did not converge within max_iter";
+    case DS_ETIMEOUT: return "bounded device wait timed out";
+    case DS_ENAN: return "non-finite value in data or iteration";
+    case DS_EPIX: return "pixel index outside the map";
+    case DS_ESTATE: return "call not valid for this plan";
+  }
+  return "unknown status";
+}
+
+ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* d_cos2psi,
+                        const float* d_sin2psi, const uint8_t* d_valid, ds_plan_t* out) {
+  if (out == nullptr) return DS_EINVAL;
+  *out = nullptr;
+  ds_status s = check_desc(desc);
+  if (s != DS_OK) return s;
+  if (d_pix == nullptr || d_cos2psi == nullptr || d_sin2psi == nullptr) return DS_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_cos2psi) & 15) || (reinterpret_cast<uintptr_t>(d_sin2psi) & 15))
+    return DS_EINVAL;
+  Plan* P = new (std::nothrow) Plan();
+  if (P == nullptr) return DS_ENOMEM;
+  std::memset(static_cast<void*>(P), 0, sizeof(Plan));
+  P->desc = *desc;
+  if (!(P->desc.rcond_min > 0.0)) P->desc.rcond_min = 1e-3;
+  P->stream = static_cast<cudaStream_t>(desc->stream);
+  P->n_o = desc->n_outputs;
+  P->kinds.n_o = desc->n_outputs;
+  for (int o = 0; o < DS_MAX_OUTPUTS; ++o) P->kinds.kind[o] = o < desc->n_outputs ? desc->kinds[o] : 0;
+  P->n_c = n_comp_of(desc->kinds, desc->n_outputs, &P->has_I_outputs);
+  P->nm = P->n_c * (P->n_c + 1) / 2;
+  P->kindset = kindset_of(desc->kinds, desc->n_outputs, P->n_c);
+  P->n_t = desc->n_samples;
+  P->L = desc->baseline_len;
+  P->n_b = (P->n_t + P->L - 1) / P->L;
+  P->n_u = P->n_b * P->n_o;
+  P->npix = int64_t(12) * desc->nside * desc->nside;
+  P->c = d_cos2psi;
+  P->s = d_sin2psi;
+  if (cudaGetDevice(&P->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
+    plan_free(P);
+    return DS_ECUDA;
+  }
+  P->red_len = 2 * P->num_sms * 8 + 64;
+  cudaError_t e = cudaSuccess;
+#define DS_ALLOC(ptr, n) \
+  if (e == cudaSuccess) e = dalloc(*P, &P->ptr, (n));
+  DS_ALLOC(pix, P->n_t);
+  DS_ALLOC(hits, P->npix);
+  DS_ALLOC(mask, P->npix);
+  DS_ALLOC(minv, P->npix * P->nm);
+  DS_ALLOC(bins, P->npix * 4);
+  DS_ALLOC(map32, P->npix * 4);
+  DS_ALLOC(map64, P->npix * 4);
+  DS_ALLOC(nvalid, P->n_b);
+  DS_ALLOC(x, P->n_u);
+  DS_ALLOC(r, P->n_u);
+  DS_ALLOC(p, P->n_u);
+  DS_ALLOC(q, P->n_u);
+  DS_ALLOC(b, P->n_u);
+  DS_ALLOC(t, P->n_u);
+  DS_ALLOC(red, P->red_len);
+  DS_ALLOC(counters, 8);
+  DS_ALLOC(state, 1);
+  DS_ALLOC(err, 1);
+  DS_ALLOC(scal, 8);
+#undef DS_ALLOC
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&P->h_state), sizeof(CgState));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&P->h_err), sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&P->h_scal), sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    plan_free(P);
+    return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
+  }
+  cudaStream_t st = P->stream;
+  e = cudaMemsetAsync(P->bins, 0, sizeof(double) * P->npix * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->counters, 0, sizeof(unsigned) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->state, 0, sizeof(CgState), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->x, 0, sizeof(double) * P->n_u, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->map32, 0, sizeof(float) * P->npix * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->map64, 0, sizeof(double) * P->npix * 4, st);
+  if (e != cudaSuccess) {
+    plan_free(P);
+    return DS_ECUDA;
+  }
+  s = plan_build(*P, d_pix, d_valid);
+  P->launches += 3;
+  if (s != DS_OK) {
+    cudaStreamSynchronize(st);
+    plan_free(P);
+    return s;
+  }
+  *out = reinterpret_cast<ds_plan_t>(P);
+  return DS_OK;
+}
+
+ds_status destripe_plan_info(ds_plan_t plan, ds_info* info) {
+  if (plan == nullptr || info == nullptr) return DS_EINVAL;
+  const Plan& P = *reinterpret_cast<Plan*>(plan);
+  info->n_samples = P.n_t;
+  info->n_baselines = P.n_b;
+  info->n_unknowns = P.n_u;
+  info->n_pix = P.npix;
+  info->n_good_pix = P.n_good;
+  info->n_valid = P.n_valid;
+  info->n_outputs = P.n_o;
+  info->n_comp = P.n_c;
+  info->device_bytes = P.device_bytes;
+  return DS_OK;
+}
+
+void destripe_destroy(ds_plan_t plan) {
+  if (plan == nullptr) return;
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  cudaStreamSynchronize(P->stream);
+  plan_free(P);
+}
+
+ds_status destripe_apply_A(ds_plan_t plan, const double* d_x, double* d_Ax) {
+  if (plan == nullptr || d_x == nullptr || d_Ax == nullptr || d_x == d_Ax) return DS_EINVAL;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  DS_CUDA_TRY(cudaMemsetAsync(d_Ax, 0, sizeof(double) * P.n_u, P.stream));
+  enqueue_apply(P, P.stream, P.desc.precision == DS_PREC_FP64, d_x, d_Ax, Gate{nullptr, nullptr});
+  P.launches += 3;
+  return launch_status();
+}
+
+ds_status destripe_rhs(ds_plan_t plan, const void* d_y, double* d_b) {
+  if (plan == nullptr || d_y == nullptr || d_b == nullptr) return DS_EINVAL;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  DS_CUDA_TRY(cudaMemsetAsync(d_b, 0, sizeof(double) * P.n_u, P.stream));
+  enqueue_rhs(P, P.stream, d_y, d_b, Gate{nullptr, nullptr});
+  P.launches += 3;
+  return launch_status();
+}
+
+static ds_status map_common(ds_plan_t plan, const void* d_y, const double* d_a, double* d_map,
+                            int32_t* d_hits, uint8_t* d_mask) {
+  if (plan == nullptr || d_y == nullptr || d_map == nullptr) return DS_EINVAL;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  enqueue_map(P, P.stream, d_y, d_a, d_map);
+  P.launches += 2;
+  if (d_hits)
+    DS_CUDA_TRY(cudaMemcpyAsync(d_hits, P.hits, sizeof(int32_t) * P.npix, cudaMemcpyDeviceToDevice, P.stream));
+  if (d_mask)
+    DS_CUDA_TRY(cudaMemcpyAsync(d_mask, P.mask, P.npix, cudaMemcpyDeviceToDevice, P.stream));
+  return launch_status();
+}
+
+ds_status destripe_bin(ds_plan_t plan, const void* d_y, const double* d_a, double* d_map,
+                       int32_t* d_hits, uint8_t* d_mask) {
+  return map_common(plan, d_y, d_a, d_map, d_hits, d_mask);
+}
+
+ds_status destripe_map(ds_plan_t plan, const void* d_y, const double* d_a, double* d_map,
+                       int32_t* d_hits, uint8_t* d_mask) {
+  if (d_a == nullptr) return DS_EINVAL;
+  return map_common(plan, d_y, d_a, d_map, d_hits, d_mask);
+}
+
+ds_status destripe_gauge(ds_plan_t plan, double* d_a) {
+  if (plan == nullptr || d_a == nullptr) return DS_EINVAL;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  enqueue_gauge(P, P.stream, d_a);
+  P.launches += 2;
+  return launch_status();
+}
+
+ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double tol,
+                         int32_t max_iter, int32_t warm_start, int32_t* iters, double* rel_resid) {
+  if (plan == nullptr || d_y == nullptr || d_a == nullptr) return DS_EINVAL;
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return DS_EINVAL;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (max_iter <= 0) max_iter = 10000;
+  cudaStream_t st = P.stream;
+  if (warm_start)
+    DS_CUDA_TRY(cudaMemcpyAsync(P.x, d_a, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
+  DS_CUDA_TRY(cudaMemsetAsync(P.b, 0, sizeof(double) * P.n_u, st));
+  enqueue_rhs(P, st, d_y, P.b, Gate{nullptr, nullptr});
+  enqueue_cg_setup(P, st, tol, max_iter, kReliableDelta, warm_start ? 1 : 0);
+  P.launches += 3 + 3 + (warm_start ? 3 : 0);
+  ds_status s = launch_status();
+  if (s != DS_OK) return s;
+  s = build_graph(P);
+  if (s != DS_OK) return s;
+  const int max_launches = max_iter / P.graph_iters + 4;
+  bool done = false;
+  int iter_before = 0;
+  for (int k = 0; k < max_launches && !done; ++k) {
+    DS_CUDA_TRY(cudaGraphLaunch(P.graph_exec, st));
+    DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    DS_CUDA_TRY(cudaStreamSynchronize(st));
+    done = P.h_state->done != 0;
+    P.graph_launches += 1;
+    P.launches += (int64_t)P.graph_iters * kernels_per_iteration(P);
+    const int ran = P.h_state->iter - iter_before;
+    iter_before = P.h_state->iter;
+    P.iterations += ran;
+    collect_times(P, ran);
+  }
+  enqueue_gauge(P, st, P.x);
+  P.launches += 2;
+  DS_CUDA_TRY(cudaMemcpyAsync(d_a, P.x, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
+  DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+  DS_CUDA_TRY(cudaStreamSynchronize(st));
+  const CgState& H = *P.h_state;
+  if (iters) *iters = H.iter;
+  if (rel_resid) *rel_resid = H.bb > 0.0 ? std::sqrt(H.rr_true / H.bb) : 0.0;
+  if (!done) return DS_ENOCONV;
+  switch (H.status) {
+    case 1: return DS_OK;
+    case 2: return DS_ENOCONV;
+    case 3: return H.rr_true <= H.tol2 ? DS_OK : DS_ENOCONV;
+    default: return DS_ENAN;
+  }
+}
+
+ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out) {
+  if (plan == nullptr) return DS_EINVAL;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (enable == 1 || enable == 0) {
+    P.profiling = enable;
+    if (enable == 1) {
+      P.launches = 0;
+      P.graph_launches = 0;
+      P.iterations = 0;
+      P.timed_iterations = 0;
+      P.t_bin = P.t_rescan = P.t_solve = P.t_iter = 0.0;
+    }
+  }
+  if (out) {
+    out->kernel_launches = P.launches;
+    out->graph_launches = P.graph_launches;
+    out->iterations = P.iterations;
+    out->timed_iterations = P.timed_iterations;
+    out->bin_ms = P.t_bin;
+    out->rescan_ms = P.t_rescan;
+    out->solve_ms = P.t_solve;
+    out->iteration_ms = P.t_iter;
+  }
+  return DS_OK;
+}
+
+ds_status destripe_run_host(const ds_desc* desc, const int32_t* h_pix, const float* h_c,
+                            const float* h_s, const uint8_t* h_valid, const void* h_y,
+                            double tol, int32_t max_iter, double* h_a, double* h_map,
+                            int32_t* h_hits, uint8_t* h_mask, int32_t* iters,
+                            double* rel_resid) {
+  ds_status s = check_desc(desc);
+  if (s != DS_OK) return s;
+  if (!h_pix || !h_c || !h_s || !h_y) return DS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(desc->stream);
+  const int64_t n_t = desc->n_samples, n_o = desc->n_outputs;
+  const int64_t n_b = (n_t + desc->baseline_len - 1) / desc->baseline_len;
+  int has_i;
+  const int64_t n_c = n_comp_of(desc->kinds, desc->n_outputs, &has_i);
+  const int64_t npix = int64_t(12) * desc->nside * desc->nside;
+  const size_t ysz = desc->precision == DS_PREC_FP64 ? sizeof(double) : sizeof(float);
+  int32_t* d_pix = nullptr;
+  float *d_c = nullptr, *d_s = nullptr;
+  uint8_t *d_valid = nullptr, *d_mask = nullptr;
+  void* d_y = nullptr;
+  double *d_a = nullptr, *d_map = nullptr;
+  int32_t* d_hits = nullptr;
+  ds_plan_t plan = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_pix), sizeof(int32_t) * n_t, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_c), sizeof(float) * n_t, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_s), sizeof(float) * n_t, st);
+  if (e == cudaSuccess && h_valid) e = cudaMallocAsync(reinterpret_cast<void**>(&d_valid), n_t, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_y, ysz * n_t * n_o, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_a), sizeof(double) * n_b * n_o, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_map), sizeof(double) * n_c * npix, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_hits), sizeof(int32_t) * npix, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_mask), npix, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_pix, h_pix, sizeof(int32_t) * n_t, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_c, h_c, sizeof(float) * n_t, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_s, h_s, sizeof(float) * n_t, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && h_valid) e = cudaMemcpyAsync(d_valid, h_valid, n_t, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_y, h_y, ysz * n_t * n_o, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) s = (e == cudaErrorMemoryAllocation) ? DS_ENOMEM : DS_ECUDA;
+  if (s == DS_OK) s = destripe_plan(desc, d_pix, d_c, d_s, d_valid, &plan);
+  ds_status solve_s = DS_OK;
+  if (s == DS_OK) {
+    solve_s = destripe_solve(plan, d_y, d_a, tol, max_iter, 0, iters, rel_resid);
+    if (solve_s != DS_OK && solve_s != DS_ENOCONV) s = solve_s;
+  }
+  if (s == DS_OK && h_map) s = destripe_map(plan, d_y, d_a, d_map, d_hits, d_mask);
+  if (s == DS_OK && h_a) s = cudaMemcpyAsync(h_a, d_a, sizeof(double) * n_b * n_o, cudaMemcpyDeviceToHost, st) == cudaSuccess ? DS_OK : DS_ECUDA;
+  if (s == DS_OK && h_map) s = cudaMemcpyAsync(h_map, d_map, sizeof(double) * n_c * npix, cudaMemcpyDeviceToHost, st) == cudaSuccess ? DS_OK : DS_ECUDA;
+  if (s == DS_OK && h_hits && h_map) s = cudaMemcpyAsync(h_hits, d_hits, sizeof(int32_t) * npix, cudaMemcpyDeviceToHost, st) == cudaSuccess ? DS_OK : DS_ECUDA;
+  if (s == DS_OK && h_mask && h_map) s = cudaMemcpyAsync(h_mask, d_mask, npix, cudaMemcpyDeviceToHost, st) == cudaSuccess ? DS_OK : DS_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess && s == DS_OK) s = DS_ECUDA;
+  if (plan) destripe_destroy(plan);
+  void* bufs[] = {d_pix, d_c, d_s, d_valid, d_y, d_a, d_map, d_hits, d_mask};
+  for (void* b : bufs)
+    if (b) cudaFreeAsync(b, st);
+  cudaStreamSynchronize(st);
+  if (s == DS_OK && solve_s == DS_ENOCONV) s = DS_ENOCONV;
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,405 @@
+// Per-sample passes of the destriping operator and the per-pixel solve
+// (Sect. 3: F~ expands baselines to the timeline, P~^T R^T bins into pixel sums,
+// M^-1 weights them into a map, R P~ rescans the map, F~^T sums per baseline).
+//
+// Work split: every thread owns 4 consecutive samples and reads them with one
+// 16-byte load per stream (pixel, cos 2psi, sin 2psi); a warp covers 128
+// consecutive samples.  Consecutive samples often share a pixel, so binning
+// aggregates runs of equal pixels in registers before each atomic add into the
+// float64 pixel sums.  Per-baseline sums are reduced across the warp by a
+// segmented shuffle scan on the baseline index and added with one atomic per
+// warp segment.
+#include <type_traits>
+
+#include "internal.cuh"
+#include "rows.cuh"
+
+namespace ds {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <typename F>
+void with_kindset(int ks, F&& f) {
+  switch (ks) {
+    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
+    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
+    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
+    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
+    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
+    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
+    default: f(std::integral_constant<int, KS_GEN3>{}); break;
+  }
+}
+
+// Load 4 samples starting at t0 = 4 v; samples past n_t get pixel -1.
+__device__ __forceinline__ void load4(const int32_t* __restrict__ pix, const float* __restrict__ cc,
+                                      const float* __restrict__ ss, int64_t v, int64_t n_t,
+                                      int (&p)[4], float (&c)[4], float (&s)[4]) {
+  const int64_t t0 = v << 2;
+  if (t0 + 4 <= n_t) {
+    const int4 pp = ld_stream(reinterpret_cast<const int4*>(pix) + v);
+    const float4 c4 = ld_stream(reinterpret_cast<const float4*>(cc) + v);
+    const float4 s4 = ld_stream(reinterpret_cast<const float4*>(ss) + v);
+    p[0] = pp.x; p[1] = pp.y; p[2] = pp.z; p[3] = pp.w;
+    c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+    s[0] = s4.x; s[1] = s4.y; s[2] = s4.z; s[3] = s4.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool in = t0 + k < n_t;
+      p[k] = in ? pix[t0 + k] : -1;
+      c[k] = in ? cc[t0 + k] : 0.f;
+      s[k] = in ? ss[t0 + k] : 0.f;
+    }
+  }
+}
+
+template <int NC, typename T>
+__device__ __forceinline__ void flush_bins(double* __restrict__ bins, int p, const T (&acc)[NC]) {
+  double* dst = bins + (int64_t)p * 4;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) atomicAdd(dst + j, (double)acc[j]);
+}
+
+template <int NC, typename T>
+__device__ __forceinline__ void load_map(const T* __restrict__ map, int p, T (&m)[NC]) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(map) + p);
+    const float a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < NC; ++j) m[j] = a[j];
+  } else {
+    const double2 v0 = __ldg(reinterpret_cast<const double2*>(map) + 2 * (int64_t)p);
+    m[0] = v0.x;
+    if constexpr (NC > 1) m[1] = v0.y;
+    if constexpr (NC > 2) m[2] = __ldg(map + 4 * (int64_t)p + 2);
+  }
+}
+
+// Segmented sum across the warp of per-lane partials keyed by baseline index
+// (keys non-decreasing with the lane; -1 = nothing).  The first lane of every
+// run of equal keys adds the run total to out[o * n_b + key].
+template <int NO, typename T>
+__device__ __forceinline__ void warp_segment_flush(int key, T (&val)[NO], int n_o,
+                                                   double* __restrict__ out, int64_t n_b) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int k2 = __shfl_down_sync(full, key, d);
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const T v2 = __shfl_down_sync(full, val[o], d);
+      if (lane + d < 32 && k2 == key) val[o] += v2;
+    }
+  }
+  const int kp = __shfl_up_sync(full, key, 1);
+  if (key >= 0 && (lane == 0 || kp != key)) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (o < n_o) atomicAdd(out + (int64_t)o * n_b + key, (double)val[o]);
+  }
+}
+
+// ---- binning: bins[p] += sum_o w_o(t) z_o(t) over samples with v = 1 ----------
+// ZY = false: z_o(t) = x[o][t / L]          (F~ x, the operator)
+// ZY = true : z_o(t) = y[o][t] - a[o][t/L]  (data minus baselines; a may be NULL)
+template <int KS, typename T, bool ZY, typename YT>
+__global__ void __launch_bounds__(kBlock) k_bin(const int32_t* __restrict__ pix,
+                                                const float* __restrict__ cc,
+                                                const float* __restrict__ ss,
+                                                const double* __restrict__ x,
+                                                const YT* __restrict__ y,
+                                                double* __restrict__ bins, int64_t n_t, int64_t L,
+                                                int64_t n_b, KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    int p[4];
+    float c[4], s[4];
+    load4(pix, cc, ss, v, n_t, p, c, s);
+    const int64_t t0 = v << 2;
+    int64_t b = t0 / L;
+    int64_t bend = (b + 1) * L;
+    T zb[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      zb[o] = (o < n_o && x != nullptr) ? (T)__ldg(x + o * n_b + b) : T(0);
+    T acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = T(0);
+    int cur = -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t t = t0 + k;
+      if (t >= n_t) break;
+      if (t >= bend) {
+        b += 1;
+        bend += L;
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          zb[o] = (o < n_o && x != nullptr) ? (T)__ldg(x + o * n_b + b) : T(0);
+      }
+      if (p[k] < 0) continue;
+      T w[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) w[j] = T(0);
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        if (o < n_o) {
+          T z = zb[o];
+          if constexpr (ZY) z = (T)y[(int64_t)o * n_t + t] - z;
+          row_bin<NC, T>(K::kind(o, kk), (T)c[k], (T)s[k], z, w);
+        }
+      }
+      if (p[k] != cur) {
+        if (cur >= 0) flush_bins<NC, T>(bins, cur, acc);
+        cur = p[k];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = w[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] += w[j];
+      }
+    }
+    if (cur >= 0) flush_bins<NC, T>(bins, cur, acc);
+  }
+}
+
+// ---- per-pixel solve: m_p = M_p^-1 s_p on kept pixels, 0 elsewhere ---------------
+// Reads the float64 sums, clears them for the next pass, writes the map in the
+// working precision (and optionally component-major float64 for the caller).
+template <int NC, typename T>
+__global__ void __launch_bounds__(kBlock) k_pixel_solve(double* __restrict__ bins,
+                                                        const double* __restrict__ minv,
+                                                        const uint8_t* __restrict__ mask,
+                                                        T* __restrict__ map,
+                                                        double* __restrict__ out_map, int64_t npix,
+                                                        Gate g) {
+  if (gate_closed(g)) return;
+  constexpr int NM = NC * (NC + 1) / 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
+    double s[NC], m[NC];
+    const double2 s01 = reinterpret_cast<const double2*>(bins)[2 * p];
+    s[0] = s01.x;
+    if constexpr (NC > 1) s[1] = s01.y;
+    if constexpr (NC > 2) s[2] = bins[4 * p + 2];
+    reinterpret_cast<double2*>(bins)[2 * p] = make_double2(0.0, 0.0);
+    if constexpr (NC > 2) bins[4 * p + 2] = 0.0;
+    if (mask[p]) {
+      double mi[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
+      sym_mul<NC>(mi, s, m);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) m[j] = 0.0;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      o4.x = (float)m[0];
+      if constexpr (NC > 1) o4.y = (float)m[1];
+      if constexpr (NC > 2) o4.z = (float)m[2];
+      reinterpret_cast<float4*>(map)[p] = o4;
+    } else {
+      reinterpret_cast<double2*>(map)[2 * p] = make_double2(m[0], NC > 1 ? m[NC > 1 ? 1 : 0] : 0.0);
+      if constexpr (NC > 2) map[4 * p + 2] = m[2];
+    }
+    if (out_map != nullptr) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) out_map[(int64_t)j * npix + p] = m[j];
+    }
+  }
+}
+
+// ---- rescan + per-baseline sum: out[o][b] += sum_{t in b} v (z_o(t) - w_o(t) . m_p(t))
+template <int KS, typename T, bool ZY, typename YT>
+__global__ void __launch_bounds__(kBlock) k_rescan(const int32_t* __restrict__ pix,
+                                                   const float* __restrict__ cc,
+                                                   const float* __restrict__ ss,
+                                                   const double* __restrict__ x,
+                                                   const YT* __restrict__ y,
+                                                   const T* __restrict__ map,
+                                                   double* __restrict__ out, int64_t n_t,
+                                                   int64_t L, int64_t n_b, KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int lane = threadIdx.x & 31;
+  const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t vb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; vb < nvec;
+       vb += stride) {
+    const int64_t v = vb + lane;
+    int key = -1;
+    T acc[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o] = T(0);
+    if (v < nvec) {
+      int p[4];
+      float c[4], s[4];
+      load4(pix, cc, ss, v, n_t, p, c, s);
+      T m[4][NC];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (p[k] >= 0) {
+          load_map<NC, T>(map, p[k], m[k]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) m[k][j] = T(0);
+        }
+      }
+      const int64_t t0 = v << 2;
+      int64_t b = t0 / L;
+      int64_t bend = (b + 1) * L;
+      T zb[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        zb[o] = (o < n_o && x != nullptr) ? (T)__ldg(x + o * n_b + b) : T(0);
+      key = (int)b;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t t = t0 + k;
+        if (t >= n_t) break;
+        if (t >= bend) {
+#pragma unroll
+          for (int o = 0; o < NO; ++o) {
+            if (o < n_o && acc[o] != T(0)) atomicAdd(out + o * n_b + b, (double)acc[o]);
+            acc[o] = T(0);
+          }
+          b += 1;
+          bend += L;
+          key = (int)b;
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+            zb[o] = (o < n_o && x != nullptr) ? (T)__ldg(x + o * n_b + b) : T(0);
+        }
+        if (p[k] < 0) continue;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          if (o < n_o) {
+            T z = zb[o];
+            if constexpr (ZY) z = (T)y[(int64_t)o * n_t + t] - z;
+            acc[o] += z - row_dot<NC, T>(K::kind(o, kk), (T)c[k], (T)s[k], m[k]);
+          }
+        }
+      }
+    }
+    warp_segment_flush<NO, T>(key, acc, n_o, out, n_b);
+  }
+}
+
+}  // namespace
+
+int stream_grid(const Plan& P, int64_t work_items, int block, int per_sm) {
+  int64_t need = (work_items + block - 1) / block;
+  int64_t cap = (int64_t)P.num_sms * per_sm;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
+}
+
+void launch_bin_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, Gate g) {
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (fp64)
+      k_bin<KS, double, false, double><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, nullptr, P.bins,
+                                                                P.n_t, P.L, P.n_b, P.kinds, g);
+    else
+      k_bin<KS, float, false, float><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, nullptr, P.bins,
+                                                              P.n_t, P.L, P.n_b, P.kinds, g);
+  });
+}
+
+void launch_bin_y(const Plan& P, cudaStream_t st, const void* y, const double* a, Gate g) {
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (P.desc.precision == DS_PREC_FP64)
+      k_bin<KS, double, true, double><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, a, static_cast<const double*>(y), P.bins, P.n_t, P.L, P.n_b, P.kinds, g);
+    else
+      k_bin<KS, double, true, float><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, a, static_cast<const float*>(y), P.bins, P.n_t, P.L, P.n_b, P.kinds, g);
+  });
+}
+
+void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_map, Gate g) {
+  const int grid = stream_grid(P, P.npix, kBlock, 8);
+  auto go = [&](auto ncc) {
+    constexpr int NC = decltype(ncc)::value;
+    if (fp64)
+      k_pixel_solve<NC, double><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map64, out_map,
+                                                          P.npix, g);
+    else
+      k_pixel_solve<NC, float><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map32, out_map,
+                                                         P.npix, g);
+  };
+  if (P.n_c == 1) go(std::integral_constant<int, 1>{});
+  else if (P.n_c == 2) go(std::integral_constant<int, 2>{});
+  else go(std::integral_constant<int, 3>{});
+}
+
+void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out,
+                     Gate g) {
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (fp64)
+      k_rescan<KS, double, false, double><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, x, nullptr, P.map64, out, P.n_t, P.L, P.n_b, P.kinds, g);
+    else
+      k_rescan<KS, float, false, float><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, x, nullptr, P.map32, out, P.n_t, P.L, P.n_b, P.kinds, g);
+  });
+}
+
+void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g) {
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (P.desc.precision == DS_PREC_FP64)
+      k_rescan<KS, double, true, double><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, nullptr, static_cast<const double*>(y), P.map64, out, P.n_t, P.L, P.n_b,
+          P.kinds, g);
+    else
+      k_rescan<KS, double, true, float><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, nullptr, static_cast<const float*>(y), P.map64, out, P.n_t, P.L, P.n_b,
+          P.kinds, g);
+  });
+}
+
+// ev (optional): events recorded before binning, after binning, after the pixel
+// solve and after the rescan.
+void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out,
+                   Gate g, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  launch_bin_x(P, st, fp64, x, g);
+  if (ev) cudaEventRecord(ev[1], st);
+  launch_pixel_solve(P, st, fp64, nullptr, g);
+  if (ev) cudaEventRecord(ev[2], st);
+  launch_rescan_x(P, st, fp64, x, out, g);
+  if (ev) cudaEventRecord(ev[3], st);
+}
+
+void enqueue_rhs(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g) {
+  launch_bin_y(P, st, y, nullptr, g);
+  launch_pixel_solve(P, st, true, nullptr, g);
+  launch_rescan_y(P, st, y, out, g);
+}
+
+void enqueue_map(const Plan& P, cudaStream_t st, const void* y, const double* a, double* out_map) {
+  Gate g{nullptr, nullptr};
+  launch_bin_y(P, st, y, a, g);
+  launch_pixel_solve(P, st, true, out_map, g);
+}
+
+}  // namespace ds

@@ -1,0 +1,334 @@
+// Conjugate gradient on the destriping equation (Sect. 3 names CG; the operator
+// F~^T Z F~ is symmetric positive semi-definite), with every scalar kept on the
+// device so that iterations run back to back inside one captured CUDA graph.
+//
+// Dot products are deterministic: each block writes its partial sum, and the
+// last block to finish (ticket counter) adds the partials in block order.
+//
+// In mixed precision the per-sample operator runs in float32.  Whenever the
+// recursive residual has dropped by a set factor since the last float64 check,
+// or claims convergence, the residual is recomputed as b - A x with the float64
+// operator and CG continues from it ("reliable updates").
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace ds {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sm[32];
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  v = 0.0;
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0.0;
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  }
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+// Writes this block's partial; returns true in exactly one thread of the last
+// block, with *total = sum of all partials in block order.
+__device__ bool finish_sum(double partial, double* __restrict__ red, unsigned* __restrict__ ticket,
+                           double* total) {
+  __shared__ bool last;
+  const double bs = block_sum(partial);
+  if (threadIdx.x == 0) {
+    red[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double v = 0.0;
+  // fixed order: thread i adds partials i, i + blockDim, ... then a block sum
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += ((volatile double*)red)[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    *total = v;
+    return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kBlock) k_dot(const double* __restrict__ a,
+                                                const double* __restrict__ b, int64_t n,
+                                                double* __restrict__ red, unsigned* ticket,
+                                                double* __restrict__ out, Gate g) {
+  if (gate_closed(g)) return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  double tot;
+  if (finish_sum(acc, red, ticket, &tot)) *out = tot;
+}
+
+// CG start: x = x0 or 0; r = b - t (t = A x0, or 0); p = r; rr = r.r.
+__global__ void __launch_bounds__(kBlock) k_cg_start(double* __restrict__ x, double* __restrict__ r,
+                                                     double* __restrict__ p, double* __restrict__ q,
+                                                     const double* __restrict__ b,
+                                                     double* __restrict__ t, int warm, int64_t n,
+                                                     double* __restrict__ red, unsigned* ticket,
+                                                     CgState* st) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = warm ? b[i] - t[i] : b[i];
+    if (!warm) x[i] = 0.0;
+    r[i] = ri;
+    p[i] = ri;
+    q[i] = 0.0;
+    t[i] = 0.0;
+    acc += ri * ri;
+  }
+  double tot;
+  if (finish_sum(acc, red, ticket, &tot)) {
+    st->rr = tot;
+    st->rr_old = tot;
+    st->rr_anchor = tot;
+    st->rr_true = tot;
+    st->iter = 0;
+    st->need = 0;
+    st->n_reliable = 0;
+    st->status = 0;
+    st->done = 0;
+    if (!isfinite(tot) || !isfinite(st->bb)) {
+      st->status = 4;
+      st->done = 1;
+    } else if (tot <= st->tol2) {
+      st->status = 1;
+      st->done = 1;
+    }
+  }
+}
+
+// pq = p . q ; alpha = rr / pq
+__global__ void __launch_bounds__(kBlock) k_cg_alpha(const double* __restrict__ p,
+                                                     const double* __restrict__ q, int64_t n,
+                                                     double* __restrict__ red, unsigned* ticket,
+                                                     CgState* st) {
+  if (st->done) return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += p[i] * q[i];
+  double tot;
+  if (finish_sum(acc, red, ticket, &tot)) {
+    st->pq = tot;
+    if (!isfinite(tot)) {
+      st->status = 4;
+      st->done = 1;
+    } else if (!(tot > 0.0)) {
+      st->status = 3;  // breakdown: the direction carries no curvature
+      st->done = 1;
+    } else {
+      st->alpha = st->rr / tot;
+    }
+  }
+}
+
+// x += alpha p ; r -= alpha q ; rr_new = r.r ; convergence / reliable-update test
+__global__ void __launch_bounds__(kBlock) k_cg_update(double* __restrict__ x,
+                                                      double* __restrict__ r,
+                                                      const double* __restrict__ p,
+                                                      const double* __restrict__ q, int64_t n,
+                                                      double* __restrict__ red, unsigned* ticket,
+                                                      CgState* st) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double tot;
+  if (finish_sum(acc, red, ticket, &tot)) {
+    st->rr_old = st->rr;
+    st->rr = tot;
+    st->iter += 1;
+    if (!isfinite(tot)) {
+      st->status = 4;
+      st->done = 1;
+      return;
+    }
+    const bool conv = tot <= st->tol2;
+    if (st->mixed) {
+      if (conv || tot < st->delta2 * st->rr_anchor || st->iter >= st->max_iter) st->need = 1;
+    } else {
+      st->rr_true = tot;
+      if (conv) {
+        st->status = 1;
+        st->done = 1;
+      } else if (st->iter >= st->max_iter) {
+        st->status = 2;
+        st->done = 1;
+      }
+    }
+  }
+}
+
+// Reliable update: r = b - t (t = A x in float64); clears t.
+__global__ void __launch_bounds__(kBlock) k_cg_reliable(double* __restrict__ r,
+                                                        const double* __restrict__ b,
+                                                        double* __restrict__ t, int64_t n,
+                                                        double* __restrict__ red, unsigned* ticket,
+                                                        CgState* st) {
+  if (st->done || !st->need) return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - t[i];
+    r[i] = ri;
+    t[i] = 0.0;
+    acc += ri * ri;
+  }
+  double tot;
+  if (finish_sum(acc, red, ticket, &tot)) {
+    st->rr = tot;
+    st->rr_anchor = tot;
+    st->rr_true = tot;
+    st->n_reliable += 1;
+    st->need = 0;
+    if (!isfinite(tot)) {
+      st->status = 4;
+      st->done = 1;
+    } else if (tot <= st->tol2) {
+      st->status = 1;
+      st->done = 1;
+    } else if (st->iter >= st->max_iter) {
+      st->status = 2;
+      st->done = 1;
+    }
+  }
+}
+
+// p = r + beta p ; q = 0
+__global__ void __launch_bounds__(kBlock) k_cg_direction(double* __restrict__ p,
+                                                         const double* __restrict__ r,
+                                                         double* __restrict__ q, int64_t n,
+                                                         const CgState* st) {
+  if (st->done) return;
+  const double beta = st->rr / st->rr_old;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    p[i] = r[i] + beta * p[i];
+    q[i] = 0.0;
+  }
+}
+
+// Gauge: mean over (I-carrying outputs, baselines with data) -> scal[0..1]
+__global__ void __launch_bounds__(kBlock) k_gauge_sum(const double* __restrict__ a,
+                                                      const int32_t* __restrict__ nvalid,
+                                                      int64_t n_b, KindsArg kk,
+                                                      double* __restrict__ red, unsigned* ticket,
+                                                      double* __restrict__ out) {
+  double s = 0.0, c = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_b;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (nvalid[i] > 0) {
+      for (int o = 0; o < kk.n_o; ++o)
+        if (kk.kind[o] == DS_KIND_I || kk.kind[o] == DS_KIND_IQU) {
+          s += a[o * n_b + i];
+          c += 1.0;
+        }
+    }
+  }
+  double tot;
+  if (finish_sum(s, red, ticket, &tot)) out[0] = tot;
+  __syncthreads();
+  if (finish_sum(c, red + gridDim.x, ticket + 1, &tot)) out[1] = tot;
+}
+
+__global__ void __launch_bounds__(kBlock) k_gauge_apply(double* __restrict__ a,
+                                                        const int32_t* __restrict__ nvalid,
+                                                        int64_t n_b, KindsArg kk,
+                                                        const double* __restrict__ sums) {
+  const double mean = sums[1] > 0.0 ? sums[0] / sums[1] : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_b;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool has = nvalid[i] > 0;
+    for (int o = 0; o < kk.n_o; ++o) {
+      double v = a[o * n_b + i];
+      if (!has) v = 0.0;
+      else if (kk.kind[o] == DS_KIND_I || kk.kind[o] == DS_KIND_IQU) v -= mean;
+      a[o * n_b + i] = v;
+    }
+  }
+}
+
+__global__ void k_set_state(CgState* st, double tol, int max_iter, int mixed, double delta) {
+  st->tol2 = tol * tol * st->bb;
+  st->max_iter = max_iter;
+  st->mixed = mixed;
+  st->delta2 = delta * delta;
+  st->done = 0;
+  st->need = 0;
+}
+
+}  // namespace
+
+static int vec_grid(const Plan& P, int64_t n) { return stream_grid(P, n, kBlock, 4); }
+
+void enqueue_dot(const Plan& P, cudaStream_t st, const double* a, const double* b, int64_t n,
+                 double* out) {
+  k_dot<<<vec_grid(P, n), kBlock, 0, st>>>(a, b, n, P.red, P.counters, out, Gate{nullptr, nullptr});
+}
+
+void enqueue_gauge(const Plan& P, cudaStream_t st, double* a) {
+  k_gauge_sum<<<vec_grid(P, P.n_b), kBlock, 0, st>>>(a, P.nvalid, P.n_b, P.kinds, P.red,
+                                                      P.counters + 2, P.scal + 4);
+  k_gauge_apply<<<vec_grid(P, P.n_b), kBlock, 0, st>>>(a, P.nvalid, P.n_b, P.kinds, P.scal + 4);
+}
+
+int kernels_per_iteration(const Plan& P) {
+  return P.desc.precision == DS_PREC_MIXED ? 10 : 6;
+}
+
+// One CG iteration (gated by state->done), used both directly and under capture.
+// ev (optional): 5 events; the first four bracket the operator kernels, the fifth
+// marks the end of the iteration.
+void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev) {
+  const bool mixed = P.desc.precision == DS_PREC_MIXED;
+  const int vg = vec_grid(P, P.n_u);
+  Gate g{&P.state->done, nullptr};
+  enqueue_apply(P, st, !mixed, P.p, P.q, g, ev);
+  k_cg_alpha<<<vg, kBlock, 0, st>>>(P.p, P.q, P.n_u, P.red, P.counters, P.state);
+  k_cg_update<<<vg, kBlock, 0, st>>>(P.x, P.r, P.p, P.q, P.n_u, P.red, P.counters, P.state);
+  if (mixed) {
+    Gate gr{&P.state->done, &P.state->need};
+    enqueue_apply(P, st, true, P.x, P.t, gr);
+    k_cg_reliable<<<vg, kBlock, 0, st>>>(P.r, P.b, P.t, P.n_u, P.red, P.counters, P.state);
+  }
+  k_cg_direction<<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.n_u, P.state);
+  if (ev) cudaEventRecord(ev[4], st);
+}
+
+void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, double delta,
+                      int warm) {
+  const bool mixed = P.desc.precision == DS_PREC_MIXED;
+  // bb = b . b
+  enqueue_dot(P, st, P.b, P.b, P.n_u, &P.state->bb);
+  k_set_state<<<1, 1, 0, st>>>(P.state, tol, max_iter, mixed ? 1 : 0, delta);
+  if (warm) {
+    cudaMemsetAsync(P.t, 0, sizeof(double) * P.n_u, st);
+    enqueue_apply(P, st, true, P.x, P.t, Gate{nullptr, nullptr});
+  }
+  k_cg_start<<<vec_grid(P, P.n_u), kBlock, 0, st>>>(P.x, P.r, P.p, P.q, P.b, P.t, warm, P.n_u,
+                                                     P.red, P.counters, P.state);
+}
+
+}  // namespace ds

@@ -1,0 +1,144 @@
+// Internal declarations of the destriper library (not part of the C ABI).
+//
+// Device data of a plan (all dense, 256-byte aligned allocations):
+//   pix      int32 [n_t]      pixel of each sample, or -1 when the sample is
+//                             flagged or falls on a cut pixel (weight v = 0)
+//   c, s     float [n_t]      caller's cos 2psi / sin 2psi (referenced)
+//   hits     int32 [n_pix]    valid samples per pixel before the cut
+//   mask     uint8 [n_pix]    1 = pixel kept
+//   minv     f64 [n_pix][NM]  packed symmetric M_p^-1 (NM = 1, 3, 6), 0 if cut
+//   bins     f64 [n_pix][4]   pixel sums, kept at zero between uses
+//   map32    f32 [n_pix][4]   map in the mixed-precision iteration
+//   map64    f64 [n_pix][4]   map in float64 passes
+//   nvalid   int32 [n_b]      valid samples per baseline (gauge)
+//   CG vectors f64 [n_u]      x, r, p, q, b, t (n_u = n_o * n_b)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/destripe.h"
+
+namespace ds {
+
+// Kind sets with their rows known at compile time; GEN* take kinds at run time.
+enum KindSet { KS_QU = 0, KS_IQU3 = 1, KS_IQU1 = 2, KS_I = 3, KS_GEN1 = 4, KS_GEN2 = 5, KS_GEN3 = 6 };
+
+struct KindsArg {
+  int n_o;
+  int kind[DS_MAX_OUTPUTS];
+};
+
+// Gate of a kernel inside the CG graph: it does nothing once *done != 0, and,
+// when need is given, unless *need != 0.
+struct Gate {
+  const int* done;
+  const int* need;
+};
+
+__device__ __forceinline__ bool gate_closed(const Gate& g) {
+  if (g.done != nullptr && *(volatile const int*)g.done) return true;
+  if (g.need != nullptr && *(volatile const int*)g.need == 0) return true;
+  return false;
+}
+
+// Device-resident CG state (float64 scalars and control words).
+struct CgState {
+  double rr;         // ||r||^2 of the current residual
+  double rr_old;     // ||r||^2 before the last update (for beta)
+  double pq;         // p . A p
+  double alpha;
+  double bb;         // ||b||^2
+  double rr_anchor;  // ||r||^2 at the last float64 residual
+  double tol2;       // tol^2 * bb
+  double delta2;     // reliable-update trigger ratio (squared)
+  double rr_true;    // float64 ||b - A x||^2 at the last check
+  int iter;
+  int max_iter;
+  int done;
+  int need;          // run the float64 residual this iteration
+  int status;        // 0 ok, 1 converged, 2 max_iter, 3 breakdown, 4 non-finite
+  int mixed;         // 1: recursive residual is confirmed in float64
+  int n_reliable;    // float64 residual updates done
+  int pad;
+};
+
+enum ErrBits { ERR_PIX = 1, ERR_NAN = 2 };
+
+struct Plan {
+  ds_desc desc;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;  // private stream used only to capture graphs
+  int device;
+  int num_sms;
+  int n_o, n_c, nm;
+  int kindset;
+  KindsArg kinds;
+  int has_I_outputs;
+  int64_t n_t, npix, L, n_b, n_u;
+  int64_t n_good, n_valid;
+  const float* c;
+  const float* s;
+  int32_t* pix;
+  int32_t* hits;
+  uint8_t* mask;
+  double* minv;
+  double* bins;
+  float* map32;
+  double* map64;
+  int32_t* nvalid;
+  double *x, *r, *p, *q, *b, *t;
+  double* red;        // reduction partials [red_len]
+  int red_len;
+  unsigned* counters; // last-block tickets [8]
+  CgState* state;     // device
+  CgState* h_state;   // pinned host mirror
+  int32_t* err;       // device error word
+  int32_t* h_err;     // pinned
+  double* scal;       // device scratch scalars [8]
+  double* h_scal;     // pinned [8]
+  int64_t device_bytes;
+  // captured iteration graph
+  cudaGraphExec_t graph_exec;
+  int graph_iters;
+  int graph_profiled;       // graph holds event nodes
+  // profiling
+  int profiling;
+  cudaEvent_t* ev;          // [graph_iters][5] when profiled
+  int64_t launches;         // kernel launches (host-side count)
+  int64_t graph_launches;
+  int64_t iterations;
+  int64_t timed_iterations;
+  double t_bin, t_rescan, t_solve, t_iter;
+};
+
+// kernels launched by one CG iteration (for the launch counter)
+int kernels_per_iteration(const Plan& P);
+
+// ---- launch helpers ---------------------------------------------------------
+int stream_grid(const Plan& P, int64_t work_items, int block, int per_sm);
+
+// apply.cu: per-sample passes and the pixel solve
+void launch_bin_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, Gate g);
+void launch_bin_y(const Plan& P, cudaStream_t st, const void* y, const double* a, Gate g);
+void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_map, Gate g);
+void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out, Gate g);
+void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g);
+// full operator pieces
+void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out, Gate g,
+                   cudaEvent_t* ev = nullptr);
+void enqueue_rhs(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g);
+void enqueue_map(const Plan& P, cudaStream_t st, const void* y, const double* a, double* out_map);
+
+// plan.cu
+ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid);
+
+}  // namespace ds
+
+#define DS_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) {                                \
+      return (e_ == cudaErrorMemoryAllocation) ? DS_ENOMEM : DS_ECUDA; \
+    }                                                       \
+  } while (0)

@@ -1,0 +1,302 @@
+// Plan construction: hits h = P^T P, per-pixel normal matrices M_p, their
+// inverses and the rcond cut, and the per-sample weights that every later pass
+// uses (Sect. 3: hitmap, Eqs. mapQ/mapU and the QU / IQU weighting).
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "internal.cuh"
+#include "rows.cuh"
+
+namespace ds {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+// Packed index of the upper triangle of a symmetric NC x NC matrix.
+template <int NC>
+__device__ __forceinline__ constexpr int sym_index(int i, int j) {
+  if (i > j) { int t = i; i = j; j = t; }
+  return i * NC - i * (i - 1) / 2 + (j - i);
+}
+
+template <int NC>
+__device__ __forceinline__ void flush_m(int32_t* __restrict__ hits, double* __restrict__ mm, int p,
+                                        int h, const double (&acc)[NC * (NC + 1) / 2]) {
+  constexpr int NM = NC * (NC + 1) / 2;
+  atomicAdd(hits + p, h);
+#pragma unroll
+  for (int j = 0; j < NM; ++j) atomicAdd(mm + (int64_t)p * NM + j, acc[j]);
+}
+
+// hits[p] += 1 and M_p += sum_o w_o w_o^T for every valid sample (float64).
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_plan_accum(const int32_t* __restrict__ pix,
+                                                       const float* __restrict__ cc,
+                                                       const float* __restrict__ ss,
+                                                       const uint8_t* __restrict__ valid,
+                                                       int32_t* __restrict__ hits,
+                                                       double* __restrict__ mm, int64_t n_t,
+                                                       int64_t npix, KindsArg kk,
+                                                       int32_t* __restrict__ err) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO, NM = NC * (NC + 1) / 2;
+  const int n_o = K::n_o(kk);
+  const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    const int64_t t0 = v << 2;
+    double acc[NM];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) acc[j] = 0.0;
+    int cur = -1, h = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t t = t0 + k;
+      if (t >= n_t) break;
+      if (valid != nullptr && valid[t] == 0) continue;
+      const int p = pix[t];
+      if (p < 0 || p >= npix) {
+        atomicOr(err, ERR_PIX);
+        continue;
+      }
+      const double c = cc[t], s = ss[t];
+      double w[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) w[j] = 0.0;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        if (o < n_o) {
+          double row[NC];
+#pragma unroll
+          for (int j = 0; j < NC; ++j) row[j] = 0.0;
+          row_bin<NC, double>(K::kind(o, kk), c, s, 1.0, row);
+#pragma unroll
+          for (int i = 0; i < NC; ++i)
+#pragma unroll
+            for (int j = i; j < NC; ++j) w[sym_index<NC>(i, j)] += row[i] * row[j];
+        }
+      }
+      if (p != cur) {
+        if (cur >= 0) flush_m<NC>(hits, mm, cur, h, acc);
+        cur = p;
+        h = 1;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) acc[j] = w[j];
+      } else {
+        h += 1;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) acc[j] += w[j];
+      }
+    }
+    if (cur >= 0) flush_m<NC>(hits, mm, cur, h, acc);
+  }
+}
+
+// Closed-form eigenvalues of a packed symmetric matrix; rcond = lambda_min / lambda_max.
+// 2x2: mid +- radius.  3x3: the trigonometric solution of the characteristic cubic.
+template <int NC>
+__device__ double rcond_of(const double (&a)[NC * (NC + 1) / 2]) {
+  if constexpr (NC == 1) {
+    return a[0] > 0.0 ? 1.0 : 0.0;
+  } else if constexpr (NC == 2) {
+    const double mid = 0.5 * (a[0] + a[2]);
+    const double half = 0.5 * (a[0] - a[2]);
+    const double rad = sqrt(half * half + a[1] * a[1]);
+    const double lmax = mid + rad;
+    if (!(lmax > 0.0)) return 0.0;
+    const double det = a[0] * a[2] - a[1] * a[1];
+    return (det / lmax) / lmax;  // lambda_min = det / lambda_max
+  } else {
+    const double a00 = a[0], a01 = a[1], a02 = a[2], a11 = a[3], a12 = a[4], a22 = a[5];
+    const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    double e1, e3;
+    if (p1 == 0.0) {
+      e1 = fmax(a00, fmax(a11, a22));
+      e3 = fmin(a00, fmin(a11, a22));
+    } else {
+      const double q = (a00 + a11 + a22) / 3.0;
+      const double d0 = a00 - q, d1 = a11 - q, d2 = a22 - q;
+      const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
+      const double pp = sqrt(p2 / 6.0);
+      const double ip = 1.0 / pp;
+      const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip;
+      const double b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
+      const double detb = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                          b02 * (b01 * b12 - b11 * b02);
+      double r = 0.5 * detb;
+      r = fmin(1.0, fmax(-1.0, r));
+      const double phi = acos(r) / 3.0;
+      e1 = q + 2.0 * pp * cos(phi);
+      e3 = q + 2.0 * pp * cos(phi + 2.0943951023931954923);  // + 2 pi / 3
+    }
+    if (!(e1 > 0.0)) return 0.0;
+    return e3 / e1;
+  }
+}
+
+template <int NC>
+__device__ void sym_inverse(const double (&a)[NC * (NC + 1) / 2], double (&inv)[NC * (NC + 1) / 2]) {
+  if constexpr (NC == 1) {
+    inv[0] = 1.0 / a[0];
+  } else if constexpr (NC == 2) {
+    const double det = a[0] * a[2] - a[1] * a[1];
+    inv[0] = a[2] / det;
+    inv[1] = -a[1] / det;
+    inv[2] = a[0] / det;
+  } else {
+    const double a00 = a[0], a01 = a[1], a02 = a[2], a11 = a[3], a12 = a[4], a22 = a[5];
+    const double c00 = a11 * a22 - a12 * a12;
+    const double c01 = a02 * a12 - a01 * a22;
+    const double c02 = a01 * a12 - a02 * a11;
+    const double c11 = a00 * a22 - a02 * a02;
+    const double c12 = a01 * a02 - a00 * a12;
+    const double c22 = a00 * a11 - a01 * a01;
+    const double det = a00 * c00 + a01 * c01 + a02 * c02;
+    const double id = 1.0 / det;
+    inv[0] = c00 * id; inv[1] = c01 * id; inv[2] = c02 * id;
+    inv[3] = c11 * id; inv[4] = c12 * id; inv[5] = c22 * id;
+  }
+}
+
+// Per pixel: rcond cut and M_p^-1 (in place over M), mask, good-pixel count.
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_pixel_invert(double* __restrict__ mm,
+                                                         const int32_t* __restrict__ hits,
+                                                         uint8_t* __restrict__ mask,
+                                                         int64_t npix, double rcond_min,
+                                                         unsigned long long* __restrict__ n_good) {
+  constexpr int NM = NC * (NC + 1) / 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long good = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
+    double a[NM], inv[NM];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) a[j] = mm[p * NM + j];
+    bool keep = false;
+    if (hits[p] > 0) {
+      const double rc = rcond_of<NC>(a);
+      keep = rc >= rcond_min;
+    }
+    if (keep) {
+      sym_inverse<NC>(a, inv);
+      good += 1;
+    } else {
+#pragma unroll
+      for (int j = 0; j < NM; ++j) inv[j] = 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < NM; ++j) mm[p * NM + j] = inv[j];
+    mask[p] = keep ? 1 : 0;
+  }
+  for (int d = 16; d > 0; d >>= 1) good += __shfl_down_sync(0xffffffffu, good, d);
+  if ((threadIdx.x & 31) == 0 && good) atomicAdd(n_good, good);
+}
+
+// Effective pixel of each sample (-1 when flagged or on a cut pixel) and the
+// number of weight-1 samples per baseline.
+__global__ void __launch_bounds__(kBlock) k_plan_weights(const int32_t* __restrict__ pix_in,
+                                                         const uint8_t* __restrict__ valid,
+                                                         const uint8_t* __restrict__ mask,
+                                                         int32_t* __restrict__ pix_out,
+                                                         int32_t* __restrict__ nvalid,
+                                                         int64_t n_t, int64_t npix, int64_t L,
+                                                         unsigned long long* __restrict__ n_valid) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long total = 0;
+  for (int64_t vb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; vb < nvec;
+       vb += stride) {
+    const int64_t v = vb + lane;
+    int key = -1, cnt = 0;
+    if (v < nvec) {
+      const int64_t t0 = v << 2;
+      int64_t b = t0 / L, bend = (b + 1) * L;
+      key = (int)b;
+      for (int k = 0; k < 4; ++k) {
+        const int64_t t = t0 + k;
+        if (t >= n_t) break;
+        if (t >= bend) {
+          if (cnt) atomicAdd(nvalid + b, cnt);
+          total += cnt;
+          cnt = 0;
+          b += 1;
+          bend += L;
+          key = (int)b;
+        }
+        const int p = pix_in[t];
+        const bool ok = (valid == nullptr || valid[t] != 0) && p >= 0 && p < npix && mask[p];
+        pix_out[t] = ok ? p : -1;
+        cnt += ok ? 1 : 0;
+      }
+    }
+    total += cnt;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int k2 = __shfl_down_sync(full, key, d);
+      const int c2 = __shfl_down_sync(full, cnt, d);
+      if (lane + d < 32 && k2 == key) cnt += c2;
+    }
+    const int kp = __shfl_up_sync(full, key, 1);
+    if (key >= 0 && (lane == 0 || kp != key) && cnt) atomicAdd(nvalid + key, cnt);
+  }
+  for (int d = 16; d > 0; d >>= 1) total += __shfl_down_sync(full, total, d);
+  if (lane == 0 && total) atomicAdd(n_valid, total);
+}
+
+template <typename F>
+void with_kindset(int ks, F&& f) {
+  switch (ks) {
+    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
+    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
+    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
+    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
+    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
+    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
+    default: f(std::integral_constant<int, KS_GEN3>{}); break;
+  }
+}
+
+}  // namespace
+
+ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid) {
+  cudaStream_t st = P.stream;
+  const int nm = P.nm;
+  DS_CUDA_TRY(cudaMemsetAsync(P.hits, 0, sizeof(int32_t) * P.npix, st));
+  DS_CUDA_TRY(cudaMemsetAsync(P.minv, 0, sizeof(double) * P.npix * nm, st));
+  DS_CUDA_TRY(cudaMemsetAsync(P.nvalid, 0, sizeof(int32_t) * P.n_b, st));
+  DS_CUDA_TRY(cudaMemsetAsync(P.err, 0, sizeof(int32_t), st));
+  DS_CUDA_TRY(cudaMemsetAsync(P.scal, 0, sizeof(double) * 8, st));
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_plan_accum<KS><<<grid, kBlock, 0, st>>>(d_pix, P.c, P.s, d_valid, P.hits, P.minv, P.n_t,
+                                               P.npix, P.kinds, P.err);
+  });
+  DS_CUDA_TRY(cudaGetLastError());
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(P.scal);
+  const int pgrid = stream_grid(P, P.npix, kBlock, 8);
+  if (P.n_c == 1)
+    k_pixel_invert<1><<<pgrid, kBlock, 0, st>>>(P.minv, P.hits, P.mask, P.npix, P.desc.rcond_min, counts);
+  else if (P.n_c == 2)
+    k_pixel_invert<2><<<pgrid, kBlock, 0, st>>>(P.minv, P.hits, P.mask, P.npix, P.desc.rcond_min, counts);
+  else
+    k_pixel_invert<3><<<pgrid, kBlock, 0, st>>>(P.minv, P.hits, P.mask, P.npix, P.desc.rcond_min, counts);
+  DS_CUDA_TRY(cudaGetLastError());
+  k_plan_weights<<<grid, kBlock, 0, st>>>(d_pix, d_valid, P.mask, P.pix, P.nvalid, P.n_t, P.npix,
+                                          P.L, counts + 1);
+  DS_CUDA_TRY(cudaGetLastError());
+  DS_CUDA_TRY(cudaMemcpyAsync(P.h_scal, P.scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  DS_CUDA_TRY(cudaMemcpyAsync(P.h_err, P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  DS_CUDA_TRY(cudaStreamSynchronize(st));
+  unsigned long long hc[2];
+  std::memcpy(hc, P.h_scal, sizeof(hc));
+  P.n_good = (int64_t)hc[0];
+  P.n_valid = (int64_t)hc[1];
+  if (*P.h_err & ERR_PIX) return DS_EPIX;
+  return DS_OK;
+}
+
+}  // namespace ds
