@@ -85,6 +85,10 @@ ds_status launch_status() {
   return e == cudaSuccess ? DS_OK : DS_ECUDA;
 }
 
+// Drops a non-sticky error left by an earlier, already-reported runtime call so
+// that launch_status() only sees this call's launches.
+void clear_stale_error() { (void)cudaGetLastError(); }
+
 ds_status build_graph(Plan& P) {
   if (P.graph_exec && P.graph_profiled == P.profiling) return DS_OK;
   if (P.graph_exec) {
@@ -119,10 +123,13 @@ void collect_times(Plan& P, int n_ran) {
   for (int k = 0; k < n_ran && k < P.graph_iters; ++k) {
     cudaEvent_t* e = P.ev + 5 * k;
     float t01 = 0.f, t12 = 0.f, t23 = 0.f, t04 = 0.f;
-    if (cudaEventElapsedTime(&t01, e[0], e[1]) != cudaSuccess) return;
-    cudaEventElapsedTime(&t12, e[1], e[2]);
-    cudaEventElapsedTime(&t23, e[2], e[3]);
-    cudaEventElapsedTime(&t04, e[0], e[4]);
+    if (cudaEventElapsedTime(&t01, e[0], e[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t12, e[1], e[2]) != cudaSuccess ||
+        cudaEventElapsedTime(&t23, e[2], e[3]) != cudaSuccess ||
+        cudaEventElapsedTime(&t04, e[0], e[4]) != cudaSuccess) {
+      clear_stale_error();
+      return;
+    }
     P.t_bin += t01;
     P.t_solve += t12;
     P.t_rescan += t23;
@@ -262,6 +269,7 @@ void destripe_destroy(ds_plan_t plan) {
 ds_status destripe_apply_A(ds_plan_t plan, const double* d_x, double* d_Ax) {
   if (plan == nullptr || d_x == nullptr || d_Ax == nullptr || d_x == d_Ax) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
+  clear_stale_error();
   DS_CUDA_TRY(cudaMemsetAsync(d_Ax, 0, sizeof(double) * P.n_u, P.stream));
   enqueue_apply(P, P.stream, P.desc.precision == DS_PREC_FP64, d_x, d_Ax, Gate{nullptr, nullptr});
   P.launches += 3;
@@ -271,6 +279,7 @@ ds_status destripe_apply_A(ds_plan_t plan, const double* d_x, double* d_Ax) {
 ds_status destripe_rhs(ds_plan_t plan, const void* d_y, double* d_b) {
   if (plan == nullptr || d_y == nullptr || d_b == nullptr) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
+  clear_stale_error();
   DS_CUDA_TRY(cudaMemsetAsync(d_b, 0, sizeof(double) * P.n_u, P.stream));
   enqueue_rhs(P, P.stream, d_y, d_b, Gate{nullptr, nullptr});
   P.launches += 3;
@@ -281,6 +290,7 @@ static ds_status map_common(ds_plan_t plan, const void* d_y, const double* d_a, 
                             int32_t* d_hits, uint8_t* d_mask) {
   if (plan == nullptr || d_y == nullptr || d_map == nullptr) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
+  clear_stale_error();
   enqueue_map(P, P.stream, d_y, d_a, d_map);
   P.launches += 2;
   if (d_hits)
@@ -304,6 +314,7 @@ ds_status destripe_map(ds_plan_t plan, const void* d_y, const double* d_a, doubl
 ds_status destripe_gauge(ds_plan_t plan, double* d_a) {
   if (plan == nullptr || d_a == nullptr) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
+  clear_stale_error();
   enqueue_gauge(P, P.stream, d_a);
   P.launches += 2;
   return launch_status();
@@ -315,6 +326,7 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   if (!(tol >= 0.0) || !std::isfinite(tol)) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
   if (max_iter <= 0) max_iter = 10000;
+  clear_stale_error();
   cudaStream_t st = P.stream;
   if (warm_start)
     DS_CUDA_TRY(cudaMemcpyAsync(P.x, d_a, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));

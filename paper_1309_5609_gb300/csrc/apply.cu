@@ -381,13 +381,14 @@ void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out,
 // solve and after the rescan.
 void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out,
                    Gate g, cudaEvent_t* ev) {
-  if (ev) cudaEventRecord(ev[0], st);
+  // External records become event nodes when the stream is being captured.
+  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   launch_bin_x(P, st, fp64, x, g);
-  if (ev) cudaEventRecord(ev[1], st);
+  if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
   launch_pixel_solve(P, st, fp64, nullptr, g);
-  if (ev) cudaEventRecord(ev[2], st);
+  if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
   launch_rescan_x(P, st, fp64, x, out, g);
-  if (ev) cudaEventRecord(ev[3], st);
+  if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
 }
 
 void enqueue_rhs(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g) {

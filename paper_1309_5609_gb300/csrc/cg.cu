@@ -314,7 +314,7 @@ void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev) {
     k_cg_reliable<<<vg, kBlock, 0, st>>>(P.r, P.b, P.t, P.n_u, P.red, P.counters, P.state);
   }
   k_cg_direction<<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.n_u, P.state);
-  if (ev) cudaEventRecord(ev[4], st);
+  if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
 }
 
 void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, double delta,

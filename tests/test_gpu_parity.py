@@ -280,3 +280,23 @@ def test_run_host_matches_device_path():
     assert np.array_equal(mask.numpy().astype(bool), op.mask)
     assert rel_rms(a.numpy(), ref["a"]) < 1e-5
     assert rel_rms(m.numpy(), ref["map"]) < 1e-5
+
+
+def test_profile_counters_time_every_iteration():
+    prob = config_problem(1, n_t=1 << 18)
+    for precision in ("fp64", "mixed"):
+        plan, g, y = gpu_plan(prob, precision)
+        ds.destripe_profile(plan, 1)
+        a = torch.zeros(plan.n_u, dtype=torch.float64, device=DEV)
+        st, iters, rel = ds.destripe_solve(plan, y, a, tol=1e-10)
+        m = torch.zeros(plan.n_c * plan.npix, dtype=torch.float64, device=DEV)
+        ds.destripe_map(plan, y, a, m)
+        p = ds.destripe_profile(plan, -1)
+        assert st == ds.DS_OK
+        assert p["iterations"] == iters == p["timed_iterations"]
+        assert p["bin_ms"] > 0 and p["rescan_ms"] > 0 and p["solve_ms"] > 0
+        assert p["iteration_ms"] >= p["bin_ms"] + p["rescan_ms"]
+        per_iter = 10 if precision == "mixed" else 6
+        assert p["kernel_launches"] >= per_iter * iters
+        ds.destripe_profile(plan, 0)
+        plan.close()
