@@ -195,6 +195,32 @@ typedef struct {
 
 ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
 
+/* Binned map without any device allocation (no counterpart in the paper: it
+ * serves callers that cannot allocate device memory when they need a map, such
+ * as processes whose device memory is owned by another allocator and loops that
+ * forbid allocation after start-up).  Same result as destripe_plan followed by
+ * destripe_bin(plan, d_y, NULL, ...), from the pointing and data directly.
+ *   desc        as for destripe_plan (desc->baseline_len is not used)
+ *   d_pix, d_cos2psi, d_sin2psi, d_valid   pointing as for destripe_plan (no
+ *               alignment requirement)
+ *   d_y         [n_o][n_t] float64 (DS_PREC_FP64) or float32 (DS_PREC_MIXED)
+ *   d_map       float64 [n_c][n_pix] output; d_hits, d_mask optional outputs
+ * Intermediate sums live in one fixed device array declared by the library
+ * (4.2 MB, held by every GPU that loads the library until exit); maps of more
+ * than DS_NOALLOC_MAX_PIX pixels (nside > 64) return DS_EINVAL.  Every call
+ * reuses that array (it clears what must start at zero), so calls that overlap
+ * on the GPU race and must be serialised by the caller.  The first call on a
+ * device looks up the array's address on that device; make it before any stream
+ * capture.  Calls no allocation routine.  Accumulates in float64; returns
+ * DS_EPIX for a valid sample with a pixel outside the map.  Synchronises
+ * desc->stream. */
+#define DS_NOALLOC_MAX_PIX 49152
+
+ds_status destripe_bin_noalloc(const ds_desc* desc, const int32_t* d_pix,
+                               const float* d_cos2psi, const float* d_sin2psi,
+                               const uint8_t* d_valid, const void* d_y, double* d_map,
+                               int32_t* d_hits, uint8_t* d_mask);
+
 #ifdef __cplusplus
 }
 #endif

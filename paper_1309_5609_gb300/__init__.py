@@ -20,7 +20,7 @@ __all__ = [
     "DS_OK", "DS_ENOCONV", "DestripeError", "Plan", "KIND_CODE", "lib_path", "load_library",
     "destripe_plan", "destripe_plan_info", "destripe_bin", "destripe_apply_A", "destripe_rhs",
     "destripe_solve", "destripe_map", "destripe_gauge", "destripe_destroy", "destripe_strerror",
-    "destripe_run_host", "destripe_profile", "components",
+    "destripe_run_host", "destripe_profile", "destripe_bin_noalloc", "components",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -78,6 +78,8 @@ _SIGS = {
     "destripe_destroy": (None, [_P]),
     "destripe_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ds_profile)]),
     "destripe_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "destripe_bin_noalloc": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P, _P, _P,
+                                            _P]),
     "destripe_run_host": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P,
                                          ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P,
                                          ctypes.POINTER(ctypes.c_int32),
@@ -314,6 +316,37 @@ def destripe_profile(plan: Plan, enable: int = -1) -> dict:
     if st != DS_OK:
         raise DestripeError(st, "destripe_profile")
     return {f: getattr(prof, f) for f, _ in ds_profile._fields_}
+
+
+NOALLOC_MAX_PIX = 49152  # DS_NOALLOC_MAX_PIX: largest map of destripe_bin_noalloc (nside 64)
+
+
+def destripe_bin_noalloc(pix, cos2psi, sin2psi, valid, y, map_out, hits_out=None,
+                         mask_out=None, *, nside: int, kinds, precision="fp64",
+                         rcond_min: float = 1e-3, stream=None):
+    """Binned map from the pointing and data without any device allocation by the
+    library (for callers that cannot allocate device memory at that point); all
+    buffers are the caller's CUDA tensors.  Maps up to NOALLOC_MAX_PIX pixels."""
+    import torch
+    n_t = pix.numel()
+    dev = pix.device
+    _check(pix, torch.int32, n_t, "pix")
+    _check(cos2psi, torch.float32, n_t, "cos2psi", dev)
+    _check(sin2psi, torch.float32, n_t, "sin2psi", dev)
+    if valid is not None:
+        _check(valid, torch.uint8, n_t, "valid", dev)
+    ydt = torch.float64 if precision == "fp64" else torch.float32
+    _check(y, ydt, len(kinds) * n_t, "y", dev)
+    npix = 12 * nside * nside
+    _check(map_out, torch.float64, len(components(kinds)) * npix, "map", dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    desc = _make_desc(n_t, nside, kinds, 1, precision, rcond_min, stream)
+    st = load_library().destripe_bin_noalloc(ctypes.byref(desc), _ptr(pix), _ptr(cos2psi),
+                                             _ptr(sin2psi), _ptr(valid), _ptr(y),
+                                             _ptr(map_out), _ptr(hits_out), _ptr(mask_out))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_bin_noalloc")
 
 
 def destripe_run_host(pix, cos2psi, sin2psi, valid, y, *, nside: int, kinds, baseline_len: int,
