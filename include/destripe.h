@@ -36,10 +36,11 @@
  *  - A plan is not thread-safe; distinct plans are independent.
  *  - Precision: DS_PREC_FP64 computes every step in float64 and takes float64
  *    timelines y.  DS_PREC_MIXED takes float32 timelines y; the per-sample work
- *    of the CG iterations (expand, bin, rescan, baseline sums) runs in float32
- *    with float64 accumulation of partial sums, while pixel matrices, their
- *    inverses and rcond cut, the right-hand side, the CG scalars, the residual
- *    updates that keep the iteration honest, and the final maps use float64.
+ *    of the CG iterations (expand, bin, rescan, baseline sums) runs in float32;
+ *    the right-hand side, the residual refreshes that keep the iteration honest
+ *    and the maps run in double-float (pairs of float32, about 48 significant
+ *    bits) with float64 accumulators; pixel matrices, their inverses and rcond
+ *    cut, pixel solves and the CG vectors and scalars are float64.
  */
 #ifndef DESTRIPE_H
 #define DESTRIPE_H
@@ -194,6 +195,29 @@ typedef struct {
 } ds_profile;
 
 ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
+
+/* Tuning knobs of a plan (no counterpart in the paper; used by the autotuner).
+ * Keys and values:
+ *   "reliable_delta"  in (0, 1): MIXED plans recompute the residual in float64 each time
+ *                     ||r|| has dropped by this factor since the last recomputation
+ *                     (default 1e-5)
+ *   "refresh_max"     MIXED plans: recompute the residual in float64 at least every this
+ *                     many iterations, whatever the drop (default 50)
+ *   "bin_mode"        MIXED plans: 1 = float32 pixel sums with one vector atomic per run
+ *                     (default), 0 = float64 pixel sums with scalar atomics
+ *   "graph_iters"     1..64 CG iterations per captured graph replay (default 16)
+ *   "accurate_df"     MIXED plans: 1 = the accurate passes (right-hand side, maps,
+ *                     float64 residual refreshes) use double-float arithmetic on the
+ *                     float32 pipes with float64 accumulators (default), 0 = float64
+ *   "stream_mode"     MIXED plans: 0 = streaming kernels read the pointing with vector
+ *                     loads (default); 1 / 2 = TMA bulk copies stage it through a
+ *                     shared-memory pipeline of 4 x 2048-sample stages at 2 blocks per SM
+ *                     / 3 x 1024-sample stages at 3 blocks per SM (persistent blocks;
+ *                     waits are bounded, DS_ETIMEOUT on expiry)
+ *   "blocks_per_sm"   1..32 resident-block target of the streaming kernels (default 16)
+ * Returns DS_EINVAL for an unknown key or value, DS_ESTATE when the plan cannot
+ * use the value.  Takes effect at the next call. */
+ds_status destripe_tune(ds_plan_t plan, const char* key, double value);
 
 /* Binned map without any device allocation (no counterpart in the paper: it
  * serves callers that cannot allocate device memory when they need a map, such

@@ -20,7 +20,8 @@ __all__ = [
     "DS_OK", "DS_ENOCONV", "DestripeError", "Plan", "KIND_CODE", "lib_path", "load_library",
     "destripe_plan", "destripe_plan_info", "destripe_bin", "destripe_apply_A", "destripe_rhs",
     "destripe_solve", "destripe_map", "destripe_gauge", "destripe_destroy", "destripe_strerror",
-    "destripe_run_host", "destripe_profile", "destripe_bin_noalloc", "components",
+    "destripe_run_host", "destripe_profile", "destripe_bin_noalloc", "destripe_tune",
+    "components",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -78,6 +79,7 @@ _SIGS = {
     "destripe_destroy": (None, [_P]),
     "destripe_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ds_profile)]),
     "destripe_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "destripe_tune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
     "destripe_bin_noalloc": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P, _P, _P,
                                             _P]),
     "destripe_run_host": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P,
@@ -307,6 +309,13 @@ def destripe_gauge(plan: Plan, a):
 
 def destripe_destroy(plan: Plan):
     plan.close()
+
+
+def destripe_tune(plan: Plan, key: str, value: float):
+    """Set a tuning knob of the plan (see include/destripe.h for the keys)."""
+    st = load_library().destripe_tune(plan.handle, key.encode(), float(value))
+    if st != DS_OK:
+        raise DestripeError(st, f"destripe_tune({key})")
 
 
 def destripe_profile(plan: Plan, enable: int = -1) -> dict:

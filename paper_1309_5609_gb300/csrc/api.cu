@@ -3,6 +3,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "internal.cuh"
 
@@ -19,8 +20,7 @@ using namespace ds;
 
 namespace {
 
-constexpr int kGraphIters = 16;        // CG iterations per captured graph launch
-constexpr double kReliableDelta = 1e-3;  // float64 residual after every 1e3 drop in ||r||
+constexpr int kGraphItersMax = 64;     // upper bound of CG iterations per captured graph
 
 int n_comp_of(const int* kinds, int n_o, int* has_i_out) {
   bool I = false, P = false;
@@ -52,10 +52,10 @@ void plan_free(Plan* P) {
   if (P == nullptr) return;
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
   if (P->ev) {
-    for (int i = 0; i < P->graph_iters * 5; ++i) cudaEventDestroy(P->ev[i]);
+    for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->pix, P->hits, P->mask, P->minv, P->bins, P->map32, P->map64, P->nvalid,
+  void* dev[] = {P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->red,   P->counters,
                  P->state, P->err, P->scal};
   for (void* d : dev)
@@ -96,14 +96,14 @@ ds_status build_graph(Plan& P) {
     P.graph_exec = nullptr;
   }
   if (P.profiling && P.ev == nullptr) {
-    P.ev = new (std::nothrow) cudaEvent_t[kGraphIters * 5];
+    P.ev = new (std::nothrow) cudaEvent_t[kGraphItersMax * 5];
     if (P.ev == nullptr) return DS_ENOMEM;
-    for (int i = 0; i < kGraphIters * 5; ++i) DS_CUDA_TRY(cudaEventCreate(&P.ev[i]));
+    for (int i = 0; i < kGraphItersMax * 5; ++i) DS_CUDA_TRY(cudaEventCreate(&P.ev[i]));
   }
-  P.graph_iters = kGraphIters;
+  P.graph_iters = P.graph_iters_cfg;
   cudaGraph_t graph = nullptr;
   DS_CUDA_TRY(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < kGraphIters; ++k)
+  for (int k = 0; k < P.graph_iters; ++k)
     enqueue_iteration(P, P.cap_stream, P.profiling ? P.ev + 5 * k : nullptr);
   cudaError_t e = cudaStreamEndCapture(P.cap_stream, &graph);
   if (e != cudaSuccess) return DS_ECUDA;
@@ -191,6 +191,13 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
     return DS_ECUDA;
   }
   P->red_len = 2 * P->num_sms * 8 + 64;
+  P->reliable_delta = 1e-5;
+  P->bin_mode = P->desc.precision == DS_PREC_MIXED ? 1 : 0;
+  P->graph_iters_cfg = 16;
+  P->blocks_per_sm = 16;
+  P->accurate_df = 1;
+  P->stream_mode = 0;
+  P->refresh_max = 50;
   cudaError_t e = cudaSuccess;
 #define DS_ALLOC(ptr, n) \
   if (e == cudaSuccess) e = dalloc(*P, &P->ptr, (n));
@@ -199,6 +206,8 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   DS_ALLOC(mask, P->npix);
   DS_ALLOC(minv, P->npix * P->nm);
   DS_ALLOC(bins, P->npix * 4);
+  if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(bins32, P->npix * 4);
+  if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(maplo, P->npix * 4);
   DS_ALLOC(map32, P->npix * 4);
   DS_ALLOC(map64, P->npix * 4);
   DS_ALLOC(nvalid, P->n_b);
@@ -224,6 +233,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   }
   cudaStream_t st = P->stream;
   e = cudaMemsetAsync(P->bins, 0, sizeof(double) * P->npix * 4, st);
+  if (e == cudaSuccess && P->bins32) e = cudaMemsetAsync(P->bins32, 0, sizeof(float) * P->npix * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->counters, 0, sizeof(unsigned) * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->state, 0, sizeof(CgState), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->x, 0, sizeof(double) * P->n_u, st);
@@ -332,7 +342,7 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
     DS_CUDA_TRY(cudaMemcpyAsync(P.x, d_a, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
   DS_CUDA_TRY(cudaMemsetAsync(P.b, 0, sizeof(double) * P.n_u, st));
   enqueue_rhs(P, st, d_y, P.b, Gate{nullptr, nullptr});
-  enqueue_cg_setup(P, st, tol, max_iter, kReliableDelta, warm_start ? 1 : 0);
+  enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, warm_start ? 1 : 0);
   P.launches += 3 + 3 + (warm_start ? 3 : 0);
   ds_status s = launch_status();
   if (s != DS_OK) return s;
@@ -357,7 +367,9 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   P.launches += 2;
   DS_CUDA_TRY(cudaMemcpyAsync(d_a, P.x, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
   DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+  DS_CUDA_TRY(cudaMemcpyAsync(P.h_err, P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (*P.h_err & ERR_TIMEOUT) return DS_ETIMEOUT;
   const CgState& H = *P.h_state;
   if (iters) *iters = H.iter;
   if (rel_resid) *rel_resid = H.bb > 0.0 ? std::sqrt(H.rr_true / H.bb) : 0.0;
@@ -392,6 +404,44 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out) {
     out->rescan_ms = P.t_rescan;
     out->solve_ms = P.t_solve;
     out->iteration_ms = P.t_iter;
+  }
+  return DS_OK;
+}
+
+ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
+  if (plan == nullptr || key == nullptr) return DS_EINVAL;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  const std::string k(key);
+  if (k == "reliable_delta") {
+    if (!(value > 0.0 && value < 1.0)) return DS_EINVAL;
+    P.reliable_delta = value;
+  } else if (k == "bin_mode") {
+    if (value != 0.0 && value != 1.0) return DS_EINVAL;
+    if (value == 1.0 && P.bins32 == nullptr) return DS_ESTATE;
+    P.bin_mode = (int)value;
+  } else if (k == "graph_iters") {
+    if (!(value >= 1.0 && value <= kGraphItersMax)) return DS_EINVAL;
+    P.graph_iters_cfg = (int)value;
+  } else if (k == "accurate_df") {
+    if (value != 0.0 && value != 1.0) return DS_EINVAL;
+    if (value == 1.0 && P.maplo == nullptr) return DS_ESTATE;
+    P.accurate_df = (int)value;
+  } else if (k == "refresh_max") {
+    if (!(value >= 1.0 && value <= 1e6)) return DS_EINVAL;
+    P.refresh_max = (int)value;
+  } else if (k == "stream_mode") {
+    if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
+    P.stream_mode = (int)value;
+  } else if (k == "blocks_per_sm") {
+    if (!(value >= 1.0 && value <= 32.0)) return DS_EINVAL;
+    P.blocks_per_sm = (int)value;
+  } else {
+    return DS_EINVAL;
+  }
+  // the captured graph bakes in launch shapes and kernel choices: rebuild it
+  if (P.graph_exec) {
+    cudaGraphExecDestroy(P.graph_exec);
+    P.graph_exec = nullptr;
   }
   return DS_OK;
 }

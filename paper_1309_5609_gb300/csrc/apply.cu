@@ -63,6 +63,19 @@ __device__ __forceinline__ void flush_bins(double* __restrict__ bins, int p, con
   for (int j = 0; j < NC; ++j) atomicAdd(dst + j, (double)acc[j]);
 }
 
+// One vector reduction (red.global.add.v4.f32) adds all components of a run to
+// the float32 pixel sums; a single L2 atomic operation instead of NC.
+template <int NC, typename T>
+__device__ __forceinline__ void flush_bins(float* __restrict__ bins, int p, const T (&acc)[NC]) {
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < NC; ++j) v[j] = (float)acc[j];
+  float* dst = bins + (int64_t)p * 4;
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3])
+               : "memory");
+}
+
 template <int NC, typename T>
 __device__ __forceinline__ void load_map(const T* __restrict__ map, int p, T (&m)[NC]) {
   if constexpr (std::is_same<T, float>::value) {
@@ -106,13 +119,13 @@ __device__ __forceinline__ void warp_segment_flush(int key, T (&val)[NO], int n_
 // ---- binning: bins[p] += sum_o w_o(t) z_o(t) over samples with v = 1 ----------
 // ZY = false: z_o(t) = x[o][t / L]          (F~ x, the operator)
 // ZY = true : z_o(t) = y[o][t] - a[o][t/L]  (data minus baselines; a may be NULL)
-template <int KS, typename T, bool ZY, typename YT>
+template <int KS, typename T, bool ZY, typename YT, typename BT>
 __global__ void __launch_bounds__(kBlock) k_bin(const int32_t* __restrict__ pix,
                                                 const float* __restrict__ cc,
                                                 const float* __restrict__ ss,
                                                 const double* __restrict__ x,
                                                 const YT* __restrict__ y,
-                                                double* __restrict__ bins, int64_t n_t, int64_t L,
+                                                BT* __restrict__ bins, int64_t n_t, int64_t L,
                                                 int64_t n_b, KindsArg kk, Gate g) {
   if (gate_closed(g)) return;
   using K = KSet<KS>;
@@ -175,8 +188,8 @@ __global__ void __launch_bounds__(kBlock) k_bin(const int32_t* __restrict__ pix,
 // ---- per-pixel solve: m_p = M_p^-1 s_p on kept pixels, 0 elsewhere ---------------
 // Reads the float64 sums, clears them for the next pass, writes the map in the
 // working precision (and optionally component-major float64 for the caller).
-template <int NC, typename T>
-__global__ void __launch_bounds__(kBlock) k_pixel_solve(double* __restrict__ bins,
+template <int NC, typename T, typename BT>
+__global__ void __launch_bounds__(kBlock) k_pixel_solve(BT* __restrict__ bins,
                                                         const double* __restrict__ minv,
                                                         const uint8_t* __restrict__ mask,
                                                         T* __restrict__ map,
@@ -187,12 +200,20 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve(double* __restrict__ bin
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
     double s[NC], m[NC];
-    const double2 s01 = reinterpret_cast<const double2*>(bins)[2 * p];
-    s[0] = s01.x;
-    if constexpr (NC > 1) s[1] = s01.y;
-    if constexpr (NC > 2) s[2] = bins[4 * p + 2];
-    reinterpret_cast<double2*>(bins)[2 * p] = make_double2(0.0, 0.0);
-    if constexpr (NC > 2) bins[4 * p + 2] = 0.0;
+    if constexpr (std::is_same<BT, float>::value) {
+      const float4 v = reinterpret_cast<const float4*>(bins)[p];
+      s[0] = v.x;
+      if constexpr (NC > 1) s[1] = v.y;
+      if constexpr (NC > 2) s[2] = v.z;
+      reinterpret_cast<float4*>(bins)[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      const double2 s01 = reinterpret_cast<const double2*>(bins)[2 * p];
+      s[0] = s01.x;
+      if constexpr (NC > 1) s[1] = s01.y;
+      if constexpr (NC > 2) s[2] = bins[4 * p + 2];
+      reinterpret_cast<double2*>(bins)[2 * p] = make_double2(0.0, 0.0);
+      if constexpr (NC > 2) bins[4 * p + 2] = 0.0;
+    }
     if (mask[p]) {
       double mi[NM];
 #pragma unroll
@@ -306,28 +327,33 @@ int stream_grid(const Plan& P, int64_t work_items, int block, int per_sm) {
   return (int)(need < cap ? need : cap);
 }
 
+static bool f32_bins(const Plan& P, bool fp64) { return !fp64 && P.bin_mode == 1; }
+
 void launch_bin_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, Gate g) {
-  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (fp64)
-      k_bin<KS, double, false, double><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, nullptr, P.bins,
-                                                                P.n_t, P.L, P.n_b, P.kinds, g);
+      k_bin<KS, double, false, double, double><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, x, nullptr, P.bins, P.n_t, P.L, P.n_b, P.kinds, g);
+    else if (f32_bins(P, fp64))
+      k_bin<KS, float, false, float, float><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, x, nullptr, P.bins32, P.n_t, P.L, P.n_b, P.kinds, g);
     else
-      k_bin<KS, float, false, float><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, nullptr, P.bins,
-                                                              P.n_t, P.L, P.n_b, P.kinds, g);
+      k_bin<KS, float, false, float, double><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, x, nullptr, P.bins, P.n_t, P.L, P.n_b, P.kinds, g);
   });
 }
 
 void launch_bin_y(const Plan& P, cudaStream_t st, const void* y, const double* a, Gate g) {
-  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (P.desc.precision == DS_PREC_FP64)
-      k_bin<KS, double, true, double><<<grid, kBlock, 0, st>>>(
+      k_bin<KS, double, true, double, double><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, a, static_cast<const double*>(y), P.bins, P.n_t, P.L, P.n_b, P.kinds, g);
     else
-      k_bin<KS, double, true, float><<<grid, kBlock, 0, st>>>(
+      k_bin<KS, double, true, float, double><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, a, static_cast<const float*>(y), P.bins, P.n_t, P.L, P.n_b, P.kinds, g);
   });
 }
@@ -337,11 +363,14 @@ void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_m
   auto go = [&](auto ncc) {
     constexpr int NC = decltype(ncc)::value;
     if (fp64)
-      k_pixel_solve<NC, double><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map64, out_map,
-                                                          P.npix, g);
+      k_pixel_solve<NC, double, double><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map64,
+                                                                  out_map, P.npix, g);
+    else if (f32_bins(P, fp64))
+      k_pixel_solve<NC, float, float><<<grid, kBlock, 0, st>>>(P.bins32, P.minv, P.mask, P.map32,
+                                                                out_map, P.npix, g);
     else
-      k_pixel_solve<NC, float><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map32, out_map,
-                                                         P.npix, g);
+      k_pixel_solve<NC, float, double><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map32,
+                                                                 out_map, P.npix, g);
   };
   if (P.n_c == 1) go(std::integral_constant<int, 1>{});
   else if (P.n_c == 2) go(std::integral_constant<int, 2>{});
@@ -350,7 +379,7 @@ void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_m
 
 void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out,
                      Gate g) {
-  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (fp64)
@@ -363,7 +392,7 @@ void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x,
 }
 
 void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g) {
-  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (P.desc.precision == DS_PREC_FP64)
@@ -377,10 +406,35 @@ void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out,
   });
 }
 
+static bool use_df(const Plan& P) {
+  return P.desc.precision == DS_PREC_MIXED && P.accurate_df && P.maplo != nullptr;
+}
+
 // ev (optional): events recorded before binning, after binning, after the pixel
-// solve and after the rescan.
+// solve and after the rescan.  fp64 selects the accurate operator: float64
+// arithmetic, or double-float in mixed plans.
 void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out,
                    Gate g, cudaEvent_t* ev) {
+  if (fp64 && use_df(P)) {
+    if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+    launch_bin_df(P, st, x, nullptr, g);
+    if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+    launch_pixel_solve_df(P, st, nullptr, g);
+    if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+    launch_rescan_df(P, st, x, nullptr, out, g);
+    if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+    return;
+  }
+  if (!fp64 && P.stream_mode >= 1 && P.bin_mode == 1 && tma_supported(P)) {
+    if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+    launch_bin_tma(P, st, x, g);
+    if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+    launch_pixel_solve(P, st, false, nullptr, g);
+    if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+    launch_rescan_tma(P, st, x, out, g);
+    if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+    return;
+  }
   // External records become event nodes when the stream is being captured.
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   launch_bin_x(P, st, fp64, x, g);
@@ -392,6 +446,12 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
 }
 
 void enqueue_rhs(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g) {
+  if (use_df(P)) {
+    launch_bin_df(P, st, nullptr, static_cast<const float*>(y), g);
+    launch_pixel_solve_df(P, st, nullptr, g);
+    launch_rescan_df(P, st, nullptr, static_cast<const float*>(y), out, g);
+    return;
+  }
   launch_bin_y(P, st, y, nullptr, g);
   launch_pixel_solve(P, st, true, nullptr, g);
   launch_rescan_y(P, st, y, out, g);
@@ -399,6 +459,11 @@ void enqueue_rhs(const Plan& P, cudaStream_t st, const void* y, double* out, Gat
 
 void enqueue_map(const Plan& P, cudaStream_t st, const void* y, const double* a, double* out_map) {
   Gate g{nullptr, nullptr};
+  if (use_df(P)) {
+    launch_bin_df(P, st, a, static_cast<const float*>(y), g);
+    launch_pixel_solve_df(P, st, out_map, g);
+    return;
+  }
   launch_bin_y(P, st, y, a, g);
   launch_pixel_solve(P, st, true, out_map, g);
 }

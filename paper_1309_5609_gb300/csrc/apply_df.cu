@@ -1,0 +1,371 @@
+// Accurate passes of mixed-precision plans in double-float arithmetic (df.cuh):
+// the right-hand side F~^T Z y, the maps M^-1 A_p^T V (y - F~ a) and the
+// float64 residual refreshes b - F~^T Z F~ x of the CG iteration (Sect. 3).
+//
+// Per sample everything is float32 pairs: cos 2psi, sin 2psi and float32 data
+// are exact float32 numbers, so their products are exact double-floats.  float64
+// appears only once per run of equal pixels (the atomic add into the float64
+// pixel sums), once per warp segment (the atomic add into the float64 baseline
+// sums), per baseline (splitting x) and per pixel (the pixel solve).  The work
+// split is that of apply.cu: 4 consecutive samples per thread, 128 per warp.
+#include <type_traits>
+
+#include "df.cuh"
+#include "internal.cuh"
+#include "rows.cuh"
+
+namespace ds {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <typename F>
+void with_kindset(int ks, F&& f) {
+  switch (ks) {
+    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
+    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
+    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
+    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
+    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
+    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
+    default: f(std::integral_constant<int, KS_GEN3>{}); break;
+  }
+}
+
+// acc += w_kind * z in double-float
+template <int NC>
+__device__ __forceinline__ void row_bin_df(int kind, float c, float s, df z, df (&acc)[NC]) {
+  using F = Frame<NC>;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) acc[F::I] = df_add(acc[F::I], z);
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) {
+      acc[F::Q] = df_add(acc[F::Q], df_mul_f(z, c));
+      acc[F::U] = df_add(acc[F::U], df_mul_f(z, s));
+    }
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) {
+      acc[F::Q] = df_sub(acc[F::Q], df_mul_f(z, s));
+      acc[F::U] = df_add(acc[F::U], df_mul_f(z, c));
+    }
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0) {
+      acc[F::I] = df_add(acc[F::I], z);
+      acc[F::Q] = df_add(acc[F::Q], df_mul_f(z, c));
+      acc[F::U] = df_add(acc[F::U], df_mul_f(z, s));
+    }
+  }
+}
+
+// w_kind . m in double-float
+template <int NC>
+__device__ __forceinline__ df row_dot_df(int kind, float c, float s, const df (&m)[NC]) {
+  using F = Frame<NC>;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) return m[F::I];
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) return df_add(df_mul_f(m[F::Q], c), df_mul_f(m[F::U], s));
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) return df_sub(df_mul_f(m[F::U], c), df_mul_f(m[F::Q], s));
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0)
+      return df_add(m[F::I], df_add(df_mul_f(m[F::Q], c), df_mul_f(m[F::U], s)));
+  }
+  return df{0.f, 0.f};
+}
+
+__device__ __forceinline__ void load4_df(const int32_t* __restrict__ pix,
+                                         const float* __restrict__ cc,
+                                         const float* __restrict__ ss, int64_t v, int64_t n_t,
+                                         int (&p)[4], float (&c)[4], float (&s)[4]) {
+  const int64_t t0 = v << 2;
+  if (t0 + 4 <= n_t) {
+    const int4 pp = ld_stream(reinterpret_cast<const int4*>(pix) + v);
+    const float4 c4 = ld_stream(reinterpret_cast<const float4*>(cc) + v);
+    const float4 s4 = ld_stream(reinterpret_cast<const float4*>(ss) + v);
+    p[0] = pp.x; p[1] = pp.y; p[2] = pp.z; p[3] = pp.w;
+    c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+    s[0] = s4.x; s[1] = s4.y; s[2] = s4.z; s[3] = s4.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool in = t0 + k < n_t;
+      p[k] = in ? pix[t0 + k] : -1;
+      c[k] = in ? cc[t0 + k] : 0.f;
+      s[k] = in ? ss[t0 + k] : 0.f;
+    }
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void flush_bins_df(double* __restrict__ bins, int p, const df (&acc)[NC]) {
+  double* dst = bins + (int64_t)p * 4;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) atomicAdd(dst + j, df_to_double(acc[j]));
+}
+
+// bins[p] += sum_o w_o(t) z_o(t), z = x[o][t/L] (ZY false) or y[o][t] - a[o][t/L] (ZY true)
+template <int KS, bool ZY>
+__global__ void __launch_bounds__(kBlock) k_bin_df(const int32_t* __restrict__ pix,
+                                                   const float* __restrict__ cc,
+                                                   const float* __restrict__ ss,
+                                                   const double* __restrict__ x,
+                                                   const float* __restrict__ y,
+                                                   double* __restrict__ bins, int64_t n_t,
+                                                   int64_t L, int64_t n_b, KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    int p[4];
+    float c[4], s[4];
+    load4_df(pix, cc, ss, v, n_t, p, c, s);
+    const int64_t t0 = v << 2;
+    int64_t b = t0 / L;
+    int64_t bend = (b + 1) * L;
+    df zb[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      zb[o] = (o < n_o && x != nullptr) ? df_from_double(__ldg(x + o * n_b + b)) : df{0.f, 0.f};
+    df acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = df{0.f, 0.f};
+    int cur = -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t t = t0 + k;
+      if (t >= n_t) break;
+      if (t >= bend) {
+        b += 1;
+        bend += L;
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          zb[o] = (o < n_o && x != nullptr) ? df_from_double(__ldg(x + o * n_b + b)) : df{0.f, 0.f};
+      }
+      if (p[k] < 0) continue;
+      df w[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) w[j] = df{0.f, 0.f};
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        if (o < n_o) {
+          df z = zb[o];
+          if constexpr (ZY) z = df_sub(df_make(y[(int64_t)o * n_t + t]), z);
+          row_bin_df<NC>(K::kind(o, kk), c[k], s[k], z, w);
+        }
+      }
+      if (p[k] != cur) {
+        if (cur >= 0) flush_bins_df<NC>(bins, cur, acc);
+        cur = p[k];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = w[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = df_add(acc[j], w[j]);
+      }
+    }
+    if (cur >= 0) flush_bins_df<NC>(bins, cur, acc);
+  }
+}
+
+// m_p = M_p^-1 s_p in float64; the map is stored as a double-float pair
+// (map_hi, map_lo) of float4 rows; optionally also component-major float64.
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_pixel_solve_df(double* __restrict__ bins,
+                                                           const double* __restrict__ minv,
+                                                           const uint8_t* __restrict__ mask,
+                                                           float* __restrict__ map_hi,
+                                                           float* __restrict__ map_lo,
+                                                           double* __restrict__ out_map,
+                                                           int64_t npix, Gate g) {
+  if (gate_closed(g)) return;
+  constexpr int NM = NC * (NC + 1) / 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
+    double s[NC], m[NC];
+    const double2 s01 = reinterpret_cast<const double2*>(bins)[2 * p];
+    s[0] = s01.x;
+    if constexpr (NC > 1) s[1] = s01.y;
+    if constexpr (NC > 2) s[2] = bins[4 * p + 2];
+    reinterpret_cast<double2*>(bins)[2 * p] = make_double2(0.0, 0.0);
+    if constexpr (NC > 2) bins[4 * p + 2] = 0.0;
+    if (mask[p]) {
+      double mi[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
+      sym_mul<NC>(mi, s, m);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) m[j] = 0.0;
+    }
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const df d = df_from_double(m[j]);
+      hi[j] = d.hi;
+      lo[j] = d.lo;
+    }
+    reinterpret_cast<float4*>(map_hi)[p] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    reinterpret_cast<float4*>(map_lo)[p] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    if (out_map != nullptr) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) out_map[(int64_t)j * npix + p] = m[j];
+    }
+  }
+}
+
+template <int NO>
+__device__ __forceinline__ void warp_segment_flush_df(int key, df (&val)[NO], int n_o,
+                                                      double* __restrict__ out, int64_t n_b) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int k2 = __shfl_down_sync(full, key, d);
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const df v2 = df_shfl_down(val[o], d);
+      if (lane + d < 32 && k2 == key) val[o] = df_add(val[o], v2);
+    }
+  }
+  const int kp = __shfl_up_sync(full, key, 1);
+  if (key >= 0 && (lane == 0 || kp != key)) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (o < n_o) atomicAdd(out + (int64_t)o * n_b + key, df_to_double(val[o]));
+  }
+}
+
+// out[o][b] += sum_{t in b} v (z_o(t) - w_o(t) . m_p(t)) in double-float
+template <int KS, bool ZY>
+__global__ void __launch_bounds__(kBlock) k_rescan_df(const int32_t* __restrict__ pix,
+                                                      const float* __restrict__ cc,
+                                                      const float* __restrict__ ss,
+                                                      const double* __restrict__ x,
+                                                      const float* __restrict__ y,
+                                                      const float* __restrict__ map_hi,
+                                                      const float* __restrict__ map_lo,
+                                                      double* __restrict__ out, int64_t n_t,
+                                                      int64_t L, int64_t n_b, KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int lane = threadIdx.x & 31;
+  const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t vb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; vb < nvec;
+       vb += stride) {
+    const int64_t v = vb + lane;
+    int key = -1;
+    df acc[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o] = df{0.f, 0.f};
+    if (v < nvec) {
+      int p[4];
+      float c[4], s[4];
+      load4_df(pix, cc, ss, v, n_t, p, c, s);
+      df m[4][NC];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (p[k] >= 0) {
+          const float4 h = __ldg(reinterpret_cast<const float4*>(map_hi) + p[k]);
+          const float4 l = __ldg(reinterpret_cast<const float4*>(map_lo) + p[k]);
+          const float hh[4] = {h.x, h.y, h.z, h.w}, ll[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+          for (int j = 0; j < NC; ++j) m[k][j] = df{hh[j], ll[j]};
+        } else {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) m[k][j] = df{0.f, 0.f};
+        }
+      }
+      const int64_t t0 = v << 2;
+      int64_t b = t0 / L;
+      int64_t bend = (b + 1) * L;
+      df zb[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        zb[o] = (o < n_o && x != nullptr) ? df_from_double(__ldg(x + o * n_b + b)) : df{0.f, 0.f};
+      key = (int)b;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t t = t0 + k;
+        if (t >= n_t) break;
+        if (t >= bend) {
+#pragma unroll
+          for (int o = 0; o < NO; ++o) {
+            if (o < n_o && (acc[o].hi != 0.f || acc[o].lo != 0.f))
+              atomicAdd(out + o * n_b + b, df_to_double(acc[o]));
+            acc[o] = df{0.f, 0.f};
+          }
+          b += 1;
+          bend += L;
+          key = (int)b;
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+            zb[o] = (o < n_o && x != nullptr) ? df_from_double(__ldg(x + o * n_b + b)) : df{0.f, 0.f};
+        }
+        if (p[k] < 0) continue;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          if (o < n_o) {
+            df z = zb[o];
+            if constexpr (ZY) z = df_sub(df_make(y[(int64_t)o * n_t + t]), z);
+            acc[o] = df_add(acc[o], df_sub(z, row_dot_df<NC>(K::kind(o, kk), c[k], s[k], m[k])));
+          }
+        }
+      }
+    }
+    warp_segment_flush_df<NO>(key, acc, n_o, out, n_b);
+  }
+}
+
+}  // namespace
+
+// ---- launchers (mixed-precision plans only: y is float32) --------------------------
+
+void launch_bin_df(const Plan& P, cudaStream_t st, const double* x, const float* y, Gate g) {
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (y != nullptr)
+      k_bin_df<KS, true><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, y, P.bins, P.n_t, P.L,
+                                                   P.n_b, P.kinds, g);
+    else
+      k_bin_df<KS, false><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, nullptr, P.bins, P.n_t,
+                                                    P.L, P.n_b, P.kinds, g);
+  });
+}
+
+void launch_pixel_solve_df(const Plan& P, cudaStream_t st, double* out_map, Gate g) {
+  const int grid = stream_grid(P, P.npix, kBlock, 8);
+  if (P.n_c == 1)
+    k_pixel_solve_df<1><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map32, P.maplo,
+                                                  out_map, P.npix, g);
+  else if (P.n_c == 2)
+    k_pixel_solve_df<2><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map32, P.maplo,
+                                                  out_map, P.npix, g);
+  else
+    k_pixel_solve_df<3><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map32, P.maplo,
+                                                  out_map, P.npix, g);
+}
+
+void launch_rescan_df(const Plan& P, cudaStream_t st, const double* x, const float* y,
+                      double* out, Gate g) {
+  const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (y != nullptr)
+      k_rescan_df<KS, true><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, y, P.map32, P.maplo,
+                                                      out, P.n_t, P.L, P.n_b, P.kinds, g);
+    else
+      k_rescan_df<KS, false><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, nullptr, P.map32,
+                                                       P.maplo, out, P.n_t, P.L, P.n_b, P.kinds, g);
+  });
+}
+
+}  // namespace ds

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_start(double* __restrict__ x, dou
     st->iter = 0;
     st->need = 0;
     st->n_reliable = 0;
+    st->last_refresh = 0;
     st->status = 0;
     st->done = 0;
     if (!isfinite(tot) || !isfinite(st->bb)) {
@@ -167,7 +168,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(double* __restrict__ x,
     }
     const bool conv = tot <= st->tol2;
     if (st->mixed) {
-      if (conv || tot < st->delta2 * st->rr_anchor || st->iter >= st->max_iter) st->need = 1;
+      // refresh when the recursive residual has dropped enough, claims convergence,
+      // has gone refresh_max iterations without a refresh (a float32 operator can
+      // stall it), or the iteration budget is spent
+      if (conv || tot < st->delta2 * st->rr_anchor || st->iter >= st->max_iter ||
+          st->iter - st->last_refresh >= st->refresh_max)
+        st->need = 1;
     } else {
       st->rr_true = tot;
       if (conv) {
@@ -202,6 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_reliable(double* __restrict__ r,
     st->rr_anchor = tot;
     st->rr_true = tot;
     st->n_reliable += 1;
+    st->last_refresh = st->iter;
     st->need = 0;
     if (!isfinite(tot)) {
       st->status = 4;
@@ -270,9 +277,11 @@ __global__ void __launch_bounds__(kBlock) k_gauge_apply(double* __restrict__ a,
   }
 }
 
-__global__ void k_set_state(CgState* st, double tol, int max_iter, int mixed, double delta) {
+__global__ void k_set_state(CgState* st, double tol, int max_iter, int mixed, double delta,
+                            int refresh_max) {
   st->tol2 = tol * tol * st->bb;
   st->max_iter = max_iter;
+  st->refresh_max = refresh_max;
   st->mixed = mixed;
   st->delta2 = delta * delta;
   st->done = 0;
@@ -322,7 +331,7 @@ void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, 
   const bool mixed = P.desc.precision == DS_PREC_MIXED;
   // bb = b . b
   enqueue_dot(P, st, P.b, P.b, P.n_u, &P.state->bb);
-  k_set_state<<<1, 1, 0, st>>>(P.state, tol, max_iter, mixed ? 1 : 0, delta);
+  k_set_state<<<1, 1, 0, st>>>(P.state, tol, max_iter, mixed ? 1 : 0, delta, P.refresh_max);
   if (warm) {
     cudaMemsetAsync(P.t, 0, sizeof(double) * P.n_u, st);
     enqueue_apply(P, st, true, P.x, P.t, Gate{nullptr, nullptr});

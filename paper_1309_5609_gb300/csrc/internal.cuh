@@ -60,10 +60,12 @@ struct CgState {
   int status;        // 0 ok, 1 converged, 2 max_iter, 3 breakdown, 4 non-finite
   int mixed;         // 1: recursive residual is confirmed in float64
   int n_reliable;    // float64 residual updates done
+  int last_refresh;  // iteration of the last float64 residual
+  int refresh_max;   // refresh at least every refresh_max iterations (stagnation guard)
   int pad;
 };
 
-enum ErrBits { ERR_PIX = 1, ERR_NAN = 2 };
+enum ErrBits { ERR_PIX = 1, ERR_NAN = 2, ERR_TIMEOUT = 4 };
 
 struct Plan {
   ds_desc desc;
@@ -84,7 +86,9 @@ struct Plan {
   uint8_t* mask;
   double* minv;
   double* bins;
+  float* bins32;      // float32 pixel sums [n_pix][4] for the mixed operator (vector atomics)
   float* map32;
+  float* maplo;       // low parts of the double-float map [n_pix][4] (mixed plans)
   double* map64;
   int32_t* nvalid;
   double *x, *r, *p, *q, *b, *t;
@@ -110,6 +114,14 @@ struct Plan {
   int64_t iterations;
   int64_t timed_iterations;
   double t_bin, t_rescan, t_solve, t_iter;
+  // tuning knobs (destripe_tune)
+  double reliable_delta;    // float64 residual after every 1/delta drop of ||r||
+  int bin_mode;             // mixed binning: 0 = float64 atomics, 1 = float32 vector atomics
+  int graph_iters_cfg;      // CG iterations per captured graph
+  int blocks_per_sm;        // streaming-kernel blocks per SM
+  int accurate_df;          // mixed plans: accurate passes in double-float (1) or float64 (0)
+  int stream_mode;          // mixed operator: 0 = direct vector loads, 1 = TMA-staged pipeline
+  int refresh_max;          // mixed plans: float64 residual at least every this many iterations
 };
 
 // kernels launched by one CG iteration (for the launch counter)
@@ -124,6 +136,15 @@ void launch_bin_y(const Plan& P, cudaStream_t st, const void* y, const double* a
 void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_map, Gate g);
 void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out, Gate g);
 void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g);
+// apply_df.cu: accurate passes of mixed plans in double-float arithmetic
+void launch_bin_df(const Plan& P, cudaStream_t st, const double* x, const float* y, Gate g);
+void launch_pixel_solve_df(const Plan& P, cudaStream_t st, double* out_map, Gate g);
+void launch_rescan_df(const Plan& P, cudaStream_t st, const double* x, const float* y,
+                      double* out, Gate g);
+// apply_tma.cu: mixed operator with TMA-staged pointing streams
+bool tma_supported(const Plan& P);
+void launch_bin_tma(const Plan& P, cudaStream_t st, const double* x, Gate g);
+void launch_rescan_tma(const Plan& P, cudaStream_t st, const double* x, double* out, Gate g);
 // full operator pieces
 void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out, Gate g,
                    cudaEvent_t* ev = nullptr);

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "df.cuh"
 #include "internal.cuh"
 #include "rows.cuh"
 
@@ -21,13 +22,95 @@ __device__ __forceinline__ constexpr int sym_index(int i, int j) {
   return i * NC - i * (i - 1) / 2 + (j - i);
 }
 
+// Entries that are exactly zero (structurally, e.g. I x Q for separate I and q
+// outputs, or the q+u cross term c s - s c) cost no atomic.
 template <int NC>
 __device__ __forceinline__ void flush_m(int32_t* __restrict__ hits, double* __restrict__ mm, int p,
                                         int h, const double (&acc)[NC * (NC + 1) / 2]) {
   constexpr int NM = NC * (NC + 1) / 2;
   atomicAdd(hits + p, h);
 #pragma unroll
-  for (int j = 0; j < NM; ++j) atomicAdd(mm + (int64_t)p * NM + j, acc[j]);
+  for (int j = 0; j < NM; ++j)
+    if (acc[j] != 0.0) atomicAdd(mm + (int64_t)p * NM + j, acc[j]);
+}
+
+template <int NC>
+__device__ __forceinline__ void flush_m_df(int32_t* __restrict__ hits, double* __restrict__ mm,
+                                           int p, int h, const df (&acc)[NC * (NC + 1) / 2]) {
+  constexpr int NM = NC * (NC + 1) / 2;
+  atomicAdd(hits + p, h);
+#pragma unroll
+  for (int j = 0; j < NM; ++j)
+    if (acc[j].hi != 0.f || acc[j].lo != 0.f) atomicAdd(mm + (int64_t)p * NM + j, df_to_double(acc[j]));
+}
+
+// Same as k_plan_accum with the products and run sums in double-float: the
+// entries of w w^T are products of float32 numbers, exact as double-floats, so
+// float64 is only needed for the atomic adds.  Used by mixed-precision plans.
+template <int KS>
+__global__ void __launch_bounds__(256) k_plan_accum_df(const int32_t* __restrict__ pix,
+                                                       const float* __restrict__ cc,
+                                                       const float* __restrict__ ss,
+                                                       const uint8_t* __restrict__ valid,
+                                                       int32_t* __restrict__ hits,
+                                                       double* __restrict__ mm, int64_t n_t,
+                                                       int64_t npix, KindsArg kk,
+                                                       int32_t* __restrict__ err) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO, NM = NC * (NC + 1) / 2;
+  const int n_o = K::n_o(kk);
+  const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    const int64_t t0 = v << 2;
+    df acc[NM];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) acc[j] = df{0.f, 0.f};
+    int cur = -1, h = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t t = t0 + k;
+      if (t >= n_t) break;
+      if (valid != nullptr && valid[t] == 0) continue;
+      const int p = pix[t];
+      if (p < 0 || p >= npix) {
+        atomicOr(err, ERR_PIX);
+        continue;
+      }
+      const float c = cc[t], s = ss[t];
+      df w[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) w[j] = df{0.f, 0.f};
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        if (o < n_o) {
+          float row[NC];
+#pragma unroll
+          for (int j = 0; j < NC; ++j) row[j] = 0.f;
+          row_bin<NC, float>(K::kind(o, kk), c, s, 1.0f, row);
+#pragma unroll
+          for (int i = 0; i < NC; ++i)
+#pragma unroll
+            for (int j = i; j < NC; ++j) {
+              if (row[i] != 0.f && row[j] != 0.f)
+                w[sym_index<NC>(i, j)] = df_add(w[sym_index<NC>(i, j)], two_prod(row[i], row[j]));
+            }
+        }
+      }
+      if (p != cur) {
+        if (cur >= 0) flush_m_df<NC>(hits, mm, cur, h, acc);
+        cur = p;
+        h = 1;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) acc[j] = w[j];
+      } else {
+        h += 1;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) acc[j] = df_add(acc[j], w[j]);
+      }
+    }
+    if (cur >= 0) flush_m_df<NC>(hits, mm, cur, h, acc);
+  }
 }
 
 // hits[p] += 1 and M_p += sum_o w_o w_o^T for every valid sample (float64).
@@ -272,8 +355,12 @@ ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid) {
   const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_plan_accum<KS><<<grid, kBlock, 0, st>>>(d_pix, P.c, P.s, d_valid, P.hits, P.minv, P.n_t,
-                                               P.npix, P.kinds, P.err);
+    if (P.desc.precision == DS_PREC_MIXED && P.accurate_df)
+      k_plan_accum_df<KS><<<grid, kBlock, 0, st>>>(d_pix, P.c, P.s, d_valid, P.hits, P.minv,
+                                                    P.n_t, P.npix, P.kinds, P.err);
+    else
+      k_plan_accum<KS><<<grid, kBlock, 0, st>>>(d_pix, P.c, P.s, d_valid, P.hits, P.minv, P.n_t,
+                                                 P.npix, P.kinds, P.err);
   });
   DS_CUDA_TRY(cudaGetLastError());
   unsigned long long* counts = reinterpret_cast<unsigned long long*>(P.scal);
