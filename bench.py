@@ -139,6 +139,16 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(t_ms, units, dist, device):
+    """Slowest rank's time and the units all ranks processed (replicas, weak scaling)."""
+    import torch
+    tt = torch.tensor([t_ms, units], dtype=torch.float64, device=device)
+    tmax = tt.clone()
+    dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tt[1])
+
+
 def workload(args, device):
     from synth import CONFIGS, WORKLOAD_NAMES, config_problem
     import torch
@@ -304,11 +314,7 @@ def run_ours(args):
     t_ms = ev0.elapsed_time(ev1)
     units = float(prob.n_t) * iters_tot
     if world > 1:
-        tt = torch.tensor([t_ms, units], dtype=torch.float64, device=dev)
-        tmax = tt.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_ms_all, units_all = float(tmax[0]), float(tt[1])
+        t_ms_all, units_all = reduce_over_ranks(t_ms, units, dist, dev)
     else:
         t_ms_all, units_all = t_ms, units
     value = units_all / (t_ms_all / 1e3)
@@ -395,11 +401,7 @@ def e2e_leg(args, prob, ds, world, dist):
     dt = time.perf_counter() - t0
     units = float(prob.n_t) * iters
     if dist is not None:
-        tt = torch.tensor([dt, units], dtype=torch.float64, device=torch.device("cuda"))
-        tmax = tt.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        dt, units = float(tmax[0]), float(tt[1])
+        dt, units = reduce_over_ranks(dt, units, dist, torch.device("cuda"))
     ysz = 4 if args.precision == "mixed" else 8
     h2d = prob.n_t * (4 + 4 + 4 + ysz * prob.n_o + (1 if prob.valid is not None else 0))
     d2h = 8 * prob.n_o * prob.n_b + 8 * n_c * prob.npix + 4 * prob.npix + prob.npix

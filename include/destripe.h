@@ -219,6 +219,46 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  * use the value.  Takes effect at the next call. */
 ds_status destripe_tune(ds_plan_t plan, const char* key, double value);
 
+/* ---- Batched and served solves ---------------------------------------------------
+ * (No counterpart in the paper, which destripes one dataset at a time.)  A batch
+ * advances many independent problems through CG together: every kernel of an
+ * iteration is one launch over the tiles of all problems still running, and a
+ * fixed number of iterations is captured in one CUDA graph that stays valid while
+ * problems are added and retired (continuous batching).  Only DS_PREC_MIXED plans
+ * with the default precision knobs can join, and all problems of a batch must
+ * have the same number of map components.  Each problem's iteration is the
+ * single-problem one (same arithmetic, same float64 residual refreshes and
+ * stopping rule), so its result does not depend on the rest of the batch beyond
+ * float32 summation order.  Work is enqueued on the batch's stream; plans stay
+ * owned by the caller and must outlive their slot.
+ *
+ * destripe_batch_create: room for max_slots (1..4096) problems.
+ * destripe_batch_add:    computes the problem's right-hand side and CG start
+ *     (d_a0: float64 [n_o][n_b] starting guess or NULL) and gives it a slot.
+ *     DS_ESTATE if the batch is full, the plan is already in it, or it cannot join.
+ * destripe_batch_step:   runs CG iterations for every running problem, at least
+ *     min_iters unless all have stopped; *n_running = problems not yet stopped.
+ *     Synchronises the stream.
+ * destripe_batch_slot_status: done flag, iterations, float64 relative residual of a
+ *     slot as of the last step.
+ * destripe_batch_retire: gauge-fixes the slot's baselines, copies them to d_a (may be
+ *     NULL), frees the slot; returns the problem's solve status (DS_OK, DS_ENOCONV, ...).
+ * destripe_batch_tune:   "tile_samples", "tile_unknowns", "blocks_per_sm" (autotuner).
+ * destripe_batch_info:   slots in use and kernels launched so far. */
+typedef struct ds_batch_s* ds_batch_t;
+
+ds_status destripe_batch_create(int32_t max_slots, void* stream, ds_batch_t* out);
+ds_status destripe_batch_add(ds_batch_t batch, ds_plan_t plan, const void* d_y,
+                             const double* d_a0, double tol, int32_t max_iter, int32_t* slot);
+ds_status destripe_batch_step(ds_batch_t batch, int32_t min_iters, int32_t* n_running);
+ds_status destripe_batch_slot_status(ds_batch_t batch, int32_t slot, int32_t* done,
+                                     int32_t* iters, double* rel_resid);
+ds_status destripe_batch_retire(ds_batch_t batch, int32_t slot, double* d_a, int32_t* iters,
+                                double* rel_resid);
+ds_status destripe_batch_tune(ds_batch_t batch, const char* key, double value);
+ds_status destripe_batch_info(ds_batch_t batch, int32_t* n_slots_used, int64_t* kernel_launches);
+void destripe_batch_destroy(ds_batch_t batch);
+
 /* Binned map without any device allocation (no counterpart in the paper: it
  * serves callers that cannot allocate device memory when they need a map, such
  * as processes whose device memory is owned by another allocator and loops that

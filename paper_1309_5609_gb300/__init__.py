@@ -21,7 +21,9 @@ __all__ = [
     "destripe_plan", "destripe_plan_info", "destripe_bin", "destripe_apply_A", "destripe_rhs",
     "destripe_solve", "destripe_map", "destripe_gauge", "destripe_destroy", "destripe_strerror",
     "destripe_run_host", "destripe_profile", "destripe_bin_noalloc", "destripe_tune",
-    "components",
+    "Batch", "destripe_batch_create", "destripe_batch_add", "destripe_batch_step",
+    "destripe_batch_slot_status", "destripe_batch_retire", "destripe_batch_tune",
+    "destripe_batch_info", "destripe_batch_destroy", "components",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -80,6 +82,19 @@ _SIGS = {
     "destripe_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ds_profile)]),
     "destripe_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "destripe_tune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
+    "destripe_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    "destripe_batch_add": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "destripe_batch_step": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "destripe_batch_slot_status": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                                  ctypes.POINTER(ctypes.c_int32),
+                                                  ctypes.POINTER(ctypes.c_double)]),
+    "destripe_batch_retire": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_double)]),
+    "destripe_batch_tune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_double]),
+    "destripe_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int64)]),
+    "destripe_batch_destroy": (None, [_P]),
     "destripe_bin_noalloc": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P, _P, _P,
                                             _P]),
     "destripe_run_host": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P,
@@ -381,3 +396,107 @@ def destripe_run_host(pix, cos2psi, sin2psi, valid, y, *, nside: int, kinds, bas
     if st not in (DS_OK, DS_ENOCONV):
         raise DestripeError(st, "destripe_run_host")
     return st, it.value, rr.value
+
+
+# ---- batched and served solves ---------------------------------------------------------
+
+class Batch:
+    """Handle of a C batch (continuous batching of independent solves)."""
+
+    def __init__(self, handle, max_slots, stream):
+        self.handle = handle
+        self.max_slots = max_slots
+        self.stream = stream
+        self._slots = {}  # slot -> (plan, y, extra refs)
+
+    def close(self):
+        if self.handle:
+            load_library().destripe_batch_destroy(self.handle)
+            self.handle = None
+            self._slots = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def destripe_batch_create(max_slots: int = 64, stream=None) -> Batch:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    h = _P()
+    st = load_library().destripe_batch_create(int(max_slots), stream, ctypes.byref(h))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_batch_create")
+    return Batch(h, max_slots, stream)
+
+
+def destripe_batch_add(batch: Batch, plan: Plan, y, a0=None, tol: float = 1e-10,
+                       max_iter: int = 10000) -> int:
+    import torch
+    _check(y, plan.y_dtype, plan.n_o * plan.n_t, "y", plan.device)
+    if a0 is not None:
+        _check(a0, torch.float64, plan.n_u, "a0", plan.device)
+    slot = ctypes.c_int32(-1)
+    st = load_library().destripe_batch_add(batch.handle, plan.handle, _ptr(y), _ptr(a0),
+                                           float(tol), int(max_iter), ctypes.byref(slot))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_batch_add")
+    batch._slots[slot.value] = (plan, y, a0)
+    return slot.value
+
+
+def destripe_batch_step(batch: Batch, min_iters: int = 1) -> int:
+    """Run at least min_iters CG iterations of every running problem; returns how
+    many problems are still running."""
+    n = ctypes.c_int32(0)
+    st = load_library().destripe_batch_step(batch.handle, int(min_iters), ctypes.byref(n))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_batch_step")
+    return n.value
+
+
+def destripe_batch_slot_status(batch: Batch, slot: int):
+    """(done, iterations, float64 relative residual) of a slot as of the last step."""
+    d, it, rr = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+    st = load_library().destripe_batch_slot_status(batch.handle, int(slot), ctypes.byref(d),
+                                                   ctypes.byref(it), ctypes.byref(rr))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_batch_slot_status")
+    return bool(d.value), it.value, rr.value
+
+
+def destripe_batch_retire(batch: Batch, slot: int, a_out=None):
+    """Gauge-fix and copy out a slot's baselines; frees the slot.  Returns
+    (status, iterations, relative residual); raises on errors other than DS_ENOCONV."""
+    import torch
+    if a_out is not None:
+        plan = batch._slots[slot][0]
+        _check(a_out, torch.float64, plan.n_u, "a_out", plan.device)
+    it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
+    st = load_library().destripe_batch_retire(batch.handle, int(slot), _ptr(a_out),
+                                              ctypes.byref(it), ctypes.byref(rr))
+    if st not in (DS_OK, DS_ENOCONV):
+        raise DestripeError(st, "destripe_batch_retire")
+    batch._slots.pop(slot, None)
+    return st, it.value, rr.value
+
+
+def destripe_batch_tune(batch: Batch, key: str, value: float):
+    st = load_library().destripe_batch_tune(batch.handle, key.encode(), float(value))
+    if st != DS_OK:
+        raise DestripeError(st, f"destripe_batch_tune({key})")
+
+
+def destripe_batch_info(batch: Batch) -> dict:
+    n, l = ctypes.c_int32(0), ctypes.c_int64(0)
+    st = load_library().destripe_batch_info(batch.handle, ctypes.byref(n), ctypes.byref(l))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_batch_info")
+    return {"slots_used": n.value, "kernel_launches": l.value}
+
+
+def destripe_batch_destroy(batch: Batch):
+    batch.close()

@@ -56,7 +56,7 @@ void plan_free(Plan* P) {
     delete[] P->ev;
   }
   void* dev[] = {P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
-                 P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->red,   P->counters,
+                 P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   for (void* d : dev)
     if (d) cudaFree(d);
@@ -217,6 +217,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   DS_ALLOC(q, P->n_u);
   DS_ALLOC(b, P->n_u);
   DS_ALLOC(t, P->n_u);
+  if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(x_best, P->n_u);
   DS_ALLOC(red, P->red_len);
   DS_ALLOC(counters, 8);
   DS_ALLOC(state, 1);
@@ -363,22 +364,29 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
     P.iterations += ran;
     collect_times(P, ran);
   }
-  enqueue_gauge(P, st, P.x);
-  P.launches += 2;
-  DS_CUDA_TRY(cudaMemcpyAsync(d_a, P.x, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
   DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
   DS_CUDA_TRY(cudaMemcpyAsync(P.h_err, P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DS_CUDA_TRY(cudaStreamSynchronize(st));
   if (*P.h_err & ERR_TIMEOUT) return DS_ETIMEOUT;
-  const CgState& H = *P.h_state;
+  const CgState H = *P.h_state;
+  // Mixed plans that did not converge return the iterate with the smallest
+  // float64 residual seen (a float32 operator can drift on ill-posed problems).
+  const bool use_best = P.x_best != nullptr && H.status != 1 && !(H.rr_true <= H.rr_best);
+  double* result = use_best ? P.x_best : P.x;
+  enqueue_gauge(P, st, result);
+  P.launches += 2;
+  DS_CUDA_TRY(cudaMemcpyAsync(d_a, result, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
+  DS_CUDA_TRY(cudaStreamSynchronize(st));
+  const double rr_out = use_best ? H.rr_best : H.rr_true;
   if (iters) *iters = H.iter;
-  if (rel_resid) *rel_resid = H.bb > 0.0 ? std::sqrt(H.rr_true / H.bb) : 0.0;
+  if (rel_resid) *rel_resid = H.bb > 0.0 ? std::sqrt(rr_out / H.bb) : 0.0;
+  if (!std::isfinite(H.bb)) return DS_ENAN;
   if (!done) return DS_ENOCONV;
   switch (H.status) {
     case 1: return DS_OK;
     case 2: return DS_ENOCONV;
     case 3: return H.rr_true <= H.tol2 ? DS_OK : DS_ENOCONV;
-    default: return DS_ENAN;
+    default: return P.x_best != nullptr ? DS_ENOCONV : DS_ENAN;
   }
 }
 

@@ -1,0 +1,1060 @@
+// Batched destriping: many independent problems (plans) advance through CG
+// together, each kernel of an iteration being one launch over the tiles of
+// every active problem, and K iterations captured in one CUDA graph.
+//
+// A batch holds up to max_slots problems.  Adding a problem computes its
+// right-hand side and CG start on the batch's stream; a step replays the graph;
+// a problem that has converged is skipped tile by tile (its state says done) and
+// is retired by the caller, who gets its gauge-fixed baselines.  The device-side
+// slot table and tile work lists live at fixed addresses, so the graph stays
+// valid while problems come and go (continuous batching); it is re-captured only
+// when a work list has to grow.
+//
+// Per problem the iteration is exactly the single-problem mixed-precision one:
+// float32 operator (vector atomics into float32 pixel sums), float64 CG vectors
+// and scalars, double-float residual refreshes gated per problem.  Per-problem
+// dot products are deterministic: every tile writes its partial and the last
+// tile of the problem (ticket counter) adds them in tile order.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "df.cuh"
+#include "internal.cuh"
+#include "rows.cuh"
+#include "stream_common.cuh"
+#include "stream_df.cuh"
+
+namespace ds {
+void enqueue_gauge(const Plan& P, cudaStream_t st, double* a);
+void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, double delta,
+                      int warm);
+}  // namespace ds
+
+namespace ds {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kGraphIters = 8;
+
+struct SlotDesc {
+  const int32_t* pix;
+  const float* c;
+  const float* s;
+  float* bins32;
+  double* bins;
+  float* map32;
+  float* maplo;
+  const double* minv;
+  const uint8_t* mask;
+  double *x, *r, *p, *q, *b, *t, *x_best;
+  CgState* state;
+  int64_t n_t, L, n_b, n_u, npix;
+  KindsArg kinds;
+  int active;
+  int u_first, u_count;  // this slot's tiles in the unknown work list
+};
+
+struct WorkTile {
+  int slot;
+  int pad;
+  int64_t begin, end;  // [begin, end) in 4-sample vectors, pixels or unknowns
+};
+
+enum { W_SAMPLES = 0, W_PIXELS = 1, W_UNKNOWNS = 2 };
+
+// problem still iterating
+__device__ __forceinline__ bool slot_live(const SlotDesc& S) {
+  return S.active && !(*(volatile const int*)&S.state->done);
+}
+// ... with the float32 operator
+__device__ __forceinline__ bool slot_f32(const SlotDesc& S) {
+  return slot_live(S) && !(*(volatile const int*)&S.state->accurate);
+}
+// double-float passes: MODE 0 = residual refresh (x -> t), 1 = operator (p -> q)
+template <int MODE>
+__device__ __forceinline__ bool slot_df(const SlotDesc& S) {
+  if (!slot_live(S)) return false;
+  return MODE == 0 ? (*(volatile const int*)&S.state->need) != 0
+                   : (*(volatile const int*)&S.state->accurate) != 0;
+}
+
+// ---- operator kernels (mixed precision: float32 per-sample work) ---------------
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_bb_bin(const SlotDesc* __restrict__ slots,
+                                                   const WorkTile* __restrict__ tiles,
+                                                   const int* __restrict__ ntiles) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int nt = ntiles[W_SAMPLES];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    if (!slot_f32(slots[T.slot])) continue;
+    const SlotDesc S = slots[T.slot];  // registers: asm memory clobbers force reloads otherwise
+    const int n_o = K::n_o(S.kinds);
+    const int64_t n_t = S.n_t, L = S.L, n_b = S.n_b;
+    for (int64_t v = T.begin + threadIdx.x; v < T.end; v += blockDim.x) {
+      int p[4];
+      float c[4], s[4];
+      load4(S.pix, S.c, S.s, v, n_t, p, c, s);
+      const int64_t t0 = v << 2;
+      int64_t b = t0 / L, bend = (b + 1) * L;
+      float zb[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? (float)S.p[o * n_b + b] : 0.f;
+      float acc[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+      int cur = -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t t = t0 + k;
+        if (t >= n_t) break;
+        if (t >= bend) {
+          b += 1;
+          bend += L;
+#pragma unroll
+          for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? (float)S.p[o * n_b + b] : 0.f;
+        }
+        if (p[k] < 0) continue;
+        float w[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) w[j] = 0.f;
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o) row_bin<NC, float>(K::kind(o, S.kinds), c[k], s[k], zb[o], w);
+        if (p[k] != cur) {
+          if (cur >= 0) flush_bins<NC, float>(S.bins32, cur, acc);
+          cur = p[k];
+#pragma unroll
+          for (int j = 0; j < NC; ++j) acc[j] = w[j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) acc[j] += w[j];
+        }
+      }
+      if (cur >= 0) flush_bins<NC, float>(S.bins32, cur, acc);
+    }
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_bb_pixel_solve(const SlotDesc* __restrict__ slots,
+                                                           const WorkTile* __restrict__ tiles,
+                                                           const int* __restrict__ ntiles) {
+  constexpr int NM = NC * (NC + 1) / 2;
+  const int nt = ntiles[W_PIXELS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    const SlotDesc& S = slots[T.slot];
+    if (!slot_f32(S)) continue;
+    for (int64_t p = T.begin + threadIdx.x; p < T.end; p += blockDim.x) {
+      const float4 v = reinterpret_cast<const float4*>(S.bins32)[p];
+      reinterpret_cast<float4*>(S.bins32)[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const double sv[4] = {v.x, v.y, v.z, v.w};
+      double s[NC], m[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) s[j] = sv[j];
+      if (S.mask[p]) {
+        double mi[NM];
+#pragma unroll
+        for (int j = 0; j < NM; ++j) mi[j] = S.minv[p * NM + j];
+        sym_mul<NC>(mi, s, m);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) m[j] = 0.0;
+      }
+      float o4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < NC; ++j) o4[j] = (float)m[j];
+      reinterpret_cast<float4*>(S.map32)[p] = make_float4(o4[0], o4[1], o4[2], o4[3]);
+    }
+  }
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_bb_rescan(const SlotDesc* __restrict__ slots,
+                                                      const WorkTile* __restrict__ tiles,
+                                                      const int* __restrict__ ntiles) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int nt = ntiles[W_SAMPLES];
+  const int lane = threadIdx.x & 31;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    if (!slot_f32(slots[T.slot])) continue;
+    const SlotDesc S = slots[T.slot];
+    const int n_o = K::n_o(S.kinds);
+    const int64_t n_t = S.n_t, L = S.L, n_b = S.n_b;
+    for (int64_t vb = T.begin + threadIdx.x - lane; vb < T.end; vb += blockDim.x) {
+      const int64_t v = vb + lane;
+      int key = -1;
+      float acc[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) acc[o] = 0.f;
+      if (v < T.end) {
+        int p[4];
+        float c[4], s[4];
+        load4(S.pix, S.c, S.s, v, n_t, p, c, s);
+        float m[4][NC];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (p[k] >= 0) {
+            load_map<NC, float>(S.map32, p[k], m[k]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) m[k][j] = 0.f;
+          }
+        }
+        const int64_t t0 = v << 2;
+        int64_t b = t0 / L, bend = (b + 1) * L;
+        float zb[NO];
+#pragma unroll
+        for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? (float)S.p[o * n_b + b] : 0.f;
+        key = (int)b;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t t = t0 + k;
+          if (t >= n_t) break;
+          if (t >= bend) {
+#pragma unroll
+            for (int o = 0; o < NO; ++o) {
+              if (o < n_o && acc[o] != 0.f) atomicAdd(S.q + o * n_b + b, (double)acc[o]);
+              acc[o] = 0.f;
+            }
+            b += 1;
+            bend += L;
+            key = (int)b;
+#pragma unroll
+            for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? (float)S.p[o * n_b + b] : 0.f;
+          }
+          if (p[k] < 0) continue;
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+            if (o < n_o) acc[o] += zb[o] - row_dot<NC, float>(K::kind(o, S.kinds), c[k], s[k], m[k]);
+        }
+      }
+      warp_segment_flush<NO, float>(key, acc, n_o, S.q, n_b);
+    }
+  }
+}
+
+// ---- double-float residual refresh, gated per problem -----------------------------
+
+template <int KS, int MODE>
+__global__ void __launch_bounds__(kBlock) k_bb_bin_df(const SlotDesc* __restrict__ slots,
+                                                      const WorkTile* __restrict__ tiles,
+                                                      const int* __restrict__ ntiles) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int nt = ntiles[W_SAMPLES];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    if (!slot_df<MODE>(slots[T.slot])) continue;
+    const SlotDesc S = slots[T.slot];
+    const double* __restrict__ src = MODE == 0 ? S.x : S.p;
+    const int n_o = K::n_o(S.kinds);
+    const int64_t n_t = S.n_t, L = S.L, n_b = S.n_b;
+    for (int64_t v = T.begin + threadIdx.x; v < T.end; v += blockDim.x) {
+      int p[4];
+      float c[4], s[4];
+      load4_df(S.pix, S.c, S.s, v, n_t, p, c, s);
+      const int64_t t0 = v << 2;
+      int64_t b = t0 / L, bend = (b + 1) * L;
+      df zb[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        zb[o] = o < n_o ? df_from_double(src[o * n_b + b]) : df{0.f, 0.f};
+      df acc[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] = df{0.f, 0.f};
+      int cur = -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t t = t0 + k;
+        if (t >= n_t) break;
+        if (t >= bend) {
+          b += 1;
+          bend += L;
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+            zb[o] = o < n_o ? df_from_double(src[o * n_b + b]) : df{0.f, 0.f};
+        }
+        if (p[k] < 0) continue;
+        df w[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) w[j] = df{0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o) row_bin_df<NC>(K::kind(o, S.kinds), c[k], s[k], zb[o], w);
+        if (p[k] != cur) {
+          if (cur >= 0) flush_bins_df<NC>(S.bins, cur, acc);
+          cur = p[k];
+#pragma unroll
+          for (int j = 0; j < NC; ++j) acc[j] = w[j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) acc[j] = df_add(acc[j], w[j]);
+        }
+      }
+      if (cur >= 0) flush_bins_df<NC>(S.bins, cur, acc);
+    }
+  }
+}
+
+template <int NC, int MODE>
+__global__ void __launch_bounds__(kBlock) k_bb_pixel_solve_df(const SlotDesc* __restrict__ slots,
+                                                              const WorkTile* __restrict__ tiles,
+                                                              const int* __restrict__ ntiles) {
+  constexpr int NM = NC * (NC + 1) / 2;
+  const int nt = ntiles[W_PIXELS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    const SlotDesc& S = slots[T.slot];
+    if (!slot_df<MODE>(S)) continue;
+    for (int64_t p = T.begin + threadIdx.x; p < T.end; p += blockDim.x) {
+      double s[NC], m[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        s[j] = S.bins[4 * p + j];
+        S.bins[4 * p + j] = 0.0;
+      }
+      if (S.mask[p]) {
+        double mi[NM];
+#pragma unroll
+        for (int j = 0; j < NM; ++j) mi[j] = S.minv[p * NM + j];
+        sym_mul<NC>(mi, s, m);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) m[j] = 0.0;
+      }
+      float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const df d = df_from_double(m[j]);
+        hi[j] = d.hi;
+        lo[j] = d.lo;
+      }
+      reinterpret_cast<float4*>(S.map32)[p] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      reinterpret_cast<float4*>(S.maplo)[p] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    }
+  }
+}
+
+template <int KS, int MODE>
+__global__ void __launch_bounds__(kBlock) k_bb_rescan_df(const SlotDesc* __restrict__ slots,
+                                                         const WorkTile* __restrict__ tiles,
+                                                         const int* __restrict__ ntiles) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int nt = ntiles[W_SAMPLES];
+  const int lane = threadIdx.x & 31;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    if (!slot_df<MODE>(slots[T.slot])) continue;
+    const SlotDesc S = slots[T.slot];
+    const double* __restrict__ src = MODE == 0 ? S.x : S.p;
+    double* __restrict__ dst = MODE == 0 ? S.t : S.q;
+    const int n_o = K::n_o(S.kinds);
+    const int64_t n_t = S.n_t, L = S.L, n_b = S.n_b;
+    for (int64_t vb = T.begin + threadIdx.x - lane; vb < T.end; vb += blockDim.x) {
+      const int64_t v = vb + lane;
+      int key = -1;
+      df acc[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) acc[o] = df{0.f, 0.f};
+      if (v < T.end) {
+        int p[4];
+        float c[4], s[4];
+        load4_df(S.pix, S.c, S.s, v, n_t, p, c, s);
+        df m[4][NC];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (p[k] >= 0) {
+            const float4 h = __ldg(reinterpret_cast<const float4*>(S.map32) + p[k]);
+            const float4 l = __ldg(reinterpret_cast<const float4*>(S.maplo) + p[k]);
+            const float hh[4] = {h.x, h.y, h.z, h.w}, ll[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+            for (int j = 0; j < NC; ++j) m[k][j] = df{hh[j], ll[j]};
+          } else {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) m[k][j] = df{0.f, 0.f};
+          }
+        }
+        const int64_t t0 = v << 2;
+        int64_t b = t0 / L, bend = (b + 1) * L;
+        df zb[NO];
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          zb[o] = o < n_o ? df_from_double(src[o * n_b + b]) : df{0.f, 0.f};
+        key = (int)b;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t t = t0 + k;
+          if (t >= n_t) break;
+          if (t >= bend) {
+#pragma unroll
+            for (int o = 0; o < NO; ++o) {
+              if (o < n_o && (acc[o].hi != 0.f || acc[o].lo != 0.f))
+                atomicAdd(dst + o * n_b + b, df_to_double(acc[o]));
+              acc[o] = df{0.f, 0.f};
+            }
+            b += 1;
+            bend += L;
+            key = (int)b;
+#pragma unroll
+            for (int o = 0; o < NO; ++o)
+              zb[o] = o < n_o ? df_from_double(src[o * n_b + b]) : df{0.f, 0.f};
+          }
+          if (p[k] < 0) continue;
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+            if (o < n_o)
+              acc[o] = df_add(acc[o], df_sub(zb[o], row_dot_df<NC>(K::kind(o, S.kinds), c[k], s[k], m[k])));
+        }
+      }
+      warp_segment_flush_df<NO>(key, acc, n_o, dst, n_b);
+    }
+  }
+}
+
+// ---- per-problem CG vector kernels ------------------------------------------------
+
+__device__ __forceinline__ double bb_block_sum(double v) {
+  __shared__ double sm[32];
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  v = 0.0;
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0.0;
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  }
+  __syncthreads();
+  return v;
+}
+
+// The block holding tile ti of slot S publishes its partial; returns true (in
+// thread 0) when it was the slot's last tile, with the slot total in *total.
+__device__ bool bb_finish(double partial, int ti, const SlotDesc& S, double* __restrict__ red,
+                          unsigned* __restrict__ ticket, double* total) {
+  __shared__ bool last;
+  const double bs = bb_block_sum(partial);
+  if (threadIdx.x == 0) {
+    red[ti] = bs;
+    __threadfence();
+    const unsigned k = atomicAdd(ticket, 1u);
+    last = (k == (unsigned)S.u_count - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < S.u_count; i += blockDim.x) v += ((volatile double*)red)[S.u_first + i];
+  v = bb_block_sum(v);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    *total = v;
+    return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kBlock) k_bb_alpha(const SlotDesc* __restrict__ slots,
+                                                     const WorkTile* __restrict__ tiles,
+                                                     const int* __restrict__ ntiles,
+                                                     double* __restrict__ red,
+                                                     unsigned* __restrict__ tickets) {
+  const int nt = ntiles[W_UNKNOWNS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    const SlotDesc& S = slots[T.slot];
+    if (!slot_live(S)) continue;
+    double acc = 0.0;
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) acc += S.p[i] * S.q[i];
+    double tot;
+    if (bb_finish(acc, ti, S, red, tickets + 4 * T.slot + 0, &tot)) {
+      CgState* st = S.state;
+      st->pq = tot;
+      st->improved = 0;
+      if (!isfinite(tot)) {
+        st->status = 4;
+        st->done = 1;
+      } else if (!(tot > 0.0)) {
+        st->status = 3;
+        st->done = 1;
+      } else {
+        st->alpha = st->rr / tot;
+        if (!isfinite(st->alpha)) {
+          st->status = 4;
+          st->done = 1;
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bb_update(const SlotDesc* __restrict__ slots,
+                                                      const WorkTile* __restrict__ tiles,
+                                                      const int* __restrict__ ntiles,
+                                                      double* __restrict__ red,
+                                                      unsigned* __restrict__ tickets) {
+  const int nt = ntiles[W_UNKNOWNS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    const SlotDesc& S = slots[T.slot];
+    if (!slot_live(S)) continue;
+    const double alpha = S.state->alpha;
+    double acc = 0.0;
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
+      S.x[i] += alpha * S.p[i];
+      const double ri = S.r[i] - alpha * S.q[i];
+      S.r[i] = ri;
+      acc += ri * ri;
+    }
+    double tot;
+    if (bb_finish(acc, ti, S, red, tickets + 4 * T.slot + 1, &tot)) {
+      CgState* st = S.state;
+      st->rr_old = st->rr;
+      st->rr = tot;
+      st->iter += 1;
+      if (!isfinite(tot)) {
+        st->status = 4;
+        st->done = 1;
+      } else {
+        const bool conv = tot <= st->tol2;
+        if (conv || tot < st->delta2 * st->rr_anchor || st->iter >= st->max_iter ||
+            st->iter - st->last_refresh >= st->refresh_max)
+          st->need = 1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bb_reliable(const SlotDesc* __restrict__ slots,
+                                                        const WorkTile* __restrict__ tiles,
+                                                        const int* __restrict__ ntiles,
+                                                        double* __restrict__ red,
+                                                        unsigned* __restrict__ tickets) {
+  const int nt = ntiles[W_UNKNOWNS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    const SlotDesc& S = slots[T.slot];
+    if (!slot_df<0>(S)) continue;
+    double acc = 0.0;
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
+      const double ri = S.b[i] - S.t[i];
+      S.r[i] = ri;
+      S.t[i] = 0.0;
+      acc += ri * ri;
+    }
+    double tot;
+    if (bb_finish(acc, ti, S, red, tickets + 4 * T.slot + 2, &tot)) {
+      CgState* st = S.state;
+      if (!st->accurate && tot > 1e4 * st->rr) st->accurate = 1;  // float32 drift: switch
+      if (tot < st->rr_best) {
+        st->rr_best = tot;
+        st->improved = 1;
+      }
+      st->rr = tot;
+      st->rr_anchor = tot;
+      st->rr_true = tot;
+      st->n_reliable += 1;
+      st->last_refresh = st->iter;
+      st->need = 0;
+      if (!isfinite(tot)) {
+        st->status = 4;
+        st->done = 1;
+      } else if (tot <= st->tol2) {
+        st->status = 1;
+        st->done = 1;
+      } else if (st->iter >= st->max_iter) {
+        st->status = 2;
+        st->done = 1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bb_keep_best(const SlotDesc* __restrict__ slots,
+                                                         const WorkTile* __restrict__ tiles,
+                                                         const int* __restrict__ ntiles) {
+  const int nt = ntiles[W_UNKNOWNS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    const SlotDesc& S = slots[T.slot];
+    if (!S.active || !(*(volatile const int*)&S.state->improved)) continue;
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) S.x_best[i] = S.x[i];
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bb_direction(const SlotDesc* __restrict__ slots,
+                                                         const WorkTile* __restrict__ tiles,
+                                                         const int* __restrict__ ntiles) {
+  const int nt = ntiles[W_UNKNOWNS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    const SlotDesc& S = slots[T.slot];
+    if (!slot_live(S)) continue;
+    const double beta = S.state->rr / S.state->rr_old;
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
+      S.p[i] = S.r[i] + beta * S.p[i];
+      S.q[i] = 0.0;
+    }
+  }
+}
+
+__global__ void k_bb_gather_states(const SlotDesc* __restrict__ slots, int n,
+                                   CgState* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && slots[i].active) out[i] = *slots[i].state;
+}
+
+}  // namespace
+}  // namespace ds
+
+using namespace ds;
+
+struct ds_batch_s {
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int max_slots = 0;
+  int num_sms = 0;
+  int nc = 0;
+  std::vector<Plan*> plans;
+  std::vector<char> stopped;     // slot's problem has stopped (as of the last step)
+  SlotDesc* h_slots = nullptr;
+  SlotDesc* d_slots = nullptr;
+  WorkTile* h_tiles[3] = {nullptr, nullptr, nullptr};
+  WorkTile* d_tiles[3] = {nullptr, nullptr, nullptr};
+  int cap[3] = {0, 0, 0};
+  int* h_ntiles = nullptr;
+  int* d_ntiles = nullptr;
+  double* d_red = nullptr;
+  int red_cap = 0;
+  unsigned* d_tickets = nullptr;
+  CgState* d_states = nullptr;
+  CgState* h_states = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_ks = -1;  // kind set the graph was captured for
+  bool dirty = true;
+  int64_t tile_vecs = 16384;     // 4-sample vectors per sample tile (65536 samples)
+  int64_t tile_pixels = 65536;
+  int64_t tile_unknowns = 32768;
+  int blocks_per_sm = 8;
+  int64_t launches = 0;
+};
+
+namespace {
+
+void batch_free(ds_batch_t B) {
+  if (B == nullptr) return;
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  if (B->d_slots) cudaFree(B->d_slots);
+  if (B->h_slots) cudaFreeHost(B->h_slots);
+  for (int w = 0; w < 3; ++w) {
+    if (B->d_tiles[w]) cudaFree(B->d_tiles[w]);
+    if (B->h_tiles[w]) cudaFreeHost(B->h_tiles[w]);
+  }
+  if (B->h_ntiles) cudaFreeHost(B->h_ntiles);
+  if (B->d_ntiles) cudaFree(B->d_ntiles);
+  if (B->d_red) cudaFree(B->d_red);
+  if (B->d_tickets) cudaFree(B->d_tickets);
+  if (B->d_states) cudaFree(B->d_states);
+  if (B->h_states) cudaFreeHost(B->h_states);
+  if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+  delete B;
+}
+
+// Grows the host and device arrays of work list w to hold n tiles.
+ds_status ensure_tiles(ds_batch_t B, int w, int n) {
+  if (n <= B->cap[w]) return DS_OK;
+  int cap = B->cap[w] > 0 ? B->cap[w] : 1024;
+  while (cap < n) cap *= 2;
+  WorkTile *h = nullptr, *d = nullptr;
+  if (cudaMallocHost(reinterpret_cast<void**>(&h), sizeof(WorkTile) * cap) != cudaSuccess)
+    return DS_ENOMEM;
+  if (cudaMalloc(reinterpret_cast<void**>(&d), sizeof(WorkTile) * cap) != cudaSuccess) {
+    cudaFreeHost(h);
+    return DS_ENOMEM;
+  }
+  // the previous device array may still be read by queued work
+  cudaStreamSynchronize(B->stream);
+  if (B->h_tiles[w]) cudaFreeHost(B->h_tiles[w]);
+  if (B->d_tiles[w]) cudaFree(B->d_tiles[w]);
+  B->h_tiles[w] = h;
+  B->d_tiles[w] = d;
+  B->cap[w] = cap;
+  if (w == W_UNKNOWNS) {
+    if (B->d_red) cudaFree(B->d_red);
+    if (cudaMalloc(reinterpret_cast<void**>(&B->d_red), sizeof(double) * cap) != cudaSuccess)
+      return DS_ENOMEM;
+    B->red_cap = cap;
+  }
+  if (B->graph) {  // device arrays moved: the captured graph is stale
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  return DS_OK;
+}
+
+// Rebuilds the three work lists from the slots whose problems are still running
+// (stopped problems drop out, so the kernels only walk live tiles).
+ds_status rebuild_tiles(ds_batch_t B) {
+  int n[3] = {0, 0, 0};
+  for (int sl = 0; sl < B->max_slots; ++sl) {
+    const Plan* P = B->plans[sl];
+    if (!P || B->stopped[sl]) continue;
+    const int64_t nvec = (P->n_t + 3) / 4;
+    n[W_SAMPLES] += (int)((nvec + B->tile_vecs - 1) / B->tile_vecs);
+    n[W_PIXELS] += (int)((P->npix + B->tile_pixels - 1) / B->tile_pixels);
+    n[W_UNKNOWNS] += (int)((P->n_u + B->tile_unknowns - 1) / B->tile_unknowns);
+  }
+  for (int w = 0; w < 3; ++w) {
+    ds_status s = ensure_tiles(B, w, n[w] > 0 ? n[w] : 1);
+    if (s != DS_OK) return s;
+  }
+  int k[3] = {0, 0, 0};
+  for (int sl = 0; sl < B->max_slots; ++sl) {
+    const Plan* P = B->plans[sl];
+    if (!P || B->stopped[sl]) continue;
+    const int64_t nvec = (P->n_t + 3) / 4;
+    for (int64_t b = 0; b < nvec; b += B->tile_vecs)
+      B->h_tiles[W_SAMPLES][k[W_SAMPLES]++] = WorkTile{sl, 0, b, b + B->tile_vecs < nvec ? b + B->tile_vecs : nvec};
+    for (int64_t b = 0; b < P->npix; b += B->tile_pixels)
+      B->h_tiles[W_PIXELS][k[W_PIXELS]++] = WorkTile{sl, 0, b, b + B->tile_pixels < P->npix ? b + B->tile_pixels : P->npix};
+    B->h_slots[sl].u_first = k[W_UNKNOWNS];
+    for (int64_t b = 0; b < P->n_u; b += B->tile_unknowns)
+      B->h_tiles[W_UNKNOWNS][k[W_UNKNOWNS]++] = WorkTile{sl, 0, b, b + B->tile_unknowns < P->n_u ? b + B->tile_unknowns : P->n_u};
+    B->h_slots[sl].u_count = k[W_UNKNOWNS] - B->h_slots[sl].u_first;
+  }
+  for (int w = 0; w < 3; ++w) B->h_ntiles[w] = k[w];
+  B->dirty = true;
+  return DS_OK;
+}
+
+template <typename F>
+void with_kindset(int ks, F&& f) {
+  switch (ks) {
+    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
+    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
+    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
+    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
+    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
+    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
+    default: f(std::integral_constant<int, KS_GEN3>{}); break;
+  }
+}
+
+// kind set of the batch: the common one when every problem has the same kinds,
+// else the generic set of its component count (kinds read per problem)
+int batch_kindset(ds_batch_t B);
+
+void enqueue_batch_iteration(ds_batch_t B, cudaStream_t st) {
+  const int sgrid = B->num_sms * B->blocks_per_sm;
+  const int ugrid = B->num_sms * 4;
+  const SlotDesc* sl = B->d_slots;
+  const int* nt = B->d_ntiles;
+  with_kindset(batch_kindset(B), [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    constexpr int NC = KSet<KS>::NC;
+    // float32 operator for problems that have not switched to the accurate one
+    k_bb_bin<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
+    k_bb_pixel_solve<NC><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_PIXELS], nt);
+    k_bb_rescan<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
+    // double-float operator for those that have
+    k_bb_bin_df<KS, 1><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
+    k_bb_pixel_solve_df<NC, 1><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_PIXELS], nt);
+    k_bb_rescan_df<KS, 1><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
+    k_bb_alpha<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt, B->d_red, B->d_tickets);
+    k_bb_update<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt, B->d_red, B->d_tickets);
+    // double-float residual refresh
+    k_bb_bin_df<KS, 0><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
+    k_bb_pixel_solve_df<NC, 0><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_PIXELS], nt);
+    k_bb_rescan_df<KS, 0><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
+    k_bb_reliable<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt, B->d_red, B->d_tickets);
+    k_bb_keep_best<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt);
+    k_bb_direction<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt);
+  });
+}
+
+ds_status batch_upload(ds_batch_t B) {
+  if (!B->dirty) return DS_OK;
+  cudaStream_t st = B->stream;
+  DS_CUDA_TRY(cudaMemcpyAsync(B->d_slots, B->h_slots, sizeof(SlotDesc) * B->max_slots,
+                              cudaMemcpyHostToDevice, st));
+  for (int w = 0; w < 3; ++w)
+    if (B->h_ntiles[w] > 0)
+      DS_CUDA_TRY(cudaMemcpyAsync(B->d_tiles[w], B->h_tiles[w], sizeof(WorkTile) * B->h_ntiles[w],
+                                  cudaMemcpyHostToDevice, st));
+  DS_CUDA_TRY(cudaMemcpyAsync(B->d_ntiles, B->h_ntiles, sizeof(int) * 4, cudaMemcpyHostToDevice, st));
+  B->dirty = false;
+  return DS_OK;
+}
+
+int batch_kindset(ds_batch_t B) {
+  int ks = -1;
+  for (int i = 0; i < B->max_slots; ++i) {
+    const Plan* P = B->plans[i];
+    if (!P) continue;
+    if (ks == -1) ks = P->kindset;
+    else if (ks != P->kindset) ks = -2;
+  }
+  if (ks >= 0) return ks;
+  return B->nc == 1 ? KS_GEN1 : (B->nc == 2 ? KS_GEN2 : KS_GEN3);
+}
+
+ds_status batch_graph(ds_batch_t B) {
+  if (B->graph && B->graph_ks == batch_kindset(B)) return DS_OK;
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  B->graph_ks = batch_kindset(B);
+  cudaGraph_t g = nullptr;
+  DS_CUDA_TRY(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < kGraphIters; ++k) enqueue_batch_iteration(B, B->cap_stream);
+  if (cudaStreamEndCapture(B->cap_stream, &g) != cudaSuccess) return DS_ECUDA;
+  const cudaError_t e = cudaGraphInstantiate(&B->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    B->graph = nullptr;
+    return DS_ECUDA;
+  }
+  return DS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ds_status destripe_batch_create(int32_t max_slots, void* stream, ds_batch_t* out) {
+  if (out == nullptr || max_slots < 1 || max_slots > 4096) return DS_EINVAL;
+  *out = nullptr;
+  ds_batch_t B = new (std::nothrow) ds_batch_s();
+  if (B == nullptr) return DS_ENOMEM;
+  B->stream = static_cast<cudaStream_t>(stream);
+  B->max_slots = max_slots;
+  B->plans.assign(max_slots, nullptr);
+  B->stopped.assign(max_slots, 0);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&B->h_slots), sizeof(SlotDesc) * max_slots);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&B->d_slots), sizeof(SlotDesc) * max_slots);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&B->h_ntiles), sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&B->d_ntiles), sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&B->d_tickets), sizeof(unsigned) * 4 * max_slots);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&B->d_states), sizeof(CgState) * max_slots);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&B->h_states), sizeof(CgState) * max_slots);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    batch_free(B);
+    return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
+  }
+  std::memset(B->h_slots, 0, sizeof(SlotDesc) * max_slots);
+  std::memset(B->h_ntiles, 0, sizeof(int) * 4);
+  std::memset(B->h_states, 0, sizeof(CgState) * max_slots);
+  e = cudaMemsetAsync(B->d_tickets, 0, sizeof(unsigned) * 4 * max_slots, B->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_slots, 0, sizeof(SlotDesc) * max_slots, B->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_ntiles, 0, sizeof(int) * 4, B->stream);
+  if (e != cudaSuccess) {
+    batch_free(B);
+    return DS_ECUDA;
+  }
+  for (int w = 0; w < 3; ++w) {
+    ds_status s = ensure_tiles(B, w, 1024);
+    if (s != DS_OK) {
+      batch_free(B);
+      return s;
+    }
+  }
+  *out = B;
+  return DS_OK;
+}
+
+void destripe_batch_destroy(ds_batch_t B) {
+  if (B == nullptr) return;
+  cudaStreamSynchronize(B->stream);
+  batch_free(B);
+}
+
+ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, const double* d_a0,
+                             double tol, int32_t max_iter, int32_t* slot_out) {
+  if (B == nullptr || plan == nullptr || d_y == nullptr || slot_out == nullptr) return DS_EINVAL;
+  if (!(tol >= 0.0)) return DS_EINVAL;
+  Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (P.desc.precision != DS_PREC_MIXED || P.bins32 == nullptr || P.maplo == nullptr ||
+      !P.accurate_df || P.bin_mode != 1)
+    return DS_ESTATE;
+  if (B->nc != 0 && B->nc != P.n_c) return DS_ESTATE;
+  int sl = -1;
+  for (int i = 0; i < B->max_slots; ++i) {
+    if (B->plans[i] == &P) return DS_ESTATE;  // already in the batch
+    if (sl < 0 && B->plans[i] == nullptr) sl = i;
+  }
+  if (sl < 0) return DS_ESTATE;  // no free slot
+  if (max_iter <= 0) max_iter = 10000;
+  cudaStream_t st = B->stream;
+  (void)cudaGetLastError();
+  if (d_a0)
+    DS_CUDA_TRY(cudaMemcpyAsync(P.x, d_a0, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
+  DS_CUDA_TRY(cudaMemsetAsync(P.b, 0, sizeof(double) * P.n_u, st));
+  enqueue_rhs(P, st, d_y, P.b, Gate{nullptr, nullptr});
+  enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, d_a0 ? 1 : 0);
+  if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
+  B->launches += 6 + (d_a0 ? 3 : 0);
+  B->nc = P.n_c;
+  B->plans[sl] = &P;
+  B->stopped[sl] = 0;
+  std::memset(&B->h_states[sl], 0, sizeof(CgState));  // no stale status before the first step
+  SlotDesc& S = B->h_slots[sl];
+  S.pix = P.pix;
+  S.c = P.c;
+  S.s = P.s;
+  S.bins32 = P.bins32;
+  S.bins = P.bins;
+  S.map32 = P.map32;
+  S.maplo = P.maplo;
+  S.minv = P.minv;
+  S.mask = P.mask;
+  S.x = P.x; S.r = P.r; S.p = P.p; S.q = P.q; S.b = P.b; S.t = P.t; S.x_best = P.x_best;
+  S.state = P.state;
+  S.n_t = P.n_t; S.L = P.L; S.n_b = P.n_b; S.n_u = P.n_u; S.npix = P.npix;
+  S.kinds = P.kinds;
+  S.active = 1;
+  ds_status s = rebuild_tiles(B);
+  if (s != DS_OK) {
+    B->plans[sl] = nullptr;
+    S.active = 0;
+    return s;
+  }
+  *slot_out = sl;
+  return DS_OK;
+}
+
+ds_status destripe_batch_step(ds_batch_t B, int32_t min_iters, int32_t* n_running) {
+  if (B == nullptr) return DS_EINVAL;
+  cudaStream_t st = B->stream;
+  (void)cudaGetLastError();
+  ds_status s = batch_upload(B);
+  if (s != DS_OK) return s;
+  s = batch_graph(B);
+  if (s != DS_OK) return s;
+  const int launches = min_iters <= kGraphIters ? 1 : (min_iters + kGraphIters - 1) / kGraphIters;
+  int running = 0;
+  for (int k = 0; k < launches; ++k) {
+    DS_CUDA_TRY(cudaGraphLaunch(B->graph, st));
+    B->launches += (int64_t)kGraphIters * 14;
+    k_bb_gather_states<<<(B->max_slots + 127) / 128, 128, 0, st>>>(B->d_slots, B->max_slots, B->d_states);
+    DS_CUDA_TRY(cudaMemcpyAsync(B->h_states, B->d_states, sizeof(CgState) * B->max_slots,
+                                cudaMemcpyDeviceToHost, st));
+    DS_CUDA_TRY(cudaStreamSynchronize(st));
+    running = 0;
+    bool changed = false;
+    for (int i = 0; i < B->max_slots; ++i) {
+      if (!B->plans[i]) continue;
+      if (B->h_states[i].done) {
+        if (!B->stopped[i]) changed = true;
+        B->stopped[i] = 1;
+      } else {
+        ++running;
+      }
+    }
+    if (running == 0) break;
+    if (changed) {  // compact the work lists to the problems still running
+      s = rebuild_tiles(B);
+      if (s == DS_OK) s = batch_upload(B);
+      if (s != DS_OK) return s;
+      if (!B->graph) {
+        s = batch_graph(B);
+        if (s != DS_OK) return s;
+      }
+    }
+  }
+  if (n_running) *n_running = running;
+  return DS_OK;
+}
+
+ds_status destripe_batch_slot_status(ds_batch_t B, int32_t slot, int32_t* done, int32_t* iters,
+                                     double* rel_resid) {
+  if (B == nullptr || slot < 0 || slot >= B->max_slots || B->plans[slot] == nullptr) return DS_EINVAL;
+  const CgState& H = B->h_states[slot];
+  if (done) *done = H.done;
+  if (iters) *iters = H.iter;
+  if (rel_resid) *rel_resid = H.bb > 0.0 ? std::sqrt(H.rr_true / H.bb) : 0.0;
+  return DS_OK;
+}
+
+ds_status destripe_batch_retire(ds_batch_t B, int32_t slot, double* d_a, int32_t* iters,
+                                double* rel_resid) {
+  if (B == nullptr || slot < 0 || slot >= B->max_slots || B->plans[slot] == nullptr) return DS_EINVAL;
+  Plan& P = *B->plans[slot];
+  cudaStream_t st = B->stream;
+  (void)cudaGetLastError();
+  DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+  DS_CUDA_TRY(cudaStreamSynchronize(st));
+  const CgState H = *P.h_state;
+  // as in destripe_solve: a problem that did not converge returns its best iterate
+  const bool use_best = H.status != 1 && !(H.rr_true <= H.rr_best);
+  double* result = use_best ? P.x_best : P.x;
+  enqueue_gauge(P, st, result);
+  B->launches += 2;
+  if (d_a) DS_CUDA_TRY(cudaMemcpyAsync(d_a, result, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
+  DS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (iters) *iters = H.iter;
+  if (rel_resid) *rel_resid = H.bb > 0.0 ? std::sqrt((use_best ? H.rr_best : H.rr_true) / H.bb) : 0.0;
+  B->plans[slot] = nullptr;
+  B->stopped[slot] = 0;
+  std::memset(&B->h_slots[slot], 0, sizeof(SlotDesc));
+  ds_status s = rebuild_tiles(B);
+  if (s != DS_OK) return s;
+  bool any = false;
+  for (int i = 0; i < B->max_slots; ++i) any |= B->plans[i] != nullptr;
+  if (!any) B->nc = 0;
+  if (!std::isfinite(H.bb)) return DS_ENAN;
+  if (!H.done) return DS_ENOCONV;
+  switch (H.status) {
+    case 1: return DS_OK;
+    case 3: return H.rr_true <= H.tol2 ? DS_OK : DS_ENOCONV;
+    default: return DS_ENOCONV;
+  }
+}
+
+ds_status destripe_batch_tune(ds_batch_t B, const char* key, double value) {
+  if (B == nullptr || key == nullptr) return DS_EINVAL;
+  const std::string k(key);
+  if (k == "tile_samples") {
+    if (!(value >= 4096 && value <= (1 << 24))) return DS_EINVAL;
+    B->tile_vecs = ((int64_t)value / 4 + 31) / 32 * 32;  // warp-aligned tile starts
+  } else if (k == "tile_unknowns") {
+    if (!(value >= 1024 && value <= (1 << 22))) return DS_EINVAL;
+    B->tile_unknowns = (int64_t)value;
+  } else if (k == "blocks_per_sm") {
+    if (!(value >= 1 && value <= 32)) return DS_EINVAL;
+    B->blocks_per_sm = (int)value;
+  } else {
+    return DS_EINVAL;
+  }
+  if (B->graph) {
+    cudaStreamSynchronize(B->stream);
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  return rebuild_tiles(B);
+}
+
+ds_status destripe_batch_info(ds_batch_t B, int32_t* n_slots_used, int64_t* kernel_launches) {
+  if (B == nullptr) return DS_EINVAL;
+  int used = 0;
+  for (int i = 0; i < B->max_slots; ++i) used += B->plans[i] != nullptr;
+  if (n_slots_used) *n_slots_used = used;
+  if (kernel_launches) *kernel_launches = B->launches;
+  return DS_OK;
+}
+
+}  // extern "C"

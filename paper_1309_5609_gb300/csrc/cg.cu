@@ -18,6 +18,7 @@ namespace ds {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr double kDriftRatio = 1e4;  // ||r_true||^2 / ||r_recursive||^2 that triggers the switch
 
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sm[32];
@@ -80,12 +81,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_start(double* __restrict__ x, dou
                                                      const double* __restrict__ b,
                                                      double* __restrict__ t, int warm, int64_t n,
                                                      double* __restrict__ red, unsigned* ticket,
-                                                     CgState* st) {
+                                                     CgState* st, double* __restrict__ x_best) {
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double ri = warm ? b[i] - t[i] : b[i];
     if (!warm) x[i] = 0.0;
+    if (x_best != nullptr) x_best[i] = warm ? x[i] : 0.0;
     r[i] = ri;
     p[i] = ri;
     q[i] = 0.0;
@@ -102,6 +104,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_start(double* __restrict__ x, dou
     st->need = 0;
     st->n_reliable = 0;
     st->last_refresh = 0;
+    st->accurate = 0;
+    st->improved = 0;
+    st->rr_best = tot;
     st->status = 0;
     st->done = 0;
     if (!isfinite(tot) || !isfinite(st->bb)) {
@@ -127,6 +132,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_alpha(const double* __restrict__ 
   double tot;
   if (finish_sum(acc, red, ticket, &tot)) {
     st->pq = tot;
+    st->improved = 0;
     if (!isfinite(tot)) {
       st->status = 4;
       st->done = 1;
@@ -135,6 +141,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_alpha(const double* __restrict__ 
       st->done = 1;
     } else {
       st->alpha = st->rr / tot;
+      if (!isfinite(st->alpha)) {
+        st->status = 4;
+        st->done = 1;
+      }
     }
   }
 }
@@ -204,6 +214,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_reliable(double* __restrict__ r,
   }
   double tot;
   if (finish_sum(acc, red, ticket, &tot)) {
+    // The float32 operator is not accurate enough for this problem when the true
+    // residual sits far above the recursive one: iterate with the accurate one.
+    if (st->mixed && !st->accurate && tot > kDriftRatio * st->rr) st->accurate = 1;
+    if (tot < st->rr_best) {
+      st->rr_best = tot;
+      st->improved = 1;
+    }
     st->rr = tot;
     st->rr_anchor = tot;
     st->rr_true = tot;
@@ -221,6 +238,16 @@ __global__ void __launch_bounds__(kBlock) k_cg_reliable(double* __restrict__ r,
       st->done = 1;
     }
   }
+}
+
+// x_best = x after a float64 residual that improved on every earlier one
+__global__ void __launch_bounds__(kBlock) k_cg_keep_best(const double* __restrict__ x,
+                                                         double* __restrict__ x_best, int64_t n,
+                                                         const CgState* st) {
+  if (!st->improved) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x_best[i] = x[i];
 }
 
 // p = r + beta p ; q = 0
@@ -304,7 +331,7 @@ void enqueue_gauge(const Plan& P, cudaStream_t st, double* a) {
 }
 
 int kernels_per_iteration(const Plan& P) {
-  return P.desc.precision == DS_PREC_MIXED ? 10 : 6;
+  return P.desc.precision == DS_PREC_MIXED ? 14 : 6;
 }
 
 // One CG iteration (gated by state->done), used both directly and under capture.
@@ -313,14 +340,23 @@ int kernels_per_iteration(const Plan& P) {
 void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev) {
   const bool mixed = P.desc.precision == DS_PREC_MIXED;
   const int vg = vec_grid(P, P.n_u);
-  Gate g{&P.state->done, nullptr};
-  enqueue_apply(P, st, !mixed, P.p, P.q, g, ev);
+  if (mixed) {
+    // float32 operator, unless the problem has switched to the accurate one
+    Gate g32{&P.state->done, nullptr, &P.state->accurate};
+    enqueue_apply(P, st, false, P.p, P.q, g32, ev);
+    Gate gacc{&P.state->done, &P.state->accurate, nullptr};
+    enqueue_apply(P, st, true, P.p, P.q, gacc, nullptr);
+  } else {
+    Gate g{&P.state->done, nullptr};
+    enqueue_apply(P, st, true, P.p, P.q, g, ev);
+  }
   k_cg_alpha<<<vg, kBlock, 0, st>>>(P.p, P.q, P.n_u, P.red, P.counters, P.state);
   k_cg_update<<<vg, kBlock, 0, st>>>(P.x, P.r, P.p, P.q, P.n_u, P.red, P.counters, P.state);
   if (mixed) {
     Gate gr{&P.state->done, &P.state->need};
     enqueue_apply(P, st, true, P.x, P.t, gr);
     k_cg_reliable<<<vg, kBlock, 0, st>>>(P.r, P.b, P.t, P.n_u, P.red, P.counters, P.state);
+    k_cg_keep_best<<<vg, kBlock, 0, st>>>(P.x, P.x_best, P.n_u, P.state);
   }
   k_cg_direction<<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.n_u, P.state);
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
@@ -337,7 +373,7 @@ void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, 
     enqueue_apply(P, st, true, P.x, P.t, Gate{nullptr, nullptr});
   }
   k_cg_start<<<vec_grid(P, P.n_u), kBlock, 0, st>>>(P.x, P.r, P.p, P.q, P.b, P.t, warm, P.n_u,
-                                                     P.red, P.counters, P.state);
+                                                     P.red, P.counters, P.state, P.x_best);
 }
 
 }  // namespace ds

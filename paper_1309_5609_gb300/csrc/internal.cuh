@@ -29,16 +29,18 @@ struct KindsArg {
   int kind[DS_MAX_OUTPUTS];
 };
 
-// Gate of a kernel inside the CG graph: it does nothing once *done != 0, and,
-// when need is given, unless *need != 0.
+// Gate of a kernel inside the CG graph: it does nothing once *done != 0; when
+// need is given, unless *need != 0; when skip is given, if *skip != 0.
 struct Gate {
   const int* done;
   const int* need;
+  const int* skip = nullptr;
 };
 
 __device__ __forceinline__ bool gate_closed(const Gate& g) {
   if (g.done != nullptr && *(volatile const int*)g.done) return true;
   if (g.need != nullptr && *(volatile const int*)g.need == 0) return true;
+  if (g.skip != nullptr && *(volatile const int*)g.skip != 0) return true;
   return false;
 }
 
@@ -62,7 +64,10 @@ struct CgState {
   int n_reliable;    // float64 residual updates done
   int last_refresh;  // iteration of the last float64 residual
   int refresh_max;   // refresh at least every refresh_max iterations (stagnation guard)
-  int pad;
+  int accurate;      // 1: the float32 operator could not follow; iterate with the accurate one
+  int improved;      // the last float64 residual is the best so far: keep x
+  int pad0, pad1;
+  double rr_best;    // smallest float64 ||b - A x||^2 seen (mixed plans keep that x)
 };
 
 enum ErrBits { ERR_PIX = 1, ERR_NAN = 2, ERR_TIMEOUT = 4 };
@@ -92,6 +97,7 @@ struct Plan {
   double* map64;
   int32_t* nvalid;
   double *x, *r, *p, *q, *b, *t;
+  double* x_best;     // mixed plans: iterate with the smallest float64 residual
   double* red;        // reduction partials [red_len]
   int red_len;
   unsigned* counters; // last-block tickets [8]
