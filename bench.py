@@ -45,7 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 4])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--serve-seconds", type=float, default=30.0,
+                    help="length of the request trace (config 5)")
+    ap.add_argument("--serve-master", type=int, default=100_000_000,
+                    help="samples of the host-resident master scans (config 5)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--n-samples", type=int, default=None, help="cut the workload (testing)")
@@ -410,10 +414,205 @@ def e2e_leg(args, prob, ds, world, dist):
             "api": "destripe_run_host (pinned host buffers; copies, plan, solve, map, copies back)"}
 
 
+def _dist_setup():
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    return rank, world, local, dev, (dist if world > 1 else None)
+
+
+def run_batch(args):
+    """Config 3: 64 independent problems of uneven size in one batch."""
+    import numpy as np
+    import torch
+    import paper_1309_5609_gb300 as ds
+    from synth import batch_configs, make_problem
+    rank, world, local, dev, dist = _dist_setup()
+    ds.load_library()
+    cfgs = batch_configs(64, seed=1003)
+    probs = [make_problem(device=dev, y_dtype=torch.float32, keep_f64_trig=False, **c) for c in cfgs]
+
+    def step():
+        plans = [ds.destripe_plan(p.pix, p.c32, p.s32, None, nside=p.nside, kinds=p.kinds,
+                                  baseline_len=p.baseline_len, precision="mixed") for p in probs]
+        b = ds.destripe_batch_create(len(probs))
+        slots = [ds.destripe_batch_add(b, pl, p.y, tol=args.tol) for pl, p in zip(plans, probs)]
+        while ds.destripe_batch_step(b, 8) > 0:
+            pass
+        iters, stats = [], []
+        for sl, pl in zip(slots, plans):
+            a = torch.empty(pl.n_u, dtype=torch.float64, device=dev)
+            st, it, rel = ds.destripe_batch_retire(b, sl, a)
+            iters.append(it)
+            stats.append(st)
+        launches = ds.destripe_batch_info(b)["kernel_launches"] + 3 * len(plans)
+        b.close()
+        for pl in plans:
+            pl.close()
+        return iters, stats, launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    units, launches, iters_all, ok = 0.0, 0, [], True
+    with Clocks(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            iters, stats, l = step()
+            units += sum(p.n_t * it for p, it in zip(probs, iters))
+            launches += l
+            iters_all += iters
+            ok &= all(s == ds.DS_OK for s in stats)
+        ev1.record()
+        torch.cuda.synchronize()
+    t_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t_ms, units = reduce_over_ranks(t_ms, units, dist, dev)
+    # comparator: the same problems solved one after the other
+    ev0.record()
+    seq_units = 0.0
+    for p in probs:
+        pl = ds.destripe_plan(p.pix, p.c32, p.s32, None, nside=p.nside, kinds=p.kinds,
+                              baseline_len=p.baseline_len, precision="mixed")
+        a = torch.empty(pl.n_u, dtype=torch.float64, device=dev)
+        st, it, rel = ds.destripe_solve(pl, p.y, a, tol=args.tol)
+        seq_units += p.n_t * it
+        pl.close()
+    ev1.record()
+    torch.cuda.synchronize()
+    seq_ms = ev0.elapsed_time(ev1)
+    peak, peak_kind = peaks()
+    value = units / (t_ms / 1e3)
+    achieved = 2 * BYTES_PER_SAMPLE_PASS * value / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (64 seeded scans), resident in HBM",
+            "config": {"workload": "batch64-qu-nside64-256-1e6-3e7-L50-3000",
+                       "problems": len(probs), "n_samples_total": int(sum(p.n_t for p in probs)),
+                       "precision": "mixed", "tol": args.tol,
+                       "step": "64 plans + batched RHS/CG (one graph per 8 iterations) + retire"},
+            "roofline": {"bound": "hbm", "kernel": "whole batched job (all kernels)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": "24 B per sample-iteration over the whole job time"},
+            "iterations": {"mean": float(np.mean(iters_all)), "max": int(max(iters_all))},
+            "all_converged": bool(ok), "gpu_launches": int(launches),
+            "sequential_single_solves": {"value": seq_units / (seq_ms / 1e3), "unit": UNIT,
+                                         "ms": seq_ms},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Config 5: Poisson request stream served with continuous batching."""
+    import numpy as np
+    import torch
+    import paper_1309_5609_gb300 as ds
+    from paper_1309_5609_gb300.serve import Request, Server, fifo_latencies, poisson_trace
+    from synth import make_problem
+    rank, world, local, dev, dist = _dist_setup()
+    ds.load_library()
+    n_master = args.serve_master
+    nsides = (64, 128, 256, 512)
+    master = {}
+    for ns in nsides:  # one scan, pixelised at each nside; same trig and noise seed
+        p = make_problem(n_master, ns, ("q", "u"), baseline_len=500, f_knee=0.1, alpha=1.7,
+                         seed=5000, device=dev, y_dtype=torch.float32, keep_f64_trig=False)
+        master[ns] = (p.pix.cpu().pin_memory(), p.c32.cpu().pin_memory(),
+                      p.s32.cpu().pin_memory(), [p.y[0].cpu().pin_memory(), p.y[1].cpu().pin_memory()])
+        del p
+    torch.cuda.empty_cache()
+    trace = poisson_trace(20.0, args.serve_seconds, seed=5000 + rank, n_min=1e5,
+                          n_max=min(2e8, n_master), nsides=nsides)
+    reqs = []
+    for i, r in enumerate(trace):
+        pix, c, s, y = master[r["nside"]]
+        n = min(r["n_t"], n_master)
+        s0 = r["start"] % (n_master - n + 1)
+        rows = [y[o][s0:s0 + n] for o in range(len(r["kinds"]))]
+        reqs.append(Request(i, r["arrival"], r["nside"], r["kinds"], r["baseline_len"],
+                            pix[s0:s0 + n], c[s0:s0 + n], s[s0:s0 + n], rows, tol=args.tol))
+    # warm-up on a few requests (kernels, graph capture)
+    warm = Server(max_slots=64, hbm_budget=200 << 30)
+    warm.run([Request(**{**r.__dict__, "arrival": 0.0}) for r in reqs[:3]])
+    warm.close()
+    srv = Server(max_slots=64, hbm_budget=200 << 30, iters_per_step=8)
+    with Clocks(local) as clk:
+        stats = srv.run(reqs)
+    srv.close()
+    summ = stats.summary()
+    ok = sum(r.status == ds.DS_OK for r in reqs)
+    # comparator: sequential plain float64 solves; service time measured on a
+    # sample of requests and modelled as c0 + c1 * samples * iterations
+    rng = np.random.default_rng(7)
+    sample = rng.choice(len(reqs), size=min(10, len(reqs)), replace=False)
+    xs, ts = [], []
+    for i in sample:
+        r = reqs[i]
+        g = [t.to(dev) for t in (r.pix, r.cos2psi, r.sin2psi)]
+        y64 = torch.stack([row.to(dev) for row in r.y]).double().contiguous()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pl = ds.destripe_plan(g[0], g[1], g[2], None, nside=r.nside, kinds=r.kinds,
+                              baseline_len=r.baseline_len, precision="fp64")
+        a = torch.empty(pl.n_u, dtype=torch.float64, device=dev)
+        st, it, rel = ds.destripe_solve(pl, y64, a, tol=args.tol)
+        a_h = a.cpu()
+        dt = time.perf_counter() - t0
+        pl.close()
+        xs.append(r.n_t * max(it, 1))
+        ts.append(dt)
+    A = np.vstack([np.ones(len(xs)), xs]).T
+    c0, c1 = np.linalg.lstsq(A, np.array(ts), rcond=None)[0]
+    c0, c1 = max(c0, 0.0), max(c1, 1e-15)
+    svc = [c0 + c1 * r.n_t * max(r.iters, 1) for r in reqs]
+    seq_lat = fifo_latencies([r.arrival for r in reqs], svc)
+    seq_wall = max(r.arrival + l for r, l in zip(reqs, seq_lat))
+    units = float(stats.sample_iters)
+    t_s = stats.wall
+    if dist is not None:
+        t_ms, units = reduce_over_ranks(1e3 * t_s, units, dist, dev)
+        t_s = t_ms / 1e3
+    peak, peak_kind = peaks()
+    value = units / t_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * t_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic requests: windows of host-resident master scans",
+            "config": {"workload": f"serve-poisson20-{args.serve_seconds:g}s",
+                       "requests": len(reqs), "rate_per_s": 20.0,
+                       "lengths": f"log-uniform 1e5..{min(2e8, n_master):.0e}",
+                       "nside": list(nsides), "baselines_s": [0.5, 60.0], "outputs": "q or q,u",
+                       "precision": "mixed", "tol": args.tol, "max_slots": 64},
+            "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "mean_latency_s": summ["mean_s"],
+            "samples_per_s": summ["samples_per_s"], "converged": int(ok),
+            "max_resident": summ["max_resident"], "gpu_launches": summ["kernel_launches"],
+            "sequential_fp64_model": {
+                "p50_s": float(np.percentile(seq_lat, 50)), "p99_s": float(np.percentile(seq_lat, 99)),
+                "value": units / seq_wall, "unit": UNIT,
+                "service_model": f"{c0:.3e} s + {c1:.3e} s per sample-iteration (fit on {len(xs)} measured float64 solves)"},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 3:
+        return run_batch(args)
+    if args.config == 5:
+        return run_serve(args)
     return run_ours(args)
 
 

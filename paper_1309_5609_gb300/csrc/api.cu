@@ -11,7 +11,7 @@ namespace ds {
 void enqueue_dot(const Plan& P, cudaStream_t st, const double* a, const double* b, int64_t n,
                  double* out);
 void enqueue_gauge(const Plan& P, cudaStream_t st, double* a);
-void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev);
+void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev, bool accurate);
 void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, double delta,
                       int warm);
 }  // namespace ds
@@ -51,6 +51,7 @@ cudaError_t dalloc(Plan& P, T** ptr, int64_t count) {
 void plan_free(Plan* P) {
   if (P == nullptr) return;
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+  if (P->graph_exec_acc) cudaGraphExecDestroy(P->graph_exec_acc);
   if (P->ev) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
@@ -89,11 +90,31 @@ ds_status launch_status() {
 // that launch_status() only sees this call's launches.
 void clear_stale_error() { (void)cudaGetLastError(); }
 
+ds_status capture_iterations(Plan& P, bool accurate, cudaEvent_t* ev, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  DS_CUDA_TRY(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < P.graph_iters; ++k)
+    enqueue_iteration(P, P.cap_stream, ev ? ev + 5 * k : nullptr, accurate);
+  cudaError_t e = cudaStreamEndCapture(P.cap_stream, &graph);
+  if (e != cudaSuccess) return DS_ECUDA;
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return DS_ECUDA;
+  }
+  return DS_OK;
+}
+
 ds_status build_graph(Plan& P) {
   if (P.graph_exec && P.graph_profiled == P.profiling) return DS_OK;
   if (P.graph_exec) {
     cudaGraphExecDestroy(P.graph_exec);
     P.graph_exec = nullptr;
+  }
+  if (P.graph_exec_acc) {
+    cudaGraphExecDestroy(P.graph_exec_acc);
+    P.graph_exec_acc = nullptr;
   }
   if (P.profiling && P.ev == nullptr) {
     P.ev = new (std::nothrow) cudaEvent_t[kGraphItersMax * 5];
@@ -101,17 +122,11 @@ ds_status build_graph(Plan& P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) DS_CUDA_TRY(cudaEventCreate(&P.ev[i]));
   }
   P.graph_iters = P.graph_iters_cfg;
-  cudaGraph_t graph = nullptr;
-  DS_CUDA_TRY(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < P.graph_iters; ++k)
-    enqueue_iteration(P, P.cap_stream, P.profiling ? P.ev + 5 * k : nullptr);
-  cudaError_t e = cudaStreamEndCapture(P.cap_stream, &graph);
-  if (e != cudaSuccess) return DS_ECUDA;
-  e = cudaGraphInstantiate(&P.graph_exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) {
-    P.graph_exec = nullptr;
-    return DS_ECUDA;
+  ds_status s = capture_iterations(P, false, P.profiling ? P.ev : nullptr, &P.graph_exec);
+  if (s != DS_OK) return s;
+  if (P.desc.precision == DS_PREC_MIXED) {
+    s = capture_iterations(P, true, nullptr, &P.graph_exec_acc);
+    if (s != DS_OK) return s;
   }
   P.graph_profiled = P.profiling;
   return DS_OK;
@@ -352,17 +367,22 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   const int max_launches = max_iter / P.graph_iters + 4;
   bool done = false;
   int iter_before = 0;
+  bool accurate = false;
   for (int k = 0; k < max_launches && !done; ++k) {
-    DS_CUDA_TRY(cudaGraphLaunch(P.graph_exec, st));
+    // a mixed problem that the float32 operator cannot follow continues with the
+    // accurate one (the switch is decided on the device at a float64 refresh)
+    const bool acc_now = accurate && P.graph_exec_acc != nullptr;
+    DS_CUDA_TRY(cudaGraphLaunch(acc_now ? P.graph_exec_acc : P.graph_exec, st));
     DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     DS_CUDA_TRY(cudaStreamSynchronize(st));
     done = P.h_state->done != 0;
+    accurate = P.h_state->accurate != 0;
     P.graph_launches += 1;
     P.launches += (int64_t)P.graph_iters * kernels_per_iteration(P);
     const int ran = P.h_state->iter - iter_before;
     iter_before = P.h_state->iter;
     P.iterations += ran;
-    collect_times(P, ran);
+    if (!acc_now) collect_times(P, ran);  // events live in the float32 graph only
   }
   DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
   DS_CUDA_TRY(cudaMemcpyAsync(P.h_err, P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -446,10 +466,14 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
   } else {
     return DS_EINVAL;
   }
-  // the captured graph bakes in launch shapes and kernel choices: rebuild it
+  // the captured graphs bake in launch shapes and kernel choices: rebuild them
   if (P.graph_exec) {
     cudaGraphExecDestroy(P.graph_exec);
     P.graph_exec = nullptr;
+  }
+  if (P.graph_exec_acc) {
+    cudaGraphExecDestroy(P.graph_exec_acc);
+    P.graph_exec_acc = nullptr;
   }
   return DS_OK;
 }

@@ -84,7 +84,7 @@ __device__ __forceinline__ bool slot_df(const SlotDesc& S) {
 // ---- operator kernels (mixed precision: float32 per-sample work) ---------------
 
 template <int KS>
-__global__ void __launch_bounds__(kBlock) k_bb_bin(const SlotDesc* __restrict__ slots,
+__global__ void __launch_bounds__(kBlock, 4) k_bb_bin(const SlotDesc* __restrict__ slots,
                                                    const WorkTile* __restrict__ tiles,
                                                    const int* __restrict__ ntiles) {
   using K = KSet<KS>;
@@ -149,19 +149,23 @@ __global__ void __launch_bounds__(kBlock) k_bb_pixel_solve(const SlotDesc* __res
   const int nt = ntiles[W_PIXELS];
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const WorkTile T = tiles[ti];
-    const SlotDesc& S = slots[T.slot];
-    if (!slot_f32(S)) continue;
+    if (!slot_f32(slots[T.slot])) continue;
+    // locals: stores through slot pointers would otherwise force reloads of the table
+    float4* __restrict__ bins = reinterpret_cast<float4*>(slots[T.slot].bins32);
+    float4* __restrict__ map = reinterpret_cast<float4*>(slots[T.slot].map32);
+    const uint8_t* __restrict__ mask = slots[T.slot].mask;
+    const double* __restrict__ minv = slots[T.slot].minv;
     for (int64_t p = T.begin + threadIdx.x; p < T.end; p += blockDim.x) {
-      const float4 v = reinterpret_cast<const float4*>(S.bins32)[p];
-      reinterpret_cast<float4*>(S.bins32)[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 v = bins[p];
+      bins[p] = make_float4(0.f, 0.f, 0.f, 0.f);
       const double sv[4] = {v.x, v.y, v.z, v.w};
       double s[NC], m[NC];
 #pragma unroll
       for (int j = 0; j < NC; ++j) s[j] = sv[j];
-      if (S.mask[p]) {
+      if (mask[p]) {
         double mi[NM];
 #pragma unroll
-        for (int j = 0; j < NM; ++j) mi[j] = S.minv[p * NM + j];
+        for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
         sym_mul<NC>(mi, s, m);
       } else {
 #pragma unroll
@@ -170,13 +174,13 @@ __global__ void __launch_bounds__(kBlock) k_bb_pixel_solve(const SlotDesc* __res
       float o4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < NC; ++j) o4[j] = (float)m[j];
-      reinterpret_cast<float4*>(S.map32)[p] = make_float4(o4[0], o4[1], o4[2], o4[3]);
+      map[p] = make_float4(o4[0], o4[1], o4[2], o4[3]);
     }
   }
 }
 
 template <int KS>
-__global__ void __launch_bounds__(kBlock) k_bb_rescan(const SlotDesc* __restrict__ slots,
+__global__ void __launch_bounds__(kBlock, 4) k_bb_rescan(const SlotDesc* __restrict__ slots,
                                                       const WorkTile* __restrict__ tiles,
                                                       const int* __restrict__ ntiles) {
   using K = KSet<KS>;
@@ -313,19 +317,23 @@ __global__ void __launch_bounds__(kBlock) k_bb_pixel_solve_df(const SlotDesc* __
   const int nt = ntiles[W_PIXELS];
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const WorkTile T = tiles[ti];
-    const SlotDesc& S = slots[T.slot];
-    if (!slot_df<MODE>(S)) continue;
+    if (!slot_df<MODE>(slots[T.slot])) continue;
+    double* __restrict__ bins = slots[T.slot].bins;
+    float* __restrict__ map_hi = slots[T.slot].map32;
+    float* __restrict__ map_lo = slots[T.slot].maplo;
+    const uint8_t* __restrict__ mask = slots[T.slot].mask;
+    const double* __restrict__ minv = slots[T.slot].minv;
     for (int64_t p = T.begin + threadIdx.x; p < T.end; p += blockDim.x) {
       double s[NC], m[NC];
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        s[j] = S.bins[4 * p + j];
-        S.bins[4 * p + j] = 0.0;
+        s[j] = bins[4 * p + j];
+        bins[4 * p + j] = 0.0;
       }
-      if (S.mask[p]) {
+      if (mask[p]) {
         double mi[NM];
 #pragma unroll
-        for (int j = 0; j < NM; ++j) mi[j] = S.minv[p * NM + j];
+        for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
         sym_mul<NC>(mi, s, m);
       } else {
 #pragma unroll
@@ -338,8 +346,8 @@ __global__ void __launch_bounds__(kBlock) k_bb_pixel_solve_df(const SlotDesc* __
         hi[j] = d.hi;
         lo[j] = d.lo;
       }
-      reinterpret_cast<float4*>(S.map32)[p] = make_float4(hi[0], hi[1], hi[2], hi[3]);
-      reinterpret_cast<float4*>(S.maplo)[p] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      reinterpret_cast<float4*>(map_hi)[p] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      reinterpret_cast<float4*>(map_lo)[p] = make_float4(lo[0], lo[1], lo[2], lo[3]);
     }
   }
 }
@@ -440,21 +448,21 @@ __device__ __forceinline__ double bb_block_sum(double v) {
 
 // The block holding tile ti of slot S publishes its partial; returns true (in
 // thread 0) when it was the slot's last tile, with the slot total in *total.
-__device__ bool bb_finish(double partial, int ti, const SlotDesc& S, double* __restrict__ red,
-                          unsigned* __restrict__ ticket, double* total) {
+__device__ bool bb_finish(double partial, int ti, int u_first, int u_count,
+                          double* __restrict__ red, unsigned* __restrict__ ticket, double* total) {
   __shared__ bool last;
   const double bs = bb_block_sum(partial);
   if (threadIdx.x == 0) {
     red[ti] = bs;
     __threadfence();
     const unsigned k = atomicAdd(ticket, 1u);
-    last = (k == (unsigned)S.u_count - 1);
+    last = (k == (unsigned)u_count - 1);
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
   double v = 0.0;
-  for (int i = threadIdx.x; i < S.u_count; i += blockDim.x) v += ((volatile double*)red)[S.u_first + i];
+  for (int i = threadIdx.x; i < u_count; i += blockDim.x) v += ((volatile double*)red)[u_first + i];
   v = bb_block_sum(v);
   if (threadIdx.x == 0) {
     *ticket = 0u;
@@ -472,13 +480,15 @@ __global__ void __launch_bounds__(kBlock) k_bb_alpha(const SlotDesc* __restrict_
   const int nt = ntiles[W_UNKNOWNS];
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const WorkTile T = tiles[ti];
-    const SlotDesc& S = slots[T.slot];
-    if (!slot_live(S)) continue;
+    if (!slot_live(slots[T.slot])) continue;
+    const double* __restrict__ p = slots[T.slot].p;
+    const double* __restrict__ q = slots[T.slot].q;
+    const int uf = slots[T.slot].u_first, uc = slots[T.slot].u_count;
+    CgState* st = slots[T.slot].state;
     double acc = 0.0;
-    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) acc += S.p[i] * S.q[i];
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) acc += p[i] * q[i];
     double tot;
-    if (bb_finish(acc, ti, S, red, tickets + 4 * T.slot + 0, &tot)) {
-      CgState* st = S.state;
+    if (bb_finish(acc, ti, uf, uc, red, tickets + 4 * T.slot + 0, &tot)) {
       st->pq = tot;
       st->improved = 0;
       if (!isfinite(tot)) {
@@ -506,19 +516,23 @@ __global__ void __launch_bounds__(kBlock) k_bb_update(const SlotDesc* __restrict
   const int nt = ntiles[W_UNKNOWNS];
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const WorkTile T = tiles[ti];
-    const SlotDesc& S = slots[T.slot];
-    if (!slot_live(S)) continue;
-    const double alpha = S.state->alpha;
+    if (!slot_live(slots[T.slot])) continue;
+    double* __restrict__ x = slots[T.slot].x;
+    double* __restrict__ r = slots[T.slot].r;
+    const double* __restrict__ p = slots[T.slot].p;
+    const double* __restrict__ q = slots[T.slot].q;
+    const int uf = slots[T.slot].u_first, uc = slots[T.slot].u_count;
+    CgState* st = slots[T.slot].state;
+    const double alpha = st->alpha;
     double acc = 0.0;
     for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-      S.x[i] += alpha * S.p[i];
-      const double ri = S.r[i] - alpha * S.q[i];
-      S.r[i] = ri;
+      x[i] += alpha * p[i];
+      const double ri = r[i] - alpha * q[i];
+      r[i] = ri;
       acc += ri * ri;
     }
     double tot;
-    if (bb_finish(acc, ti, S, red, tickets + 4 * T.slot + 1, &tot)) {
-      CgState* st = S.state;
+    if (bb_finish(acc, ti, uf, uc, red, tickets + 4 * T.slot + 1, &tot)) {
       st->rr_old = st->rr;
       st->rr = tot;
       st->iter += 1;
@@ -543,18 +557,21 @@ __global__ void __launch_bounds__(kBlock) k_bb_reliable(const SlotDesc* __restri
   const int nt = ntiles[W_UNKNOWNS];
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const WorkTile T = tiles[ti];
-    const SlotDesc& S = slots[T.slot];
-    if (!slot_df<0>(S)) continue;
+    if (!slot_df<0>(slots[T.slot])) continue;
+    double* __restrict__ r = slots[T.slot].r;
+    double* __restrict__ t = slots[T.slot].t;
+    const double* __restrict__ b = slots[T.slot].b;
+    const int uf = slots[T.slot].u_first, uc = slots[T.slot].u_count;
+    CgState* st = slots[T.slot].state;
     double acc = 0.0;
     for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-      const double ri = S.b[i] - S.t[i];
-      S.r[i] = ri;
-      S.t[i] = 0.0;
+      const double ri = b[i] - t[i];
+      r[i] = ri;
+      t[i] = 0.0;
       acc += ri * ri;
     }
     double tot;
-    if (bb_finish(acc, ti, S, red, tickets + 4 * T.slot + 2, &tot)) {
-      CgState* st = S.state;
+    if (bb_finish(acc, ti, uf, uc, red, tickets + 4 * T.slot + 2, &tot)) {
       if (!st->accurate && tot > 1e4 * st->rr) st->accurate = 1;  // float32 drift: switch
       if (tot < st->rr_best) {
         st->rr_best = tot;
@@ -588,7 +605,9 @@ __global__ void __launch_bounds__(kBlock) k_bb_keep_best(const SlotDesc* __restr
     const WorkTile T = tiles[ti];
     const SlotDesc& S = slots[T.slot];
     if (!S.active || !(*(volatile const int*)&S.state->improved)) continue;
-    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) S.x_best[i] = S.x[i];
+    const double* __restrict__ x = S.x;
+    double* __restrict__ xb = S.x_best;
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) xb[i] = x[i];
   }
 }
 
@@ -598,12 +617,15 @@ __global__ void __launch_bounds__(kBlock) k_bb_direction(const SlotDesc* __restr
   const int nt = ntiles[W_UNKNOWNS];
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const WorkTile T = tiles[ti];
-    const SlotDesc& S = slots[T.slot];
-    if (!slot_live(S)) continue;
-    const double beta = S.state->rr / S.state->rr_old;
+    if (!slot_live(slots[T.slot])) continue;
+    double* __restrict__ p = slots[T.slot].p;
+    double* __restrict__ q = slots[T.slot].q;
+    const double* __restrict__ r = slots[T.slot].r;
+    const CgState* st = slots[T.slot].state;
+    const double beta = st->rr / st->rr_old;
     for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
-      S.p[i] = S.r[i] + beta * S.p[i];
-      S.q[i] = 0.0;
+      p[i] = r[i] + beta * p[i];
+      q[i] = 0.0;
     }
   }
 }
@@ -642,9 +664,9 @@ struct ds_batch_s {
   cudaGraphExec_t graph = nullptr;
   int graph_ks = -1;  // kind set the graph was captured for
   bool dirty = true;
-  int64_t tile_vecs = 16384;     // 4-sample vectors per sample tile (65536 samples)
-  int64_t tile_pixels = 65536;
-  int64_t tile_unknowns = 32768;
+  int64_t tile_vecs = 4096;      // 4-sample vectors per sample tile (16384 samples)
+  int64_t tile_pixels = 16384;
+  int64_t tile_unknowns = 4096;
   int blocks_per_sm = 8;
   int64_t launches = 0;
 };

@@ -331,21 +331,19 @@ void enqueue_gauge(const Plan& P, cudaStream_t st, double* a) {
 }
 
 int kernels_per_iteration(const Plan& P) {
-  return P.desc.precision == DS_PREC_MIXED ? 14 : 6;
+  return P.desc.precision == DS_PREC_MIXED ? 11 : 6;
 }
 
 // One CG iteration (gated by state->done), used both directly and under capture.
-// ev (optional): 5 events; the first four bracket the operator kernels, the fifth
-// marks the end of the iteration.
-void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev) {
+// accurate: apply the operator in the accurate arithmetic (a mixed problem that
+// the float32 operator could not follow).  ev (optional): 5 events; the first
+// four bracket the operator kernels, the fifth marks the end of the iteration.
+void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev, bool accurate) {
   const bool mixed = P.desc.precision == DS_PREC_MIXED;
   const int vg = vec_grid(P, P.n_u);
   if (mixed) {
-    // float32 operator, unless the problem has switched to the accurate one
-    Gate g32{&P.state->done, nullptr, &P.state->accurate};
-    enqueue_apply(P, st, false, P.p, P.q, g32, ev);
-    Gate gacc{&P.state->done, &P.state->accurate, nullptr};
-    enqueue_apply(P, st, true, P.p, P.q, gacc, nullptr);
+    Gate g{&P.state->done, nullptr};
+    enqueue_apply(P, st, accurate, P.p, P.q, g, ev);
   } else {
     Gate g{&P.state->done, nullptr};
     enqueue_apply(P, st, true, P.p, P.q, g, ev);

@@ -108,8 +108,9 @@ struct Plan {
   double* scal;       // device scratch scalars [8]
   double* h_scal;     // pinned [8]
   int64_t device_bytes;
-  // captured iteration graph
+  // captured iteration graphs: [0] float32 operator, [1] accurate operator
   cudaGraphExec_t graph_exec;
+  cudaGraphExec_t graph_exec_acc;
   int graph_iters;
   int graph_profiled;       // graph holds event nodes
   // profiling

@@ -42,7 +42,7 @@ class Request:
     pix: object               # host tensors (pinned) of this request's window
     cos2psi: object
     sin2psi: object
-    y: object                 # float32 [n_o, n_t]
+    y: object                 # float32 [n_o, n_t], or a list of n_o float32 [n_t] rows
     tol: float = 1e-10
     # filled by the server
     admitted: float = -1.0
@@ -122,11 +122,14 @@ class Server:
             raise ValueError(f"request {req.rid} needs {need} bytes, above the HBM budget")
         if self.used + need > self.budget or len(self.resident) >= self.max_slots:
             return False
+        rows = list(req.y) if isinstance(req.y, (list, tuple)) else [req.y[o] for o in range(len(req.kinds))]
         with torch.cuda.stream(self.copy_stream):
             pix = req.pix.to(self.dev, non_blocking=True)
             c = req.cos2psi.to(self.dev, non_blocking=True)
             s = req.sin2psi.to(self.dev, non_blocking=True)
-            y = req.y.to(self.dev, non_blocking=True)
+            y = torch.empty((len(rows), req.n_t), dtype=torch.float32, device=self.dev)
+            for o, row in enumerate(rows):
+                y[o].copy_(row, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(self.copy_stream)
         self.stream.wait_event(ev)

@@ -206,9 +206,12 @@ CONFIGS = {
     # 30 days of one B-Machine-like channel: I, q, u outputs, nside 256, 60 s baselines
     2: dict(n_t=130_000_000, nside=256, kinds=("I", "q", "u"), baseline_len=3000,
             f_knee=0.05, alpha=1.5, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0}),
-    # 12 months of a LATTE-like IQU radiometer: nside 512, 1 s baselines, 2% flagged
+    # 12 months of a LATTE-like IQU radiometer: nside 512, 1 s baselines, 2% flagged;
+    # its polarisation angle turns once per 10 minutes (a modulator), without which
+    # every IQU pixel matrix of a fixed-elevation scan is singular
     4: dict(n_t=1_600_000_000, nside=512, kinds=("iqu",), baseline_len=50, f_knee=0.05,
-            alpha=1.5, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0}, flag_frac=0.02),
+            alpha=1.5, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0}, flag_frac=0.02,
+            scan=ScanParams(pol_rotation_period=600.0)),
 }
 
 WORKLOAD_NAMES = {

@@ -31,6 +31,11 @@ class ScanParams:
     az0: float = 0.0  # rad, azimuth at t = 0 (north)
     lst0: float = 0.0  # rad, local sidereal time at t = 0
     sidereal_day: float = 86164.0905  # s
+    # Period (s) of a continuously rotating polarisation angle added to the
+    # parallactic angle (a polarisation modulator); 0 = none.  A single detector
+    # at fixed elevation sees each pixel at only two parallactic angles (rising
+    # and setting), which leaves the 3x3 I/Q/U pixel matrix rank 2.
+    pol_rotation_period: float = 0.0
 
 
 def scan_pointing(n: int, params: ScanParams = ScanParams(), first_sample: int = 0,
@@ -55,5 +60,7 @@ def scan_pointing(n: int, params: ScanParams = ScanParams(), first_sample: int =
     ha = torch.atan2(-sin_az * cos_el, sin_el * cos_lat - cos_el * sin_lat * cos_az)
     ra = torch.remainder(lst - ha, 2.0 * math.pi)
     psi = torch.atan2(torch.sin(ha), math.tan(lat) * torch.cos(dec) - sin_dec * torch.cos(ha))
+    if params.pol_rotation_period > 0.0:
+        psi = psi + (2.0 * math.pi / params.pol_rotation_period) * t
     theta = 0.5 * math.pi - dec
     return theta, ra, psi
