@@ -57,7 +57,17 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-samples", type=int, default=1_000_000)
     ap.add_argument("--oracle-iters", type=int, default=20)
+    ap.add_argument("--tune", default="",
+                    help="plan tuning knobs for the single-problem workloads, key=value,...")
     return ap.parse_args()
+
+
+def parse_tune(text):
+    out = {}
+    for item in filter(None, (t.strip() for t in text.split(","))):
+        k, v = item.split("=")
+        out[k.strip()] = float(v)
+    return out
 
 
 def dist_env():
@@ -77,19 +87,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_traffic(n_t, kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, scaled by
-    samples, or None if the summary is missing or the kernel source has changed."""
+def kernel_traffic(n_t, kernel, workload):
+    """Per-launch DRAM bytes of `kernel` on `workload` from the committed ncu
+    summary (bytes per sample times samples), or None if the summary is missing,
+    has no line for the workload, or the kernel source has changed since."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
     src = os.path.join(ROOT, "paper_1309_5609_gb300", "csrc", "apply.cu")
     try:
         text = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         m_sha = re.search(r"apply\.cu sha256\[:16\]:\s*([0-9a-f]+)", text)
-        m_bps = re.search(r"dram bytes per sample:\s*([0-9.]+)", text)
-        if not m_sha or not m_bps or m_sha.group(1) != sha:
+        if not m_sha or m_sha.group(1) != sha:
             return None
-        return float(m_bps.group(1)) * n_t
+        for key, bps in re.findall(r"dram bytes per sample \[([\w.-]+)\]:\s*([0-9.]+)", text):
+            if workload.startswith(key):
+                return float(bps) * n_t
+        return None
     except Exception:
         return None
 
@@ -273,10 +286,16 @@ def run_ours(args):
     hits = torch.zeros(npix, dtype=torch.int32, device=dev)
     mask = torch.zeros(npix, dtype=torch.uint8, device=dev)
 
+    tune = parse_tune(args.tune)
+    chunked = args.precision == "mixed" and tune.get("layout", 0) == 1 and \
+        tune.get("stream_mode", 0) == 0
+
     def step(prof_acc):
         plan = ds.destripe_plan(prob.pix, prob.c32, prob.s32, prob.valid, nside=prob.nside,
                                 kinds=prob.kinds, baseline_len=prob.baseline_len,
                                 precision=args.precision)
+        for k, v in tune.items():
+            ds.destripe_tune(plan, k, v)
         if prof_acc is not None:
             ds.destripe_profile(plan, 1)
         st, iters, rel = ds.destripe_solve(plan, prob.y, a, tol=args.tol)
@@ -331,10 +350,11 @@ def run_ours(args):
     peak, peak_kind = peaks()
     dur_s = per_launch[dom] / 1e3
     achieved = alg_bytes / dur_s / 1e9 if dur_s > 0 else None
-    kname = {"bin": "k_bin", "rescan": "k_rescan"}[dom]
+    kname = ({"bin": "k_ck_bin", "rescan": "k_ck_rescan"} if chunked else
+             {"bin": "k_bin", "rescan": "k_rescan"})[dom]
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": kernel_traffic(prob.n_t, kname),
+            "traffic": kernel_traffic(prob.n_t, kname, name),
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
             "algorithmic_bytes_per_launch": alg_bytes,
             "launch_ms": per_launch[dom],
@@ -347,7 +367,9 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic (seeded scan, Gaussian sky, 1/f noise), resident in HBM",
-            "config": config_dict(args, name), "roofline": roof,
+            "config": dict(config_dict(args, name), tune=tune,
+                           operator_layout="chunk-local pixel index" if chunked
+                           else "time-ordered pixels"), "roofline": roof,
             "iterations_per_step": iters_tot / args.steps,
             "rel_resid_max": max(rels) if rels else None,
             "gpu_launches": int(prof.get("kernel_launches", 0)),

@@ -215,6 +215,16 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     / 3 x 1024-sample stages at 3 blocks per SM (persistent blocks;
  *                     waits are bounded, DS_ETIMEOUT on expiry)
  *   "blocks_per_sm"   1..32 resident-block target of the streaming kernels (default 16)
+ *   "layout"          MIXED plans: 0 = the float32 operator reads the time-ordered pixel
+ *                     indices (default); 1 = it reads a chunk-local index (per chunk of
+ *                     consecutive samples: the sorted distinct pixels and a 16-bit rank per
+ *                     sample), bins into shared memory and stages the chunk's map in
+ *                     shared memory.  The index is built on the plan's stream when first
+ *                     requested (6 bytes per sample of device memory; synchronises)
+ *   "chunk"           MIXED plans: rebuild the chunk-local index with this many samples
+ *                     per chunk (2048, 4096, 8192 or 16384; synchronises)
+ *   "rescan_dedup"    MIXED plans: 1 = the float32 rescan reads the map once per run of
+ *                     equal pixels within a thread's 4 samples (default), 0 = once per sample
  * Returns DS_EINVAL for an unknown key or value, DS_ESTATE when the plan cannot
  * use the value.  Takes effect at the next call. */
 ds_status destripe_tune(ds_plan_t plan, const char* key, double value);

@@ -56,7 +56,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   for (void* d : dev)
@@ -153,6 +153,38 @@ void collect_times(Plan& P, int n_ran) {
   }
 }
 
+// Allocates (once) and builds the chunk-local pixel index for chunk length C
+// (mixed plans, on request: the default operator reads the time-ordered pixels).
+ds_status chunk_index(Plan& P, int C) {
+  clear_stale_error();
+  cudaError_t e = cudaSuccess;
+  if (P.lid == nullptr) {
+    const int64_t n_pad = (P.n_t + kChunkMax - 1) / kChunkMax * kChunkMax;
+    if (e == cudaSuccess) e = dalloc(P, &P.lid, n_pad);
+    if (e == cudaSuccess) e = dalloc(P, &P.upix, n_pad);
+    if (e == cudaSuccess) e = dalloc(P, &P.ucnt, (P.n_t + kChunkMin - 1) / kChunkMin);
+    if (e != cudaSuccess) {
+      for (void* d : {(void*)P.lid, (void*)P.upix, (void*)P.ucnt})
+        if (d) cudaFree(d);
+      P.lid = nullptr;
+      P.upix = nullptr;
+      P.ucnt = nullptr;
+      return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
+    }
+  }
+  unsigned long long* umax = reinterpret_cast<unsigned long long*>(P.scal) + 2;
+  DS_CUDA_TRY(cudaMemsetAsync(umax, 0, sizeof(unsigned long long), P.stream));
+  DS_CUDA_TRY(ck_build(P, C, umax));
+  DS_CUDA_TRY(cudaMemcpyAsync(P.h_scal + 2, umax, sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, P.stream));
+  DS_CUDA_TRY(cudaStreamSynchronize(P.stream));
+  unsigned long long hu = 0;
+  std::memcpy(&hu, P.h_scal + 2, sizeof(hu));
+  DS_CUDA_TRY(ck_finish(P, (int64_t)hu));
+  P.launches += 1;
+  return DS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -213,6 +245,8 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->accurate_df = 1;
   P->stream_mode = 0;
   P->refresh_max = 50;
+  P->layout = 0;
+  P->rescan_dedup = 1;
   cudaError_t e = cudaSuccess;
 #define DS_ALLOC(ptr, n) \
   if (e == cudaSuccess) e = dalloc(*P, &P->ptr, (n));
@@ -233,6 +267,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   DS_ALLOC(b, P->n_u);
   DS_ALLOC(t, P->n_u);
   if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(x_best, P->n_u);
+
   DS_ALLOC(red, P->red_len);
   DS_ALLOC(counters, 8);
   DS_ALLOC(state, 1);
@@ -460,6 +495,25 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
   } else if (k == "stream_mode") {
     if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
     P.stream_mode = (int)value;
+  } else if (k == "layout") {
+    if (value != 0.0 && value != 1.0) return DS_EINVAL;
+    if (value == 1.0) {
+      if (P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
+      if (P.lid == nullptr) {
+        const ds_status s = chunk_index(P, ck_default_chunk(P.n_t, P.num_sms));
+        if (s != DS_OK) return s;
+      }
+    }
+    P.layout = (int)value;
+  } else if (k == "chunk") {
+    const int C = (int)value;
+    if ((double)C != value || C < kChunkMin || C > kChunkMax || (C & (C - 1)) != 0) return DS_EINVAL;
+    if (P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
+    const ds_status s = chunk_index(P, C);
+    if (s != DS_OK) return s;
+  } else if (k == "rescan_dedup") {
+    if (value != 0.0 && value != 1.0) return DS_EINVAL;
+    P.rescan_dedup = (int)value;
   } else if (k == "blocks_per_sm") {
     if (!(value >= 1.0 && value <= 32.0)) return DS_EINVAL;
     P.blocks_per_sm = (int)value;

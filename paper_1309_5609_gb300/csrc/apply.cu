@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve(BT* __restrict__ bins,
 }
 
 // ---- rescan + per-baseline sum: out[o][b] += sum_{t in b} v (z_o(t) - w_o(t) . m_p(t))
-template <int KS, typename T, bool ZY, typename YT>
+template <int KS, typename T, bool ZY, typename YT, bool DEDUP = false>
 __global__ void __launch_bounds__(kBlock) k_rescan(const int32_t* __restrict__ pix,
                                                    const float* __restrict__ cc,
                                                    const float* __restrict__ ss,
@@ -187,13 +187,36 @@ __global__ void __launch_bounds__(kBlock) k_rescan(const int32_t* __restrict__ p
       float c[4], s[4];
       load4(pix, cc, ss, v, n_t, p, c, s);
       T m[4][NC];
+      if constexpr (DEDUP) {
+        // a sample on the same pixel as the one before it reuses that map value:
+        // the other gathers are all issued first, the copies made after
+        bool dup[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (p[k] >= 0) {
-          load_map<NC, T>(map, p[k], m[k]);
-        } else {
+        for (int k = 0; k < 4; ++k) dup[k] = k > 0 && p[k] >= 0 && p[k] == p[k - 1];
 #pragma unroll
-          for (int j = 0; j < NC; ++j) m[k][j] = T(0);
+        for (int k = 0; k < 4; ++k) {
+          if (p[k] >= 0 && !dup[k]) {
+            load_map<NC, T>(map, p[k], m[k]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) m[k][j] = T(0);
+          }
+        }
+#pragma unroll
+        for (int k = 1; k < 4; ++k)
+          if (dup[k]) {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) m[k][j] = m[k - 1][j];
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (p[k] >= 0) {
+            load_map<NC, T>(map, p[k], m[k]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) m[k][j] = T(0);
+          }
         }
       }
       const int64_t t0 = v << 2;
@@ -303,6 +326,9 @@ void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x,
     if (fp64)
       k_rescan<KS, double, false, double><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, x, nullptr, P.map64, out, P.n_t, P.L, P.n_b, P.kinds, g);
+    else if (P.rescan_dedup)
+      k_rescan<KS, float, false, float, true><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, x, nullptr, P.map32, out, P.n_t, P.L, P.n_b, P.kinds, g);
     else
       k_rescan<KS, float, false, float><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, x, nullptr, P.map32, out, P.n_t, P.L, P.n_b, P.kinds, g);
@@ -340,6 +366,16 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     launch_pixel_solve_df(P, st, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
     launch_rescan_df(P, st, x, nullptr, out, g);
+    if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+    return;
+  }
+  if (!fp64 && P.stream_mode == 0 && P.bin_mode == 1 && ck_ready(P)) {
+    if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+    launch_bin_ck(P, st, x, g);
+    if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+    launch_pixel_solve(P, st, false, nullptr, g);
+    if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+    launch_rescan_ck(P, st, x, out, g);
     if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
     return;
   }

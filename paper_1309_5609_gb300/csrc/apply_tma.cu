@@ -384,12 +384,9 @@ __global__ void __launch_bounds__(kThreads, Cfg::BPS) k_stream_tma(const int32_t
 template <class Cfg, class Body>
 void launch_stream_cfg(const Plan& P, cudaStream_t st, const Body& body, Gate g) {
   constexpr size_t kSmemBytes = sizeof(PipeSmem<Cfg>);
-  static bool attr_set = false;  // one attribute call per instantiation
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_stream_tma<Cfg, Body>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kSmemBytes);
-    attr_set = true;
-  }
+  // the limit is per kernel and per device: set it on every launch (a host call)
+  cudaFuncSetAttribute(k_stream_tma<Cfg, Body>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kSmemBytes);
   const int64_t n_tiles = (P.n_t + Cfg::TILE - 1) / Cfg::TILE;
   int64_t grid = (int64_t)P.num_sms * Cfg::BPS;
   if (grid > n_tiles) grid = n_tiles;

@@ -62,15 +62,27 @@ __device__ bool finish_sum(double partial, double* __restrict__ red, unsigned* _
   return false;
 }
 
+// The vector kernels below read pairs of elements with one 16-byte load (the
+// vectors are 256-byte aligned allocations); with odd n, thread 0 of block 0 also
+// takes the last element.  Every thread's share is fixed, so sums stay
+// deterministic.
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
 __global__ void __launch_bounds__(kBlock) k_dot(const double* __restrict__ a,
                                                 const double* __restrict__ b, int64_t n,
                                                 double* __restrict__ red, unsigned* ticket,
                                                 double* __restrict__ out, Gate g) {
   if (gate_closed(g)) return;
+  const double2* a2 = reinterpret_cast<const double2*>(a);
+  const double2* b2 = reinterpret_cast<const double2*>(b);
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    acc += a[i] * b[i];
+  for (int64_t i = gtid(); i < (n >> 1); i += gstride()) {
+    const double2 u = a2[i], v = b2[i];
+    acc = fma(u.x, v.x, acc);
+    acc = fma(u.y, v.y, acc);
+  }
+  if ((n & 1) && gtid() == 0) acc = fma(a[n - 1], b[n - 1], acc);
   double tot;
   if (finish_sum(acc, red, ticket, &tot)) *out = tot;
 }
@@ -125,10 +137,15 @@ __global__ void __launch_bounds__(kBlock) k_cg_alpha(const double* __restrict__ 
                                                      double* __restrict__ red, unsigned* ticket,
                                                      CgState* st) {
   if (st->done) return;
+  const double2* p2 = reinterpret_cast<const double2*>(p);
+  const double2* q2 = reinterpret_cast<const double2*>(q);
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    acc += p[i] * q[i];
+  for (int64_t i = gtid(); i < (n >> 1); i += gstride()) {
+    const double2 u = p2[i], v = q2[i];
+    acc = fma(u.x, v.x, acc);
+    acc = fma(u.y, v.y, acc);
+  }
+  if ((n & 1) && gtid() == 0) acc = fma(p[n - 1], q[n - 1], acc);
   double tot;
   if (finish_sum(acc, red, ticket, &tot)) {
     st->pq = tot;
@@ -158,13 +175,28 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(double* __restrict__ x,
                                                       CgState* st) {
   if (st->done) return;
   const double alpha = st->alpha;
+  double2* x2 = reinterpret_cast<double2*>(x);
+  double2* r2 = reinterpret_cast<double2*>(r);
+  const double2* p2 = reinterpret_cast<const double2*>(p);
+  const double2* q2 = reinterpret_cast<const double2*>(q);
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
-    r[i] = ri;
-    acc += ri * ri;
+  for (int64_t i = gtid(); i < (n >> 1); i += gstride()) {
+    double2 xv = x2[i], rv = r2[i];
+    const double2 pv = p2[i], qv = q2[i];
+    xv.x = fma(alpha, pv.x, xv.x);
+    xv.y = fma(alpha, pv.y, xv.y);
+    rv.x = fma(-alpha, qv.x, rv.x);
+    rv.y = fma(-alpha, qv.y, rv.y);
+    x2[i] = xv;
+    r2[i] = rv;
+    acc = fma(rv.x, rv.x, acc);
+    acc = fma(rv.y, rv.y, acc);
+  }
+  if ((n & 1) && gtid() == 0) {
+    x[n - 1] = fma(alpha, p[n - 1], x[n - 1]);
+    const double ri = fma(-alpha, q[n - 1], r[n - 1]);
+    r[n - 1] = ri;
+    acc = fma(ri, ri, acc);
   }
   double tot;
   if (finish_sum(acc, red, ticket, &tot)) {
@@ -204,13 +236,23 @@ __global__ void __launch_bounds__(kBlock) k_cg_reliable(double* __restrict__ r,
                                                         double* __restrict__ red, unsigned* ticket,
                                                         CgState* st) {
   if (st->done || !st->need) return;
+  double2* r2 = reinterpret_cast<double2*>(r);
+  double2* t2 = reinterpret_cast<double2*>(t);
+  const double2* b2 = reinterpret_cast<const double2*>(b);
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double ri = b[i] - t[i];
-    r[i] = ri;
-    t[i] = 0.0;
-    acc += ri * ri;
+  for (int64_t i = gtid(); i < (n >> 1); i += gstride()) {
+    const double2 bv = b2[i], tv = t2[i];
+    const double2 rv = make_double2(bv.x - tv.x, bv.y - tv.y);
+    r2[i] = rv;
+    t2[i] = make_double2(0.0, 0.0);
+    acc = fma(rv.x, rv.x, acc);
+    acc = fma(rv.y, rv.y, acc);
+  }
+  if ((n & 1) && gtid() == 0) {
+    const double ri = b[n - 1] - t[n - 1];
+    r[n - 1] = ri;
+    t[n - 1] = 0.0;
+    acc = fma(ri, ri, acc);
   }
   double tot;
   if (finish_sum(acc, red, ticket, &tot)) {
@@ -245,9 +287,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_keep_best(const double* __restric
                                                          double* __restrict__ x_best, int64_t n,
                                                          const CgState* st) {
   if (!st->improved) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x_best[i] = x[i];
+  const double2* a2 = reinterpret_cast<const double2*>(x);
+  double2* b2 = reinterpret_cast<double2*>(x_best);
+  for (int64_t i = gtid(); i < (n >> 1); i += gstride()) b2[i] = a2[i];
+  if ((n & 1) && gtid() == 0) x_best[n - 1] = x[n - 1];
 }
 
 // p = r + beta p ; q = 0
@@ -257,10 +300,20 @@ __global__ void __launch_bounds__(kBlock) k_cg_direction(double* __restrict__ p,
                                                          const CgState* st) {
   if (st->done) return;
   const double beta = st->rr / st->rr_old;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    p[i] = r[i] + beta * p[i];
-    q[i] = 0.0;
+  double2* p2 = reinterpret_cast<double2*>(p);
+  double2* q2 = reinterpret_cast<double2*>(q);
+  const double2* r2 = reinterpret_cast<const double2*>(r);
+  for (int64_t i = gtid(); i < (n >> 1); i += gstride()) {
+    const double2 rv = r2[i];
+    double2 pv = p2[i];
+    pv.x = fma(beta, pv.x, rv.x);
+    pv.y = fma(beta, pv.y, rv.y);
+    p2[i] = pv;
+    q2[i] = make_double2(0.0, 0.0);
+  }
+  if ((n & 1) && gtid() == 0) {
+    p[n - 1] = fma(beta, p[n - 1], r[n - 1]);
+    q[n - 1] = 0.0;
   }
 }
 
@@ -317,7 +370,7 @@ __global__ void k_set_state(CgState* st, double tol, int max_iter, int mixed, do
 
 }  // namespace
 
-static int vec_grid(const Plan& P, int64_t n) { return stream_grid(P, n, kBlock, 4); }
+static int vec_grid(const Plan& P, int64_t n) { return stream_grid(P, (n + 1) / 2, kBlock, 8); }
 
 void enqueue_dot(const Plan& P, cudaStream_t st, const double* a, const double* b, int64_t n,
                  double* out) {

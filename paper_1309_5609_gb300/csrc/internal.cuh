@@ -11,6 +11,9 @@
 //   map32    f32 [n_pix][4]   map in the mixed-precision iteration
 //   map64    f64 [n_pix][4]   map in float64 passes
 //   nvalid   int32 [n_b]      valid samples per baseline (gauge)
+//   lid      uint16 [n_pad]   mixed plans: chunk-local pixel rank of each sample
+//   upix     int32 [n_pad]    mixed plans: sorted distinct pixels of each chunk
+//   ucnt     int32 [chunks]   mixed plans: distinct pixels per chunk
 //   CG vectors f64 [n_u]      x, r, p, q, b, t (n_u = n_o * n_b)
 #pragma once
 
@@ -129,7 +132,29 @@ struct Plan {
   int accurate_df;          // mixed plans: accurate passes in double-float (1) or float64 (0)
   int stream_mode;          // mixed operator: 0 = direct vector loads, 1 = TMA-staged pipeline
   int refresh_max;          // mixed plans: float64 residual at least every this many iterations
+  int layout;               // mixed operator: 0 = time-ordered pixels, 1 = chunk-local index
+  int rescan_dedup;         // float32 rescan: reuse the map value of a repeated pixel
+  // chunk-local pixel index (chunked.cu)
+  uint16_t* lid;
+  int32_t* upix;
+  int32_t* ucnt;
+  int ck_C;                 // samples per chunk
+  int64_t ck_nchunks;
+  int ck_umax;              // most distinct pixels in one chunk
+  int ck_ustride;           // shared-array stride (>= ck_umax)
+  int ck_threads;           // threads per block of the chunked passes
+  int ck_bin_blocks;        // resident blocks per SM (occupancy)
+  int ck_rescan_blocks;
 };
+
+// chunked.cu
+constexpr int kChunkMin = 2048, kChunkMax = 16384;
+int ck_default_chunk(int64_t n_t, int num_sms);
+cudaError_t ck_build(Plan& P, int C, unsigned long long* umax);
+cudaError_t ck_finish(Plan& P, int64_t umax);
+bool ck_ready(const Plan& P);
+void launch_bin_ck(const Plan& P, cudaStream_t st, const double* x, Gate g);
+void launch_rescan_ck(const Plan& P, cudaStream_t st, const double* x, double* out, Gate g);
 
 // kernels launched by one CG iteration (for the launch counter)
 int kernels_per_iteration(const Plan& P);

@@ -1,0 +1,165 @@
+"""Float32 operator over the chunk-local pixel index against the oracle and
+against the time-ordered layout: every kind set, every chunk length, ragged
+tails, flagged and cut samples, and chunks where nearly every sample has its own
+pixel (the largest shared arrays)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1309_5609_gb300 as ds
+from synth import ScanParams, make_problem
+from synth.problems import Problem
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+IQU_SKY = ScanParams(f_samp=5.0, sidereal_day=7200.0)
+
+CASES = [
+    # kinds, nside, n_t, L, flag_frac, scan
+    (("q", "u"), 64, 2048 * 9 + 3, 97, 0.0, ScanParams()),
+    (("I", "q", "u"), 32, 40_001, 50, 0.05, ScanParams()),
+    (("iqu",), 8, 120_000, 64, 0.03, IQU_SKY),
+    (("I",), 16, 10_007, 1, 0.0, ScanParams()),
+    (("u", "q", "I"), 16, 30_011, 40, 0.02, ScanParams()),
+]
+IDS = ["qu_ragged", "Iqu_flags", "iqu_flags", "I_L1", "generic3"]
+
+
+def rel_err(got, ref):
+    scale = max(1e-300, float(np.sqrt(np.mean(ref ** 2))))
+    return float(np.sqrt(np.mean((got - ref) ** 2))) / scale
+
+
+def random_pixel_problem(n_t, nside, kinds, L, seed):
+    """Every sample on an independent uniform pixel: almost no pixel repeats
+    within a chunk."""
+    g = torch.Generator().manual_seed(seed)
+    npix = 12 * nside * nside
+    pix = torch.randint(0, npix, (n_t,), generator=g, dtype=torch.int64).to(torch.int32)
+    psi = torch.rand(n_t, generator=g, dtype=torch.float64) * math.pi
+    c32 = torch.cos(2 * psi).float()
+    s32 = torch.sin(2 * psi).float()
+    y = torch.randn((len(kinds), n_t), generator=g, dtype=torch.float64)
+    sky = torch.zeros((3, npix), dtype=torch.float64)
+    return Problem(n_t, nside, tuple(kinds), L, pix, c32, s32, y, sky)
+
+
+def check_apply(prob, chunk, layout=1, reps=2, tune=None):
+    d = prob.numpy()
+    op = oracle.make_plan(d["pix"], d["c"], d["s"], d["valid"], prob.nside, prob.kinds,
+                          prob.baseline_len)
+    gp = prob.to(DEV)
+    plan = ds.destripe_plan(gp.pix, gp.c32, gp.s32, gp.valid, nside=prob.nside,
+                            kinds=prob.kinds, baseline_len=prob.baseline_len, precision="mixed")
+    ds.destripe_tune(plan, "layout", layout)
+    if chunk is not None:
+        ds.destripe_tune(plan, "chunk", chunk)
+    for k, v in (tune or {}).items():
+        ds.destripe_tune(plan, k, v)
+    rng = np.random.default_rng(17)
+    out = []
+    for _ in range(reps):  # repeated: the pixel sums must come back cleared
+        x = rng.standard_normal(plan.n_u)
+        Ax = torch.empty(plan.n_u, dtype=torch.float64, device=DEV)
+        ds.destripe_apply_A(plan, torch.from_numpy(x).to(DEV), Ax)
+        ref = oracle.apply_A(op, x)
+        got = Ax.cpu().numpy()
+        assert rel_err(got, ref) < 1e-5 or np.abs(ref).max() < 1e-9, rel_err(got, ref)
+        out.append(got)
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("chunk", [2048, 4096, 8192, 16384])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_chunked_operator_parity(case, chunk):
+    kinds, nside, n_t, L, ff, scan = case
+    prob = make_problem(n_t, nside, kinds, baseline_len=L, seed=21, scan=scan, flag_frac=ff,
+                        flag_mean_len=200, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
+    check_apply(prob, chunk)
+
+
+@pytest.mark.parametrize("kinds", [("q", "u"), ("iqu",), ("I",)])
+def test_chunked_operator_with_distinct_pixels(kinds):
+    # nside 128: 196 608 pixels, so a 16384-sample chunk holds ~15 700 distinct ones
+    prob = random_pixel_problem(16384 * 3 + 11, 128, kinds, 7, seed=3)
+    for chunk in (2048, 16384):
+        check_apply(prob, chunk)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_rescan_reusing_repeated_pixels(case):
+    kinds, nside, n_t, L, ff, scan = case
+    prob = make_problem(n_t, nside, kinds, baseline_len=L, seed=22, scan=scan, flag_frac=ff,
+                        flag_mean_len=200, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
+    check_apply(prob, None, layout=0, tune={"rescan_dedup": 1})
+
+
+def test_layouts_agree():
+    prob = make_problem(100_000, 64, ("I", "q", "u"), baseline_len=300, seed=4)
+    a = check_apply(prob, None, layout=1, reps=1)[0]
+    b = check_apply(prob, None, layout=0, reps=1)[0]
+    assert rel_err(a, b) < 2e-6
+
+
+def test_plans_with_different_chunk_sizes_coexist():
+    # the shared-memory limit of a kernel is shared by all plans: a plan built
+    # after another (with smaller shared arrays) must not break the first one
+    prob = make_problem(200_000, 64, ("q", "u"), baseline_len=100, seed=9)
+    gp = prob.to(DEV)
+    plans = []
+    for chunk in (16384, 2048):
+        pl = ds.destripe_plan(gp.pix, gp.c32, gp.s32, None, nside=64, kinds=("q", "u"),
+                              baseline_len=100, precision="mixed")
+        ds.destripe_tune(pl, "chunk", chunk)
+        ds.destripe_tune(pl, "layout", 1)
+        plans.append(pl)
+    x = torch.randn(plans[0].n_u, dtype=torch.float64, device=DEV)
+    outs = []
+    for pl in plans:
+        out = torch.empty_like(x)
+        ds.destripe_apply_A(pl, x, out)
+        outs.append(out.cpu().numpy())
+        pl.close()
+    assert rel_err(outs[0], outs[1]) < 2e-6
+
+
+def test_chunked_solve_matches_oracle():
+    prob = make_problem(300_000, 32, ("q", "u"), baseline_len=250, seed=8, flag_frac=0.01,
+                        flag_mean_len=300)
+    d = prob.numpy()
+    op = oracle.make_plan(d["pix"], d["c"], d["s"], d["valid"], prob.nside, prob.kinds,
+                          prob.baseline_len)
+    ref = oracle.destripe(op, prob.y.float().double().numpy(), tol=1e-10)
+    gp = prob.to(DEV)
+    for chunk in (2048, 8192):
+        plan = ds.destripe_plan(gp.pix, gp.c32, gp.s32, gp.valid, nside=prob.nside,
+                                kinds=prob.kinds, baseline_len=prob.baseline_len,
+                                precision="mixed")
+        ds.destripe_tune(plan, "chunk", chunk)
+        a = torch.zeros(plan.n_u, dtype=torch.float64, device=DEV)
+        st, it, rel = ds.destripe_solve(plan, gp.y.float().contiguous(), a, tol=1e-10)
+        plan.close()
+        assert st == ds.DS_OK, (st, it, rel)
+        assert np.abs(a.cpu().numpy() - ref["a"]).max() < 1e-4
+
+
+def test_tune_rejects_bad_chunks():
+    prob = make_problem(5000, 8, ("q", "u"), baseline_len=50, seed=1)
+    gp = prob.to(DEV)
+    plan = ds.destripe_plan(gp.pix, gp.c32, gp.s32, None, nside=8, kinds=("q", "u"),
+                            baseline_len=50, precision="mixed")
+    for bad in (1000, 1024, 32768, 3000):
+        with pytest.raises(ds.DestripeError) as e:
+            ds.destripe_tune(plan, "chunk", bad)
+        assert e.value.status == ds.DS_EINVAL
+    plan.close()
+    p64 = ds.destripe_plan(gp.pix, gp.c32, gp.s32, None, nside=8, kinds=("q", "u"),
+                           baseline_len=50, precision="fp64")
+    with pytest.raises(ds.DestripeError) as e:
+        ds.destripe_tune(p64, "layout", 1)
+    assert e.value.status == ds.DS_ESTATE
+    p64.close()
