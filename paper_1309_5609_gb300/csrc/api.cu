@@ -56,7 +56,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   for (void* d : dev)
@@ -257,6 +257,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   DS_ALLOC(bins, P->npix * 4);
   if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(bins32, P->npix * 4);
   if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(maplo, P->npix * 4);
+  if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(xdf, P->n_u);
   DS_ALLOC(map32, P->npix * 4);
   DS_ALLOC(map64, P->npix * 4);
   DS_ALLOC(nvalid, P->n_b);
@@ -413,7 +414,7 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
     done = P.h_state->done != 0;
     accurate = P.h_state->accurate != 0;
     P.graph_launches += 1;
-    P.launches += (int64_t)P.graph_iters * kernels_per_iteration(P);
+    P.launches += (int64_t)P.graph_iters * kernels_per_iteration(P, acc_now);
     const int ran = P.h_state->iter - iter_before;
     iter_before = P.h_state->iter;
     P.iterations += ran;

@@ -361,6 +361,7 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
                    Gate g, cudaEvent_t* ev) {
   if (fp64 && use_df(P)) {
     if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+    launch_split_df(P, st, x, g);
     launch_bin_df(P, st, x, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     launch_pixel_solve_df(P, st, nullptr, g);
@@ -414,6 +415,7 @@ void enqueue_rhs(const Plan& P, cudaStream_t st, const void* y, double* out, Gat
 void enqueue_map(const Plan& P, cudaStream_t st, const void* y, const double* a, double* out_map) {
   Gate g{nullptr, nullptr};
   if (use_df(P)) {
+    if (a != nullptr) launch_split_df(P, st, a, g);
     launch_bin_df(P, st, a, static_cast<const float*>(y), g);
     launch_pixel_solve_df(P, st, out_map, g);
     return;

@@ -34,12 +34,51 @@ void with_kindset(int ks, F&& f) {
   }
 }
 
-// bins[p] += sum_o w_o(t) z_o(t), z = x[o][t/L] (ZY false) or y[o][t] - a[o][t/L] (ZY true)
+// x[i] -> (hi, lo) with hi = x rounded to float32, lo = the rest rounded to float32
+__global__ void __launch_bounds__(kBlock) k_split_df(const double* __restrict__ x,
+                                                     float2* __restrict__ xs, int64_t n, Gate g) {
+  if (gate_closed(g)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const df d = df_from_double(x[i]);
+    xs[i] = make_float2(d.hi, d.lo);
+  }
+}
+
+// y[o][4v .. 4v + 3] of every output: one 16-byte load per output when the rows
+// are 16-byte aligned (n_t a multiple of 4) and the 4 samples are in range
+template <int NO>
+__device__ __forceinline__ void load_y4(const float* __restrict__ y, int n_o, int64_t n_t,
+                                        int64_t v, float (&yv)[NO][4]) {
+  const int64_t t0 = v << 2;
+  const bool vec = ((n_t & 3) == 0) && t0 + 4 <= n_t;
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    if (o >= n_o) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) yv[o][k] = 0.f;
+    } else if (vec) {
+      const float4 q = __ldcs(reinterpret_cast<const float4*>(y + (int64_t)o * n_t) + v);
+      yv[o][0] = q.x; yv[o][1] = q.y; yv[o][2] = q.z; yv[o][3] = q.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) yv[o][k] = t0 + k < n_t ? y[(int64_t)o * n_t + t0 + k] : 0.f;
+    }
+  }
+}
+
+__device__ __forceinline__ df df_load(const float2* __restrict__ xs, int64_t i) {
+  const float2 v = __ldg(xs + i);
+  return df{v.x, v.y};
+}
+
+// bins[p] += sum_o w_o(t) z_o(t), z = x[o][t/L] (ZY false) or y[o][t] - a[o][t/L] (ZY true);
+// the baselines come split into double-float pairs (xs, NULL for none)
 template <int KS, bool ZY>
 __global__ void __launch_bounds__(kBlock) k_bin_df(const int32_t* __restrict__ pix,
                                                    const float* __restrict__ cc,
                                                    const float* __restrict__ ss,
-                                                   const double* __restrict__ x,
+                                                   const float2* __restrict__ x,
                                                    const float* __restrict__ y,
                                                    double* __restrict__ bins, int64_t n_t,
                                                    int64_t L, int64_t n_b, KindsArg kk, Gate g) {
@@ -53,13 +92,15 @@ __global__ void __launch_bounds__(kBlock) k_bin_df(const int32_t* __restrict__ p
     int p[4];
     float c[4], s[4];
     load4_df(pix, cc, ss, v, n_t, p, c, s);
+    float yv[NO][4];
+    if constexpr (ZY) load_y4<NO>(y, n_o, n_t, v, yv);
     const int64_t t0 = v << 2;
     int64_t b = t0 / L;
     int64_t bend = (b + 1) * L;
     df zb[NO];
 #pragma unroll
     for (int o = 0; o < NO; ++o)
-      zb[o] = (o < n_o && x != nullptr) ? df_from_double(__ldg(x + o * n_b + b)) : df{0.f, 0.f};
+      zb[o] = (o < n_o && x != nullptr) ? df_load(x, o * n_b + b) : df{0.f, 0.f};
     df acc[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) acc[j] = df{0.f, 0.f};
@@ -73,7 +114,7 @@ __global__ void __launch_bounds__(kBlock) k_bin_df(const int32_t* __restrict__ p
         bend += L;
 #pragma unroll
         for (int o = 0; o < NO; ++o)
-          zb[o] = (o < n_o && x != nullptr) ? df_from_double(__ldg(x + o * n_b + b)) : df{0.f, 0.f};
+          zb[o] = (o < n_o && x != nullptr) ? df_load(x, o * n_b + b) : df{0.f, 0.f};
       }
       if (p[k] < 0) continue;
       df w[NC];
@@ -83,7 +124,7 @@ __global__ void __launch_bounds__(kBlock) k_bin_df(const int32_t* __restrict__ p
       for (int o = 0; o < NO; ++o) {
         if (o < n_o) {
           df z = zb[o];
-          if constexpr (ZY) z = df_sub(df_make(y[(int64_t)o * n_t + t]), z);
+          if constexpr (ZY) z = df_sub(df_make(yv[o][k]), z);
           row_bin_df<NC>(K::kind(o, kk), c[k], s[k], z, w);
         }
       }
@@ -152,7 +193,7 @@ template <int KS, bool ZY>
 __global__ void __launch_bounds__(kBlock) k_rescan_df(const int32_t* __restrict__ pix,
                                                       const float* __restrict__ cc,
                                                       const float* __restrict__ ss,
-                                                      const double* __restrict__ x,
+                                                      const float2* __restrict__ x,
                                                       const float* __restrict__ y,
                                                       const float* __restrict__ map_hi,
                                                       const float* __restrict__ map_lo,
@@ -176,10 +217,14 @@ __global__ void __launch_bounds__(kBlock) k_rescan_df(const int32_t* __restrict_
       int p[4];
       float c[4], s[4];
       load4_df(pix, cc, ss, v, n_t, p, c, s);
+      // the map pair is gathered once per run of equal pixels in the thread's samples
       df m[4][NC];
+      bool dup[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dup[k] = k > 0 && p[k] >= 0 && p[k] == p[k - 1];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        if (p[k] >= 0) {
+        if (p[k] >= 0 && !dup[k]) {
           const float4 h = __ldg(reinterpret_cast<const float4*>(map_hi) + p[k]);
           const float4 l = __ldg(reinterpret_cast<const float4*>(map_lo) + p[k]);
           const float hh[4] = {h.x, h.y, h.z, h.w}, ll[4] = {l.x, l.y, l.z, l.w};
@@ -190,13 +235,21 @@ __global__ void __launch_bounds__(kBlock) k_rescan_df(const int32_t* __restrict_
           for (int j = 0; j < NC; ++j) m[k][j] = df{0.f, 0.f};
         }
       }
+#pragma unroll
+      for (int k = 1; k < 4; ++k)
+        if (dup[k]) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) m[k][j] = m[k - 1][j];
+        }
+      float yv[NO][4];
+      if constexpr (ZY) load_y4<NO>(y, n_o, n_t, v, yv);
       const int64_t t0 = v << 2;
       int64_t b = t0 / L;
       int64_t bend = (b + 1) * L;
       df zb[NO];
 #pragma unroll
       for (int o = 0; o < NO; ++o)
-        zb[o] = (o < n_o && x != nullptr) ? df_from_double(__ldg(x + o * n_b + b)) : df{0.f, 0.f};
+        zb[o] = (o < n_o && x != nullptr) ? df_load(x, o * n_b + b) : df{0.f, 0.f};
       key = (int)b;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -214,14 +267,14 @@ __global__ void __launch_bounds__(kBlock) k_rescan_df(const int32_t* __restrict_
           key = (int)b;
 #pragma unroll
           for (int o = 0; o < NO; ++o)
-            zb[o] = (o < n_o && x != nullptr) ? df_from_double(__ldg(x + o * n_b + b)) : df{0.f, 0.f};
+            zb[o] = (o < n_o && x != nullptr) ? df_load(x, o * n_b + b) : df{0.f, 0.f};
         }
         if (p[k] < 0) continue;
 #pragma unroll
         for (int o = 0; o < NO; ++o) {
           if (o < n_o) {
             df z = zb[o];
-            if constexpr (ZY) z = df_sub(df_make(y[(int64_t)o * n_t + t]), z);
+            if constexpr (ZY) z = df_sub(df_make(yv[o][k]), z);
             acc[o] = df_add(acc[o], df_sub(z, row_dot_df<NC>(K::kind(o, kk), c[k], s[k], m[k])));
           }
         }
@@ -235,15 +288,23 @@ __global__ void __launch_bounds__(kBlock) k_rescan_df(const int32_t* __restrict_
 
 // ---- launchers (mixed-precision plans only: y is float32) --------------------------
 
+// Splits the baselines of an accurate pass into P.xdf (once per pass: the
+// per-sample kernels then read float32 pairs and do no float64 work per sample).
+void launch_split_df(const Plan& P, cudaStream_t st, const double* x, Gate g) {
+  k_split_df<<<stream_grid(P, P.n_u, kBlock, 8), kBlock, 0, st>>>(x, P.xdf, P.n_u, g);
+}
+
+// x: baselines already split by launch_split_df (then P.xdf is read), or NULL
 void launch_bin_df(const Plan& P, cudaStream_t st, const double* x, const float* y, Gate g) {
   const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
+  const float2* xs = x != nullptr ? P.xdf : nullptr;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (y != nullptr)
-      k_bin_df<KS, true><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, y, P.bins, P.n_t, P.L,
+      k_bin_df<KS, true><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, xs, y, P.bins, P.n_t, P.L,
                                                    P.n_b, P.kinds, g);
     else
-      k_bin_df<KS, false><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, nullptr, P.bins, P.n_t,
+      k_bin_df<KS, false><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, xs, nullptr, P.bins, P.n_t,
                                                     P.L, P.n_b, P.kinds, g);
   });
 }
@@ -264,13 +325,14 @@ void launch_pixel_solve_df(const Plan& P, cudaStream_t st, double* out_map, Gate
 void launch_rescan_df(const Plan& P, cudaStream_t st, const double* x, const float* y,
                       double* out, Gate g) {
   const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
+  const float2* xs = x != nullptr ? P.xdf : nullptr;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (y != nullptr)
-      k_rescan_df<KS, true><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, y, P.map32, P.maplo,
+      k_rescan_df<KS, true><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, xs, y, P.map32, P.maplo,
                                                       out, P.n_t, P.L, P.n_b, P.kinds, g);
     else
-      k_rescan_df<KS, false><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, x, nullptr, P.map32,
+      k_rescan_df<KS, false><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, xs, nullptr, P.map32,
                                                        P.maplo, out, P.n_t, P.L, P.n_b, P.kinds, g);
   });
 }

@@ -383,8 +383,11 @@ void enqueue_gauge(const Plan& P, cudaStream_t st, double* a) {
   k_gauge_apply<<<vec_grid(P, P.n_b), kBlock, 0, st>>>(a, P.nvalid, P.n_b, P.kinds, P.scal + 4);
 }
 
-int kernels_per_iteration(const Plan& P) {
-  return P.desc.precision == DS_PREC_MIXED ? 11 : 6;
+// accurate: the iteration applies the operator in the accurate arithmetic
+int kernels_per_iteration(const Plan& P, bool accurate) {
+  if (P.desc.precision != DS_PREC_MIXED) return 6;
+  const bool df = P.accurate_df && P.maplo != nullptr;  // + the baseline split kernel
+  return 11 + (df ? 1 : 0) + (df && accurate ? 1 : 0);
 }
 
 // One CG iteration (gated by state->done), used both directly and under capture.

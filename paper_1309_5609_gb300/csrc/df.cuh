@@ -59,7 +59,29 @@ __device__ __forceinline__ df df_from_double(double d) {
   return df{hi, __double2float_rn(d - (double)hi)};
 }
 
-__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+// float32 -> float64 by re-encoding the IEEE 754 fields with integer operations
+// (exponent rebiased by 1023 - 127, the 23 fraction bits moved to the top of the
+// 52): exact for normal numbers, infinities and NaNs; float32 subnormals (below
+// 1.2e-38) become signed zero.  It keeps the conversions off GB300's float64
+// pipe, which the run flushes of the accurate passes would otherwise saturate.
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  unsigned hi = sign, lo = 0u;
+  if (e == 0xFFu) {
+    hi = sign | 0x7FF00000u | (m >> 3);
+    lo = m << 29;
+  } else if (e != 0u) {
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// hi + lo in float64: one float64 addition (exact, the pair holds <= 48 bits)
+__device__ __forceinline__ double df_to_double(df x) { return f64_of_f32(x.hi) + f64_of_f32(x.lo); }
 
 __device__ __forceinline__ df df_shfl_down(df x, int d) {
   return df{__shfl_down_sync(0xffffffffu, x.hi, d), __shfl_down_sync(0xffffffffu, x.lo, d)};

@@ -10,6 +10,8 @@
 //   bins     f64 [n_pix][4]   pixel sums, kept at zero between uses
 //   map32    f32 [n_pix][4]   map in the mixed-precision iteration
 //   map64    f64 [n_pix][4]   map in float64 passes
+//   xdf      f32x2 [n_u]      mixed plans: the baselines of an accurate pass as
+//                             double-float pairs (split once per pass)
 //   nvalid   int32 [n_b]      valid samples per baseline (gauge)
 //   lid      uint16 [n_pad]   mixed plans: chunk-local pixel rank of each sample
 //   upix     int32 [n_pad]    mixed plans: sorted distinct pixels of each chunk
@@ -97,6 +99,7 @@ struct Plan {
   float* bins32;      // float32 pixel sums [n_pix][4] for the mixed operator (vector atomics)
   float* map32;
   float* maplo;       // low parts of the double-float map [n_pix][4] (mixed plans)
+  float2* xdf;        // baselines split into double-float pairs [n_u] (mixed plans)
   double* map64;
   int32_t* nvalid;
   double *x, *r, *p, *q, *b, *t;
@@ -157,7 +160,7 @@ void launch_bin_ck(const Plan& P, cudaStream_t st, const double* x, Gate g);
 void launch_rescan_ck(const Plan& P, cudaStream_t st, const double* x, double* out, Gate g);
 
 // kernels launched by one CG iteration (for the launch counter)
-int kernels_per_iteration(const Plan& P);
+int kernels_per_iteration(const Plan& P, bool accurate);
 
 // ---- launch helpers ---------------------------------------------------------
 int stream_grid(const Plan& P, int64_t work_items, int block, int per_sm);
@@ -169,6 +172,7 @@ void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_m
 void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out, Gate g);
 void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g);
 // apply_df.cu: accurate passes of mixed plans in double-float arithmetic
+void launch_split_df(const Plan& P, cudaStream_t st, const double* x, Gate g);
 void launch_bin_df(const Plan& P, cudaStream_t st, const double* x, const float* y, Gate g);
 void launch_pixel_solve_df(const Plan& P, cudaStream_t st, double* out_map, Gate g);
 void launch_rescan_df(const Plan& P, cudaStream_t st, const double* x, const float* y,
