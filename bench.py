@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-samples", type=int, default=1_000_000)
     ap.add_argument("--oracle-iters", type=int, default=20)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workload: keep the default launch shape")
+    ap.add_argument("--no-fp64-comparator", action="store_true",
+                    help="batched workload: skip the sequential float64 comparator")
     ap.add_argument("--tune", default="",
                     help="plan tuning knobs for the single-problem workloads, key=value,...")
     return ap.parse_args()
@@ -458,11 +462,22 @@ def run_batch(args):
     cfgs = batch_configs(64, seed=1003)
     probs = [make_problem(device=dev, y_dtype=torch.float32, keep_f64_trig=False, **c) for c in cfgs]
 
-    def step():
+    shape, tuning = {}, None
+
+    def step(tune=False):
+        nonlocal tuning
         plans = [ds.destripe_plan(p.pix, p.c32, p.s32, None, nside=p.nside, kinds=p.kinds,
                                   baseline_len=p.baseline_len, precision="mixed") for p in probs]
         b = ds.destripe_batch_create(len(probs))
+        for k, v in shape.items():
+            ds.destripe_batch_tune(b, k, v)
         slots = [ds.destripe_batch_add(b, pl, p.y, tol=args.tol) for pl, p in zip(plans, probs)]
+        if tune:
+            # the autotuner's trials are CG iterations of this job; its shape is
+            # kept for the timed jobs
+            tuning = ds.destripe_batch_autotune(b)
+            shape.update({k: tuning[k] for k in ("tile_samples", "tile_pixels",
+                                                 "tile_unknowns", "blocks_per_sm")})
         while ds.destripe_batch_step(b, 8) > 0:
             pass
         iters, stats = [], []
@@ -477,8 +492,8 @@ def run_batch(args):
             pl.close()
         return iters, stats, launches
 
-    for _ in range(args.warmup):
-        step()
+    for w in range(args.warmup):
+        step(tune=(w == 0 and not args.no_autotune))
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     units, launches, iters_all, ok = 0.0, 0, [], True
@@ -508,6 +523,24 @@ def run_batch(args):
     ev1.record()
     torch.cuda.synchronize()
     seq_ms = ev0.elapsed_time(ev1)
+    # the plain float64 single-problem path on the same problems
+    seq64 = None
+    if not args.no_fp64_comparator:
+        ev0.record()
+        s64_units = 0.0
+        for p in probs:
+            pl = ds.destripe_plan(p.pix, p.c32, p.s32, None, nside=p.nside, kinds=p.kinds,
+                                  baseline_len=p.baseline_len, precision="fp64")
+            a = torch.empty(pl.n_u, dtype=torch.float64, device=dev)
+            st, it, rel = ds.destripe_solve(pl, p.y.double().contiguous(), a, tol=args.tol)
+            s64_units += p.n_t * it
+            pl.close()
+        ev1.record()
+        torch.cuda.synchronize()
+        s64_ms = ev0.elapsed_time(ev1)
+        seq64 = {"value": s64_units / (s64_ms / 1e3), "unit": UNIT, "ms": s64_ms,
+                 "note": "float64 plans, one solve after another (y promoted to float64 "
+                         "inside the timed region)"}
     peak, peak_kind = peaks()
     value = units / (t_ms / 1e3)
     achieved = 2 * BYTES_PER_SAMPLE_PASS * value / 1e9
@@ -527,6 +560,8 @@ def run_batch(args):
             "all_converged": bool(ok), "gpu_launches": int(launches),
             "sequential_single_solves": {"value": seq_units / (seq_ms / 1e3), "unit": UNIT,
                                          "ms": seq_ms},
+            "sequential_fp64_single_solves": seq64,
+            "autotune": tuning, "launch_shape": shape or "defaults",
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -253,7 +253,20 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value);
  *     slot as of the last step.
  * destripe_batch_retire: gauge-fixes the slot's baselines, copies them to d_a (may be
  *     NULL), frees the slot; returns the problem's solve status (DS_OK, DS_ENOCONV, ...).
- * destripe_batch_tune:   "tile_samples", "tile_unknowns", "blocks_per_sm" (autotuner).
+ * destripe_batch_tune:   launch shape of the batched kernels: "tile_samples" (samples per
+ *     work tile of the per-sample passes, 4096..2^24, default 16384), "tile_pixels"
+ *     (pixels per tile of the pixel solve, default 16384), "tile_unknowns" (unknowns
+ *     per tile of the CG vector kernels, default 4096), "blocks_per_sm" (1..32,
+ *     default 8).  Re-captures the iteration graph at the next step.
+ * destripe_batch_autotune: picks the launch shape for the problems in the batch
+ *     (no counterpart in the paper).  Coordinate descent over blocks_per_sm
+ *     {4, 8, 16}, tile_samples {8192 .. 65536}, tile_pixels {4096, 16384, 65536} and
+ *     tile_unknowns {2048, 4096, 16384}, starting from the shape in force: each trial
+ *     replays the iteration graph once (8 real CG iterations of every running
+ *     problem), times it with CUDA events and scores sample-iterations per second; a
+ *     candidate must beat the best by 2%.  At most max_trials timed replays (<= 0: 12).
+ *     The chosen shape stays in force; *out (may be NULL) reports it.  Problems that
+ *     converge during tuning stop as in destripe_batch_step.  Synchronises the stream.
  * destripe_batch_info:   slots in use and kernels launched so far. */
 typedef struct ds_batch_s* ds_batch_t;
 
@@ -266,6 +279,19 @@ ds_status destripe_batch_slot_status(ds_batch_t batch, int32_t slot, int32_t* do
 ds_status destripe_batch_retire(ds_batch_t batch, int32_t slot, double* d_a, int32_t* iters,
                                 double* rel_resid);
 ds_status destripe_batch_tune(ds_batch_t batch, const char* key, double value);
+
+typedef struct {
+  int32_t tile_samples;   /* chosen launch shape */
+  int32_t tile_pixels;
+  int32_t tile_unknowns;
+  int32_t blocks_per_sm;
+  int32_t trials;         /* timed graph replays */
+  int32_t pad;
+  double rate;            /* sample-iterations per second of the chosen shape */
+  double rate_initial;    /* ... of the shape in force before the call */
+} ds_batch_tuning;
+
+ds_status destripe_batch_autotune(ds_batch_t batch, int32_t max_trials, ds_batch_tuning* out);
 ds_status destripe_batch_info(ds_batch_t batch, int32_t* n_slots_used, int64_t* kernel_launches);
 void destripe_batch_destroy(ds_batch_t batch);
 

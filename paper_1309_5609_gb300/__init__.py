@@ -23,7 +23,7 @@ __all__ = [
     "destripe_run_host", "destripe_profile", "destripe_bin_noalloc", "destripe_tune",
     "Batch", "destripe_batch_create", "destripe_batch_add", "destripe_batch_step",
     "destripe_batch_slot_status", "destripe_batch_retire", "destripe_batch_tune",
-    "destripe_batch_info", "destripe_batch_destroy", "components",
+    "destripe_batch_info", "destripe_batch_destroy", "destripe_batch_autotune", "components",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -55,6 +55,13 @@ class ds_profile(ctypes.Structure):
                 ("iterations", ctypes.c_int64), ("timed_iterations", ctypes.c_int64),
                 ("bin_ms", ctypes.c_double), ("rescan_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("iteration_ms", ctypes.c_double)]
+
+
+class ds_batch_tuning(ctypes.Structure):
+    _fields_ = [("tile_samples", ctypes.c_int32), ("tile_pixels", ctypes.c_int32),
+                ("tile_unknowns", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("trials", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("rate", ctypes.c_double), ("rate_initial", ctypes.c_double)]
 
 
 class DestripeError(RuntimeError):
@@ -95,6 +102,7 @@ _SIGS = {
     "destripe_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int64)]),
     "destripe_batch_destroy": (None, [_P]),
+    "destripe_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ds_batch_tuning)]),
     "destripe_bin_noalloc": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P, _P, _P,
                                             _P]),
     "destripe_run_host": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P,
@@ -488,6 +496,16 @@ def destripe_batch_tune(batch: Batch, key: str, value: float):
     st = load_library().destripe_batch_tune(batch.handle, key.encode(), float(value))
     if st != DS_OK:
         raise DestripeError(st, f"destripe_batch_tune({key})")
+
+
+def destripe_batch_autotune(batch: Batch, max_trials: int = 12) -> dict:
+    """Pick the batch's launch shape by timing graph replays of its own problems
+    (see include/destripe.h); returns the chosen shape and the measured rates."""
+    res = ds_batch_tuning()
+    st = load_library().destripe_batch_autotune(batch.handle, int(max_trials), ctypes.byref(res))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_batch_autotune")
+    return {f: getattr(res, f) for f, _ in ds_batch_tuning._fields_ if f != "pad"}
 
 
 def destripe_batch_info(batch: Batch) -> dict:

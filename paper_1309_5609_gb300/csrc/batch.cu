@@ -38,6 +38,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kGraphIters = 8;
+constexpr int kBatchKernelsPerIteration = 16;
 
 struct SlotDesc {
   const int32_t* pix;
@@ -50,6 +51,7 @@ struct SlotDesc {
   const double* minv;
   const uint8_t* mask;
   double *x, *r, *p, *q, *b, *t, *x_best;
+  float2* xdf;  // baselines of a double-float pass split into float32 pairs
   CgState* state;
   int64_t n_t, L, n_b, n_u, npix;
   KindsArg kinds;
@@ -248,6 +250,27 @@ __global__ void __launch_bounds__(kBlock, 4) k_bb_rescan(const SlotDesc* __restr
 
 // ---- double-float residual refresh, gated per problem -----------------------------
 
+__device__ __forceinline__ df df_of(float2 v) { return df{v.x, v.y}; }
+
+// Splits the baselines of a double-float pass (MODE 0: x, 1: p) into float32
+// pairs, once per unknown, for the problems that run that pass this iteration.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_bb_split(const SlotDesc* __restrict__ slots,
+                                                     const WorkTile* __restrict__ tiles,
+                                                     const int* __restrict__ ntiles) {
+  const int nt = ntiles[W_UNKNOWNS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    if (!slot_df<MODE>(slots[T.slot])) continue;
+    const double* __restrict__ src = MODE == 0 ? slots[T.slot].x : slots[T.slot].p;
+    float2* __restrict__ dst = slots[T.slot].xdf;
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
+      const df d = df_from_double(src[i]);
+      dst[i] = make_float2(d.hi, d.lo);
+    }
+  }
+}
+
 template <int KS, int MODE>
 __global__ void __launch_bounds__(kBlock) k_bb_bin_df(const SlotDesc* __restrict__ slots,
                                                       const WorkTile* __restrict__ tiles,
@@ -259,7 +282,6 @@ __global__ void __launch_bounds__(kBlock) k_bb_bin_df(const SlotDesc* __restrict
     const WorkTile T = tiles[ti];
     if (!slot_df<MODE>(slots[T.slot])) continue;
     const SlotDesc S = slots[T.slot];
-    const double* __restrict__ src = MODE == 0 ? S.x : S.p;
     const int n_o = K::n_o(S.kinds);
     const int64_t n_t = S.n_t, L = S.L, n_b = S.n_b;
     for (int64_t v = T.begin + threadIdx.x; v < T.end; v += blockDim.x) {
@@ -271,7 +293,7 @@ __global__ void __launch_bounds__(kBlock) k_bb_bin_df(const SlotDesc* __restrict
       df zb[NO];
 #pragma unroll
       for (int o = 0; o < NO; ++o)
-        zb[o] = o < n_o ? df_from_double(src[o * n_b + b]) : df{0.f, 0.f};
+        zb[o] = o < n_o ? df_of(S.xdf[o * n_b + b]) : df{0.f, 0.f};
       df acc[NC];
 #pragma unroll
       for (int j = 0; j < NC; ++j) acc[j] = df{0.f, 0.f};
@@ -285,7 +307,7 @@ __global__ void __launch_bounds__(kBlock) k_bb_bin_df(const SlotDesc* __restrict
           bend += L;
 #pragma unroll
           for (int o = 0; o < NO; ++o)
-            zb[o] = o < n_o ? df_from_double(src[o * n_b + b]) : df{0.f, 0.f};
+            zb[o] = o < n_o ? df_of(S.xdf[o * n_b + b]) : df{0.f, 0.f};
         }
         if (p[k] < 0) continue;
         df w[NC];
@@ -364,7 +386,6 @@ __global__ void __launch_bounds__(kBlock) k_bb_rescan_df(const SlotDesc* __restr
     const WorkTile T = tiles[ti];
     if (!slot_df<MODE>(slots[T.slot])) continue;
     const SlotDesc S = slots[T.slot];
-    const double* __restrict__ src = MODE == 0 ? S.x : S.p;
     double* __restrict__ dst = MODE == 0 ? S.t : S.q;
     const int n_o = K::n_o(S.kinds);
     const int64_t n_t = S.n_t, L = S.L, n_b = S.n_b;
@@ -397,7 +418,7 @@ __global__ void __launch_bounds__(kBlock) k_bb_rescan_df(const SlotDesc* __restr
         df zb[NO];
 #pragma unroll
         for (int o = 0; o < NO; ++o)
-          zb[o] = o < n_o ? df_from_double(src[o * n_b + b]) : df{0.f, 0.f};
+          zb[o] = o < n_o ? df_of(S.xdf[o * n_b + b]) : df{0.f, 0.f};
         key = (int)b;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -415,7 +436,7 @@ __global__ void __launch_bounds__(kBlock) k_bb_rescan_df(const SlotDesc* __restr
             key = (int)b;
 #pragma unroll
             for (int o = 0; o < NO; ++o)
-              zb[o] = o < n_o ? df_from_double(src[o * n_b + b]) : df{0.f, 0.f};
+              zb[o] = o < n_o ? df_of(S.xdf[o * n_b + b]) : df{0.f, 0.f};
           }
           if (p[k] < 0) continue;
 #pragma unroll
@@ -789,12 +810,14 @@ void enqueue_batch_iteration(ds_batch_t B, cudaStream_t st) {
     k_bb_pixel_solve<NC><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_PIXELS], nt);
     k_bb_rescan<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
     // double-float operator for those that have
+    k_bb_split<1><<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt);
     k_bb_bin_df<KS, 1><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
     k_bb_pixel_solve_df<NC, 1><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_PIXELS], nt);
     k_bb_rescan_df<KS, 1><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
     k_bb_alpha<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt, B->d_red, B->d_tickets);
     k_bb_update<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt, B->d_red, B->d_tickets);
     // double-float residual refresh
+    k_bb_split<0><<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt);
     k_bb_bin_df<KS, 0><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
     k_bb_pixel_solve_df<NC, 0><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_PIXELS], nt);
     k_bb_rescan_df<KS, 0><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
@@ -848,6 +871,87 @@ ds_status batch_graph(ds_batch_t B) {
     return DS_ECUDA;
   }
   return DS_OK;
+}
+
+// ---- autotuner helpers ---------------------------------------------------------
+
+struct Shape {
+  int tile_samples, tile_pixels, tile_unknowns, blocks_per_sm;
+};
+
+Shape current_shape(ds_batch_t B) {
+  return Shape{(int)(B->tile_vecs * 4), (int)B->tile_pixels, (int)B->tile_unknowns, B->blocks_per_sm};
+}
+
+ds_status apply_shape(ds_batch_t B, const Shape& sh) {
+  const Shape cur = current_shape(B);
+  if (cur.tile_samples == sh.tile_samples && cur.tile_pixels == sh.tile_pixels &&
+      cur.tile_unknowns == sh.tile_unknowns && cur.blocks_per_sm == sh.blocks_per_sm)
+    return DS_OK;
+  B->tile_vecs = ((int64_t)sh.tile_samples / 4 + 31) / 32 * 32;
+  B->tile_pixels = sh.tile_pixels;
+  B->tile_unknowns = sh.tile_unknowns;
+  B->blocks_per_sm = sh.blocks_per_sm;
+  if (B->graph) {  // launch shapes are baked into the graph
+    cudaStreamSynchronize(B->stream);
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  return rebuild_tiles(B);
+}
+
+int running_count(ds_batch_t B) {
+  int n = 0;
+  for (int i = 0; i < B->max_slots; ++i) n += B->plans[i] != nullptr && !B->stopped[i];
+  return n;
+}
+
+// Reads every slot's CG state into h_states (synchronises the stream).
+ds_status read_states(ds_batch_t B) {
+  k_bb_gather_states<<<(B->max_slots + 127) / 128, 128, 0, B->stream>>>(B->d_slots, B->max_slots,
+                                                                       B->d_states);
+  DS_CUDA_TRY(cudaMemcpyAsync(B->h_states, B->d_states, sizeof(CgState) * B->max_slots,
+                              cudaMemcpyDeviceToHost, B->stream));
+  DS_CUDA_TRY(cudaStreamSynchronize(B->stream));
+  return DS_OK;
+}
+
+// One timed replay of the iteration graph with launch shape sh: *rate = samples
+// times CG iterations advanced, over the replay's event-timed duration.  The
+// iterations are real ones; problems that stop are dropped from the work lists
+// as in destripe_batch_step.
+ds_status tune_trial(ds_batch_t B, const Shape& sh, cudaEvent_t e0, cudaEvent_t e1, double* rate,
+                     bool timed) {
+  *rate = 0.0;
+  ds_status s = apply_shape(B, sh);
+  if (s == DS_OK) s = batch_upload(B);
+  if (s == DS_OK) s = batch_graph(B);
+  if (s == DS_OK) s = read_states(B);
+  if (s != DS_OK) return s;
+  std::vector<int> before(B->max_slots, 0);
+  for (int i = 0; i < B->max_slots; ++i) before[i] = B->h_states[i].iter;
+  DS_CUDA_TRY(cudaEventRecord(e0, B->stream));
+  DS_CUDA_TRY(cudaGraphLaunch(B->graph, B->stream));
+  DS_CUDA_TRY(cudaEventRecord(e1, B->stream));
+  B->launches += (int64_t)kGraphIters * kBatchKernelsPerIteration;
+  s = read_states(B);
+  if (s != DS_OK) return s;
+  float ms = 0.f;
+  DS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  double work = 0.0;
+  bool changed = false;
+  for (int i = 0; i < B->max_slots; ++i) {
+    const Plan* P = B->plans[i];
+    if (!P || B->stopped[i]) continue;
+    work += (double)P->n_t * (double)(B->h_states[i].iter - before[i]);
+    if (B->h_states[i].done) {
+      B->stopped[i] = 1;
+      changed = true;
+    }
+  }
+  if (timed && ms > 0.f) *rate = work / (ms * 1e-3);
+  if (changed) s = rebuild_tiles(B);
+  return s;
 }
 
 }  // namespace
@@ -911,7 +1015,7 @@ ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, cons
   if (!(tol >= 0.0)) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
   if (P.desc.precision != DS_PREC_MIXED || P.bins32 == nullptr || P.maplo == nullptr ||
-      !P.accurate_df || P.bin_mode != 1)
+      P.xdf == nullptr || !P.accurate_df || P.bin_mode != 1)
     return DS_ESTATE;
   if (B->nc != 0 && B->nc != P.n_c) return DS_ESTATE;
   int sl = -1;
@@ -945,6 +1049,7 @@ ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, cons
   S.minv = P.minv;
   S.mask = P.mask;
   S.x = P.x; S.r = P.r; S.p = P.p; S.q = P.q; S.b = P.b; S.t = P.t; S.x_best = P.x_best;
+  S.xdf = P.xdf;
   S.state = P.state;
   S.n_t = P.n_t; S.L = P.L; S.n_b = P.n_b; S.n_u = P.n_u; S.npix = P.npix;
   S.kinds = P.kinds;
@@ -971,7 +1076,7 @@ ds_status destripe_batch_step(ds_batch_t B, int32_t min_iters, int32_t* n_runnin
   int running = 0;
   for (int k = 0; k < launches; ++k) {
     DS_CUDA_TRY(cudaGraphLaunch(B->graph, st));
-    B->launches += (int64_t)kGraphIters * 14;
+    B->launches += (int64_t)kGraphIters * kBatchKernelsPerIteration;
     k_bb_gather_states<<<(B->max_slots + 127) / 128, 128, 0, st>>>(B->d_slots, B->max_slots, B->d_states);
     DS_CUDA_TRY(cudaMemcpyAsync(B->h_states, B->d_states, sizeof(CgState) * B->max_slots,
                                 cudaMemcpyDeviceToHost, st));
@@ -1056,6 +1161,9 @@ ds_status destripe_batch_tune(ds_batch_t B, const char* key, double value) {
   } else if (k == "tile_unknowns") {
     if (!(value >= 1024 && value <= (1 << 22))) return DS_EINVAL;
     B->tile_unknowns = (int64_t)value;
+  } else if (k == "tile_pixels") {
+    if (!(value >= 1024 && value <= (1 << 24))) return DS_EINVAL;
+    B->tile_pixels = (int64_t)value;
   } else if (k == "blocks_per_sm") {
     if (!(value >= 1 && value <= 32)) return DS_EINVAL;
     B->blocks_per_sm = (int)value;
@@ -1068,6 +1176,69 @@ ds_status destripe_batch_tune(ds_batch_t B, const char* key, double value) {
     B->graph = nullptr;
   }
   return rebuild_tiles(B);
+}
+
+ds_status destripe_batch_autotune(ds_batch_t B, int32_t max_trials, ds_batch_tuning* out) {
+  if (B == nullptr) return DS_EINVAL;
+  if (max_trials <= 0) max_trials = 12;
+  (void)cudaGetLastError();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return DS_ECUDA;
+  }
+  Shape best = current_shape(B);
+  double rate0 = 0.0, best_rate = 0.0;
+  int trials = 0;
+  ds_status s = DS_OK;
+  // one untimed replay: first-launch costs stay out of the comparison
+  double r = 0.0;
+  s = tune_trial(B, best, e0, e1, &r, false);
+  if (s == DS_OK && running_count(B) > 0) {
+    s = tune_trial(B, best, e0, e1, &rate0, true);
+    ++trials;
+    best_rate = rate0;
+  }
+  // coordinate descent over the grid, starting from the shape in force
+  static const int kBps[] = {4, 8, 16};
+  static const int kSamples[] = {8192, 16384, 32768, 65536};
+  static const int kPixels[] = {4096, 16384, 65536};
+  static const int kUnknowns[] = {2048, 4096, 16384};
+  for (int coord = 0; coord < 4 && s == DS_OK; ++coord) {
+    const int* grid = coord == 0 ? kBps : coord == 1 ? kSamples : coord == 2 ? kPixels : kUnknowns;
+    const int n = coord == 1 ? 4 : 3;
+    for (int i = 0; i < n && s == DS_OK; ++i) {
+      if (trials >= max_trials || running_count(B) == 0) break;
+      Shape cand = best;
+      int* field = coord == 0 ? &cand.blocks_per_sm : coord == 1 ? &cand.tile_samples
+                 : coord == 2 ? &cand.tile_pixels : &cand.tile_unknowns;
+      if (*field == grid[i]) continue;
+      *field = grid[i];
+      double rate = 0.0;
+      s = tune_trial(B, cand, e0, e1, &rate, true);
+      ++trials;
+      if (s == DS_OK && rate > best_rate * 1.02) {  // 2% margin against timing noise
+        best = cand;
+        best_rate = rate;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != DS_OK) return s;
+  s = apply_shape(B, best);
+  if (s != DS_OK) return s;
+  if (out) {
+    out->tile_samples = best.tile_samples;
+    out->tile_pixels = best.tile_pixels;
+    out->tile_unknowns = best.tile_unknowns;
+    out->blocks_per_sm = best.blocks_per_sm;
+    out->trials = trials;
+    out->pad = 0;
+    out->rate = best_rate;
+    out->rate_initial = rate0;
+  }
+  return DS_OK;
 }
 
 ds_status destripe_batch_info(ds_batch_t B, int32_t* n_slots_used, int64_t* kernel_launches) {

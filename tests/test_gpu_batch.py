@@ -125,3 +125,37 @@ def test_batch_rejects_what_it_cannot_run():
         pass
     assert ds.destripe_batch_retire(batch, 0, None)[0] == ds.DS_OK
     batch.close()
+
+
+def test_autotune_picks_a_shape_and_keeps_results():
+    probs = problems(5, seed=17)
+    ref, _ = run_batch(probs)
+    plans = [plan_of(p) for p in probs]
+    batch = ds.destripe_batch_create(len(probs))
+    slots = [ds.destripe_batch_add(batch, pl, p.y, tol=1e-10) for pl, p in zip(plans, probs)]
+    res = ds.destripe_batch_autotune(batch, max_trials=6)
+    assert 1 <= res["trials"] <= 6
+    assert res["rate"] > 0 and res["rate"] >= res["rate_initial"]
+    assert res["blocks_per_sm"] in (4, 8, 16)
+    assert res["tile_samples"] in (8192, 16384, 32768, 65536)
+    assert res["tile_pixels"] in (4096, 16384, 65536)
+    assert res["tile_unknowns"] in (2048, 4096, 16384)
+    while ds.destripe_batch_step(batch, 8) > 0:
+        pass
+    for i, (sl, pl) in enumerate(zip(slots, plans)):
+        a = torch.zeros(pl.n_u, dtype=torch.float64, device=DEV)
+        st, it, rel = ds.destripe_batch_retire(batch, sl, a)
+        assert st == ds.DS_OK
+        assert np.abs(a.cpu().numpy() - ref[i][3]).max() < 1e-5
+    batch.close()
+    for pl in plans:
+        pl.close()
+
+
+def test_autotune_on_an_empty_batch_does_nothing():
+    batch = ds.destripe_batch_create(4)
+    res = ds.destripe_batch_autotune(batch)
+    assert res["trials"] == 0
+    assert (res["tile_samples"], res["tile_pixels"], res["tile_unknowns"],
+            res["blocks_per_sm"]) == (16384, 16384, 4096, 8)
+    batch.close()
