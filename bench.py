@@ -236,11 +236,20 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    from synth import WORKLOAD_NAMES, config_problem
+    from synth import WORKLOAD_NAMES, batch_configs, config_problem, make_problem
     import torch
     n = min(args.oracle_samples, args.n_samples or 10 ** 12)
-    prob = config_problem(args.config, n_t=n, keep_f64_trig=False,
-                          y_dtype=torch.float32 if args.precision == "mixed" else torch.float64)
+    ydt = torch.float32 if args.precision == "mixed" else torch.float64
+    if args.config == 3:  # the batch's first problem
+        c = dict(batch_configs(64, seed=1003)[0], n_t=n)
+        prob, name = make_problem(keep_f64_trig=False, y_dtype=ydt, **c), "batch64 problem 0"
+    elif args.config == 5:  # a two-output request of the serving trace's kind
+        prob = make_problem(n, 256, ("q", "u"), baseline_len=500, f_knee=0.1, alpha=1.7,
+                            seed=5000, keep_f64_trig=False, y_dtype=ydt)
+        name = "serving request (q,u, nside 256, L 500)"
+    else:
+        prob = config_problem(args.config, n_t=n, keep_f64_trig=False, y_dtype=ydt)
+        name = WORKLOAD_NAMES[args.config]
     d, n = prefix_numpy(prob, n)
     iters_per_step = max(1, args.oracle_iters // 2)
     for _ in range(args.warmup):
@@ -252,10 +261,9 @@ def run_reference(args):
         tot_t += dt
         tot_it += it
     value = tot_si / tot_t
-    name = WORKLOAD_NAMES[args.config]
     sample = (f"prefix of {n} samples of {name}: plan + RHS + {iters_per_step} CG iterations "
               f"per step, float64 numpy, 1 thread")
-    cfg = config_dict(args)
+    cfg = config_dict(args) if args.config in (1, 2, 4) else {"workload": name, "n_samples": n}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
@@ -568,6 +576,19 @@ def run_batch(args):
     return 0
 
 
+def iteration_stats(reqs, ok_status):
+    """Iterations of converged requests, and the share of the work spent on the rest."""
+    import numpy as np
+    it_ok = [r.iters for r in reqs if r.status == ok_status]
+    work = [r.n_t * r.iters for r in reqs]
+    bad = [r.n_t * r.iters for r in reqs if r.status != ok_status]
+    return {"converged_p50": float(np.percentile(it_ok, 50)) if it_ok else None,
+            "converged_p99": float(np.percentile(it_ok, 99)) if it_ok else None,
+            "converged_max": int(max(it_ok)) if it_ok else None,
+            "not_converged": len(bad),
+            "not_converged_work_share": float(sum(bad) / sum(work)) if sum(work) else 0.0}
+
+
 def run_serve(args):
     """Config 5: Poisson request stream served with continuous batching."""
     import numpy as np
@@ -650,6 +671,7 @@ def run_serve(args):
                        "nside": list(nsides), "baselines_s": [0.5, 60.0], "outputs": "q or q,u",
                        "precision": "mixed", "tol": args.tol, "max_slots": 64},
             "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "mean_latency_s": summ["mean_s"],
+            "iterations": iteration_stats(reqs, ds.DS_OK),
             "samples_per_s": summ["samples_per_s"], "converged": int(ok),
             "max_resident": summ["max_resident"], "gpu_launches": summ["kernel_launches"],
             "sequential_fp64_model": {

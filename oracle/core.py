@@ -141,11 +141,16 @@ def pixel_cut(M, hits, rcond_min):
     return Minv, mask, rcond
 
 
-def make_plan(pix, c, s, valid, nside, kinds, baseline_len, rcond_min=1e-3) -> OraclePlan:
-    """Everything that depends on the pointing only: hits, M, the cut, M^-1."""
+def make_plan(pix, c, s, valid, nside, kinds, baseline_len, rcond_min=1e-3,
+              npix=None) -> OraclePlan:
+    """Everything that depends on the pointing only: hits, M, the cut, M^-1.
+
+    npix overrides the map size 12 nside^2, for pixel indices that have been
+    renumbered 0..npix-1 (a subset of the samples that holds every sample of the
+    pixels it touches has the same per-pixel quantities as the whole problem)."""
     pix = np.asarray(pix, dtype=np.int64)
     n_t = pix.shape[0]
-    npix = 12 * nside * nside
+    npix = 12 * nside * nside if npix is None else int(npix)
     if n_t and (pix.min() < 0 or pix.max() >= npix):
         raise ValueError("pixel index out of range")
     c = np.asarray(c, dtype=np.float64)
