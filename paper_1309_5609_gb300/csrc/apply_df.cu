@@ -21,6 +21,12 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Resident blocks per SM requested for the double-float streaming passes: their
+// register count limits occupancy.  3 caps them at 85 registers (from 80-100):
+// measured 16% faster right-hand side on the B-Machine-like workload; 4 (64
+// registers) spills and gains nothing more.
+constexpr int kDfMinBlocks = 3;
+
 template <typename F>
 void with_kindset(int ks, F&& f) {
   switch (ks) {
@@ -75,7 +81,7 @@ __device__ __forceinline__ df df_load(const float2* __restrict__ xs, int64_t i) 
 // bins[p] += sum_o w_o(t) z_o(t), z = x[o][t/L] (ZY false) or y[o][t] - a[o][t/L] (ZY true);
 // the baselines come split into double-float pairs (xs, NULL for none)
 template <int KS, bool ZY>
-__global__ void __launch_bounds__(kBlock) k_bin_df(const int32_t* __restrict__ pix,
+__global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_bin_df(const int32_t* __restrict__ pix,
                                                    const float* __restrict__ cc,
                                                    const float* __restrict__ ss,
                                                    const float2* __restrict__ x,
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve_df(double* __restrict__ 
 
 // out[o][b] += sum_{t in b} v (z_o(t) - w_o(t) . m_p(t)) in double-float
 template <int KS, bool ZY>
-__global__ void __launch_bounds__(kBlock) k_rescan_df(const int32_t* __restrict__ pix,
+__global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_rescan_df(const int32_t* __restrict__ pix,
                                                       const float* __restrict__ cc,
                                                       const float* __restrict__ ss,
                                                       const float2* __restrict__ x,

@@ -205,16 +205,26 @@ __global__ void __launch_bounds__(kBlock, 4) k_bb_rescan(const SlotDesc* __restr
         int p[4];
         float c[4], s[4];
         load4(S.pix, S.c, S.s, v, n_t, p, c, s);
+        // the map row is gathered once per run of equal pixels in the thread's samples
         float m[4][NC];
+        bool dup[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dup[k] = k > 0 && p[k] >= 0 && p[k] == p[k - 1];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          if (p[k] >= 0) {
+          if (p[k] >= 0 && !dup[k]) {
             load_map<NC, float>(S.map32, p[k], m[k]);
           } else {
 #pragma unroll
             for (int j = 0; j < NC; ++j) m[k][j] = 0.f;
           }
         }
+#pragma unroll
+        for (int k = 1; k < 4; ++k)
+          if (dup[k]) {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) m[k][j] = m[k - 1][j];
+          }
         const int64_t t0 = v << 2;
         int64_t b = t0 / L, bend = (b + 1) * L;
         float zb[NO];
