@@ -3,6 +3,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <string>
 
 #include "internal.cuh"
@@ -41,11 +42,46 @@ int kindset_of(const int* k, int n_o, int n_c) {
   return n_c == 1 ? KS_GEN1 : (n_c == 2 ? KS_GEN2 : KS_GEN3);
 }
 
+// Plan memory comes from one stream-ordered pool per device, owned by the library:
+// freeing a plan needs no device-wide synchronisation (cudaFree has one), and a
+// plan built after another reuses its memory without a trip to the driver.  Up
+// to kPoolKeep bytes of freed memory stay in the pool.
+constexpr uint64_t kPoolKeep = uint64_t(8) << 30;
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+cudaError_t plan_pool(int device, cudaMemPool_t* out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (g_pools[device] == nullptr) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = kPoolKeep;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pools[device] = pool;
+  }
+  *out = g_pools[device];
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t dalloc(Plan& P, T** ptr, int64_t count) {
   const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
   P.device_bytes += (int64_t)bytes;
-  return cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+  cudaMemPool_t pool = nullptr;
+  const cudaError_t e = plan_pool(P.device, &pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(reinterpret_cast<void**>(ptr), bytes, pool, P.stream);
 }
 
 void plan_free(Plan* P) {
@@ -59,8 +95,10 @@ void plan_free(Plan* P) {
   void* dev[] = {P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
+  // the plan's own stream is the last user of its memory (batches retire a
+  // problem, synchronising their stream, before its plan may be destroyed)
   for (void* d : dev)
-    if (d) cudaFree(d);
+    if (d) cudaFreeAsync(d, P->stream);
   if (P->h_state) cudaFreeHost(P->h_state);
   if (P->h_err) cudaFreeHost(P->h_err);
   if (P->h_scal) cudaFreeHost(P->h_scal);
@@ -122,12 +160,9 @@ ds_status build_graph(Plan& P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) DS_CUDA_TRY(cudaEventCreate(&P.ev[i]));
   }
   P.graph_iters = P.graph_iters_cfg;
+  // the accurate-operator graph is captured when a problem first needs it
   ds_status s = capture_iterations(P, false, P.profiling ? P.ev : nullptr, &P.graph_exec);
   if (s != DS_OK) return s;
-  if (P.desc.precision == DS_PREC_MIXED) {
-    s = capture_iterations(P, true, nullptr, &P.graph_exec_acc);
-    if (s != DS_OK) return s;
-  }
   P.graph_profiled = P.profiling;
   return DS_OK;
 }
@@ -165,7 +200,7 @@ ds_status chunk_index(Plan& P, int C) {
     if (e == cudaSuccess) e = dalloc(P, &P.ucnt, (P.n_t + kChunkMin - 1) / kChunkMin);
     if (e != cudaSuccess) {
       for (void* d : {(void*)P.lid, (void*)P.upix, (void*)P.ucnt})
-        if (d) cudaFree(d);
+        if (d) cudaFreeAsync(d, P.stream);
       P.lid = nullptr;
       P.upix = nullptr;
       P.ucnt = nullptr;
@@ -407,6 +442,10 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   for (int k = 0; k < max_launches && !done; ++k) {
     // a mixed problem that the float32 operator cannot follow continues with the
     // accurate one (the switch is decided on the device at a float64 refresh)
+    if (accurate && P.graph_exec_acc == nullptr && P.desc.precision == DS_PREC_MIXED) {
+      const ds_status sa = capture_iterations(P, true, nullptr, &P.graph_exec_acc);
+      if (sa != DS_OK) return sa;
+    }
     const bool acc_now = accurate && P.graph_exec_acc != nullptr;
     DS_CUDA_TRY(cudaGraphLaunch(acc_now ? P.graph_exec_acc : P.graph_exec, st));
     DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
@@ -555,23 +594,38 @@ ds_status destripe_run_host(const ds_desc* desc, const int32_t* h_pix, const flo
   double *d_a = nullptr, *d_map = nullptr;
   int32_t* d_hits = nullptr;
   ds_plan_t plan = nullptr;
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_pix), sizeof(int32_t) * n_t, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_c), sizeof(float) * n_t, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_s), sizeof(float) * n_t, st);
-  if (e == cudaSuccess && h_valid) e = cudaMallocAsync(reinterpret_cast<void**>(&d_valid), n_t, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&d_y, ysz * n_t * n_o, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_a), sizeof(double) * n_b * n_o, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_map), sizeof(double) * n_c * npix, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_hits), sizeof(int32_t) * npix, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_mask), npix, st);
+  // device buffers come from the library's pool (reused across calls)
+  int device = 0;
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e == cudaSuccess) e = plan_pool(device, &pool);
+  auto dmalloc = [&](void** ptr, size_t bytes) { return cudaMallocFromPoolAsync(ptr, bytes, pool, st); };
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&d_pix), sizeof(int32_t) * n_t);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&d_c), sizeof(float) * n_t);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&d_s), sizeof(float) * n_t);
+  if (e == cudaSuccess && h_valid) e = dmalloc(reinterpret_cast<void**>(&d_valid), n_t);
+  if (e == cudaSuccess) e = dmalloc(&d_y, ysz * n_t * n_o);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&d_a), sizeof(double) * n_b * n_o);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&d_map), sizeof(double) * n_c * npix);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&d_hits), sizeof(int32_t) * npix);
+  if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void**>(&d_mask), npix);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_pix, h_pix, sizeof(int32_t) * n_t, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_c, h_c, sizeof(float) * n_t, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_s, h_s, sizeof(float) * n_t, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && h_valid) e = cudaMemcpyAsync(d_valid, h_valid, n_t, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_y, h_y, ysz * n_t * n_o, cudaMemcpyHostToDevice, st);
+  // the timelines travel on a second stream while the plan (pointing only) is built
+  cudaStream_t st_y = nullptr;
+  cudaEvent_t ev_alloc = nullptr, ev_y = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st_y, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_alloc, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_y, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_alloc, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st_y, ev_alloc, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_y, h_y, ysz * n_t * n_o, cudaMemcpyHostToDevice, st_y);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_y, st_y);
   if (e != cudaSuccess) s = (e == cudaErrorMemoryAllocation) ? DS_ENOMEM : DS_ECUDA;
   if (s == DS_OK) s = destripe_plan(desc, d_pix, d_c, d_s, d_valid, &plan);
+  if (ev_y != nullptr && cudaStreamWaitEvent(st, ev_y, 0) != cudaSuccess && s == DS_OK) s = DS_ECUDA;
   ds_status solve_s = DS_OK;
   if (s == DS_OK) {
     solve_s = destripe_solve(plan, d_y, d_a, tol, max_iter, 0, iters, rel_resid);
@@ -583,6 +637,12 @@ ds_status destripe_run_host(const ds_desc* desc, const int32_t* h_pix, const flo
   if (s == DS_OK && h_hits && h_map) s = cudaMemcpyAsync(h_hits, d_hits, sizeof(int32_t) * npix, cudaMemcpyDeviceToHost, st) == cudaSuccess ? DS_OK : DS_ECUDA;
   if (s == DS_OK && h_mask && h_map) s = cudaMemcpyAsync(h_mask, d_mask, npix, cudaMemcpyDeviceToHost, st) == cudaSuccess ? DS_OK : DS_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess && s == DS_OK) s = DS_ECUDA;
+  if (st_y != nullptr) {
+    cudaStreamSynchronize(st_y);  // the timeline copy has ended even on an early error
+    cudaStreamDestroy(st_y);
+  }
+  if (ev_alloc) cudaEventDestroy(ev_alloc);
+  if (ev_y) cudaEventDestroy(ev_y);
   if (plan) destripe_destroy(plan);
   void* bufs[] = {d_pix, d_c, d_s, d_valid, d_y, d_a, d_map, d_hits, d_mask};
   for (void* b : bufs)
