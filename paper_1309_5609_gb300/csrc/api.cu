@@ -92,7 +92,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a
@@ -293,6 +293,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(bins32, P->npix * 4);
   if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(maplo, P->npix * 4);
   if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(xdf, P->n_u);
+  if (P->desc.precision == DS_PREC_MIXED) DS_ALLOC(x32, P->n_u);
   DS_ALLOC(map32, P->npix * 4);
   DS_ALLOC(map64, P->npix * 4);
   DS_ALLOC(nvalid, P->n_b);

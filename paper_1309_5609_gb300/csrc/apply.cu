@@ -37,11 +37,11 @@ void with_kindset(int ks, F&& f) {
 // ---- binning: bins[p] += sum_o w_o(t) z_o(t) over samples with v = 1 ----------
 // ZY = false: z_o(t) = x[o][t / L]          (F~ x, the operator)
 // ZY = true : z_o(t) = y[o][t] - a[o][t/L]  (data minus baselines; a may be NULL)
-template <int KS, typename T, bool ZY, typename YT, typename BT>
+template <int KS, typename T, bool ZY, typename YT, typename BT, typename XT = double>
 __global__ void __launch_bounds__(kBlock) k_bin(const int32_t* __restrict__ pix,
                                                 const float* __restrict__ cc,
                                                 const float* __restrict__ ss,
-                                                const double* __restrict__ x,
+                                                const XT* __restrict__ x,
                                                 const YT* __restrict__ y,
                                                 BT* __restrict__ bins, int64_t n_t, int64_t L,
                                                 int64_t n_b, KindsArg kk, Gate g) {
@@ -103,6 +103,16 @@ __global__ void __launch_bounds__(kBlock) k_bin(const int32_t* __restrict__ pix,
   }
 }
 
+// x rounded to float32 once per operator apply, so that the float32 passes read
+// float32 baselines (no float64 conversion per sample group)
+__global__ void __launch_bounds__(kBlock) k_to_f32(const double* __restrict__ x,
+                                                   float* __restrict__ x32, int64_t n, Gate g) {
+  if (gate_closed(g)) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    x32[i] = (float)x[i];
+}
+
 // ---- per-pixel solve: m_p = M_p^-1 s_p on kept pixels, 0 elsewhere ---------------
 // Reads the float64 sums, clears them for the next pass, writes the map in the
 // working precision (and optionally component-major float64 for the caller).
@@ -159,11 +169,11 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve(BT* __restrict__ bins,
 }
 
 // ---- rescan + per-baseline sum: out[o][b] += sum_{t in b} v (z_o(t) - w_o(t) . m_p(t))
-template <int KS, typename T, bool ZY, typename YT, bool DEDUP = false>
+template <int KS, typename T, bool ZY, typename YT, bool DEDUP = false, typename XT = double>
 __global__ void __launch_bounds__(kBlock) k_rescan(const int32_t* __restrict__ pix,
                                                    const float* __restrict__ cc,
                                                    const float* __restrict__ ss,
-                                                   const double* __restrict__ x,
+                                                   const XT* __restrict__ x,
                                                    const YT* __restrict__ y,
                                                    const T* __restrict__ map,
                                                    double* __restrict__ out, int64_t n_t,
@@ -234,7 +244,7 @@ __global__ void __launch_bounds__(kBlock) k_rescan(const int32_t* __restrict__ p
         if (t >= bend) {
 #pragma unroll
           for (int o = 0; o < NO; ++o) {
-            if (o < n_o && acc[o] != T(0)) atomicAdd(out + o * n_b + b, (double)acc[o]);
+            if (o < n_o && acc[o] != T(0)) atomicAdd(out + o * n_b + b, to_f64(acc[o]));
             acc[o] = T(0);
           }
           b += 1;
@@ -277,6 +287,9 @@ void launch_bin_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, Ga
     if (fp64)
       k_bin<KS, double, false, double, double><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, x, nullptr, P.bins, P.n_t, P.L, P.n_b, P.kinds, g);
+    else if (f32_bins(P, fp64) && P.x32 != nullptr)
+      k_bin<KS, float, false, float, float, float><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, P.x32, nullptr, P.bins32, P.n_t, P.L, P.n_b, P.kinds, g);
     else if (f32_bins(P, fp64))
       k_bin<KS, float, false, float, float><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, x, nullptr, P.bins32, P.n_t, P.L, P.n_b, P.kinds, g);
@@ -326,6 +339,9 @@ void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x,
     if (fp64)
       k_rescan<KS, double, false, double><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, x, nullptr, P.map64, out, P.n_t, P.L, P.n_b, P.kinds, g);
+    else if (P.rescan_dedup && P.x32 != nullptr)
+      k_rescan<KS, float, false, float, true, float><<<grid, kBlock, 0, st>>>(
+          P.pix, P.c, P.s, P.x32, nullptr, P.map32, out, P.n_t, P.L, P.n_b, P.kinds, g);
     else if (P.rescan_dedup)
       k_rescan<KS, float, false, float, true><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, x, nullptr, P.map32, out, P.n_t, P.L, P.n_b, P.kinds, g);
@@ -341,11 +357,13 @@ void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out,
     constexpr int KS = decltype(ksc)::value;
     if (P.desc.precision == DS_PREC_FP64)
       k_rescan<KS, double, true, double><<<grid, kBlock, 0, st>>>(
-          P.pix, P.c, P.s, nullptr, static_cast<const double*>(y), P.map64, out, P.n_t, P.L, P.n_b,
+          P.pix, P.c, P.s, static_cast<const double*>(nullptr), static_cast<const double*>(y),
+          P.map64, out, P.n_t, P.L, P.n_b,
           P.kinds, g);
     else
       k_rescan<KS, double, true, float><<<grid, kBlock, 0, st>>>(
-          P.pix, P.c, P.s, nullptr, static_cast<const float*>(y), P.map64, out, P.n_t, P.L, P.n_b,
+          P.pix, P.c, P.s, static_cast<const double*>(nullptr), static_cast<const float*>(y),
+          P.map64, out, P.n_t, P.L, P.n_b,
           P.kinds, g);
   });
 }
@@ -391,6 +409,8 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     return;
   }
   // External records become event nodes when the stream is being captured.
+  if (!fp64 && P.x32 != nullptr)
+    k_to_f32<<<stream_grid(P, P.n_u, kBlock, 8), kBlock, 0, st>>>(x, P.x32, P.n_u, g);
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   launch_bin_x(P, st, fp64, x, g);
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);

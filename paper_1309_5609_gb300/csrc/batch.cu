@@ -38,7 +38,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kGraphIters = 8;
-constexpr int kBatchKernelsPerIteration = 16;
+constexpr int kBatchKernelsPerIteration = 17;
 
 struct SlotDesc {
   const int32_t* pix;
@@ -52,6 +52,7 @@ struct SlotDesc {
   const uint8_t* mask;
   double *x, *r, *p, *q, *b, *t, *x_best;
   float2* xdf;  // baselines of a double-float pass split into float32 pairs
+  float* x32;   // the search direction rounded to float32 for the float32 operator
   CgState* state;
   int64_t n_t, L, n_b, n_u, npix;
   KindsArg kinds;
@@ -85,6 +86,20 @@ __device__ __forceinline__ bool slot_df(const SlotDesc& S) {
 
 // ---- operator kernels (mixed precision: float32 per-sample work) ---------------
 
+// p rounded to float32 once per iteration for the problems on the float32 operator
+__global__ void __launch_bounds__(kBlock) k_bb_to_f32(const SlotDesc* __restrict__ slots,
+                                                      const WorkTile* __restrict__ tiles,
+                                                      const int* __restrict__ ntiles) {
+  const int nt = ntiles[W_UNKNOWNS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    if (!slot_f32(slots[T.slot])) continue;
+    const double* __restrict__ src = slots[T.slot].p;
+    float* __restrict__ dst = slots[T.slot].x32;
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) dst[i] = (float)src[i];
+  }
+}
+
 template <int KS>
 __global__ void __launch_bounds__(kBlock, 4) k_bb_bin(const SlotDesc* __restrict__ slots,
                                                    const WorkTile* __restrict__ tiles,
@@ -106,7 +121,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bb_bin(const SlotDesc* __restrict
       int64_t b = t0 / L, bend = (b + 1) * L;
       float zb[NO];
 #pragma unroll
-      for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? (float)S.p[o * n_b + b] : 0.f;
+      for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? S.x32[o * n_b + b] : 0.f;
       float acc[NC];
 #pragma unroll
       for (int j = 0; j < NC; ++j) acc[j] = 0.f;
@@ -119,7 +134,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bb_bin(const SlotDesc* __restrict
           b += 1;
           bend += L;
 #pragma unroll
-          for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? (float)S.p[o * n_b + b] : 0.f;
+          for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? S.x32[o * n_b + b] : 0.f;
         }
         if (p[k] < 0) continue;
         float w[NC];
@@ -229,7 +244,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bb_rescan(const SlotDesc* __restr
         int64_t b = t0 / L, bend = (b + 1) * L;
         float zb[NO];
 #pragma unroll
-        for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? (float)S.p[o * n_b + b] : 0.f;
+        for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? S.x32[o * n_b + b] : 0.f;
         key = (int)b;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -238,14 +253,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_bb_rescan(const SlotDesc* __restr
           if (t >= bend) {
 #pragma unroll
             for (int o = 0; o < NO; ++o) {
-              if (o < n_o && acc[o] != 0.f) atomicAdd(S.q + o * n_b + b, (double)acc[o]);
+              if (o < n_o && acc[o] != 0.f) atomicAdd(S.q + o * n_b + b, to_f64(acc[o]));
               acc[o] = 0.f;
             }
             b += 1;
             bend += L;
             key = (int)b;
 #pragma unroll
-            for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? (float)S.p[o * n_b + b] : 0.f;
+            for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? S.x32[o * n_b + b] : 0.f;
           }
           if (p[k] < 0) continue;
 #pragma unroll
@@ -816,6 +831,7 @@ void enqueue_batch_iteration(ds_batch_t B, cudaStream_t st) {
     constexpr int KS = decltype(ksc)::value;
     constexpr int NC = KSet<KS>::NC;
     // float32 operator for problems that have not switched to the accurate one
+    k_bb_to_f32<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt);
     k_bb_bin<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
     k_bb_pixel_solve<NC><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_PIXELS], nt);
     k_bb_rescan<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
@@ -1025,7 +1041,7 @@ ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, cons
   if (!(tol >= 0.0)) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
   if (P.desc.precision != DS_PREC_MIXED || P.bins32 == nullptr || P.maplo == nullptr ||
-      P.xdf == nullptr || !P.accurate_df || P.bin_mode != 1)
+      P.xdf == nullptr || P.x32 == nullptr || !P.accurate_df || P.bin_mode != 1)
     return DS_ESTATE;
   if (B->nc != 0 && B->nc != P.n_c) return DS_ESTATE;
   int sl = -1;
@@ -1060,6 +1076,7 @@ ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, cons
   S.mask = P.mask;
   S.x = P.x; S.r = P.r; S.p = P.p; S.q = P.q; S.b = P.b; S.t = P.t; S.x_best = P.x_best;
   S.xdf = P.xdf;
+  S.x32 = P.x32;
   S.state = P.state;
   S.n_t = P.n_t; S.L = P.L; S.n_b = P.n_b; S.n_u = P.n_u; S.npix = P.npix;
   S.kinds = P.kinds;

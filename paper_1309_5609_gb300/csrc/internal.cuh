@@ -100,6 +100,7 @@ struct Plan {
   float* map32;
   float* maplo;       // low parts of the double-float map [n_pix][4] (mixed plans)
   float2* xdf;        // baselines split into double-float pairs [n_u] (mixed plans)
+  float* x32;         // baselines of the float32 operator, rounded once per apply [n_u]
   double* map64;
   int32_t* nvalid;
   double *x, *r, *p, *q, *b, *t;

@@ -5,6 +5,7 @@
 
 #include <type_traits>
 
+#include "df.cuh"
 #include "internal.cuh"
 #include "rows.cuh"
 
@@ -32,6 +33,11 @@ __device__ __forceinline__ void load4(const int32_t* __restrict__ pix, const flo
     }
   }
 }
+
+// Value for a float64 atomic: float32 sums are widened by bit re-encoding
+// (f64_of_f32), which keeps the conversion off the narrow float64 pipe.
+__device__ __forceinline__ double to_f64(float v) { return f64_of_f32(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
 
 template <int NC, typename T>
 __device__ __forceinline__ void flush_bins(double* __restrict__ bins, int p, const T (&acc)[NC]) {
@@ -89,7 +95,7 @@ __device__ __forceinline__ void warp_segment_flush(int key, T (&val)[NO], int n_
   if (key >= 0 && (lane == 0 || kp != key)) {
 #pragma unroll
     for (int o = 0; o < NO; ++o)
-      if (o < n_o) atomicAdd(out + (int64_t)o * n_b + key, (double)val[o]);
+      if (o < n_o) atomicAdd(out + (int64_t)o * n_b + key, to_f64(val[o]));
   }
 }
 
