@@ -6,10 +6,11 @@ no code with the CUDA library.  See core.py for the method and its readings.
 """
 from .core import (OraclePlan, apply_A, apply_Z, baseline_has_data, baseline_sums,
                        bin_map, cg, components, destripe, expand, gauge, hitmap, make_plan,
-                       pixel_cut, pixel_matrices, rescan, rhs, row_coefficients)
+                       pixel_cut, pixel_matrices, pixel_solve, pixel_sums, rescan, rhs,
+                       row_coefficients)
 
 __all__ = [
     "OraclePlan", "apply_A", "apply_Z", "baseline_has_data", "baseline_sums", "bin_map",
     "cg", "components", "destripe", "expand", "gauge", "hitmap", "make_plan", "pixel_cut",
-    "pixel_matrices", "rescan", "rhs", "row_coefficients",
+    "pixel_matrices", "pixel_solve", "pixel_sums", "rescan", "rhs", "row_coefficients",
 ]

@@ -173,9 +173,10 @@ def expand(plan: OraclePlan, x):
     return x[:, np.arange(plan.n_t) // plan.L]
 
 
-def bin_map(plan: OraclePlan, z):
-    """m = M^-1 sum_t sum_o v w_o(t) z_o(t), the ML map of Eqs. mapQ/mapU with the
-    general pixel weight; 0 on cut pixels.  z is [n_o, n_t]."""
+def pixel_sums(plan: OraclePlan, z):
+    """s_p = sum_t sum_o v w_o(t) z_o(t) per component and pixel: the binning
+    P~^T R^T V of Sect. 3 before the pixel weight.  z is [n_o, n_t]; returns
+    [n_c, npix]."""
     z = np.asarray(z, dtype=np.float64)
     summap = np.zeros((plan.n_c, plan.npix))
     for o, kind in enumerate(plan.kinds):
@@ -183,9 +184,21 @@ def bin_map(plan: OraclePlan, z):
         for i, wi in w.items():
             summap[i] += np.bincount(plan.pix, weights=plan.v * _as_array(wi, plan.n_t) * z[o],
                                      minlength=plan.npix)
+    return summap
+
+
+def pixel_solve(plan: OraclePlan, summap):
+    """m_p = M_p^-1 s_p on kept pixels, 0 on cut pixels (Eqs. mapQ/mapU with the
+    general pixel weight)."""
     m = np.einsum("pij,jp->ip", plan.Minv, summap)
     m[:, ~plan.mask] = 0.0
     return m
+
+
+def bin_map(plan: OraclePlan, z):
+    """m = M^-1 sum_t sum_o v w_o(t) z_o(t), the ML map of Eqs. mapQ/mapU with the
+    general pixel weight; 0 on cut pixels.  z is [n_o, n_t]."""
+    return pixel_solve(plan, pixel_sums(plan, z))
 
 
 def rescan(plan: OraclePlan, m):
