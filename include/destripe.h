@@ -225,6 +225,8 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     per chunk (2048, 4096, 8192 or 16384; synchronises)
  *   "rescan_dedup"    MIXED plans: 1 = the float32 rescan reads the map once per run of
  *                     equal pixels within a thread's 4 samples (default), 0 = once per sample
+ *   "samples_per_thread"  MIXED plans: 4 (default) or 8 consecutive samples per thread in
+ *                     the float32 operator (8: two 16-byte loads per stream per thread)
  * Returns DS_EINVAL for an unknown key or value, DS_ESTATE when the plan cannot
  * use the value.  Takes effect at the next call. */
 ds_status destripe_tune(ds_plan_t plan, const char* key, double value);

@@ -282,6 +282,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->refresh_max = 50;
   P->layout = 0;
   P->rescan_dedup = 1;
+  P->samples_per_thread = 4;
   cudaError_t e = cudaSuccess;
 #define DS_ALLOC(ptr, n) \
   if (e == cudaSuccess) e = dalloc(*P, &P->ptr, (n));
@@ -552,6 +553,9 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
     if (P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
     const ds_status s = chunk_index(P, C);
     if (s != DS_OK) return s;
+  } else if (k == "samples_per_thread") {
+    if (value != 4.0 && value != 8.0) return DS_EINVAL;
+    P.samples_per_thread = (int)value;
   } else if (k == "rescan_dedup") {
     if (value != 0.0 && value != 1.0) return DS_EINVAL;
     P.rescan_dedup = (int)value;

@@ -103,6 +103,178 @@ __global__ void __launch_bounds__(kBlock) k_bin(const int32_t* __restrict__ pix,
   }
 }
 
+// ---- float32 operator, 8 samples per thread ------------------------------------
+// The same passes as k_bin / k_rescan (float32 arithmetic, float32 baselines and
+// map, float32 pixel sums) with two 16-byte loads per stream per thread, so that
+// twice the bytes are in flight per resident warp.
+
+// Samples 8 u .. 8 u + 7; past n_t: pixel -1.
+__device__ __forceinline__ void load8(const int32_t* __restrict__ pix,
+                                      const float* __restrict__ cc,
+                                      const float* __restrict__ ss, int64_t u, int64_t n_t,
+                                      int (&p)[8], float (&c)[8], float (&s)[8]) {
+  const int64_t t0 = u << 3;
+  if (t0 + 8 <= n_t) {
+    const int4 p0 = ld_stream(reinterpret_cast<const int4*>(pix) + 2 * u);
+    const int4 p1 = ld_stream(reinterpret_cast<const int4*>(pix) + 2 * u + 1);
+    const float4 c0 = ld_stream(reinterpret_cast<const float4*>(cc) + 2 * u);
+    const float4 c1 = ld_stream(reinterpret_cast<const float4*>(cc) + 2 * u + 1);
+    const float4 s0 = ld_stream(reinterpret_cast<const float4*>(ss) + 2 * u);
+    const float4 s1 = ld_stream(reinterpret_cast<const float4*>(ss) + 2 * u + 1);
+    p[0] = p0.x; p[1] = p0.y; p[2] = p0.z; p[3] = p0.w;
+    p[4] = p1.x; p[5] = p1.y; p[6] = p1.z; p[7] = p1.w;
+    c[0] = c0.x; c[1] = c0.y; c[2] = c0.z; c[3] = c0.w;
+    c[4] = c1.x; c[5] = c1.y; c[6] = c1.z; c[7] = c1.w;
+    s[0] = s0.x; s[1] = s0.y; s[2] = s0.z; s[3] = s0.w;
+    s[4] = s1.x; s[5] = s1.y; s[6] = s1.z; s[7] = s1.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const bool in = t0 + k < n_t;
+      p[k] = in ? pix[t0 + k] : -1;
+      c[k] = in ? cc[t0 + k] : 0.f;
+      s[k] = in ? ss[t0 + k] : 0.f;
+    }
+  }
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_bin8(const int32_t* __restrict__ pix,
+                                                 const float* __restrict__ cc,
+                                                 const float* __restrict__ ss,
+                                                 const float* __restrict__ x,
+                                                 float* __restrict__ bins, int64_t n_t, int64_t L,
+                                                 int64_t n_b, KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int64_t n8 = (n_t + 7) >> 3;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n8; u += stride) {
+    int p[8];
+    float c[8], s[8];
+    load8(pix, cc, ss, u, n_t, p, c, s);
+    const int64_t t0 = u << 3;
+    int64_t b = t0 / L;
+    int64_t bend = (b + 1) * L;
+    float zb[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? __ldg(x + o * n_b + b) : 0.f;
+    float acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+    int cur = -1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t t = t0 + k;
+      if (t >= n_t) break;
+      if (t >= bend) {
+        b += 1;
+        bend += L;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? __ldg(x + o * n_b + b) : 0.f;
+      }
+      if (p[k] < 0) continue;
+      float w[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) w[j] = 0.f;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < n_o) row_bin<NC, float>(K::kind(o, kk), c[k], s[k], zb[o], w);
+      if (p[k] != cur) {
+        if (cur >= 0) flush_bins<NC, float>(bins, cur, acc);
+        cur = p[k];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = w[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] += w[j];
+      }
+    }
+    if (cur >= 0) flush_bins<NC, float>(bins, cur, acc);
+  }
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_rescan8(const int32_t* __restrict__ pix,
+                                                    const float* __restrict__ cc,
+                                                    const float* __restrict__ ss,
+                                                    const float* __restrict__ x,
+                                                    const float* __restrict__ map,
+                                                    double* __restrict__ out, int64_t n_t,
+                                                    int64_t L, int64_t n_b, KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int lane = threadIdx.x & 31;
+  const int64_t n8 = (n_t + 7) >> 3;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t ub = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; ub < n8;
+       ub += stride) {
+    const int64_t u = ub + lane;
+    int key = -1;
+    float acc[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o] = 0.f;
+    if (u < n8) {
+      int p[8];
+      float c[8], s[8];
+      load8(pix, cc, ss, u, n_t, p, c, s);
+      // the map row is gathered once per run of equal pixels in the thread's samples
+      float m[8][NC];
+      bool dup[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dup[k] = k > 0 && p[k] >= 0 && p[k] == p[k - 1];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (p[k] >= 0 && !dup[k]) {
+          load_map<NC, float>(map, p[k], m[k]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) m[k][j] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int k = 1; k < 8; ++k)
+        if (dup[k]) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) m[k][j] = m[k - 1][j];
+        }
+      const int64_t t0 = u << 3;
+      int64_t b = t0 / L;
+      int64_t bend = (b + 1) * L;
+      float zb[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? __ldg(x + o * n_b + b) : 0.f;
+      key = (int)b;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int64_t t = t0 + k;
+        if (t >= n_t) break;
+        if (t >= bend) {
+#pragma unroll
+          for (int o = 0; o < NO; ++o) {
+            if (o < n_o && acc[o] != 0.f) atomicAdd(out + o * n_b + b, to_f64(acc[o]));
+            acc[o] = 0.f;
+          }
+          b += 1;
+          bend += L;
+          key = (int)b;
+#pragma unroll
+          for (int o = 0; o < NO; ++o) zb[o] = o < n_o ? __ldg(x + o * n_b + b) : 0.f;
+        }
+        if (p[k] < 0) continue;
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o) acc[o] += zb[o] - row_dot<NC, float>(K::kind(o, kk), c[k], s[k], m[k]);
+      }
+    }
+    warp_segment_flush<NO, float>(key, acc, n_o, out, n_b);
+  }
+}
+
 // x rounded to float32 once per operator apply, so that the float32 passes read
 // float32 baselines (no float64 conversion per sample group)
 __global__ void __launch_bounds__(kBlock) k_to_f32(const double* __restrict__ x,
@@ -287,6 +459,9 @@ void launch_bin_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, Ga
     if (fp64)
       k_bin<KS, double, false, double, double><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, x, nullptr, P.bins, P.n_t, P.L, P.n_b, P.kinds, g);
+    else if (f32_bins(P, fp64) && P.x32 != nullptr && P.samples_per_thread == 8)
+      k_bin8<KS><<<stream_grid(P, (P.n_t + 7) / 8, kBlock, P.blocks_per_sm), kBlock, 0, st>>>(
+          P.pix, P.c, P.s, P.x32, P.bins32, P.n_t, P.L, P.n_b, P.kinds, g);
     else if (f32_bins(P, fp64) && P.x32 != nullptr)
       k_bin<KS, float, false, float, float, float><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, P.x32, nullptr, P.bins32, P.n_t, P.L, P.n_b, P.kinds, g);
@@ -339,6 +514,9 @@ void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x,
     if (fp64)
       k_rescan<KS, double, false, double><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, x, nullptr, P.map64, out, P.n_t, P.L, P.n_b, P.kinds, g);
+    else if (P.x32 != nullptr && P.samples_per_thread == 8)
+      k_rescan8<KS><<<stream_grid(P, (P.n_t + 7) / 8, kBlock, P.blocks_per_sm), kBlock, 0, st>>>(
+          P.pix, P.c, P.s, P.x32, P.map32, out, P.n_t, P.L, P.n_b, P.kinds, g);
     else if (P.rescan_dedup && P.x32 != nullptr)
       k_rescan<KS, float, false, float, true, float><<<grid, kBlock, 0, st>>>(
           P.pix, P.c, P.s, P.x32, nullptr, P.map32, out, P.n_t, P.L, P.n_b, P.kinds, g);

@@ -138,6 +138,7 @@ struct Plan {
   int refresh_max;          // mixed plans: float64 residual at least every this many iterations
   int layout;               // mixed operator: 0 = time-ordered pixels, 1 = chunk-local index
   int rescan_dedup;         // float32 rescan: reuse the map value of a repeated pixel
+  int samples_per_thread;   // float32 operator: 4 or 8 consecutive samples per thread
   // chunk-local pixel index (chunked.cu)
   uint16_t* lid;
   int32_t* upix;

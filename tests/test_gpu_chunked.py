@@ -90,12 +90,14 @@ def test_chunked_operator_with_distinct_pixels(kinds):
         check_apply(prob, chunk)
 
 
+@pytest.mark.parametrize("tune", [{"rescan_dedup": 1}, {"rescan_dedup": 0},
+                                  {"samples_per_thread": 8}], ids=["dedup", "no_dedup", "spt8"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_rescan_reusing_repeated_pixels(case):
+def test_time_ordered_operator_variants(case, tune):
     kinds, nside, n_t, L, ff, scan = case
     prob = make_problem(n_t, nside, kinds, baseline_len=L, seed=22, scan=scan, flag_frac=ff,
                         flag_mean_len=200, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
-    check_apply(prob, None, layout=0, tune={"rescan_dedup": 1})
+    check_apply(prob, None, layout=0, tune=tune)
 
 
 def test_layouts_agree():
