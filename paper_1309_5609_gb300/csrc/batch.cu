@@ -770,17 +770,44 @@ ds_status ensure_tiles(ds_batch_t B, int w, int n) {
   return DS_OK;
 }
 
+// Tile length for a work list: the configured one, shrunk when the live problems
+// would give fewer than two tiles per resident block (a batch's tail, when few
+// problems are still iterating, would otherwise leave most blocks idle).
+int64_t effective_tile(int64_t configured, int64_t total, int64_t blocks, int64_t floor,
+                       int64_t align) {
+  int64_t t = configured;
+  if (total / t < 2 * blocks) {
+    t = total / (2 * blocks);
+    t = (t + align - 1) / align * align;
+    if (t < floor) t = floor;
+    if (t > configured) t = configured;
+  }
+  return t;
+}
+
 // Rebuilds the three work lists from the slots whose problems are still running
 // (stopped problems drop out, so the kernels only walk live tiles).
 ds_status rebuild_tiles(ds_batch_t B) {
+  int64_t tot_vec = 0, tot_pix = 0, tot_u = 0;
+  for (int sl = 0; sl < B->max_slots; ++sl) {
+    const Plan* P = B->plans[sl];
+    if (!P || B->stopped[sl]) continue;
+    tot_vec += (P->n_t + 3) / 4;
+    tot_pix += P->npix;
+    tot_u += P->n_u;
+  }
+  const int64_t sblocks = (int64_t)B->num_sms * B->blocks_per_sm, ublocks = (int64_t)B->num_sms * 4;
+  const int64_t tv = effective_tile(B->tile_vecs, tot_vec, sblocks, 256, 32);  // >= 1024 samples
+  const int64_t tp = effective_tile(B->tile_pixels, tot_pix, sblocks, 1024, 256);
+  const int64_t tu = effective_tile(B->tile_unknowns, tot_u, ublocks, 1024, 256);
   int n[3] = {0, 0, 0};
   for (int sl = 0; sl < B->max_slots; ++sl) {
     const Plan* P = B->plans[sl];
     if (!P || B->stopped[sl]) continue;
     const int64_t nvec = (P->n_t + 3) / 4;
-    n[W_SAMPLES] += (int)((nvec + B->tile_vecs - 1) / B->tile_vecs);
-    n[W_PIXELS] += (int)((P->npix + B->tile_pixels - 1) / B->tile_pixels);
-    n[W_UNKNOWNS] += (int)((P->n_u + B->tile_unknowns - 1) / B->tile_unknowns);
+    n[W_SAMPLES] += (int)((nvec + tv - 1) / tv);
+    n[W_PIXELS] += (int)((P->npix + tp - 1) / tp);
+    n[W_UNKNOWNS] += (int)((P->n_u + tu - 1) / tu);
   }
   for (int w = 0; w < 3; ++w) {
     ds_status s = ensure_tiles(B, w, n[w] > 0 ? n[w] : 1);
@@ -791,13 +818,13 @@ ds_status rebuild_tiles(ds_batch_t B) {
     const Plan* P = B->plans[sl];
     if (!P || B->stopped[sl]) continue;
     const int64_t nvec = (P->n_t + 3) / 4;
-    for (int64_t b = 0; b < nvec; b += B->tile_vecs)
-      B->h_tiles[W_SAMPLES][k[W_SAMPLES]++] = WorkTile{sl, 0, b, b + B->tile_vecs < nvec ? b + B->tile_vecs : nvec};
-    for (int64_t b = 0; b < P->npix; b += B->tile_pixels)
-      B->h_tiles[W_PIXELS][k[W_PIXELS]++] = WorkTile{sl, 0, b, b + B->tile_pixels < P->npix ? b + B->tile_pixels : P->npix};
+    for (int64_t b = 0; b < nvec; b += tv)
+      B->h_tiles[W_SAMPLES][k[W_SAMPLES]++] = WorkTile{sl, 0, b, b + tv < nvec ? b + tv : nvec};
+    for (int64_t b = 0; b < P->npix; b += tp)
+      B->h_tiles[W_PIXELS][k[W_PIXELS]++] = WorkTile{sl, 0, b, b + tp < P->npix ? b + tp : P->npix};
     B->h_slots[sl].u_first = k[W_UNKNOWNS];
-    for (int64_t b = 0; b < P->n_u; b += B->tile_unknowns)
-      B->h_tiles[W_UNKNOWNS][k[W_UNKNOWNS]++] = WorkTile{sl, 0, b, b + B->tile_unknowns < P->n_u ? b + B->tile_unknowns : P->n_u};
+    for (int64_t b = 0; b < P->n_u; b += tu)
+      B->h_tiles[W_UNKNOWNS][k[W_UNKNOWNS]++] = WorkTile{sl, 0, b, b + tu < P->n_u ? b + tu : P->n_u};
     B->h_slots[sl].u_count = k[W_UNKNOWNS] - B->h_slots[sl].u_first;
   }
   for (int w = 0; w < 3; ++w) B->h_ntiles[w] = k[w];
