@@ -582,11 +582,16 @@ def iteration_stats(reqs, ok_status):
     it_ok = [r.iters for r in reqs if r.status == ok_status]
     work = [r.n_t * r.iters for r in reqs]
     bad = [r.n_t * r.iters for r in reqs if r.status != ok_status]
+    tot = float(sum(work)) or 1.0
+    share = lambda sel: float(sum(r.n_t * r.iters for r in reqs if sel(r)) / tot)
     return {"converged_p50": float(np.percentile(it_ok, 50)) if it_ok else None,
             "converged_p99": float(np.percentile(it_ok, 99)) if it_ok else None,
             "converged_max": int(max(it_ok)) if it_ok else None,
             "not_converged": len(bad),
-            "not_converged_work_share": float(sum(bad) / sum(work)) if sum(work) else 0.0}
+            "not_converged_work_share": float(sum(bad) / tot),
+            "work_share_lone_q": share(lambda r: len(r.kinds) == 1),
+            "work_share_over_1000_iterations": share(lambda r: r.iters > 1000),
+            "requests_over_1000_iterations": sum(1 for r in reqs if r.iters > 1000)}
 
 
 def run_serve(args):
@@ -673,6 +678,7 @@ def run_serve(args):
             "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "mean_latency_s": summ["mean_s"],
             "iterations": iteration_stats(reqs, ds.DS_OK),
             "samples_per_s": summ["samples_per_s"], "converged": int(ok),
+            "host_time_s": {k: summ[k] for k in ("host_admit_s", "host_step_s", "host_retire_s")},
             "max_resident": summ["max_resident"], "gpu_launches": summ["kernel_launches"],
             "sequential_fp64_model": {
                 "p50_s": float(np.percentile(seq_lat, 50)), "p99_s": float(np.percentile(seq_lat, 99)),

@@ -203,6 +203,15 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     (default 1e-5)
  *   "refresh_max"     MIXED plans: recompute the residual in float64 at least every this
  *                     many iterations, whatever the drop (default 50)
+ *   "drift_ratio"     MIXED plans: when a recomputed ||r||^2 exceeds this many times the
+ *                     recursive one, the float32 operator cannot follow the problem and
+ *                     the solve continues with the accurate operator (default 1e4)
+ *   "accurate_start"  MIXED plans: 1 = iterate with the accurate operator from the start
+ *                     (small ill-conditioned problems converge in several times fewer
+ *                     iterations with it)
+ *   "stall_iters"     stop a solve, with DS_ENOCONV and its best iterate, when its residual
+ *                     has not dropped 10x within this many iterations: an ill-posed
+ *                     system has reached its floor (default 2000; 0 = never)
  *   "bin_mode"        MIXED plans: 1 = float32 pixel sums with one vector atomic per run
  *                     (default), 0 = float64 pixel sums with scalar atomics
  *   "graph_iters"     1..64 CG iterations per captured graph replay (default 16)

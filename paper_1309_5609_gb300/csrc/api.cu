@@ -39,6 +39,7 @@ int kindset_of(const int* k, int n_o, int n_c) {
   if (n_o == 3 && k[0] == DS_KIND_I && k[1] == DS_KIND_Q && k[2] == DS_KIND_U) return KS_IQU3;
   if (n_o == 1 && k[0] == DS_KIND_IQU) return KS_IQU1;
   if (n_o == 1 && k[0] == DS_KIND_I) return KS_I;
+  if (n_c == 2 && n_o <= 2) return KS_QU12;  // q and u outputs only, at most two
   return n_c == 1 ? KS_GEN1 : (n_c == 2 ? KS_GEN2 : KS_GEN3);
 }
 
@@ -280,6 +281,9 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->accurate_df = 1;
   P->stream_mode = 0;
   P->refresh_max = 50;
+  P->drift_ratio = 1e4;
+  P->accurate_start = 0;
+  P->stall_iters = 2000;
   P->layout = 0;
   P->rescan_dedup = 1;
   P->samples_per_thread = 4;
@@ -440,7 +444,7 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   const int max_launches = max_iter / P.graph_iters + 4;
   bool done = false;
   int iter_before = 0;
-  bool accurate = false;
+  bool accurate = P.accurate_start != 0 && P.desc.precision == DS_PREC_MIXED;
   for (int k = 0; k < max_launches && !done; ++k) {
     // a mixed problem that the float32 operator cannot follow continues with the
     // accurate one (the switch is decided on the device at a float64 refresh)
@@ -483,6 +487,7 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
     case 1: return DS_OK;
     case 2: return DS_ENOCONV;
     case 3: return H.rr_true <= H.tol2 ? DS_OK : DS_ENOCONV;
+    case 5: return DS_ENOCONV;  // stalled: no 10x residual drop in stall_iters iterations
     default: return P.x_best != nullptr ? DS_ENOCONV : DS_ENAN;
   }
 }
@@ -553,6 +558,16 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
     if (P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
     const ds_status s = chunk_index(P, C);
     if (s != DS_OK) return s;
+  } else if (k == "drift_ratio") {
+    if (!(value > 1.0 && value < 1e30)) return DS_EINVAL;
+    P.drift_ratio = value;
+  } else if (k == "stall_iters") {
+    if (!(value >= 0.0 && value <= 1e9)) return DS_EINVAL;
+    P.stall_iters = (int)value;
+  } else if (k == "accurate_start") {
+    if (value != 0.0 && value != 1.0) return DS_EINVAL;
+    if (value == 1.0 && P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
+    P.accurate_start = (int)value;
   } else if (k == "samples_per_thread") {
     if (value != 4.0 && value != 8.0) return DS_EINVAL;
     P.samples_per_thread = (int)value;

@@ -21,19 +21,6 @@ namespace {
 
 constexpr int kBlock = 256;
 
-template <typename F>
-void with_kindset(int ks, F&& f) {
-  switch (ks) {
-    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
-    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
-    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
-    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
-    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
-    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
-    default: f(std::integral_constant<int, KS_GEN3>{}); break;
-  }
-}
-
 // ---- binning: bins[p] += sum_o w_o(t) z_o(t) over samples with v = 1 ----------
 // ZY = false: z_o(t) = x[o][t / L]          (F~ x, the operator)
 // ZY = true : z_o(t) = y[o][t] - a[o][t/L]  (data minus baselines; a may be NULL)

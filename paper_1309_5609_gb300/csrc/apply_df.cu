@@ -27,19 +27,6 @@ constexpr int kBlock = 256;
 // registers) spills and gains nothing more.
 constexpr int kDfMinBlocks = 3;
 
-template <typename F>
-void with_kindset(int ks, F&& f) {
-  switch (ks) {
-    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
-    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
-    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
-    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
-    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
-    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
-    default: f(std::integral_constant<int, KS_GEN3>{}); break;
-  }
-}
-
 // x[i] -> (hi, lo) with hi = x rounded to float32, lo = the rest rounded to float32
 __global__ void __launch_bounds__(kBlock) k_split_df(const double* __restrict__ x,
                                                      float2* __restrict__ xs, int64_t n, Gate g) {

@@ -53,19 +53,6 @@ struct PipeSmem {
   unsigned long long empty[Cfg::STAGES];
 };
 
-template <typename F>
-void with_kindset(int ks, F&& f) {
-  switch (ks) {
-    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
-    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
-    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
-    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
-    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
-    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
-    default: f(std::integral_constant<int, KS_GEN3>{}); break;
-  }
-}
-
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }

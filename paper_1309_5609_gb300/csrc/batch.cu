@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "cg_state.cuh"
 #include "df.cuh"
 #include "internal.cuh"
 #include "rows.cuh"
@@ -617,29 +618,7 @@ __global__ void __launch_bounds__(kBlock) k_bb_reliable(const SlotDesc* __restri
       acc += ri * ri;
     }
     double tot;
-    if (bb_finish(acc, ti, uf, uc, red, tickets + 4 * T.slot + 2, &tot)) {
-      if (!st->accurate && tot > 1e4 * st->rr) st->accurate = 1;  // float32 drift: switch
-      if (tot < st->rr_best) {
-        st->rr_best = tot;
-        st->improved = 1;
-      }
-      st->rr = tot;
-      st->rr_anchor = tot;
-      st->rr_true = tot;
-      st->n_reliable += 1;
-      st->last_refresh = st->iter;
-      st->need = 0;
-      if (!isfinite(tot)) {
-        st->status = 4;
-        st->done = 1;
-      } else if (tot <= st->tol2) {
-        st->status = 1;
-        st->done = 1;
-      } else if (st->iter >= st->max_iter) {
-        st->status = 2;
-        st->done = 1;
-      }
-    }
+    if (bb_finish(acc, ti, uf, uc, red, tickets + 4 * T.slot + 2, &tot)) after_refresh(st, tot);
   }
 }
 
@@ -832,19 +811,6 @@ ds_status rebuild_tiles(ds_batch_t B) {
   return DS_OK;
 }
 
-template <typename F>
-void with_kindset(int ks, F&& f) {
-  switch (ks) {
-    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
-    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
-    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
-    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
-    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
-    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
-    default: f(std::integral_constant<int, KS_GEN3>{}); break;
-  }
-}
-
 // kind set of the batch: the common one when every problem has the same kinds,
 // else the generic set of its component count (kinds read per problem)
 int batch_kindset(ds_batch_t B);
@@ -896,13 +862,16 @@ ds_status batch_upload(ds_batch_t B) {
 
 int batch_kindset(ds_batch_t B) {
   int ks = -1;
+  bool qu12 = true;  // every problem has one or two q / u outputs
   for (int i = 0; i < B->max_slots; ++i) {
     const Plan* P = B->plans[i];
     if (!P) continue;
+    qu12 &= P->kindset == KS_QU || P->kindset == KS_QU12;
     if (ks == -1) ks = P->kindset;
     else if (ks != P->kindset) ks = -2;
   }
   if (ks >= 0) return ks;
+  if (qu12) return KS_QU12;
   return B->nc == 1 ? KS_GEN1 : (B->nc == 2 ? KS_GEN2 : KS_GEN3);
 }
 

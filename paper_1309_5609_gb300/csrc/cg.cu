@@ -11,6 +11,7 @@
 // operator and CG continues from it ("reliable updates").
 #include <cmath>
 
+#include "cg_state.cuh"
 #include "internal.cuh"
 
 namespace ds {
@@ -18,7 +19,6 @@ namespace ds {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr double kDriftRatio = 1e4;  // ||r_true||^2 / ||r_recursive||^2 that triggers the switch
 
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sm[32];
@@ -116,9 +116,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_start(double* __restrict__ x, dou
     st->need = 0;
     st->n_reliable = 0;
     st->last_refresh = 0;
-    st->accurate = 0;
+    st->accurate = st->accurate_start;
     st->improved = 0;
     st->rr_best = tot;
+    st->rr_progress = tot;
+    st->progress_iter = 0;
     st->status = 0;
     st->done = 0;
     if (!isfinite(tot) || !isfinite(st->bb)) {
@@ -218,11 +220,15 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(double* __restrict__ x,
         st->need = 1;
     } else {
       st->rr_true = tot;
+      track_progress(st, tot);
       if (conv) {
-        st->status = 1;
+        st->status = CG_CONVERGED;
         st->done = 1;
       } else if (st->iter >= st->max_iter) {
-        st->status = 2;
+        st->status = CG_MAX_ITER;
+        st->done = 1;
+      } else if (stalled(st)) {
+        st->status = CG_STALLED;
         st->done = 1;
       }
     }
@@ -256,29 +262,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_reliable(double* __restrict__ r,
   }
   double tot;
   if (finish_sum(acc, red, ticket, &tot)) {
-    // The float32 operator is not accurate enough for this problem when the true
-    // residual sits far above the recursive one: iterate with the accurate one.
-    if (st->mixed && !st->accurate && tot > kDriftRatio * st->rr) st->accurate = 1;
-    if (tot < st->rr_best) {
-      st->rr_best = tot;
-      st->improved = 1;
-    }
-    st->rr = tot;
-    st->rr_anchor = tot;
-    st->rr_true = tot;
-    st->n_reliable += 1;
-    st->last_refresh = st->iter;
-    st->need = 0;
-    if (!isfinite(tot)) {
-      st->status = 4;
-      st->done = 1;
-    } else if (tot <= st->tol2) {
-      st->status = 1;
-      st->done = 1;
-    } else if (st->iter >= st->max_iter) {
-      st->status = 2;
-      st->done = 1;
-    }
+    after_refresh(st, tot);
   }
 }
 
@@ -358,8 +342,12 @@ __global__ void __launch_bounds__(kBlock) k_gauge_apply(double* __restrict__ a,
 }
 
 __global__ void k_set_state(CgState* st, double tol, int max_iter, int mixed, double delta,
-                            int refresh_max) {
+                            int refresh_max, double drift2, int accurate_start,
+                            int stall_iters) {
   st->tol2 = tol * tol * st->bb;
+  st->stall_iters = stall_iters;
+  st->drift2 = drift2;
+  st->accurate_start = mixed ? accurate_start : 0;
   st->max_iter = max_iter;
   st->refresh_max = refresh_max;
   st->mixed = mixed;
@@ -422,7 +410,8 @@ void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, 
   const bool mixed = P.desc.precision == DS_PREC_MIXED;
   // bb = b . b
   enqueue_dot(P, st, P.b, P.b, P.n_u, &P.state->bb);
-  k_set_state<<<1, 1, 0, st>>>(P.state, tol, max_iter, mixed ? 1 : 0, delta, P.refresh_max);
+  k_set_state<<<1, 1, 0, st>>>(P.state, tol, max_iter, mixed ? 1 : 0, delta, P.refresh_max,
+                               P.drift_ratio, P.accurate_start, P.stall_iters);
   if (warm) {
     cudaMemsetAsync(P.t, 0, sizeof(double) * P.n_u, st);
     enqueue_apply(P, st, true, P.x, P.t, Gate{nullptr, nullptr});

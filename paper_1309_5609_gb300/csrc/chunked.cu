@@ -29,19 +29,6 @@ namespace {
 constexpr uint16_t kNoPix = 0xFFFF;
 constexpr int kBuildThreads = 1024;
 
-template <typename F>
-void with_kindset(int ks, F&& f) {
-  switch (ks) {
-    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
-    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
-    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
-    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
-    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
-    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
-    default: f(std::integral_constant<int, KS_GEN3>{}); break;
-  }
-}
-
 // ---- plan time: sort each chunk's (pixel, position) keys, rank the distinct pixels
 // One block per chunk.  Keys are (pixel << 32 | position in chunk); weight-0
 // samples carry pixel 0xFFFFFFFF and sort last.  Bitonic sort in shared memory.

@@ -27,7 +27,10 @@
 namespace ds {
 
 // Kind sets with their rows known at compile time; GEN* take kinds at run time.
-enum KindSet { KS_QU = 0, KS_IQU3 = 1, KS_IQU1 = 2, KS_I = 3, KS_GEN1 = 4, KS_GEN2 = 5, KS_GEN3 = 6 };
+enum KindSet {
+  KS_QU = 0, KS_IQU3 = 1, KS_IQU1 = 2, KS_I = 3, KS_GEN1 = 4, KS_GEN2 = 5, KS_GEN3 = 6,
+  KS_QU12 = 7  // one or two outputs, each q or u (components Q, U): lone q / u, and mixes of them
+};
 
 struct KindsArg {
   int n_o;
@@ -71,8 +74,13 @@ struct CgState {
   int refresh_max;   // refresh at least every refresh_max iterations (stagnation guard)
   int accurate;      // 1: the float32 operator could not follow; iterate with the accurate one
   int improved;      // the last float64 residual is the best so far: keep x
-  int pad0, pad1;
+  int accurate_start;  // 1: iterate with the accurate operator from the start
+  int pad1;
   double rr_best;    // smallest float64 ||b - A x||^2 seen (mixed plans keep that x)
+  double drift2;     // ||r_true||^2 / ||r_recursive||^2 above which the accurate operator takes over
+  double rr_progress;  // the residual at the last 10x improvement
+  int progress_iter;   // ... and its iteration
+  int stall_iters;     // stop when no 10x improvement for this many iterations (0 = never)
 };
 
 enum ErrBits { ERR_PIX = 1, ERR_NAN = 2, ERR_TIMEOUT = 4 };
@@ -136,6 +144,9 @@ struct Plan {
   int accurate_df;          // mixed plans: accurate passes in double-float (1) or float64 (0)
   int stream_mode;          // mixed operator: 0 = direct vector loads, 1 = TMA-staged pipeline
   int refresh_max;          // mixed plans: float64 residual at least every this many iterations
+  double drift_ratio;       // mixed plans: squared true / recursive residual ratio of the switch
+  int accurate_start;       // mixed plans: 1 = accurate operator from the first iteration
+  int stall_iters;          // stop a solve whose residual has not dropped 10x in this many iterations
   int layout;               // mixed operator: 0 = time-ordered pixels, 1 = chunk-local index
   int rescan_dedup;         // float32 rescan: reuse the map value of a repeated pixel
   int samples_per_thread;   // float32 operator: 4 or 8 consecutive samples per thread

@@ -329,19 +329,6 @@ __global__ void __launch_bounds__(kBlock) k_plan_weights(const int32_t* __restri
   if (lane == 0 && total) atomicAdd(n_valid, total);
 }
 
-template <typename F>
-void with_kindset(int ks, F&& f) {
-  switch (ks) {
-    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
-    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
-    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
-    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
-    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
-    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
-    default: f(std::integral_constant<int, KS_GEN3>{}); break;
-  }
-}
-
 }  // namespace
 
 ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid) {

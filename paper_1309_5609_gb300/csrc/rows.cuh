@@ -7,6 +7,8 @@
 // Component frame: NC = 1 -> (I); NC = 2 -> (Q, U); NC = 3 -> (I, Q, U).
 #pragma once
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace ds {
@@ -88,9 +90,30 @@ template <int NC_> struct KSetGen {
   __device__ static int n_o(const KindsArg& k) { return k.n_o; }
   __device__ static int kind(int o, const KindsArg& k) { return k.kind[o]; }
 };
+template <> struct KSet<KS_QU12> {
+  static constexpr int NC = 2, NO = 2;
+  __device__ static int n_o(const KindsArg& k) { return k.n_o; }
+  __device__ static int kind(int o, const KindsArg& k) { return k.kind[o]; }
+};
 template <> struct KSet<KS_GEN1> : KSetGen<1> {};
 template <> struct KSet<KS_GEN2> : KSetGen<2> {};
 template <> struct KSet<KS_GEN3> : KSetGen<3> {};
+
+// Calls f(std::integral_constant<int, KS>{}) for the run-time kind set ks, so that
+// kernels are instantiated per kind set and chosen on the host.
+template <typename F>
+void with_kindset(int ks, F&& f) {
+  switch (ks) {
+    case KS_QU: f(std::integral_constant<int, KS_QU>{}); break;
+    case KS_IQU3: f(std::integral_constant<int, KS_IQU3>{}); break;
+    case KS_IQU1: f(std::integral_constant<int, KS_IQU1>{}); break;
+    case KS_I: f(std::integral_constant<int, KS_I>{}); break;
+    case KS_QU12: f(std::integral_constant<int, KS_QU12>{}); break;
+    case KS_GEN1: f(std::integral_constant<int, KS_GEN1>{}); break;
+    case KS_GEN2: f(std::integral_constant<int, KS_GEN2>{}); break;
+    default: f(std::integral_constant<int, KS_GEN3>{}); break;
+  }
+}
 
 // Packed symmetric inverse times a vector: m = Minv s.
 template <int NC>

@@ -29,7 +29,7 @@ import numpy as np
 
 from . import (DS_OK, destripe_batch_add, destripe_batch_create, destripe_batch_info,
                destripe_batch_retire, destripe_batch_slot_status, destripe_batch_step,
-               destripe_plan)
+               destripe_plan, destripe_tune)
 
 
 @dataclass
@@ -44,6 +44,7 @@ class Request:
     sin2psi: object
     y: object                 # float32 [n_o, n_t], or a list of n_o float32 [n_t] rows
     tol: float = 1e-10
+    accurate_start: Optional[bool] = None  # None: the server's size rule
     # filled by the server
     admitted: float = -1.0
     finished: float = -1.0
@@ -79,6 +80,9 @@ class ServeStats:
     steps: int = 0
     max_resident: int = 0
     kernel_launches: int = 0
+    t_admit: float = 0.0     # host seconds in admission (copies, plan, right-hand side)
+    t_step: float = 0.0      # host seconds in batch steps (graph replays, waits)
+    t_retire: float = 0.0    # host seconds in retirement (gauge, copy back)
 
     def summary(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.array([np.nan])
@@ -87,14 +91,21 @@ class ServeStats:
                 "samples_per_s": self.samples / self.wall if self.wall else None,
                 "sample_iters_per_s": self.sample_iters / self.wall if self.wall else None,
                 "wall_s": self.wall, "steps": self.steps, "max_resident": self.max_resident,
-                "kernel_launches": self.kernel_launches}
+                "kernel_launches": self.kernel_launches, "host_admit_s": self.t_admit,
+                "host_step_s": self.t_step, "host_retire_s": self.t_retire}
 
 
 class Server:
-    """Continuous-batching destriping server on the current CUDA device."""
+    """Continuous-batching destriping server on the current CUDA device.
+
+    Requests shorter than accurate_below samples iterate with the accurate
+    operator from the start: on small, ill-conditioned problems the float32
+    operator costs CG its conjugacy and several times the iterations, while their
+    accurate iterations are cheap."""
 
     def __init__(self, max_slots: int = 64, hbm_budget: int = 64 << 30,
-                 iters_per_step: int = 8, clock: Callable[[], float] = time.perf_counter):
+                 iters_per_step: int = 8, clock: Callable[[], float] = time.perf_counter,
+                 accurate_below: int = 3_000_000):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
@@ -104,6 +115,7 @@ class Server:
         self.max_slots = max_slots
         self.budget = int(hbm_budget)
         self.iters_per_step = iters_per_step
+        self.accurate_below = accurate_below
         self.clock = clock
         self.used = 0
         self.queue: List[Request] = []       # arrived, not admitted
@@ -138,6 +150,9 @@ class Server:
         plan = destripe_plan(pix, c, s, None, nside=req.nside, kinds=req.kinds,
                              baseline_len=req.baseline_len, precision="mixed",
                              stream=self.stream.cuda_stream)
+        acc = req.accurate_start if req.accurate_start is not None else req.n_t < self.accurate_below
+        if acc:
+            destripe_tune(plan, "accurate_start", 1)
         slot = destripe_batch_add(self.batch, plan, y, tol=req.tol)
         req.admitted = self.now()
         self.resident[slot] = (req, plan, (pix, c, s, y), need)
@@ -172,12 +187,18 @@ class Server:
             t = self.now()
             while pending and pending[0].arrival <= t:
                 self.queue.append(pending.pop(0))
+            c0 = self.clock()
             while self.queue and self._admit(self.queue[0]):
                 self.queue.pop(0)
+            c1 = self.clock()
+            self.stats.t_admit += c1 - c0
             if self.resident:
                 destripe_batch_step(self.batch, self.iters_per_step)
                 self.stats.steps += 1
+                c2 = self.clock()
+                self.stats.t_step += c2 - c1
                 self._retire_finished()
+                self.stats.t_retire += self.clock() - c2
             elif pending:
                 time.sleep(max(0.0, min(0.01, pending[0].arrival - self.now())))
             if time_limit is not None and self.now() > time_limit:

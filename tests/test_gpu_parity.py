@@ -405,3 +405,39 @@ def test_solve_every_case(case, precision):
     yo = y.double().cpu().numpy().reshape(plan.n_o, plan.n_t)
     ref = oracle.destripe(op, yo, tol=1e-10)
     assert np.abs(a.cpu().numpy() - ref["a"]).max() < 1e-4
+
+
+def test_stalled_solve_stops_early_with_best_iterate():
+    # an unreachable tolerance: the recomputed residual of a mixed plan reaches its
+    # rounding floor and stalls (a float64 plan's recursive residual has no floor)
+    prob = case_problem(CASES[0])
+    op, d = oracle_plan(prob)
+    plan, g, y = gpu_plan(prob, "mixed")
+    ds.destripe_tune(plan, "stall_iters", 60)
+    a = torch.zeros(plan.n_u, dtype=torch.float64, device=DEV)
+    st, iters, rel = ds.destripe_solve(plan, y, a, tol=1e-30, max_iter=100000)
+    assert st == ds.DS_ENOCONV, st
+    assert iters < 2000
+    assert rel < 1e-9  # the best iterate is returned
+    yo = y.double().cpu().numpy().reshape(plan.n_o, plan.n_t)
+    ref = oracle.destripe(op, yo, tol=1e-10)
+    assert np.abs(a.cpu().numpy() - ref["a"]).max() < 1e-4
+    plan.close()
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[4]], ids=["qu", "q_only"])
+def test_accurate_start_matches_oracle(case):
+    prob = case_problem(case)
+    op, d = oracle_plan(prob)
+    plan, g, y = gpu_plan(prob, "mixed")
+    ds.destripe_tune(plan, "accurate_start", 1)
+    ds.destripe_profile(plan, 1)
+    a = torch.zeros(plan.n_u, dtype=torch.float64, device=DEV)
+    st, iters, rel = ds.destripe_solve(plan, y, a, tol=1e-10)
+    prof = ds.destripe_profile(plan, -1)
+    assert st == ds.DS_OK, (st, iters, rel)
+    assert prof["iterations"] == iters and prof["timed_iterations"] == 0  # accurate graph only
+    yo = y.double().cpu().numpy().reshape(plan.n_o, plan.n_t)
+    ref = oracle.destripe(op, yo, tol=1e-10)
+    assert np.abs(a.cpu().numpy() - ref["a"]).max() < 1e-4
+    plan.close()
