@@ -299,8 +299,7 @@ def run_ours(args):
     mask = torch.zeros(npix, dtype=torch.uint8, device=dev)
 
     tune = parse_tune(args.tune)
-    chunked = args.precision == "mixed" and tune.get("layout", 0) == 1 and \
-        tune.get("stream_mode", 0) == 0
+    layout = {}  # the float32 operator's form, as the plans report it
 
     def step(prof_acc):
         plan = ds.destripe_plan(prob.pix, prob.c32, prob.s32, prob.valid, nside=prob.nside,
@@ -308,6 +307,8 @@ def run_ours(args):
                                 precision=args.precision)
         for k, v in tune.items():
             ds.destripe_tune(plan, k, v)
+        info = ds.destripe_plan_info(plan)
+        layout.update(layout=info["layout"], n_runs=info["n_runs"])
         if prof_acc is not None:
             ds.destripe_profile(plan, 1)
         st, iters, rel = ds.destripe_solve(plan, prob.y, a, tol=args.tol)
@@ -362,8 +363,11 @@ def run_ours(args):
     peak, peak_kind = peaks()
     dur_s = per_launch[dom] / 1e3
     achieved = alg_bytes / dur_s / 1e9 if dur_s > 0 else None
-    kname = ({"bin": "k_ck_bin", "rescan": "k_ck_rescan"} if chunked else
-             {"bin": "k_bin", "rescan": "k_rescan"})[dom]
+    mixed = args.precision == "mixed" and tune.get("stream_mode", 0) == 0
+    form = layout.get("layout", 0) if mixed else 0
+    kname = {0: {"bin": "k_bin", "rescan": "k_rescan"},
+             1: {"bin": "k_ck_bin", "rescan": "k_ck_rescan"},
+             2: {"bin": "k_rl_bin", "rescan": "k_rl_rescan"}}[form][dom]
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
             "traffic": kernel_traffic(prob.n_t, kname, name),
@@ -380,8 +384,9 @@ def run_ours(args):
             "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic (seeded scan, Gaussian sky, 1/f noise), resident in HBM",
             "config": dict(config_dict(args, name), tune=tune,
-                           operator_layout="chunk-local pixel index" if chunked
-                           else "time-ordered pixels"), "roofline": roof,
+                           operator_layout={0: "time-ordered pixels", 1: "chunk-local pixel index",
+                                            2: "run-length records"}[form],
+                           runs_per_sample=layout.get("n_runs", 0) / prob.n_t), "roofline": roof,
             "iterations_per_step": iters_tot / args.steps,
             "rel_resid_max": max(rels) if rels else None,
             "gpu_launches": int(prof.get("kernel_launches", 0)),

@@ -100,6 +100,9 @@ typedef struct {
   int32_t n_outputs;
   int32_t n_comp;        /* 1, 2 or 3 */
   int64_t device_bytes;  /* bytes the plan holds on the device */
+  int32_t layout;        /* form of the float32 operator in use (tune key "layout") */
+  int32_t reserved_;
+  int64_t n_runs;        /* run-length records held (0 if none) */
 } ds_info;
 
 /* Build a plan: hits, per-pixel normal matrices M_p, their inverses and the
@@ -225,7 +228,11 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     waits are bounded, DS_ETIMEOUT on expiry)
  *   "blocks_per_sm"   1..32 resident-block target of the streaming kernels (default 16)
  *   "layout"          MIXED plans: 0 = the float32 operator reads the time-ordered pixel
- *                     indices (default); 1 = it reads a chunk-local index (per chunk of
+ *                     indices; 2 = run-length records: per run of consecutive samples on
+ *                     one pixel within a baseline, (pixel, count, sum cos 2psi, sum
+ *                     sin 2psi) and the baseline (20 bytes per run; built by
+ *                     destripe_plan, and used by default, when there are at most 0.6 runs
+ *                     per sample; built on request otherwise); 1 = a chunk-local index (per chunk of
  *                     consecutive samples: the sorted distinct pixels and a 16-bit rank per
  *                     sample), bins into shared memory and stages the chunk's map in
  *                     shared memory.  The index is built on the plan's stream when first

@@ -75,6 +75,18 @@ cudaError_t plan_pool(int device, cudaMemPool_t* out) {
   return cudaSuccess;
 }
 
+}  // namespace
+
+cudaError_t ds::plan_alloc(Plan& P, void** ptr, size_t bytes, bool count) {
+  if (count) P.device_bytes += (int64_t)bytes;
+  cudaMemPool_t pool = nullptr;
+  const cudaError_t e = plan_pool(P.device, &pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(ptr, bytes, pool, P.stream);
+}
+
+namespace {
+
 template <typename T>
 cudaError_t dalloc(Plan& P, T** ptr, int64_t count) {
   const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
@@ -93,7 +105,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a
@@ -359,6 +371,8 @@ ds_status destripe_plan_info(ds_plan_t plan, ds_info* info) {
   info->n_outputs = P.n_o;
   info->n_comp = P.n_c;
   info->device_bytes = P.device_bytes;
+  info->layout = P.layout;
+  info->n_runs = P.rl_rec != nullptr ? P.rl_n : 0;
   return DS_OK;
 }
 
@@ -543,13 +557,16 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
     if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
     P.stream_mode = (int)value;
   } else if (k == "layout") {
-    if (value != 0.0 && value != 1.0) return DS_EINVAL;
-    if (value == 1.0) {
-      if (P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
-      if (P.lid == nullptr) {
-        const ds_status s = chunk_index(P, ck_default_chunk(P.n_t, P.num_sms));
-        if (s != DS_OK) return s;
-      }
+    if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
+    if (value != 0.0 && P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
+    if (value == 1.0 && P.lid == nullptr) {
+      const ds_status s = chunk_index(P, ck_default_chunk(P.n_t, P.num_sms));
+      if (s != DS_OK) return s;
+    }
+    if (value == 2.0 && P.rl_rec == nullptr) {
+      clear_stale_error();
+      const ds_status s = rl_build(P);
+      if (s != DS_OK) return s;
     }
     P.layout = (int)value;
   } else if (k == "chunk") {

@@ -375,7 +375,7 @@ void enqueue_gauge(const Plan& P, cudaStream_t st, double* a) {
 int kernels_per_iteration(const Plan& P, bool accurate) {
   if (P.desc.precision != DS_PREC_MIXED) return 6;
   const bool df = P.accurate_df && P.maplo != nullptr;  // + the baseline split kernel
-  const bool f32 = P.x32 != nullptr && !accurate && P.stream_mode == 0 && P.layout == 0;
+  const bool f32 = P.x32 != nullptr && !accurate && P.stream_mode == 0 && P.layout != 1;
   return 11 + (df ? 1 : 0) + (df && accurate ? 1 : 0) + (f32 ? 1 : 0);
 }
 

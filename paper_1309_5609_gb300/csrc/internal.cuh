@@ -52,6 +52,13 @@ __device__ __forceinline__ bool gate_closed(const Gate& g) {
   return false;
 }
 
+// One run of consecutive samples on one pixel within a baseline (runs.cu):
+// its samples' count and sums of cos 2psi and sin 2psi.
+struct RunRec {
+  int pix;
+  float n, c, s;
+};
+
 // Device-resident CG state (float64 scalars and control words).
 struct CgState {
   double rr;         // ||r||^2 of the current residual
@@ -147,7 +154,8 @@ struct Plan {
   double drift_ratio;       // mixed plans: squared true / recursive residual ratio of the switch
   int accurate_start;       // mixed plans: 1 = accurate operator from the first iteration
   int stall_iters;          // stop a solve whose residual has not dropped 10x in this many iterations
-  int layout;               // mixed operator: 0 = time-ordered pixels, 1 = chunk-local index
+  int layout;               // mixed operator: 0 = time-ordered pixels, 1 = chunk-local index,
+                            // 2 = run-length records
   int rescan_dedup;         // float32 rescan: reuse the map value of a repeated pixel
   int samples_per_thread;   // float32 operator: 4 or 8 consecutive samples per thread
   // chunk-local pixel index (chunked.cu)
@@ -161,7 +169,25 @@ struct Plan {
   int ck_threads;           // threads per block of the chunked passes
   int ck_bin_blocks;        // resident blocks per SM (occupancy)
   int ck_rescan_blocks;
+  // run-length records (runs.cu), built on request
+  RunRec* rl_rec;
+  int32_t* rl_b;
+  int64_t rl_n;
+  int64_t* rl_tiles;        // runs per construction tile, between count and fill
 };
+
+// api.cu: device memory of a plan from the library's stream-ordered pool;
+// counted in device_bytes when count is set
+cudaError_t plan_alloc(Plan& P, void** ptr, size_t bytes, bool count);
+
+// runs.cu
+ds_status rl_count(Plan& P, int64_t* d_total);
+ds_status rl_fill(Plan& P, int64_t n_runs);
+ds_status rl_build(Plan& P);
+constexpr double kRunsPerSampleMax = 0.6;  // plans build run records at or below this ratio
+bool rl_ready(const Plan& P);
+void launch_bin_rl(const Plan& P, cudaStream_t st, Gate g);
+void launch_rescan_rl(const Plan& P, cudaStream_t st, double* out, Gate g);
 
 // chunked.cu
 constexpr int kChunkMin = 2048, kChunkMax = 16384;

@@ -362,14 +362,32 @@ ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid) {
   k_plan_weights<<<grid, kBlock, 0, st>>>(d_pix, d_valid, P.mask, P.pix, P.nvalid, P.n_t, P.npix,
                                           P.L, counts + 1);
   DS_CUDA_TRY(cudaGetLastError());
-  DS_CUDA_TRY(cudaMemcpyAsync(P.h_scal, P.scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  // mixed plans: count the run-length records of the float32 operator (counts + 2)
+  const bool runs = P.desc.precision == DS_PREC_MIXED && P.x32 != nullptr;
+  if (runs) {
+    const ds_status s = rl_count(P, reinterpret_cast<int64_t*>(counts + 2));
+    if (s != DS_OK) return s;
+  }
+  DS_CUDA_TRY(cudaMemcpyAsync(P.h_scal, P.scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
   DS_CUDA_TRY(cudaMemcpyAsync(P.h_err, P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DS_CUDA_TRY(cudaStreamSynchronize(st));
-  unsigned long long hc[2];
+  unsigned long long hc[3];
   std::memcpy(hc, P.h_scal, sizeof(hc));
   P.n_good = (int64_t)hc[0];
   P.n_valid = (int64_t)hc[1];
   if (*P.h_err & ERR_PIX) return DS_EPIX;
+  // the records pay when runs are long enough (short runs: the time-ordered passes)
+  if (runs) {
+    const int64_t n_runs = (int64_t)hc[2];
+    if ((double)n_runs <= kRunsPerSampleMax * (double)P.n_t) {
+      const ds_status s = rl_fill(P, n_runs);
+      if (s != DS_OK) return s;
+      P.layout = 2;
+    } else {
+      cudaFreeAsync(P.rl_tiles, st);
+      P.rl_tiles = nullptr;
+    }
+  }
   return DS_OK;
 }
 

@@ -1,0 +1,310 @@
+// Run-length form of the float32 operator.
+//
+// Within a baseline the expanded baselines F~ x are constant, so the samples of
+// a run of consecutive samples on one pixel enter the binning only through
+//   n = number of samples,  C = sum cos 2psi,  S = sum sin 2psi
+// and every row of Sect. 3 is linear in (1, cos 2psi, sin 2psi):
+//   I: n z   q: (C z, S z)   u: (-S z, C z)   iqu: (n z, C z, S z)
+// and the same run contributes to the per-baseline sum of the rescan
+//   n z_o - (row_o summed over the run) . m_p.
+// At plan time each run becomes one 16-byte record (pixel, n, C, S) plus its
+// baseline index; the per-iteration passes then stream 20 bytes per run instead
+// of 12 bytes per sample (an exact reformulation: only float32 rounding order
+// changes).  Runs are cut at baseline ends and at samples of weight 0.
+#include "internal.cuh"
+#include "rows.cuh"
+#include "stream_common.cuh"
+
+namespace ds {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kTile = 4096;                 // samples per block in the construction
+constexpr int kPerThread = kTile / kBlock;  // 16 consecutive samples per thread
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ bool run_start(const int32_t* __restrict__ pix, int64_t t, int64_t L) {
+  const int p = pix[t];
+  return p >= 0 && (t % L == 0 || pix[t - 1] != p);
+}
+
+// Runs starting in each tile of kTile samples.  Samples are visited in rounds of
+// blockDim consecutive samples (coalesced loads).
+__global__ void __launch_bounds__(kBlock) k_rl_count(const int32_t* __restrict__ pix, int64_t n_t,
+                                                     int64_t L, int64_t n_tiles,
+                                                     int64_t* __restrict__ tile_runs) {
+  __shared__ int wsum[kBlock / 32];
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    int cnt = 0;
+    for (int k = 0; k < kPerThread; ++k) {
+      const int64_t t = tile * kTile + (int64_t)k * kBlock + threadIdx.x;
+      if (t < n_t && run_start(pix, t, L)) ++cnt;
+    }
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t s = 0;
+      for (int w = 0; w < kBlock / 32; ++w) s += wsum[w];
+      tile_runs[tile] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive prefix sum of tile_runs in place, total in *total (one block).
+__global__ void __launch_bounds__(kScanThreads) k_rl_scan(int64_t* __restrict__ v, int64_t n,
+                                                          int64_t* __restrict__ total) {
+  __shared__ int64_t part[kScanThreads];
+  const int64_t per = (n + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = (int64_t)threadIdx.x * per;
+  const int64_t hi = lo + per < n ? lo + per : n;
+  int64_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += v[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int i = 0; i < kScanThreads; ++i) {
+      const int64_t x = part[i];
+      part[i] = run;
+      run += x;
+    }
+    *total = run;
+  }
+  __syncthreads();
+  int64_t run = part[threadIdx.x];
+  for (int64_t i = lo; i < hi; ++i) {
+    const int64_t x = v[i];
+    v[i] = run;
+    run += x;
+  }
+}
+
+// One record per run, its samples summed in order from the run's start.  A tile
+// is visited in rounds of blockDim consecutive samples; a block-wide scan of the
+// run starts of each round gives every run its place, in sample order.
+__global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ pix,
+                                                    const float* __restrict__ cc,
+                                                    const float* __restrict__ ss, int64_t n_t,
+                                                    int64_t L, int64_t n_tiles,
+                                                    const int64_t* __restrict__ tile_off,
+                                                    RunRec* __restrict__ rec,
+                                                    int32_t* __restrict__ rb) {
+  __shared__ int wsum[kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    int64_t base = tile_off[tile];
+    for (int k = 0; k < kPerThread; ++k) {
+      const int64_t t = tile * kTile + (int64_t)k * kBlock + threadIdx.x;
+      const int start = (t < n_t && run_start(pix, t, L)) ? 1 : 0;
+      int incl = start;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      if (lane == 31) wsum[warp] = incl;
+      __syncthreads();
+      int before = 0, round = 0;
+      for (int w = 0; w < kBlock / 32; ++w) {
+        if (w < warp) before += wsum[w];
+        round += wsum[w];
+      }
+      if (start) {
+        const int p = pix[t];
+        const int64_t bend = (t / L + 1) * L;
+        float n = 0.f, sc = 0.f, sn = 0.f;
+        for (int64_t u = t; u < n_t && u < bend && pix[u] == p; ++u) {
+          n += 1.f;
+          sc += cc[u];
+          sn += ss[u];
+        }
+        const int64_t r = base + before + incl - 1;
+        rec[r] = RunRec{p, n, sc, sn};
+        rb[r] = (int32_t)(t / L);
+      }
+      base += round;
+      __syncthreads();
+    }
+  }
+}
+
+// acc += (row of one output summed over the run) * z
+template <int NC>
+__device__ __forceinline__ void run_bin(int kind, float n, float C, float S, float z,
+                                        float (&acc)[NC]) {
+  using F = Frame<NC>;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) acc[F::I] = fmaf(n, z, acc[F::I]);
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) {
+      acc[F::Q] = fmaf(C, z, acc[F::Q]);
+      acc[F::U] = fmaf(S, z, acc[F::U]);
+    }
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) {
+      acc[F::Q] = fmaf(-S, z, acc[F::Q]);
+      acc[F::U] = fmaf(C, z, acc[F::U]);
+    }
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0) {
+      acc[F::I] = fmaf(n, z, acc[F::I]);
+      acc[F::Q] = fmaf(C, z, acc[F::Q]);
+      acc[F::U] = fmaf(S, z, acc[F::U]);
+    }
+  }
+}
+
+// (row of one output summed over the run) . m
+template <int NC>
+__device__ __forceinline__ float run_dot(int kind, float n, float C, float S, const float (&m)[NC]) {
+  using F = Frame<NC>;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) return n * m[F::I];
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) return fmaf(C, m[F::Q], S * m[F::U]);
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) return fmaf(C, m[F::U], -S * m[F::Q]);
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0) return fmaf(n, m[F::I], fmaf(C, m[F::Q], S * m[F::U]));
+  }
+  return 0.f;
+}
+
+__device__ __forceinline__ RunRec load_run(const RunRec* __restrict__ rec, int64_t i) {
+  const int4 v = __ldcs(reinterpret_cast<const int4*>(rec) + i);
+  return RunRec{v.x, __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w)};
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_rl_bin(const RunRec* __restrict__ rec,
+                                                   const int32_t* __restrict__ rb, int64_t n_runs,
+                                                   const float* __restrict__ x,
+                                                   float* __restrict__ bins, int64_t n_b,
+                                                   KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_runs; i += stride) {
+    const RunRec r = load_run(rec, i);
+    const int64_t b = __ldcs(rb + i);
+    float acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (o < n_o) run_bin<NC>(K::kind(o, kk), r.n, r.c, r.s, __ldg(x + o * n_b + b), acc);
+    flush_bins<NC, float>(bins, r.pix, acc);
+  }
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_rl_rescan(const RunRec* __restrict__ rec,
+                                                      const int32_t* __restrict__ rb,
+                                                      int64_t n_runs, const float* __restrict__ x,
+                                                      const float* __restrict__ map,
+                                                      double* __restrict__ out, int64_t n_b,
+                                                      KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; ib < n_runs;
+       ib += stride) {
+    const int64_t i = ib + lane;
+    int key = -1;
+    float acc[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o] = 0.f;
+    if (i < n_runs) {
+      const RunRec r = load_run(rec, i);
+      const int b = __ldcs(rb + i);
+      float m[NC];
+      load_map<NC, float>(map, r.pix, m);
+      key = b;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < n_o) {
+          const float z = __ldg(x + o * n_b + b);
+          acc[o] = fmaf(r.n, z, -run_dot<NC>(K::kind(o, kk), r.n, r.c, r.s, m));
+        }
+    }
+    warp_segment_flush<NO, float>(key, acc, n_o, out, n_b);
+  }
+}
+
+}  // namespace
+
+// Run records are built in two steps around the plan's synchronisation: the
+// count (and its prefix over tiles) is enqueued first; once the host knows the
+// total it allocates the records and enqueues the fill.
+ds_status rl_count(Plan& P, int64_t* d_total) {
+  const int64_t n_tiles = (P.n_t + kTile - 1) / kTile;
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_tiles), sizeof(int64_t) * n_tiles, false));
+  const int grid = stream_grid(P, n_tiles * kBlock, kBlock, 8);
+  k_rl_count<<<grid, kBlock, 0, P.stream>>>(P.pix, P.n_t, P.L, n_tiles, P.rl_tiles);
+  k_rl_scan<<<1, kScanThreads, 0, P.stream>>>(P.rl_tiles, n_tiles, d_total);
+  P.launches += 2;
+  DS_CUDA_TRY(cudaGetLastError());
+  return DS_OK;
+}
+
+ds_status rl_fill(Plan& P, int64_t n_runs) {
+  const int64_t n_tiles = (P.n_t + kTile - 1) / kTile;
+  P.rl_n = n_runs;
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_rec),
+                         sizeof(RunRec) * (n_runs > 0 ? n_runs : 1), true));
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_b),
+                         sizeof(int32_t) * (n_runs > 0 ? n_runs : 1), true));
+  const int grid = stream_grid(P, n_tiles * kBlock, kBlock, 8);
+  k_rl_fill<<<grid, kBlock, 0, P.stream>>>(P.pix, P.c, P.s, P.n_t, P.L, n_tiles, P.rl_tiles,
+                                           P.rl_rec, P.rl_b);
+  P.launches += 1;
+  DS_CUDA_TRY(cudaGetLastError());
+  cudaFreeAsync(P.rl_tiles, P.stream);
+  P.rl_tiles = nullptr;
+  return DS_OK;
+}
+
+// On request after the plan exists (synchronises once).
+ds_status rl_build(Plan& P) {
+  int64_t* total = nullptr;
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&total), sizeof(int64_t), false));
+  ds_status s = rl_count(P, total);
+  int64_t n_runs = 0;
+  if (s == DS_OK &&
+      cudaMemcpyAsync(&n_runs, total, sizeof(int64_t), cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
+    s = DS_ECUDA;
+  if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
+  cudaFreeAsync(total, P.stream);
+  if (s == DS_OK) s = rl_fill(P, n_runs);
+  if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
+  return s;
+}
+
+bool rl_ready(const Plan& P) { return P.layout == 2 && P.rl_rec != nullptr && P.x32 != nullptr; }
+
+void launch_bin_rl(const Plan& P, cudaStream_t st, Gate g) {
+  const int grid = stream_grid(P, P.rl_n, kBlock, P.blocks_per_sm);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_rl_bin<KS><<<grid, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.rl_n, P.x32, P.bins32, P.n_b,
+                                          P.kinds, g);
+  });
+}
+
+void launch_rescan_rl(const Plan& P, cudaStream_t st, double* out, Gate g) {
+  const int grid = stream_grid(P, P.rl_n, kBlock, P.blocks_per_sm);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_rl_rescan<KS><<<grid, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.rl_n, P.x32, P.map32, out,
+                                             P.n_b, P.kinds, g);
+  });
+}
+
+}  // namespace ds

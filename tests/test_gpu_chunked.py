@@ -1,7 +1,7 @@
-"""Float32 operator over the chunk-local pixel index against the oracle and
-against the time-ordered layout: every kind set, every chunk length, ragged
-tails, flagged and cut samples, and chunks where nearly every sample has its own
-pixel (the largest shared arrays)."""
+"""Alternative forms of the float32 operator against the oracle and against the
+time-ordered layout: the chunk-local pixel index (every chunk length, chunks
+where nearly every sample has its own pixel), the run-length records, and the
+time-ordered variants; every kind set, ragged tails, flagged and cut samples."""
 import math
 
 import numpy as np
@@ -100,11 +100,45 @@ def test_time_ordered_operator_variants(case, tune):
     check_apply(prob, None, layout=0, tune=tune)
 
 
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_run_length_operator_parity(case):
+    kinds, nside, n_t, L, ff, scan = case
+    prob = make_problem(n_t, nside, kinds, baseline_len=L, seed=23, scan=scan, flag_frac=ff,
+                        flag_mean_len=200, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
+    check_apply(prob, None, layout=2)
+
+
+@pytest.mark.parametrize("kinds", [("q", "u"), ("iqu",), ("I",)])
+def test_run_length_operator_with_distinct_pixels(kinds):
+    # every run is a single sample
+    check_apply(random_pixel_problem(50_003, 128, kinds, 7, seed=4), None, layout=2)
+
+
+def test_run_length_solve_matches_oracle():
+    prob = make_problem(300_000, 32, ("I", "q", "u"), baseline_len=250, seed=8, flag_frac=0.01,
+                        flag_mean_len=300, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
+    d = prob.numpy()
+    op = oracle.make_plan(d["pix"], d["c"], d["s"], d["valid"], prob.nside, prob.kinds,
+                          prob.baseline_len)
+    ref = oracle.destripe(op, prob.y.float().double().numpy(), tol=1e-10)
+    gp = prob.to(DEV)
+    plan = ds.destripe_plan(gp.pix, gp.c32, gp.s32, gp.valid, nside=prob.nside, kinds=prob.kinds,
+                            baseline_len=prob.baseline_len, precision="mixed")
+    ds.destripe_tune(plan, "layout", 2)
+    a = torch.zeros(plan.n_u, dtype=torch.float64, device=DEV)
+    st, it, rel = ds.destripe_solve(plan, gp.y.float().contiguous(), a, tol=1e-10)
+    plan.close()
+    assert st == ds.DS_OK, (st, it, rel)
+    assert np.abs(a.cpu().numpy() - ref["a"]).max() < 1e-4
+
+
 def test_layouts_agree():
     prob = make_problem(100_000, 64, ("I", "q", "u"), baseline_len=300, seed=4)
     a = check_apply(prob, None, layout=1, reps=1)[0]
     b = check_apply(prob, None, layout=0, reps=1)[0]
+    c = check_apply(prob, None, layout=2, reps=1)[0]
     assert rel_err(a, b) < 2e-6
+    assert rel_err(c, b) < 2e-6
 
 
 def test_plans_with_different_chunk_sizes_coexist():

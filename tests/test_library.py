@@ -50,10 +50,11 @@ def test_struct_layout_matches_c():
     #include <stddef.h>
     #include "{HEADER}"
     int main(void) {{
-      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ds_desc), offsetof(ds_desc, kinds),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ds_desc), offsetof(ds_desc, kinds),
              offsetof(ds_desc, baseline_len), offsetof(ds_desc, rcond_min),
              offsetof(ds_desc, stream), sizeof(ds_info), offsetof(ds_info, device_bytes),
-             sizeof(ds_profile), sizeof(ds_batch_tuning), offsetof(ds_batch_tuning, rate_initial));
+             sizeof(ds_profile), sizeof(ds_batch_tuning), offsetof(ds_batch_tuning, rate_initial),
+             offsetof(ds_info, n_runs));
       return 0;
     }}"""
     with tempfile.TemporaryDirectory() as d:
@@ -66,7 +67,8 @@ def test_struct_layout_matches_c():
     exp = [ctypes.sizeof(ds.ds_desc), ds.ds_desc.kinds.offset, ds.ds_desc.baseline_len.offset,
            ds.ds_desc.rcond_min.offset, ds.ds_desc.stream.offset, ctypes.sizeof(ds.ds_info),
            ds.ds_info.device_bytes.offset, ctypes.sizeof(ds.ds_profile),
-           ctypes.sizeof(ds.ds_batch_tuning), ds.ds_batch_tuning.rate_initial.offset]
+           ctypes.sizeof(ds.ds_batch_tuning), ds.ds_batch_tuning.rate_initial.offset,
+           ds.ds_info.n_runs.offset]
     assert vals == exp
 
 
