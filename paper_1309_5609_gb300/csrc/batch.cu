@@ -25,6 +25,7 @@
 #include "df.cuh"
 #include "internal.cuh"
 #include "rows.cuh"
+#include "runs.cuh"
 #include "stream_common.cuh"
 #include "stream_df.cuh"
 
@@ -39,7 +40,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kGraphIters = 8;
-constexpr int kBatchKernelsPerIteration = 17;
+constexpr int kBatchKernelsPerIteration = 19;
 
 struct SlotDesc {
   const int32_t* pix;
@@ -54,6 +55,9 @@ struct SlotDesc {
   double *x, *r, *p, *q, *b, *t, *x_best;
   float2* xdf;  // baselines of a double-float pass split into float32 pairs
   float* x32;   // the search direction rounded to float32 for the float32 operator
+  const RunRec* rl_rec;  // run-length records of the float32 operator, or NULL
+  const int32_t* rl_b;
+  int64_t rl_n;
   CgState* state;
   int64_t n_t, L, n_b, n_u, npix;
   KindsArg kinds;
@@ -64,10 +68,11 @@ struct SlotDesc {
 struct WorkTile {
   int slot;
   int pad;
-  int64_t begin, end;  // [begin, end) in 4-sample vectors, pixels or unknowns
+  int64_t begin, end;  // [begin, end) in 4-sample vectors, pixels, unknowns or runs
 };
 
-enum { W_SAMPLES = 0, W_PIXELS = 1, W_UNKNOWNS = 2 };
+enum { W_SAMPLES = 0, W_PIXELS = 1, W_UNKNOWNS = 2, W_RUNS = 3 };
+constexpr int kLists = 4;
 
 // problem still iterating
 __device__ __forceinline__ bool slot_live(const SlotDesc& S) {
@@ -83,6 +88,69 @@ __device__ __forceinline__ bool slot_df(const SlotDesc& S) {
   if (!slot_live(S)) return false;
   return MODE == 0 ? (*(volatile const int*)&S.state->need) != 0
                    : (*(volatile const int*)&S.state->accurate) != 0;
+}
+
+// ---- run-length float32 operator for problems that hold run records ------------
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_bb_rl_bin(const SlotDesc* __restrict__ slots,
+                                                      const WorkTile* __restrict__ tiles,
+                                                      const int* __restrict__ ntiles) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int nt = ntiles[W_RUNS];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    if (!slot_f32(slots[T.slot])) continue;
+    const SlotDesc S = slots[T.slot];
+    const int n_o = K::n_o(S.kinds);
+    for (int64_t i = T.begin + threadIdx.x; i < T.end; i += blockDim.x) {
+      const RunRec r = load_run(S.rl_rec, i);
+      const int64_t b = __ldcs(S.rl_b + i);
+      float acc[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < n_o) run_bin<NC>(K::kind(o, S.kinds), r.n, r.c, r.s, S.x32[o * S.n_b + b], acc);
+      flush_bins<NC, float>(S.bins32, r.pix, acc);
+    }
+  }
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_bb_rl_rescan(const SlotDesc* __restrict__ slots,
+                                                         const WorkTile* __restrict__ tiles,
+                                                         const int* __restrict__ ntiles) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int nt = ntiles[W_RUNS];
+  const int lane = threadIdx.x & 31;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const WorkTile T = tiles[ti];
+    if (!slot_f32(slots[T.slot])) continue;
+    const SlotDesc S = slots[T.slot];
+    const int n_o = K::n_o(S.kinds);
+    for (int64_t ib = T.begin + threadIdx.x - lane; ib < T.end; ib += blockDim.x) {
+      const int64_t i = ib + lane;
+      int key = -1;
+      float acc[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) acc[o] = 0.f;
+      if (i < T.end) {
+        const RunRec r = load_run(S.rl_rec, i);
+        const int b = __ldcs(S.rl_b + i);
+        float m[NC];
+        load_map<NC, float>(S.map32, r.pix, m);
+        key = b;
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o)
+            acc[o] = fmaf(r.n, S.x32[o * S.n_b + b], -run_dot<NC>(K::kind(o, S.kinds), r.n, r.c, r.s, m));
+      }
+      warp_segment_flush<NO, float>(key, acc, n_o, S.q, S.n_b);
+    }
+  }
 }
 
 // ---- operator kernels (mixed precision: float32 per-sample work) ---------------
@@ -110,7 +178,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bb_bin(const SlotDesc* __restrict
   const int nt = ntiles[W_SAMPLES];
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const WorkTile T = tiles[ti];
-    if (!slot_f32(slots[T.slot])) continue;
+    if (!slot_f32(slots[T.slot]) || slots[T.slot].rl_rec != nullptr) continue;
     const SlotDesc S = slots[T.slot];  // registers: asm memory clobbers force reloads otherwise
     const int n_o = K::n_o(S.kinds);
     const int64_t n_t = S.n_t, L = S.L, n_b = S.n_b;
@@ -207,7 +275,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bb_rescan(const SlotDesc* __restr
   const int lane = threadIdx.x & 31;
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const WorkTile T = tiles[ti];
-    if (!slot_f32(slots[T.slot])) continue;
+    if (!slot_f32(slots[T.slot]) || slots[T.slot].rl_rec != nullptr) continue;
     const SlotDesc S = slots[T.slot];
     const int n_o = K::n_o(S.kinds);
     const int64_t n_t = S.n_t, L = S.L, n_b = S.n_b;
@@ -676,9 +744,9 @@ struct ds_batch_s {
   std::vector<char> stopped;     // slot's problem has stopped (as of the last step)
   SlotDesc* h_slots = nullptr;
   SlotDesc* d_slots = nullptr;
-  WorkTile* h_tiles[3] = {nullptr, nullptr, nullptr};
-  WorkTile* d_tiles[3] = {nullptr, nullptr, nullptr};
-  int cap[3] = {0, 0, 0};
+  WorkTile* h_tiles[kLists] = {nullptr, nullptr, nullptr, nullptr};
+  WorkTile* d_tiles[kLists] = {nullptr, nullptr, nullptr, nullptr};
+  int cap[kLists] = {0, 0, 0, 0};
   int* h_ntiles = nullptr;
   int* d_ntiles = nullptr;
   double* d_red = nullptr;
@@ -703,7 +771,7 @@ void batch_free(ds_batch_t B) {
   if (B->graph) cudaGraphExecDestroy(B->graph);
   if (B->d_slots) cudaFree(B->d_slots);
   if (B->h_slots) cudaFreeHost(B->h_slots);
-  for (int w = 0; w < 3; ++w) {
+  for (int w = 0; w < kLists; ++w) {
     if (B->d_tiles[w]) cudaFree(B->d_tiles[w]);
     if (B->h_tiles[w]) cudaFreeHost(B->h_tiles[w]);
   }
@@ -749,6 +817,10 @@ ds_status ensure_tiles(ds_batch_t B, int w, int n) {
   return DS_OK;
 }
 
+// A problem runs the run-length float32 operator when its plan holds records and
+// uses them (the same test for its slot descriptor and for the work lists).
+bool uses_runs(const Plan* P) { return P->layout == 2 && P->rl_rec != nullptr; }
+
 // Tile length for a work list: the configured one, shrunk when the live problems
 // would give fewer than two tiles per resident block (a batch's tail, when few
 // problems are still iterating, would otherwise leave most blocks idle).
@@ -767,19 +839,21 @@ int64_t effective_tile(int64_t configured, int64_t total, int64_t blocks, int64_
 // Rebuilds the three work lists from the slots whose problems are still running
 // (stopped problems drop out, so the kernels only walk live tiles).
 ds_status rebuild_tiles(ds_batch_t B) {
-  int64_t tot_vec = 0, tot_pix = 0, tot_u = 0;
+  int64_t tot_vec = 0, tot_pix = 0, tot_u = 0, tot_runs = 0;
   for (int sl = 0; sl < B->max_slots; ++sl) {
     const Plan* P = B->plans[sl];
     if (!P || B->stopped[sl]) continue;
     tot_vec += (P->n_t + 3) / 4;
     tot_pix += P->npix;
     tot_u += P->n_u;
+    if (uses_runs(P)) tot_runs += P->rl_n;
   }
   const int64_t sblocks = (int64_t)B->num_sms * B->blocks_per_sm, ublocks = (int64_t)B->num_sms * 4;
   const int64_t tv = effective_tile(B->tile_vecs, tot_vec, sblocks, 256, 32);  // >= 1024 samples
   const int64_t tp = effective_tile(B->tile_pixels, tot_pix, sblocks, 1024, 256);
   const int64_t tu = effective_tile(B->tile_unknowns, tot_u, ublocks, 1024, 256);
-  int n[3] = {0, 0, 0};
+  const int64_t tr = effective_tile(B->tile_vecs * 4, tot_runs > 0 ? tot_runs : 1, sblocks, 1024, 256);
+  int n[kLists] = {0, 0, 0, 0};
   for (int sl = 0; sl < B->max_slots; ++sl) {
     const Plan* P = B->plans[sl];
     if (!P || B->stopped[sl]) continue;
@@ -787,12 +861,13 @@ ds_status rebuild_tiles(ds_batch_t B) {
     n[W_SAMPLES] += (int)((nvec + tv - 1) / tv);
     n[W_PIXELS] += (int)((P->npix + tp - 1) / tp);
     n[W_UNKNOWNS] += (int)((P->n_u + tu - 1) / tu);
+    if (uses_runs(P)) n[W_RUNS] += (int)((P->rl_n + tr - 1) / tr);
   }
-  for (int w = 0; w < 3; ++w) {
+  for (int w = 0; w < kLists; ++w) {
     ds_status s = ensure_tiles(B, w, n[w] > 0 ? n[w] : 1);
     if (s != DS_OK) return s;
   }
-  int k[3] = {0, 0, 0};
+  int k[kLists] = {0, 0, 0, 0};
   for (int sl = 0; sl < B->max_slots; ++sl) {
     const Plan* P = B->plans[sl];
     if (!P || B->stopped[sl]) continue;
@@ -805,8 +880,11 @@ ds_status rebuild_tiles(ds_batch_t B) {
     for (int64_t b = 0; b < P->n_u; b += tu)
       B->h_tiles[W_UNKNOWNS][k[W_UNKNOWNS]++] = WorkTile{sl, 0, b, b + tu < P->n_u ? b + tu : P->n_u};
     B->h_slots[sl].u_count = k[W_UNKNOWNS] - B->h_slots[sl].u_first;
+    if (uses_runs(P))
+      for (int64_t b = 0; b < P->rl_n; b += tr)
+        B->h_tiles[W_RUNS][k[W_RUNS]++] = WorkTile{sl, 0, b, b + tr < P->rl_n ? b + tr : P->rl_n};
   }
-  for (int w = 0; w < 3; ++w) B->h_ntiles[w] = k[w];
+  for (int w = 0; w < kLists; ++w) B->h_ntiles[w] = k[w];
   B->dirty = true;
   return DS_OK;
 }
@@ -826,8 +904,10 @@ void enqueue_batch_iteration(ds_batch_t B, cudaStream_t st) {
     // float32 operator for problems that have not switched to the accurate one
     k_bb_to_f32<<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt);
     k_bb_bin<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
+    k_bb_rl_bin<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_RUNS], nt);
     k_bb_pixel_solve<NC><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_PIXELS], nt);
     k_bb_rescan<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
+    k_bb_rl_rescan<KS><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_RUNS], nt);
     // double-float operator for those that have
     k_bb_split<1><<<ugrid, kBlock, 0, st>>>(sl, B->d_tiles[W_UNKNOWNS], nt);
     k_bb_bin_df<KS, 1><<<sgrid, kBlock, 0, st>>>(sl, B->d_tiles[W_SAMPLES], nt);
@@ -851,7 +931,7 @@ ds_status batch_upload(ds_batch_t B) {
   cudaStream_t st = B->stream;
   DS_CUDA_TRY(cudaMemcpyAsync(B->d_slots, B->h_slots, sizeof(SlotDesc) * B->max_slots,
                               cudaMemcpyHostToDevice, st));
-  for (int w = 0; w < 3; ++w)
+  for (int w = 0; w < kLists; ++w)
     if (B->h_ntiles[w] > 0)
       DS_CUDA_TRY(cudaMemcpyAsync(B->d_tiles[w], B->h_tiles[w], sizeof(WorkTile) * B->h_ntiles[w],
                                   cudaMemcpyHostToDevice, st));
@@ -1014,7 +1094,7 @@ ds_status destripe_batch_create(int32_t max_slots, void* stream, ds_batch_t* out
     batch_free(B);
     return DS_ECUDA;
   }
-  for (int w = 0; w < 3; ++w) {
+  for (int w = 0; w < kLists; ++w) {
     ds_status s = ensure_tiles(B, w, 1024);
     if (s != DS_OK) {
       batch_free(B);
@@ -1073,6 +1153,9 @@ ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, cons
   S.x = P.x; S.r = P.r; S.p = P.p; S.q = P.q; S.b = P.b; S.t = P.t; S.x_best = P.x_best;
   S.xdf = P.xdf;
   S.x32 = P.x32;
+  S.rl_rec = uses_runs(&P) ? P.rl_rec : nullptr;
+  S.rl_b = P.rl_b;
+  S.rl_n = P.rl_n;
   S.state = P.state;
   S.n_t = P.n_t; S.L = P.L; S.n_b = P.n_b; S.n_u = P.n_u; S.npix = P.npix;
   S.kinds = P.kinds;
