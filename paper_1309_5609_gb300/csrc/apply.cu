@@ -543,13 +543,16 @@ static bool use_df(const Plan& P) {
 void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out,
                    Gate g, cudaEvent_t* ev) {
   if (fp64 && use_df(P)) {
+    const bool runs = rl_df_ready(P);
     if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
     launch_split_df(P, st, x, g);
-    launch_bin_df(P, st, x, nullptr, g);
+    if (runs) launch_bin_rl_df(P, st, g);
+    else launch_bin_df(P, st, x, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     launch_pixel_solve_df(P, st, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
-    launch_rescan_df(P, st, x, nullptr, out, g);
+    if (runs) launch_rescan_rl_df(P, st, out, g);
+    else launch_rescan_df(P, st, x, nullptr, out, g);
     if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
     return;
   }

@@ -53,6 +53,13 @@ __device__ __forceinline__ df df_mul_f(df x, float f) {
   return fast_two_sum(p.hi, __fmaf_rn(x.lo, f, p.lo));
 }
 
+// x * y for two double-float numbers (the lo * lo term is below the precision)
+__device__ __forceinline__ df df_mul(df x, df y) {
+  df p = two_prod(x.hi, y.hi);
+  const float e = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+  return fast_two_sum(p.hi, __fadd_rn(p.lo, e));
+}
+
 // float64 <-> double-float
 __device__ __forceinline__ df df_from_double(double d) {
   const float hi = __double2float_rn(d);

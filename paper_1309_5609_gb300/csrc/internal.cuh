@@ -174,6 +174,7 @@ struct Plan {
   int32_t* rl_b;
   int64_t rl_n;
   int64_t* rl_tiles;        // runs per construction tile, between count and fill
+  float4* rl_df;            // per run: (sum cos 2psi, sum sin 2psi) as double-float pairs
 };
 
 // api.cu: device memory of a plan from the library's stream-ordered pool;
@@ -188,6 +189,9 @@ constexpr double kRunsPerSampleMax = 0.6;  // plans build run records at or belo
 bool rl_ready(const Plan& P);
 void launch_bin_rl(const Plan& P, cudaStream_t st, Gate g);
 void launch_rescan_rl(const Plan& P, cudaStream_t st, double* out, Gate g);
+bool rl_df_ready(const Plan& P);
+void launch_bin_rl_df(const Plan& P, cudaStream_t st, Gate g);
+void launch_rescan_rl_df(const Plan& P, cudaStream_t st, double* out, Gate g);
 
 // chunked.cu
 constexpr int kChunkMin = 2048, kChunkMax = 16384;

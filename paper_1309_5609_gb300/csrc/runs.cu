@@ -11,10 +11,12 @@
 // baseline index; the per-iteration passes then stream 20 bytes per run instead
 // of 12 bytes per sample (an exact reformulation: only float32 rounding order
 // changes).  Runs are cut at baseline ends and at samples of weight 0.
+#include "df.cuh"
 #include "internal.cuh"
 #include "rows.cuh"
 #include "runs.cuh"
 #include "stream_common.cuh"
+#include "stream_df.cuh"
 
 namespace ds {
 
@@ -92,7 +94,8 @@ __global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ 
                                                     int64_t L, int64_t n_tiles,
                                                     const int64_t* __restrict__ tile_off,
                                                     RunRec* __restrict__ rec,
-                                                    int32_t* __restrict__ rb) {
+                                                    int32_t* __restrict__ rb,
+                                                    float4* __restrict__ rdf) {
   __shared__ int wsum[kBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -115,15 +118,17 @@ __global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ 
       if (start) {
         const int p = pix[t];
         const int64_t bend = (t / L + 1) * L;
-        float n = 0.f, sc = 0.f, sn = 0.f;
+        float n = 0.f;
+        df sc{0.f, 0.f}, sn{0.f, 0.f};  // exact sums for the accurate passes
         for (int64_t u = t; u < n_t && u < bend && pix[u] == p; ++u) {
           n += 1.f;
-          sc += cc[u];
-          sn += ss[u];
+          sc = df_add(sc, df_make(cc[u]));
+          sn = df_add(sn, df_make(ss[u]));
         }
         const int64_t r = base + before + incl - 1;
-        rec[r] = RunRec{p, n, sc, sn};
+        rec[r] = RunRec{p, n, sc.hi, sn.hi};
         rb[r] = (int32_t)(t / L);
+        rdf[r] = make_float4(sc.hi, sc.lo, sn.hi, sn.lo);
       }
       base += round;
       __syncthreads();
@@ -192,6 +197,126 @@ __global__ void __launch_bounds__(kBlock) k_rl_rescan(const RunRec* __restrict__
   }
 }
 
+// ---- accurate operator over runs (passes over baselines: F~ x, no timelines) ----
+// Double-float throughout: the run sums C, S are exact double-float pairs, the
+// baselines come split (xdf), the map as (map_hi, map_lo).
+
+template <int NC>
+__device__ __forceinline__ void run_bin_df(int kind, float n, df C, df S, df z, df (&acc)[NC]) {
+  using F = Frame<NC>;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) acc[F::I] = df_add(acc[F::I], df_mul_f(z, n));
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) {
+      acc[F::Q] = df_add(acc[F::Q], df_mul(z, C));
+      acc[F::U] = df_add(acc[F::U], df_mul(z, S));
+    }
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) {
+      acc[F::Q] = df_sub(acc[F::Q], df_mul(z, S));
+      acc[F::U] = df_add(acc[F::U], df_mul(z, C));
+    }
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0) {
+      acc[F::I] = df_add(acc[F::I], df_mul_f(z, n));
+      acc[F::Q] = df_add(acc[F::Q], df_mul(z, C));
+      acc[F::U] = df_add(acc[F::U], df_mul(z, S));
+    }
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ df run_dot_df(int kind, float n, df C, df S, const df (&m)[NC]) {
+  using F = Frame<NC>;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) return df_mul_f(m[F::I], n);
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) return df_add(df_mul(C, m[F::Q]), df_mul(S, m[F::U]));
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) return df_sub(df_mul(C, m[F::U]), df_mul(S, m[F::Q]));
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0)
+      return df_add(df_mul_f(m[F::I], n), df_add(df_mul(C, m[F::Q]), df_mul(S, m[F::U])));
+  }
+  return df{0.f, 0.f};
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_rl_bin_df(const RunRec* __restrict__ rec,
+                                                      const float4* __restrict__ rdf,
+                                                      const int32_t* __restrict__ rb,
+                                                      int64_t n_runs, const float2* __restrict__ x,
+                                                      double* __restrict__ bins, int64_t n_b,
+                                                      KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_runs; i += stride) {
+    const RunRec r = load_run(rec, i);
+    const float4 cs = __ldcs(rdf + i);
+    const df C{cs.x, cs.y}, S{cs.z, cs.w};
+    const int64_t b = __ldcs(rb + i);
+    df acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = df{0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (o < n_o) {
+        const float2 z2 = __ldg(x + o * n_b + b);
+        run_bin_df<NC>(K::kind(o, kk), r.n, C, S, df{z2.x, z2.y}, acc);
+      }
+    flush_bins_df<NC>(bins, r.pix, acc);
+  }
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_rl_rescan_df(const RunRec* __restrict__ rec,
+                                                         const float4* __restrict__ rdf,
+                                                         const int32_t* __restrict__ rb,
+                                                         int64_t n_runs,
+                                                         const float2* __restrict__ x,
+                                                         const float* __restrict__ map_hi,
+                                                         const float* __restrict__ map_lo,
+                                                         double* __restrict__ out, int64_t n_b,
+                                                         KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t ib = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; ib < n_runs;
+       ib += stride) {
+    const int64_t i = ib + lane;
+    int key = -1;
+    df acc[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o] = df{0.f, 0.f};
+    if (i < n_runs) {
+      const RunRec r = load_run(rec, i);
+      const float4 cs = __ldcs(rdf + i);
+      const df C{cs.x, cs.y}, S{cs.z, cs.w};
+      const int b = __ldcs(rb + i);
+      const float4 h = __ldg(reinterpret_cast<const float4*>(map_hi) + r.pix);
+      const float4 l = __ldg(reinterpret_cast<const float4*>(map_lo) + r.pix);
+      const float hh[4] = {h.x, h.y, h.z, h.w}, ll[4] = {l.x, l.y, l.z, l.w};
+      df m[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) m[j] = df{hh[j], ll[j]};
+      key = b;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < n_o) {
+          const float2 z2 = __ldg(x + o * n_b + b);
+          acc[o] = df_sub(df_mul_f(df{z2.x, z2.y}, r.n), run_dot_df<NC>(K::kind(o, kk), r.n, C, S, m));
+        }
+    }
+    warp_segment_flush_df<NO>(key, acc, n_o, out, n_b);
+  }
+}
+
 }  // namespace
 
 // Run records are built in two steps around the plan's synchronisation: the
@@ -216,8 +341,10 @@ ds_status rl_fill(Plan& P, int64_t n_runs) {
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_b),
                          sizeof(int32_t) * (n_runs > 0 ? n_runs : 1), true));
   const int grid = stream_grid(P, n_tiles * kBlock, kBlock, 8);
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_df),
+                         sizeof(float4) * (n_runs > 0 ? n_runs : 1), true));
   k_rl_fill<<<grid, kBlock, 0, P.stream>>>(P.pix, P.c, P.s, P.n_t, P.L, n_tiles, P.rl_tiles,
-                                           P.rl_rec, P.rl_b);
+                                           P.rl_rec, P.rl_b, P.rl_df);
   P.launches += 1;
   DS_CUDA_TRY(cudaGetLastError());
   cudaFreeAsync(P.rl_tiles, P.stream);
@@ -258,6 +385,31 @@ void launch_rescan_rl(const Plan& P, cudaStream_t st, double* out, Gate g) {
     constexpr int KS = decltype(ksc)::value;
     k_rl_rescan<KS><<<grid, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.rl_n, P.x32, P.map32, out,
                                              P.n_b, P.kinds, g);
+  });
+}
+
+}  // namespace ds
+
+namespace ds {
+
+bool rl_df_ready(const Plan& P) { return P.layout == 2 && P.rl_df != nullptr && P.xdf != nullptr; }
+
+// x must have been split into P.xdf (launch_split_df)
+void launch_bin_rl_df(const Plan& P, cudaStream_t st, Gate g) {
+  const int grid = stream_grid(P, P.rl_n, kBlock, P.blocks_per_sm);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_rl_bin_df<KS><<<grid, kBlock, 0, st>>>(P.rl_rec, P.rl_df, P.rl_b, P.rl_n, P.xdf, P.bins,
+                                             P.n_b, P.kinds, g);
+  });
+}
+
+void launch_rescan_rl_df(const Plan& P, cudaStream_t st, double* out, Gate g) {
+  const int grid = stream_grid(P, P.rl_n, kBlock, P.blocks_per_sm);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_rl_rescan_df<KS><<<grid, kBlock, 0, st>>>(P.rl_rec, P.rl_df, P.rl_b, P.rl_n, P.xdf,
+                                                P.map32, P.maplo, out, P.n_b, P.kinds, g);
   });
 }
 
