@@ -94,14 +94,15 @@ def peaks():
 def kernel_traffic(n_t, kernel, workload):
     """Per-launch DRAM bytes of `kernel` on `workload` from the committed ncu
     summary (bytes per sample times samples), or None if the summary is missing,
-    has no line for the workload, or the kernel source has changed since."""
+    has no line for the workload, or the kernel's source file has changed since."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
-    src = os.path.join(ROOT, "paper_1309_5609_gb300", "csrc", "apply.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        m_sha = re.search(r"apply\.cu sha256\[:16\]:\s*([0-9a-f]+)", text)
-        if not m_sha or m_sha.group(1) != sha:
+        m_sha = re.search(r"(\w+\.cu) sha256\[:16\]:\s*([0-9a-f]+)", text)
+        if not m_sha:
+            return None
+        src = os.path.join(ROOT, "paper_1309_5609_gb300", "csrc", m_sha.group(1))
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != m_sha.group(2):
             return None
         for key, bps in re.findall(r"dram bytes per sample \[([\w.-]+)\]:\s*([0-9.]+)", text):
             if workload.startswith(key):

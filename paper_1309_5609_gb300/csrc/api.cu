@@ -154,6 +154,8 @@ ds_status capture_iterations(Plan& P, bool accurate, cudaEvent_t* ev, cudaGraphE
     *out = nullptr;
     return DS_ECUDA;
   }
+  // upload now, off the plan's stream: the first replay then starts at once
+  if (cudaGraphUpload(*out, P.cap_stream) != cudaSuccess) return DS_ECUDA;
   return DS_OK;
 }
 
