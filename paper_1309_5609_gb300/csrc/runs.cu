@@ -7,10 +7,11 @@
 //   I: n z   q: (C z, S z)   u: (-S z, C z)   iqu: (n z, C z, S z)
 // and the same run contributes to the per-baseline sum of the rescan
 //   n z_o - (row_o summed over the run) . m_p.
-// At plan time each run becomes one 16-byte record (pixel, n, C, S) plus its
-// baseline index; the per-iteration passes then stream 20 bytes per run instead
-// of 12 bytes per sample (an exact reformulation: only float32 rounding order
-// changes).  Runs are cut at baseline ends and at samples of weight 0.
+// At plan time (runs_build.cu) each run becomes one 16-byte record (pixel, n, C,
+// S) plus its baseline index; the per-iteration passes here stream 20 bytes per
+// run instead of 12 bytes per sample (an exact reformulation: only float32
+// rounding order changes).  Runs are cut at baseline ends and at samples of
+// weight 0.
 #include "df.cuh"
 #include "internal.cuh"
 #include "rows.cuh"
@@ -23,118 +24,6 @@ namespace ds {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kTile = 4096;                 // samples per block in the construction
-constexpr int kPerThread = kTile / kBlock;  // 16 consecutive samples per thread
-constexpr int kScanThreads = 1024;
-
-__device__ __forceinline__ bool run_start(const int32_t* __restrict__ pix, int64_t t, int64_t L) {
-  const int p = pix[t];
-  return p >= 0 && (t % L == 0 || pix[t - 1] != p);
-}
-
-// Runs starting in each tile of kTile samples.  Samples are visited in rounds of
-// blockDim consecutive samples (coalesced loads).
-__global__ void __launch_bounds__(kBlock) k_rl_count(const int32_t* __restrict__ pix, int64_t n_t,
-                                                     int64_t L, int64_t n_tiles,
-                                                     int64_t* __restrict__ tile_runs) {
-  __shared__ int wsum[kBlock / 32];
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    int cnt = 0;
-    for (int k = 0; k < kPerThread; ++k) {
-      const int64_t t = tile * kTile + (int64_t)k * kBlock + threadIdx.x;
-      if (t < n_t && run_start(pix, t, L)) ++cnt;
-    }
-    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int64_t s = 0;
-      for (int w = 0; w < kBlock / 32; ++w) s += wsum[w];
-      tile_runs[tile] = s;
-    }
-    __syncthreads();
-  }
-}
-
-// Exclusive prefix sum of tile_runs in place, total in *total (one block).
-__global__ void __launch_bounds__(kScanThreads) k_rl_scan(int64_t* __restrict__ v, int64_t n,
-                                                          int64_t* __restrict__ total) {
-  __shared__ int64_t part[kScanThreads];
-  const int64_t per = (n + kScanThreads - 1) / kScanThreads;
-  const int64_t lo = (int64_t)threadIdx.x * per;
-  const int64_t hi = lo + per < n ? lo + per : n;
-  int64_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += v[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t run = 0;
-    for (int i = 0; i < kScanThreads; ++i) {
-      const int64_t x = part[i];
-      part[i] = run;
-      run += x;
-    }
-    *total = run;
-  }
-  __syncthreads();
-  int64_t run = part[threadIdx.x];
-  for (int64_t i = lo; i < hi; ++i) {
-    const int64_t x = v[i];
-    v[i] = run;
-    run += x;
-  }
-}
-
-// One record per run, its samples summed in order from the run's start.  A tile
-// is visited in rounds of blockDim consecutive samples; a block-wide scan of the
-// run starts of each round gives every run its place, in sample order.
-__global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ pix,
-                                                    const float* __restrict__ cc,
-                                                    const float* __restrict__ ss, int64_t n_t,
-                                                    int64_t L, int64_t n_tiles,
-                                                    const int64_t* __restrict__ tile_off,
-                                                    RunRec* __restrict__ rec,
-                                                    int32_t* __restrict__ rb,
-                                                    float4* __restrict__ rdf) {
-  __shared__ int wsum[kBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    int64_t base = tile_off[tile];
-    for (int k = 0; k < kPerThread; ++k) {
-      const int64_t t = tile * kTile + (int64_t)k * kBlock + threadIdx.x;
-      const int start = (t < n_t && run_start(pix, t, L)) ? 1 : 0;
-      int incl = start;
-      for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += y;
-      }
-      if (lane == 31) wsum[warp] = incl;
-      __syncthreads();
-      int before = 0, round = 0;
-      for (int w = 0; w < kBlock / 32; ++w) {
-        if (w < warp) before += wsum[w];
-        round += wsum[w];
-      }
-      if (start) {
-        const int p = pix[t];
-        const int64_t bend = (t / L + 1) * L;
-        float n = 0.f;
-        df sc{0.f, 0.f}, sn{0.f, 0.f};  // exact sums for the accurate passes
-        for (int64_t u = t; u < n_t && u < bend && pix[u] == p; ++u) {
-          n += 1.f;
-          sc = df_add(sc, df_make(cc[u]));
-          sn = df_add(sn, df_make(ss[u]));
-        }
-        const int64_t r = base + before + incl - 1;
-        rec[r] = RunRec{p, n, sc.hi, sn.hi};
-        rb[r] = (int32_t)(t / L);
-        rdf[r] = make_float4(sc.hi, sc.lo, sn.hi, sn.lo);
-      }
-      base += round;
-      __syncthreads();
-    }
-  }
-}
 
 template <int KS>
 __global__ void __launch_bounds__(kBlock) k_rl_bin(const RunRec* __restrict__ rec,
@@ -318,55 +207,6 @@ __global__ void __launch_bounds__(kBlock) k_rl_rescan_df(const RunRec* __restric
 }
 
 }  // namespace
-
-// Run records are built in two steps around the plan's synchronisation: the
-// count (and its prefix over tiles) is enqueued first; once the host knows the
-// total it allocates the records and enqueues the fill.
-ds_status rl_count(Plan& P, int64_t* d_total) {
-  const int64_t n_tiles = (P.n_t + kTile - 1) / kTile;
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_tiles), sizeof(int64_t) * n_tiles, false));
-  const int grid = stream_grid(P, n_tiles * kBlock, kBlock, 8);
-  k_rl_count<<<grid, kBlock, 0, P.stream>>>(P.pix, P.n_t, P.L, n_tiles, P.rl_tiles);
-  k_rl_scan<<<1, kScanThreads, 0, P.stream>>>(P.rl_tiles, n_tiles, d_total);
-  P.launches += 2;
-  DS_CUDA_TRY(cudaGetLastError());
-  return DS_OK;
-}
-
-ds_status rl_fill(Plan& P, int64_t n_runs) {
-  const int64_t n_tiles = (P.n_t + kTile - 1) / kTile;
-  P.rl_n = n_runs;
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_rec),
-                         sizeof(RunRec) * (n_runs > 0 ? n_runs : 1), true));
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_b),
-                         sizeof(int32_t) * (n_runs > 0 ? n_runs : 1), true));
-  const int grid = stream_grid(P, n_tiles * kBlock, kBlock, 8);
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_df),
-                         sizeof(float4) * (n_runs > 0 ? n_runs : 1), true));
-  k_rl_fill<<<grid, kBlock, 0, P.stream>>>(P.pix, P.c, P.s, P.n_t, P.L, n_tiles, P.rl_tiles,
-                                           P.rl_rec, P.rl_b, P.rl_df);
-  P.launches += 1;
-  DS_CUDA_TRY(cudaGetLastError());
-  cudaFreeAsync(P.rl_tiles, P.stream);
-  P.rl_tiles = nullptr;
-  return DS_OK;
-}
-
-// On request after the plan exists (synchronises once).
-ds_status rl_build(Plan& P) {
-  int64_t* total = nullptr;
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&total), sizeof(int64_t), false));
-  ds_status s = rl_count(P, total);
-  int64_t n_runs = 0;
-  if (s == DS_OK &&
-      cudaMemcpyAsync(&n_runs, total, sizeof(int64_t), cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
-    s = DS_ECUDA;
-  if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
-  cudaFreeAsync(total, P.stream);
-  if (s == DS_OK) s = rl_fill(P, n_runs);
-  if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
-  return s;
-}
 
 bool rl_ready(const Plan& P) { return P.layout == 2 && P.rl_rec != nullptr && P.x32 != nullptr; }
 
