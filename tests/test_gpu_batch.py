@@ -159,3 +159,33 @@ def test_autotune_on_an_empty_batch_does_nothing():
     assert (res["tile_samples"], res["tile_pixels"], res["tile_unknowns"],
             res["blocks_per_sm"]) == (16384, 16384, 4096, 8)
     batch.close()
+
+
+def test_batch_mixing_run_length_and_time_ordered_problems():
+    # some plans use run-length records, others the time-ordered passes (one
+    # forced, one with L = 1 where every sample is its own run); each result
+    # equals its problem solved alone
+    probs = problems(4, seed=19)
+    probs.append(make_problem(150_000, 32, ("q", "u"), baseline_len=1, seed=3, device=DEV,
+                              y_dtype=torch.float32, keep_f64_trig=False))
+    plans = [plan_of(p) for p in probs]
+    ds.destripe_tune(plans[1], "layout", 0)
+    layouts = [ds.destripe_plan_info(pl)["layout"] for pl in plans]
+    assert 0 in layouts and 2 in layouts
+    batch = ds.destripe_batch_create(len(probs))
+    slots = [ds.destripe_batch_add(batch, pl, p.y, tol=1e-10) for pl, p in zip(plans, probs)]
+    while ds.destripe_batch_step(batch, 8) > 0:
+        pass
+    for sl, pl, p in zip(slots, plans, probs):
+        a = torch.zeros(pl.n_u, dtype=torch.float64, device=DEV)
+        st, it, rel = ds.destripe_batch_retire(batch, sl, a)
+        assert st == ds.DS_OK, (st, it, rel)
+        alone = plan_of(p)
+        a1 = torch.zeros(alone.n_u, dtype=torch.float64, device=DEV)
+        st1, _, _ = ds.destripe_solve(alone, p.y, a1, tol=1e-10)
+        alone.close()
+        assert st1 == ds.DS_OK
+        assert np.abs(a.cpu().numpy() - a1.cpu().numpy()).max() < 1e-5
+    batch.close()
+    for pl in plans:
+        pl.close()
