@@ -243,6 +243,11 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     equal pixels within a thread's 4 samples (default), 0 = once per sample
  *   "samples_per_thread"  MIXED plans: 4 (default) or 8 consecutive samples per thread in
  *                     the float32 operator (8: two 16-byte loads per stream per thread)
+ *   "rescan_rounds"   MIXED plans: rounds of 32 work items (runs, or 4-sample groups)
+ *                     per warp chunk in the rescans that keep per-lane baseline sums
+ *                     across rounds and flush them across the warp only where a baseline
+ *                     ends: 0 = chosen from the problem size and the grid (default, up to
+ *                     16), 1..16 = fixed (1: a flush after every round)
  * Returns DS_EINVAL for an unknown key or value, DS_ESTATE when the plan cannot
  * use the value.  Takes effect at the next call. */
 ds_status destripe_tune(ds_plan_t plan, const char* key, double value);

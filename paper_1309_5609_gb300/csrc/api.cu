@@ -300,6 +300,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->stall_iters = 2000;
   P->layout = 0;
   P->rescan_dedup = 1;
+  P->rescan_rounds = 0;
   P->samples_per_thread = 4;
   cudaError_t e = cudaSuccess;
 #define DS_ALLOC(ptr, n) \
@@ -593,6 +594,9 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
   } else if (k == "rescan_dedup") {
     if (value != 0.0 && value != 1.0) return DS_EINVAL;
     P.rescan_dedup = (int)value;
+  } else if (k == "rescan_rounds") {
+    if (!(value >= 0.0 && value <= 16.0) || (double)(int)value != value) return DS_EINVAL;
+    P.rescan_rounds = (int)value;
   } else if (k == "blocks_per_sm") {
     if (!(value >= 1.0 && value <= 32.0)) return DS_EINVAL;
     P.blocks_per_sm = (int)value;

@@ -1,13 +1,14 @@
-// Accurate passes of mixed-precision plans in double-float arithmetic (df.cuh):
-// the right-hand side F~^T Z y, the maps M^-1 A_p^T V (y - F~ a) and the
-// float64 residual refreshes b - F~^T Z F~ x of the CG iteration (Sect. 3).
+// Accurate passes of mixed-precision plans in compensated float32 arithmetic
+// (df.cuh): the right-hand side F~^T Z y, the maps M^-1 A_p^T V (y - F~ a) and
+// the float64 residual refreshes b - F~^T Z F~ x of the CG iteration (Sect. 3).
 //
-// Per sample everything is float32 pairs: cos 2psi, sin 2psi and float32 data
-// are exact float32 numbers, so their products are exact double-floats.  float64
-// appears only once per run of equal pixels (the atomic add into the float64
-// pixel sums), once per warp segment (the atomic add into the float64 baseline
-// sums), per baseline (splitting x) and per pixel (the pixel solve).  The work
-// split is that of apply.cu: 4 consecutive samples per thread, 128 per warp.
+// Per sample everything is float32: cos 2psi, sin 2psi and float32 data are
+// exact float32 numbers, so their products are exact as (product, error) pairs,
+// and the sums are the compensated (hi, lo) sums of df.cuh.  float64 appears only
+// once per run of equal pixels (the atomic add into the float64 pixel sums), once
+// per flushed baseline sum, per baseline (splitting x) and per pixel (the pixel
+// solve).  The binning pass takes 4 consecutive samples per thread; the rescan
+// walks chunks of consecutive samples per warp.
 #include <type_traits>
 
 #include "df.cuh"
@@ -26,6 +27,13 @@ constexpr int kBlock = 256;
 // measured 16% faster right-hand side on the B-Machine-like workload; 4 (64
 // registers) spills and gains nothing more.
 constexpr int kDfMinBlocks = 3;
+
+// 4-sample groups per thread in k_bin_df.  Every run end among a thread's samples
+// costs one float64 atomic add per component (the pass's bound), so longer
+// stretches per thread would end fewer runs early; measured on the B-Machine-like
+// workload, 4 groups (16 samples) took 1.59 ms against 1.29 ms for one: the
+// warp's 16-byte loads then stride 64 bytes apart.
+constexpr int kDfGroups = 1;
 
 // x[i] -> (hi, lo) with hi = x rounded to float32, lo = the rest rounded to float32
 __global__ void __launch_bounds__(kBlock) k_split_df(const double* __restrict__ x,
@@ -60,13 +68,10 @@ __device__ __forceinline__ void load_y4(const float* __restrict__ y, int n_o, in
   }
 }
 
-__device__ __forceinline__ df df_load(const float2* __restrict__ xs, int64_t i) {
-  const float2 v = __ldg(xs + i);
-  return df{v.x, v.y};
-}
-
 // bins[p] += sum_o w_o(t) z_o(t), z = x[o][t/L] (ZY false) or y[o][t] - a[o][t/L] (ZY true);
-// the baselines come split into double-float pairs (xs, NULL for none)
+// the baselines come split into double-float pairs (xs, NULL for none).  A thread
+// takes kDfGroups x 4 consecutive samples; each run of equal pixels among them
+// is one compensated sum and one float64 atomic add per component.
 template <int KS, bool ZY>
 __global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_bin_df(const int32_t* __restrict__ pix,
                                                    const float* __restrict__ cc,
@@ -79,59 +84,71 @@ __global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_bin_df(const int32_t* 
   using K = KSet<KS>;
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
+  const bool hasx = x != nullptr;
   const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t n_units = (nvec + kDfGroups - 1) / kDfGroups;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
-    int p[4];
-    float c[4], s[4];
-    load4_df(pix, cc, ss, v, n_t, p, c, s);
-    float yv[NO][4];
-    if constexpr (ZY) load_y4<NO>(y, n_o, n_t, v, yv);
-    const int64_t t0 = v << 2;
-    int64_t b = t0 / L;
-    int64_t bend = (b + 1) * L;
+  const int64_t u0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  BaselineCursor bc(u0 * 4 * kDfGroups, stride * 4 * kDfGroups, L);
+  for (int64_t u = u0; u < n_units; u += stride, bc.advance(L)) {
+    int64_t b = bc.b;
+    int64_t bend = bc.next_start(u * 4 * kDfGroups, L);
     df zb[NO];
 #pragma unroll
     for (int o = 0; o < NO; ++o)
-      zb[o] = (o < n_o && x != nullptr) ? df_load(x, o * n_b + b) : df{0.f, 0.f};
-    df acc[NC];
+      zb[o] = (o < n_o && hasx) ? df_ldg(x, o * n_b + b) : df{0.f, 0.f};
+    dsum acc[NC];
 #pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = df{0.f, 0.f};
+    for (int j = 0; j < NC; ++j) acc[j] = ds_zero();
     int cur = -1;
+    for (int gi = 0; gi < kDfGroups; ++gi) {
+      const int64_t v = u * kDfGroups + gi;
+      if (v >= nvec) break;
+      int p[4];
+      float c[4], s[4];
+      load4_df(pix, cc, ss, v, n_t, p, c, s);
+      float yv[NO][4];
+      if constexpr (ZY) load_y4<NO>(y, n_o, n_t, v, yv);
+      const int64_t t0 = v << 2;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int64_t t = t0 + k;
-      if (t >= n_t) break;
-      if (t >= bend) {
-        b += 1;
-        bend += L;
+      for (int k = 0; k < 4; ++k) {
+        const int64_t t = t0 + k;
+        if (t >= n_t) break;
+        if (t >= bend) {
+          b += 1;
+          bend += L;
 #pragma unroll
-        for (int o = 0; o < NO; ++o)
-          zb[o] = (o < n_o && x != nullptr) ? df_load(x, o * n_b + b) : df{0.f, 0.f};
-      }
-      if (p[k] < 0) continue;
-      df w[NC];
+          for (int o = 0; o < NO; ++o)
+            zb[o] = (o < n_o && hasx) ? df_ldg(x, o * n_b + b) : df{0.f, 0.f};
+        }
+        if (p[k] < 0) continue;
+        if (p[k] != cur) {
+          if (cur >= 0) flush_bins_ds<NC>(bins, cur, acc);
+          cur = p[k];
 #pragma unroll
-      for (int j = 0; j < NC; ++j) w[j] = df{0.f, 0.f};
+          for (int j = 0; j < NC; ++j) acc[j] = ds_zero();
+        }
 #pragma unroll
-      for (int o = 0; o < NO; ++o) {
-        if (o < n_o) {
-          df z = zb[o];
-          if constexpr (ZY) z = df_sub(df_make(yv[o][k]), z);
-          row_bin_df<NC>(K::kind(o, kk), c[k], s[k], z, w);
+        for (int o = 0; o < NO; ++o) {
+          if (o < n_o) {
+            if constexpr (ZY) {
+              if (hasx) {
+                // z = y - a exactly as an unnormalised pair
+                const df e = two_sum(yv[o][k], -zb[o].hi);
+                row_bin_ds<NC>(K::kind(o, kk), c[k], s[k], df{e.hi, __fsub_rn(e.lo, zb[o].lo)}, acc);
+              } else {
+                row_bin_ds<NC>(K::kind(o, kk), c[k], s[k], yv[o][k], acc);
+              }
+            } else {
+              row_bin_ds<NC>(K::kind(o, kk), c[k], s[k], zb[o], acc);
+            }
+          }
         }
       }
-      if (p[k] != cur) {
-        if (cur >= 0) flush_bins_df<NC>(bins, cur, acc);
-        cur = p[k];
 #pragma unroll
-        for (int j = 0; j < NC; ++j) acc[j] = w[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < NC; ++j) acc[j] = df_add(acc[j], w[j]);
-      }
+      for (int j = 0; j < NC; ++j) ds_norm(acc[j]);
     }
-    if (cur >= 0) flush_bins_df<NC>(bins, cur, acc);
+    if (cur >= 0) flush_bins_ds<NC>(bins, cur, acc);
   }
 }
 
@@ -181,7 +198,15 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve_df(double* __restrict__ 
   }
 }
 
-// out[o][b] += sum_{t in b} v (z_o(t) - w_o(t) . m_p(t)) in double-float
+// out[o][b] += sum_{t in b} v (z_o(t) - w_o(t) . m_p(t)), z = x[o][b] (ZY false) or
+// y[o][t] - x[o][b] (ZY true), in compensated sums.  Each warp walks a chunk of
+// `rounds` x 128 consecutive samples, 4 per lane per round.  A lane keeps the sums
+// of its current baseline across rounds together with the count of their samples
+// (whose baseline term, count x x[o][b], joins the sums when they are flushed).
+// The warp flushes every lane's sums at once (a segmented sum over the lanes)
+// only when some lane's next samples start another baseline or some lane runs
+// out of samples; a lane whose four samples cross a baseline end flushes its own
+// sums there; the chunk's end flushes the rest.
 template <int KS, bool ZY>
 __global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_rescan_df(const int32_t* __restrict__ pix,
                                                       const float* __restrict__ cc,
@@ -191,95 +216,115 @@ __global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_rescan_df(const int32_
                                                       const float* __restrict__ map_hi,
                                                       const float* __restrict__ map_lo,
                                                       double* __restrict__ out, int64_t n_t,
-                                                      int64_t L, int64_t n_b, KindsArg kk, Gate g) {
+                                                      int64_t L, int64_t n_b, KindsArg kk,
+                                                      int rounds, Gate g) {
   if (gate_closed(g)) return;
   using K = KSet<KS>;
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
+  const bool hasx = x != nullptr;
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t nvec = (n_t + 3) >> 2;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t vb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; vb < nvec;
-       vb += stride) {
-    const int64_t v = vb + lane;
-    int key = -1;
-    df acc[NO];
+  const int64_t span = (int64_t)rounds * 32;
+  const int64_t n_chunks = (nvec + span - 1) / span;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t ch = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < n_chunks;
+       ch += warps) {
+    int key = -1;     // baseline of the lane's open sums (-1: none)
+    float cnt = 0.f;  // their valid samples
+    dsum acc[NO];
 #pragma unroll
-    for (int o = 0; o < NO; ++o) acc[o] = df{0.f, 0.f};
-    if (v < nvec) {
+    for (int o = 0; o < NO; ++o) acc[o] = ds_zero();
+    // the baseline term of the open sums: -cnt x (ZY) or +cnt x
+    auto fold = [&]() {
+      if (hasx && key >= 0 && cnt != 0.f) {
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o) ds_add_prod(acc[o], df_ldg(x, o * n_b + key), ZY ? -cnt : cnt);
+      }
+    };
+    auto reset = [&]() {
+      key = -1;
+      cnt = 0.f;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) acc[o] = ds_zero();
+    };
+    BaselineCursor bc((ch * span + lane) << 2, 128, L);
+    for (int r = 0; r < rounds; ++r, bc.advance(L)) {
+      const int64_t v = ch * span + (int64_t)r * 32 + lane;
+      const bool active = v < nvec;
+      if (!__any_sync(full, active)) break;
+      const int bf = (int)bc.b;  // baseline of the lane's first sample this round
+      if (__any_sync(full, !active || (key >= 0 && bf != key))) {
+        fold();
+        warp_segment_flush_ds<NO>(key, acc, n_o, out, n_b);
+        reset();
+      }
+      if (!active) continue;
+      if (key < 0) key = bf;
       int p[4];
       float c[4], s[4];
       load4_df(pix, cc, ss, v, n_t, p, c, s);
-      // the map pair is gathered once per run of equal pixels in the thread's samples
-      df m[4][NC];
-      bool dup[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) dup[k] = k > 0 && p[k] >= 0 && p[k] == p[k - 1];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (p[k] >= 0 && !dup[k]) {
-          const float4 h = __ldg(reinterpret_cast<const float4*>(map_hi) + p[k]);
-          const float4 l = __ldg(reinterpret_cast<const float4*>(map_lo) + p[k]);
-          const float hh[4] = {h.x, h.y, h.z, h.w}, ll[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-          for (int j = 0; j < NC; ++j) m[k][j] = df{hh[j], ll[j]};
-        } else {
-#pragma unroll
-          for (int j = 0; j < NC; ++j) m[k][j] = df{0.f, 0.f};
-        }
-      }
-#pragma unroll
-      for (int k = 1; k < 4; ++k)
-        if (dup[k]) {
-#pragma unroll
-          for (int j = 0; j < NC; ++j) m[k][j] = m[k - 1][j];
-        }
+      df m[NC] = {};  // the map pair, gathered once per run of equal pixels
+      int mp = -1;
       float yv[NO][4];
       if constexpr (ZY) load_y4<NO>(y, n_o, n_t, v, yv);
       const int64_t t0 = v << 2;
-      int64_t b = t0 / L;
-      int64_t bend = (b + 1) * L;
-      df zb[NO];
-#pragma unroll
-      for (int o = 0; o < NO; ++o)
-        zb[o] = (o < n_o && x != nullptr) ? df_load(x, o * n_b + b) : df{0.f, 0.f};
-      key = (int)b;
+      int64_t bend = bc.next_start(t0, L);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int64_t t = t0 + k;
         if (t >= n_t) break;
         if (t >= bend) {
-#pragma unroll
-          for (int o = 0; o < NO; ++o) {
-            if (o < n_o && (acc[o].hi != 0.f || acc[o].lo != 0.f))
-              atomicAdd(out + o * n_b + b, df_to_double(acc[o]));
-            acc[o] = df{0.f, 0.f};
-          }
-          b += 1;
-          bend += L;
-          key = (int)b;
+          fold();
 #pragma unroll
           for (int o = 0; o < NO; ++o)
-            zb[o] = (o < n_o && x != nullptr) ? df_load(x, o * n_b + b) : df{0.f, 0.f};
+            if (o < n_o && ds_nonzero(acc[o]))
+              atomicAdd(out + (int64_t)o * n_b + key, ds_to_double(acc[o]));
+          const int next = key + 1;
+          reset();
+          key = next;
+          bend += L;
         }
         if (p[k] < 0) continue;
+        if (p[k] != mp) {
+          mp = p[k];
+          const float4 h = __ldg(reinterpret_cast<const float4*>(map_hi) + mp);
+          const float4 l = __ldg(reinterpret_cast<const float4*>(map_lo) + mp);
+          const float hh[4] = {h.x, h.y, h.z, h.w}, ll[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+          for (int j = 0; j < NC; ++j) m[j] = df{hh[j], ll[j]};
+        }
+        cnt += 1.f;
 #pragma unroll
         for (int o = 0; o < NO; ++o) {
           if (o < n_o) {
-            df z = zb[o];
-            if constexpr (ZY) z = df_sub(df_make(yv[o][k]), z);
-            acc[o] = df_add(acc[o], df_sub(z, row_dot_df<NC>(K::kind(o, kk), c[k], s[k], m[k])));
+            if constexpr (ZY) ds_add(acc[o], yv[o][k]);
+            row_sub_dot_ds<NC>(K::kind(o, kk), c[k], s[k], m, acc[o]);
           }
         }
       }
+#pragma unroll
+      for (int o = 0; o < NO; ++o) ds_norm(acc[o]);
     }
-    warp_segment_flush_df<NO>(key, acc, n_o, out, n_b);
+    fold();
+    warp_segment_flush_ds<NO>(key, acc, n_o, out, n_b);
   }
 }
 
 }  // namespace
 
 // ---- launchers (mixed-precision plans only: y is float32) --------------------------
+
+// Long chunks amortise the warp flushes of the carried-sum rescans; at least four
+// chunks per warp of the grid keep the warps evenly loaded.
+int rescan_rounds(const Plan& P, int64_t n_units, int grid) {
+  if (P.rescan_rounds > 0) return P.rescan_rounds;
+  const int64_t warps = (int64_t)grid * (kBlock / 32);
+  const int64_t r = n_units / (32 * warps * 4);
+  return (int)(r < 1 ? 1 : (r > 16 ? 16 : r));
+}
 
 // Splits the baselines of an accurate pass into P.xdf (once per pass: the
 // per-sample kernels then read float32 pairs and do no float64 work per sample).
@@ -318,15 +363,17 @@ void launch_pixel_solve_df(const Plan& P, cudaStream_t st, double* out_map, Gate
 void launch_rescan_df(const Plan& P, cudaStream_t st, const double* x, const float* y,
                       double* out, Gate g) {
   const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, P.blocks_per_sm);
+  const int rounds = rescan_rounds(P, (P.n_t + 3) / 4, grid);
   const float2* xs = x != nullptr ? P.xdf : nullptr;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (y != nullptr)
       k_rescan_df<KS, true><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, xs, y, P.map32, P.maplo,
-                                                      out, P.n_t, P.L, P.n_b, P.kinds, g);
+                                                      out, P.n_t, P.L, P.n_b, P.kinds, rounds, g);
     else
       k_rescan_df<KS, false><<<grid, kBlock, 0, st>>>(P.pix, P.c, P.s, xs, nullptr, P.map32,
-                                                       P.maplo, out, P.n_t, P.L, P.n_b, P.kinds, g);
+                                                       P.maplo, out, P.n_t, P.L, P.n_b, P.kinds,
+                                                       rounds, g);
   });
 }
 

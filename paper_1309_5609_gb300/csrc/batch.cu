@@ -388,9 +388,9 @@ __global__ void __launch_bounds__(kBlock) k_bb_bin_df(const SlotDesc* __restrict
 #pragma unroll
       for (int o = 0; o < NO; ++o)
         zb[o] = o < n_o ? df_of(S.xdf[o * n_b + b]) : df{0.f, 0.f};
-      df acc[NC];
+      dsum acc[NC];
 #pragma unroll
-      for (int j = 0; j < NC; ++j) acc[j] = df{0.f, 0.f};
+      for (int j = 0; j < NC; ++j) acc[j] = ds_zero();
       int cur = -1;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -404,23 +404,17 @@ __global__ void __launch_bounds__(kBlock) k_bb_bin_df(const SlotDesc* __restrict
             zb[o] = o < n_o ? df_of(S.xdf[o * n_b + b]) : df{0.f, 0.f};
         }
         if (p[k] < 0) continue;
-        df w[NC];
-#pragma unroll
-        for (int j = 0; j < NC; ++j) w[j] = df{0.f, 0.f};
-#pragma unroll
-        for (int o = 0; o < NO; ++o)
-          if (o < n_o) row_bin_df<NC>(K::kind(o, S.kinds), c[k], s[k], zb[o], w);
         if (p[k] != cur) {
-          if (cur >= 0) flush_bins_df<NC>(S.bins, cur, acc);
+          if (cur >= 0) flush_bins_ds<NC>(S.bins, cur, acc);
           cur = p[k];
 #pragma unroll
-          for (int j = 0; j < NC; ++j) acc[j] = w[j];
-        } else {
-#pragma unroll
-          for (int j = 0; j < NC; ++j) acc[j] = df_add(acc[j], w[j]);
+          for (int j = 0; j < NC; ++j) acc[j] = ds_zero();
         }
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o) row_bin_ds<NC>(K::kind(o, S.kinds), c[k], s[k], zb[o], acc);
       }
-      if (cur >= 0) flush_bins_df<NC>(S.bins, cur, acc);
+      if (cur >= 0) flush_bins_ds<NC>(S.bins, cur, acc);
     }
   }
 }
@@ -486,9 +480,9 @@ __global__ void __launch_bounds__(kBlock) k_bb_rescan_df(const SlotDesc* __restr
     for (int64_t vb = T.begin + threadIdx.x - lane; vb < T.end; vb += blockDim.x) {
       const int64_t v = vb + lane;
       int key = -1;
-      df acc[NO];
+      dsum acc[NO];
 #pragma unroll
-      for (int o = 0; o < NO; ++o) acc[o] = df{0.f, 0.f};
+      for (int o = 0; o < NO; ++o) acc[o] = ds_zero();
       if (v < T.end) {
         int p[4];
         float c[4], s[4];
@@ -521,9 +515,8 @@ __global__ void __launch_bounds__(kBlock) k_bb_rescan_df(const SlotDesc* __restr
           if (t >= bend) {
 #pragma unroll
             for (int o = 0; o < NO; ++o) {
-              if (o < n_o && (acc[o].hi != 0.f || acc[o].lo != 0.f))
-                atomicAdd(dst + o * n_b + b, df_to_double(acc[o]));
-              acc[o] = df{0.f, 0.f};
+              if (o < n_o && ds_nonzero(acc[o])) atomicAdd(dst + o * n_b + b, ds_to_double(acc[o]));
+              acc[o] = ds_zero();
             }
             b += 1;
             bend += L;
@@ -535,11 +528,13 @@ __global__ void __launch_bounds__(kBlock) k_bb_rescan_df(const SlotDesc* __restr
           if (p[k] < 0) continue;
 #pragma unroll
           for (int o = 0; o < NO; ++o)
-            if (o < n_o)
-              acc[o] = df_add(acc[o], df_sub(zb[o], row_dot_df<NC>(K::kind(o, S.kinds), c[k], s[k], m[k])));
+            if (o < n_o) {
+              ds_add(acc[o], zb[o]);
+              row_sub_dot_ds<NC>(K::kind(o, S.kinds), c[k], s[k], m[k], acc[o]);
+            }
         }
       }
-      warp_segment_flush_df<NO>(key, acc, n_o, dst, n_b);
+      warp_segment_flush_ds<NO>(key, acc, n_o, dst, n_b);
     }
   }
 }

@@ -45,21 +45,6 @@ __device__ __forceinline__ df df_add(df x, df y) {
 
 __device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
 
-__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
-
-// x * f for a float32 factor f
-__device__ __forceinline__ df df_mul_f(df x, float f) {
-  df p = two_prod(x.hi, f);
-  return fast_two_sum(p.hi, __fmaf_rn(x.lo, f, p.lo));
-}
-
-// x * y for two double-float numbers (the lo * lo term is below the precision)
-__device__ __forceinline__ df df_mul(df x, df y) {
-  df p = two_prod(x.hi, y.hi);
-  const float e = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
-  return fast_two_sum(p.hi, __fadd_rn(p.lo, e));
-}
-
 // float64 <-> double-float
 __device__ __forceinline__ df df_from_double(double d) {
   const float hi = __double2float_rn(d);
@@ -87,11 +72,72 @@ __device__ __forceinline__ double f64_of_f32(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// hi + lo in float64: one float64 addition (exact, the pair holds <= 48 bits)
-__device__ __forceinline__ double df_to_double(df x) { return f64_of_f32(x.hi) + f64_of_f32(x.lo); }
+// Lazily normalised compensated sum (the Sum2 / Dot2 scheme of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005)): hi is
+// the float32 sum of the terms, each added by an error-free TwoSum, and lo the
+// float32 sum of the TwoSum errors, the product errors and the terms' low parts.
+// hi + lo is as accurate as a double-float sum over the few dozen terms a pass
+// adds between renormalisations (ds_norm) at about half the instructions, since
+// no step renormalises and no product is rounded to a pair first.
+struct dsum {
+  float hi, lo;
+};
 
-__device__ __forceinline__ df df_shfl_down(df x, int d) {
-  return df{__shfl_down_sync(0xffffffffu, x.hi, d), __shfl_down_sync(0xffffffffu, x.lo, d)};
+__device__ __forceinline__ dsum ds_zero() { return dsum{0.f, 0.f}; }
+
+__device__ __forceinline__ void ds_add(dsum& a, float x) {
+  const df s = two_sum(a.hi, x);
+  a.hi = s.hi;
+  a.lo = __fadd_rn(a.lo, s.lo);
 }
+
+// a += x for a double-float (or unnormalised) pair x
+__device__ __forceinline__ void ds_add(dsum& a, df x) {
+  const df s = two_sum(a.hi, x.hi);
+  a.hi = s.hi;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, x.lo));
+}
+
+// a += u * v for float32 factors (the product is exact as p + pe)
+__device__ __forceinline__ void ds_add_prod(dsum& a, float u, float v) {
+  const df p = two_prod(u, v);
+  const df s = two_sum(a.hi, p.hi);
+  a.hi = s.hi;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, p.lo));
+}
+
+// a += x * f for a pair x and a float32 f (x.lo * f is rounded: below the precision)
+__device__ __forceinline__ void ds_add_prod(dsum& a, df x, float f) {
+  const float p = __fmul_rn(x.hi, f);
+  const float pe = __fmaf_rn(x.hi, f, -p);
+  const df s = two_sum(a.hi, p);
+  a.hi = s.hi;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, __fmaf_rn(x.lo, f, pe)));
+}
+
+// a += x * y for two pairs (the lo * lo term is below the precision)
+__device__ __forceinline__ void ds_add_prod(dsum& a, df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float pe = __fmaf_rn(x.hi, y.hi, -p);
+  const float cross = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+  const df s = two_sum(a.hi, p);
+  a.hi = s.hi;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, __fadd_rn(pe, cross)));
+}
+
+// hi + lo renormalised to a double-float (TwoSum: no ordering precondition)
+__device__ __forceinline__ void ds_norm(dsum& a) {
+  const df s = two_sum(a.hi, a.lo);
+  a.hi = s.hi;
+  a.lo = s.lo;
+}
+
+__device__ __forceinline__ df ds_pair(dsum a) { return df{a.hi, a.lo}; }
+
+__device__ __forceinline__ bool ds_nonzero(dsum a) { return a.hi != 0.f || a.lo != 0.f; }
+
+// hi + lo in float64 (one float64 addition; exact while the pair spans <= 53 bits)
+__device__ __forceinline__ double ds_to_double(dsum a) { return f64_of_f32(a.hi) + f64_of_f32(a.lo); }
+
 
 }  // namespace ds

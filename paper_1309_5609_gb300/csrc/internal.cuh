@@ -52,6 +52,25 @@ __device__ __forceinline__ bool gate_closed(const Gate& g) {
   return false;
 }
 
+// Baseline of a thread's sample position as it strides through the timeline by
+// a fixed step: b = t / L and the offset r = t - b L, advanced by additions
+// instead of a 64-bit division per step.
+struct BaselineCursor {
+  int64_t b, r, dq, dr;
+  __device__ __forceinline__ BaselineCursor(int64_t t, int64_t step, int64_t L)
+      : b(t / L), r(t - (t / L) * L), dq(step / L), dr(step - (step / L) * L) {}
+  __device__ __forceinline__ void advance(int64_t L) {
+    b += dq;
+    r += dr;
+    if (r >= L) {
+      r -= L;
+      b += 1;
+    }
+  }
+  // first sample of the next baseline
+  __device__ __forceinline__ int64_t next_start(int64_t t, int64_t L) const { return t + (L - r); }
+};
+
 // One run of consecutive samples on one pixel within a baseline (runs.cu):
 // its samples' count and sums of cos 2psi and sin 2psi.
 struct RunRec {
@@ -157,6 +176,7 @@ struct Plan {
   int layout;               // mixed operator: 0 = time-ordered pixels, 1 = chunk-local index,
                             // 2 = run-length records
   int rescan_dedup;         // float32 rescan: reuse the map value of a repeated pixel
+  int rescan_rounds;        // rounds per warp chunk of the carried-sum rescans (0: automatic)
   int samples_per_thread;   // float32 operator: 4 or 8 consecutive samples per thread
   // chunk-local pixel index (chunked.cu)
   uint16_t* lid;
@@ -215,6 +235,8 @@ void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_m
 void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out, Gate g);
 void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g);
 // apply_df.cu: accurate passes of mixed plans in double-float arithmetic
+// rounds of 32 work items per warp chunk of the carried-sum rescans over n_units items
+int rescan_rounds(const Plan& P, int64_t n_units, int grid);
 void launch_split_df(const Plan& P, cudaStream_t st, const double* x, Gate g);
 void launch_bin_df(const Plan& P, cudaStream_t st, const double* x, const float* y, Gate g);
 void launch_pixel_solve_df(const Plan& P, cudaStream_t st, double* out_map, Gate g);

@@ -15,6 +15,11 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// 4-sample groups per thread in k_plan_accum_df: longer stretches per thread end
+// fewer runs of equal pixels early (each run end: one float64 atomic add per
+// nonzero matrix entry, the pass's bound).
+constexpr int kAccumGroups = 4;
+
 // Packed index of the upper triangle of a symmetric NC x NC matrix.
 template <int NC>
 __device__ __forceinline__ constexpr int sym_index(int i, int j) {
@@ -35,18 +40,18 @@ __device__ __forceinline__ void flush_m(int32_t* __restrict__ hits, double* __re
 }
 
 template <int NC>
-__device__ __forceinline__ void flush_m_df(int32_t* __restrict__ hits, double* __restrict__ mm,
-                                           int p, int h, const df (&acc)[NC * (NC + 1) / 2]) {
+__device__ __forceinline__ void flush_m_ds(int32_t* __restrict__ hits, double* __restrict__ mm,
+                                           int p, int h, const dsum (&acc)[NC * (NC + 1) / 2]) {
   constexpr int NM = NC * (NC + 1) / 2;
   atomicAdd(hits + p, h);
 #pragma unroll
   for (int j = 0; j < NM; ++j)
-    if (acc[j].hi != 0.f || acc[j].lo != 0.f) atomicAdd(mm + (int64_t)p * NM + j, df_to_double(acc[j]));
+    if (ds_nonzero(acc[j])) atomicAdd(mm + (int64_t)p * NM + j, ds_to_double(acc[j]));
 }
 
-// Same as k_plan_accum with the products and run sums in double-float: the
-// entries of w w^T are products of float32 numbers, exact as double-floats, so
-// float64 is only needed for the atomic adds.  Used by mixed-precision plans.
+// Same as k_plan_accum with the run sums of w w^T as compensated float32 sums:
+// the entries are products of float32 numbers, exact as (product, error) pairs,
+// so float64 is only needed for the atomic adds.  Used by mixed-precision plans.
 template <int KS>
 __global__ void __launch_bounds__(256) k_plan_accum_df(const int32_t* __restrict__ pix,
                                                        const float* __restrict__ cc,
@@ -60,56 +65,79 @@ __global__ void __launch_bounds__(256) k_plan_accum_df(const int32_t* __restrict
   constexpr int NC = K::NC, NO = K::NO, NM = NC * (NC + 1) / 2;
   const int n_o = K::n_o(kk);
   const int64_t nvec = (n_t + 3) >> 2;
+  const int64_t n_units = (nvec + kAccumGroups - 1) / kAccumGroups;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
-    const int64_t t0 = v << 2;
-    df acc[NM];
+  // cos / sin are 16-byte aligned (checked when the plan is made); the pixels may not be
+  const bool pix4 = (reinterpret_cast<uintptr_t>(pix) & 15) == 0;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += stride) {
+    dsum acc[NM];
 #pragma unroll
-    for (int j = 0; j < NM; ++j) acc[j] = df{0.f, 0.f};
+    for (int j = 0; j < NM; ++j) acc[j] = ds_zero();
     int cur = -1, h = 0;
+    for (int gi = 0; gi < kAccumGroups; ++gi) {
+      const int64_t v = u * kAccumGroups + gi;
+      if (v >= nvec) break;
+      const int64_t t0 = v << 2;
+      int p[4];
+      float c[4], s[4];
+      if (t0 + 4 <= n_t) {
+        if (pix4) {
+          const int4 pp = __ldcs(reinterpret_cast<const int4*>(pix) + v);
+          p[0] = pp.x; p[1] = pp.y; p[2] = pp.z; p[3] = pp.w;
+        } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int64_t t = t0 + k;
-      if (t >= n_t) break;
-      if (valid != nullptr && valid[t] == 0) continue;
-      const int p = pix[t];
-      if (p < 0 || p >= npix) {
-        atomicOr(err, ERR_PIX);
-        continue;
-      }
-      const float c = cc[t], s = ss[t];
-      df w[NM];
+          for (int k = 0; k < 4; ++k) p[k] = pix[t0 + k];
+        }
+        const float4 c4 = __ldcs(reinterpret_cast<const float4*>(cc) + v);
+        const float4 s4 = __ldcs(reinterpret_cast<const float4*>(ss) + v);
+        c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+        s[0] = s4.x; s[1] = s4.y; s[2] = s4.z; s[3] = s4.w;
+      } else {
 #pragma unroll
-      for (int j = 0; j < NM; ++j) w[j] = df{0.f, 0.f};
-#pragma unroll
-      for (int o = 0; o < NO; ++o) {
-        if (o < n_o) {
-          float row[NC];
-#pragma unroll
-          for (int j = 0; j < NC; ++j) row[j] = 0.f;
-          row_bin<NC, float>(K::kind(o, kk), c, s, 1.0f, row);
-#pragma unroll
-          for (int i = 0; i < NC; ++i)
-#pragma unroll
-            for (int j = i; j < NC; ++j) {
-              if (row[i] != 0.f && row[j] != 0.f)
-                w[sym_index<NC>(i, j)] = df_add(w[sym_index<NC>(i, j)], two_prod(row[i], row[j]));
-            }
+        for (int k = 0; k < 4; ++k) {
+          const bool in = t0 + k < n_t;
+          p[k] = in ? pix[t0 + k] : -1;
+          c[k] = in ? cc[t0 + k] : 0.f;
+          s[k] = in ? ss[t0 + k] : 0.f;
         }
       }
-      if (p != cur) {
-        if (cur >= 0) flush_m_df<NC>(hits, mm, cur, h, acc);
-        cur = p;
-        h = 1;
 #pragma unroll
-        for (int j = 0; j < NM; ++j) acc[j] = w[j];
-      } else {
+      for (int k = 0; k < 4; ++k) {
+        const int64_t t = t0 + k;
+        if (t >= n_t) break;
+        if (valid != nullptr && valid[t] == 0) continue;
+        if (p[k] < 0 || p[k] >= npix) {
+          atomicOr(err, ERR_PIX);
+          continue;
+        }
+        if (p[k] != cur) {
+          if (cur >= 0) flush_m_ds<NC>(hits, mm, cur, h, acc);
+          cur = p[k];
+          h = 0;
+#pragma unroll
+          for (int j = 0; j < NM; ++j) acc[j] = ds_zero();
+        }
         h += 1;
 #pragma unroll
-        for (int j = 0; j < NM; ++j) acc[j] = df_add(acc[j], w[j]);
+        for (int o = 0; o < NO; ++o) {
+          if (o < n_o) {
+            float row[NC];
+#pragma unroll
+            for (int j = 0; j < NC; ++j) row[j] = 0.f;
+            row_bin<NC, float>(K::kind(o, kk), c[k], s[k], 1.0f, row);
+#pragma unroll
+            for (int i = 0; i < NC; ++i)
+#pragma unroll
+              for (int j = i; j < NC; ++j) {
+                if (row[i] != 0.f && row[j] != 0.f) ds_add_prod(acc[sym_index<NC>(i, j)], row[i], row[j]);
+              }
+          }
+        }
       }
+#pragma unroll
+      for (int j = 0; j < NM; ++j) ds_norm(acc[j]);
     }
-    if (cur >= 0) flush_m_df<NC>(hits, mm, cur, h, acc);
+    if (cur >= 0) flush_m_ds<NC>(hits, mm, cur, h, acc);
   }
 }
 

@@ -14,30 +14,116 @@ constexpr int kBlock = 256;
 constexpr int kSub = 512;  // samples per warp in the construction: 16 rounds of 32
 constexpr int kScanThreads = 1024;
 
-__device__ __forceinline__ bool run_start(const int32_t* __restrict__ pix, int64_t t, int64_t L) {
-  const int p = pix[t];
-  return p >= 0 && (t % L == 0 || pix[t - 1] != p);
+// Baseline cursor of a warp walking the timeline in rounds of 32 samples: the
+// baseline b0 and offset r0 (< L) of the round's first sample t0, advanced without
+// a 64-bit division per sample.
+struct Cursor {
+  int64_t b0, r0;
+  __device__ __forceinline__ Cursor(int64_t t0, int64_t L) : b0(t0 / L), r0(t0 - (t0 / L) * L) {}
+  // baselines crossed between t0 and t0 + k (k < 64), and the offset of t0 + k
+  __device__ __forceinline__ void at(int k, int64_t L, int64_t& b, int64_t& off) const {
+    const int64_t q = r0 + k;
+    if (L >= 32) {
+      const bool wrap = q >= L;  // q < L + 32 <= 2 L
+      b = b0 + (wrap ? 1 : 0);
+      off = wrap ? q - L : q;
+    } else {
+      const unsigned w = (unsigned)q / (unsigned)L;  // q < 64
+      b = b0 + w;
+      off = q - (int64_t)w * L;
+    }
+  }
+  __device__ __forceinline__ void advance(int64_t L) {
+    int64_t b, off;
+    at(32, L, b, off);
+    b0 = b;
+    r0 = off;
+  }
+};
+
+// A run starts at a valid sample whose predecessor is another pixel or in
+// another baseline (off: the sample's offset in its baseline; prev: the pixel
+// before it).
+__device__ __forceinline__ bool run_start(int p, int prev, int64_t off) {
+  return p >= 0 && (off == 0 || prev != p);
 }
 
-// Runs starting in each stretch of kSub samples, one warp per stretch (ballots
-// over coalesced rounds of 32 samples; no block-wide synchronisation).
+// Round loads: the pixel (-1 past the end) and the angles of sample t0 + lane.
+// Issued one round ahead of their use, so that a warp's next round is in flight
+// while it works on the current one.
+__device__ __forceinline__ void fetch_round(const int32_t* __restrict__ pix,
+                                            const float* __restrict__ cc,
+                                            const float* __restrict__ ss, int64_t t0, int64_t n_t,
+                                            int lane, int& p, float& c, float& s) {
+  const int64_t t = t0 + lane;
+  const bool in = t < n_t;
+  p = in ? pix[t] : -1;
+  c = in && cc != nullptr ? cc[t] : 0.f;
+  s = in && ss != nullptr ? ss[t] : 0.f;
+}
+
+// Runs starting in each stretch of kSub samples.  Block j takes the S consecutive
+// stretches [j S, (j + 1) S), each warp a contiguous share of them, walked in
+// coalesced rounds of 32 samples (ballots of the run starts).  sub_off[w] gets the
+// runs before stretch w within its block, blk[j] the block's total (made into
+// block offsets by k_rl_scan).
 __global__ void __launch_bounds__(kBlock) k_rl_count(const int32_t* __restrict__ pix, int64_t n_t,
-                                                     int64_t L, int64_t n_sub,
-                                                     int64_t* __restrict__ sub_runs) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n_sub;
-       w += warps) {
-    int cnt = 0;
-    for (int k = 0; k < kSub / 32; ++k) {
-      const int64_t t = w * kSub + k * 32 + lane;
-      cnt += __popc(__ballot_sync(0xffffffffu, t < n_t && run_start(pix, t, L)));
+                                                     int64_t L, int64_t n_sub, int64_t S,
+                                                     int64_t* __restrict__ sub_off,
+                                                     int64_t* __restrict__ blk) {
+  __shared__ int64_t wsum[kBlock / 32];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  constexpr int kWarps = kBlock / 32;
+  const int64_t b0 = (int64_t)blockIdx.x * S;
+  const int64_t b1 = b0 + S < n_sub ? b0 + S : n_sub;
+  const int64_t per = (S + kWarps - 1) / kWarps;
+  const int64_t lo = b0 + wq * per < b1 ? b0 + wq * per : b1;
+  const int64_t hi = lo + per < b1 ? lo + per : b1;
+  int64_t run = 0;
+  if (lo < hi) {
+    int64_t t0 = lo * kSub;
+    Cursor cur(t0, L);
+    int prev0 = t0 > 0 ? pix[t0 - 1] : -1;  // pixel before the round's lane 0
+    int pn;
+    float unused_c, unused_s;
+    fetch_round(pix, nullptr, nullptr, t0, n_t, lane, pn, unused_c, unused_s);
+    for (int64_t w = lo; w < hi; ++w) {
+      int cnt = 0;
+      for (int k = 0; k < kSub / 32; ++k, t0 += 32) {
+        const int p = pn;
+        fetch_round(pix, nullptr, nullptr, t0 + 32, n_t, lane, pn, unused_c, unused_s);
+        int prev = __shfl_up_sync(full, p, 1);
+        if (lane == 0) prev = prev0;
+        prev0 = __shfl_sync(full, p, 31);
+        int64_t b, off;
+        cur.at(lane, L, b, off);
+        cnt += __popc(__ballot_sync(full, run_start(p, prev, off)));
+        cur.advance(L);
+      }
+      if (lane == 0) sub_off[w] = run;
+      run += cnt;
     }
-    if (lane == 0) sub_runs[w] = cnt;
+  }
+  if (lane == 0) wsum[wq] = run;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int q = 0; q < kWarps; ++q) {
+      const int64_t x = wsum[q];
+      wsum[q] = acc;
+      acc += x;
+    }
+    blk[blockIdx.x] = acc;
+  }
+  __syncthreads();
+  if (lane == 0) {
+    const int64_t wo = wsum[wq];
+    for (int64_t w = lo; w < hi; ++w) sub_off[w] += wo;
   }
 }
 
-// Exclusive prefix sum of the per-stretch counts in place, total in *total (one block).
+// Exclusive prefix sum in place, total in *total (one block; used on the block totals).
 __global__ void __launch_bounds__(kScanThreads) k_rl_scan(int64_t* __restrict__ v, int64_t n,
                                                           int64_t* __restrict__ total) {
   __shared__ int64_t part[kScanThreads];
@@ -76,30 +162,42 @@ __global__ void __launch_bounds__(kScanThreads) k_rl_scan(int64_t* __restrict__ 
 __global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ pix,
                                                     const float* __restrict__ cc,
                                                     const float* __restrict__ ss, int64_t n_t,
-                                                    int64_t L, int64_t n_sub,
+                                                    int64_t L, int64_t n_sub, int64_t S,
                                                     const int64_t* __restrict__ sub_off,
+                                                    const int64_t* __restrict__ blk,
                                                     RunRec* __restrict__ rec,
                                                     int32_t* __restrict__ rb,
                                                     float4* __restrict__ rdf) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const unsigned below = (1u << lane) - 1u;
   const unsigned upto = lane == 31 ? full : (2u << lane) - 1u;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n_sub;
        w += warps) {
-    int64_t base = sub_off[w];
+    int64_t base = sub_off[w] + blk[w / S];
     // partial sums of a run opened in an earlier round (cr < 0: none)
     float cn = 0.f;
     df cC{0.f, 0.f}, cS{0.f, 0.f};
     int64_t cr = -1;
-    for (int64_t t0 = w * kSub; ; t0 += 32) {
+    Cursor cur(w * kSub, L);
+    int prev0 = w > 0 ? pix[w * kSub - 1] : -1;  // pixel before the round's lane 0
+    int pn;
+    float cv_n, sv_n;
+    fetch_round(pix, cc, ss, w * kSub, n_t, lane, pn, cv_n, sv_n);
+    for (int64_t t0 = w * kSub; ; t0 += 32, cur.advance(L)) {
       const bool own = t0 < (w + 1) * kSub;  // rounds past the stretch only finish a carried run
       if (!own && cr < 0) break;
+      const int p = pn;
+      const float cv = cv_n, sv = sv_n;
+      fetch_round(pix, cc, ss, t0 + 32, n_t, lane, pn, cv_n, sv_n);
+      int prev = __shfl_up_sync(full, p, 1);
+      if (lane == 0) prev = prev0;
+      prev0 = __shfl_sync(full, p, 31);
       const int64_t t = t0 + lane;
-      const int p = t < n_t ? pix[t] : -1;
+      int64_t bl, off;
+      cur.at(lane, L, bl, off);
       const bool valid = p >= 0;
-      const bool rstart = valid && run_start(pix, t, L);
+      const bool rstart = run_start(p, prev, off);
       const unsigned rmask = __ballot_sync(full, rstart);
       const unsigned smask = own ? rmask : 0u;  // runs this warp fills
       const bool start = own && rstart;
@@ -109,11 +207,14 @@ __global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ 
       // at or before this lane the sample continues the carried run, if any
       const bool member = valid && (head >= 0 ? own : cr >= 0);
       float n = member ? 1.f : 0.f;
-      df C = member ? df_make(cc[t]) : df{0.f, 0.f};
-      df S = member ? df_make(ss[t]) : df{0.f, 0.f};
+      df C = member ? df_make(cv) : df{0.f, 0.f};
+      df S = member ? df_make(sv) : df{0.f, 0.f};
       const int seg0 = head >= 0 ? head : 0;
+      // the scan needs only the steps that reach the longest run's first lane
+      const unsigned reach = __reduce_max_sync(full, member ? (unsigned)(lane - seg0) : 0u);
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
+        if ((unsigned)d > reach) break;
         const float n2 = __shfl_up_sync(full, n, d);
         const df C2 = df{__shfl_up_sync(full, C.hi, d), __shfl_up_sync(full, C.lo, d)};
         const df S2 = df{__shfl_up_sync(full, S.hi, d), __shfl_up_sync(full, S.lo, d)};
@@ -131,17 +232,17 @@ __global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ 
       // does the next sample continue this lane's run?
       const bool nstart = __shfl_down_sync(full, start, 1);
       const bool nmember = __shfl_down_sync(full, member, 1);
+      const int pnext = __shfl_sync(full, pn, 0);  // the sample after lane 31 (-1 past the end)
       bool cont;
       if (lane < 31) {
         cont = nmember && !nstart;
       } else {
-        const int64_t u = t + 1;
-        cont = member && u < n_t && u % L != 0 && pix[u] == p;
+        cont = member && t + 1 < n_t && off + 1 != L && pnext == p;
       }
       const int64_t r = head >= 0 ? base + __popc(smask & ((1u << head) - 1u)) : cr;
       if (member && !cont) {
         rec[r] = RunRec{p, n, C.hi, S.hi};
-        rb[r] = (int32_t)(t / L);
+        rb[r] = (int32_t)bl;
         rdf[r] = make_float4(C.hi, C.lo, S.hi, S.lo);
       }
       // carry lane 31's open run into the next round
@@ -161,12 +262,24 @@ __global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ 
 // Run records are built in two steps around the plan's synchronisation: the
 // count (and its prefix over tiles) is enqueued first; once the host knows the
 // total it allocates the records and enqueues the fill.
+// Stretches per counting block (S) and counting blocks (G) for n_sub stretches:
+// G x S >= n_sub with S a whole number of warp shares.
+static void count_split(const Plan& P, int64_t n_sub, int64_t& S, int64_t& G) {
+  const int64_t g = stream_grid(P, n_sub * 32, kBlock, 8);
+  S = (n_sub + g - 1) / g;
+  G = (n_sub + S - 1) / S;
+}
+
 ds_status rl_count(Plan& P, int64_t* d_total) {
   const int64_t n_sub = (P.n_t + kSub - 1) / kSub;
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_tiles), sizeof(int64_t) * n_sub, false));
-  const int grid = stream_grid(P, n_sub * 32, kBlock, 8);
-  k_rl_count<<<grid, kBlock, 0, P.stream>>>(P.pix, P.n_t, P.L, n_sub, P.rl_tiles);
-  k_rl_scan<<<1, kScanThreads, 0, P.stream>>>(P.rl_tiles, n_sub, d_total);
+  int64_t S, G;
+  count_split(P, n_sub, S, G);
+  // per-stretch offsets within their block, then the block offsets
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_tiles), sizeof(int64_t) * (n_sub + G),
+                         false));
+  k_rl_count<<<(unsigned)G, kBlock, 0, P.stream>>>(P.pix, P.n_t, P.L, n_sub, S, P.rl_tiles,
+                                                   P.rl_tiles + n_sub);
+  k_rl_scan<<<1, kScanThreads, 0, P.stream>>>(P.rl_tiles + n_sub, G, d_total);
   P.launches += 2;
   DS_CUDA_TRY(cudaGetLastError());
   return DS_OK;
@@ -182,8 +295,10 @@ ds_status rl_fill(Plan& P, int64_t n_runs) {
   const int grid = stream_grid(P, n_sub * 32, kBlock, 8);
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_df),
                          sizeof(float4) * (n_runs > 0 ? n_runs : 1), true));
-  k_rl_fill<<<grid, kBlock, 0, P.stream>>>(P.pix, P.c, P.s, P.n_t, P.L, n_sub, P.rl_tiles,
-                                           P.rl_rec, P.rl_b, P.rl_df);
+  int64_t S, G;
+  count_split(P, n_sub, S, G);
+  k_rl_fill<<<grid, kBlock, 0, P.stream>>>(P.pix, P.c, P.s, P.n_t, P.L, n_sub, S, P.rl_tiles,
+                                           P.rl_tiles + n_sub, P.rl_rec, P.rl_b, P.rl_df);
   P.launches += 1;
   DS_CUDA_TRY(cudaGetLastError());
   cudaFreeAsync(P.rl_tiles, P.stream);

@@ -9,46 +9,86 @@
 
 namespace ds {
 
-// acc += w_kind * z in double-float
+// A split baseline (hi, lo) through the read-only path
+__device__ __forceinline__ df df_ldg(const float2* __restrict__ xs, int64_t i) {
+  const float2 v = __ldg(xs + i);
+  return df{v.x, v.y};
+}
+
+// acc += w_kind * z for a pair z (compensated sums)
 template <int NC>
-__device__ __forceinline__ void row_bin_df(int kind, float c, float s, df z, df (&acc)[NC]) {
+__device__ __forceinline__ void row_bin_ds(int kind, float c, float s, df z, dsum (&acc)[NC]) {
   using F = Frame<NC>;
   if (kind == DS_KIND_I) {
-    if constexpr (F::I >= 0) acc[F::I] = df_add(acc[F::I], z);
+    if constexpr (F::I >= 0) ds_add(acc[F::I], z);
   } else if (kind == DS_KIND_Q) {
     if constexpr (F::Q >= 0) {
-      acc[F::Q] = df_add(acc[F::Q], df_mul_f(z, c));
-      acc[F::U] = df_add(acc[F::U], df_mul_f(z, s));
+      ds_add_prod(acc[F::Q], z, c);
+      ds_add_prod(acc[F::U], z, s);
     }
   } else if (kind == DS_KIND_U) {
     if constexpr (F::Q >= 0) {
-      acc[F::Q] = df_sub(acc[F::Q], df_mul_f(z, s));
-      acc[F::U] = df_add(acc[F::U], df_mul_f(z, c));
+      ds_add_prod(acc[F::Q], z, -s);
+      ds_add_prod(acc[F::U], z, c);
     }
   } else {
     if constexpr (F::I >= 0 && F::Q >= 0) {
-      acc[F::I] = df_add(acc[F::I], z);
-      acc[F::Q] = df_add(acc[F::Q], df_mul_f(z, c));
-      acc[F::U] = df_add(acc[F::U], df_mul_f(z, s));
+      ds_add(acc[F::I], z);
+      ds_add_prod(acc[F::Q], z, c);
+      ds_add_prod(acc[F::U], z, s);
     }
   }
 }
 
-// w_kind . m in double-float
+// acc += w_kind * y for a float32 y (exact products)
 template <int NC>
-__device__ __forceinline__ df row_dot_df(int kind, float c, float s, const df (&m)[NC]) {
+__device__ __forceinline__ void row_bin_ds(int kind, float c, float s, float y, dsum (&acc)[NC]) {
   using F = Frame<NC>;
   if (kind == DS_KIND_I) {
-    if constexpr (F::I >= 0) return m[F::I];
+    if constexpr (F::I >= 0) ds_add(acc[F::I], y);
   } else if (kind == DS_KIND_Q) {
-    if constexpr (F::Q >= 0) return df_add(df_mul_f(m[F::Q], c), df_mul_f(m[F::U], s));
+    if constexpr (F::Q >= 0) {
+      ds_add_prod(acc[F::Q], y, c);
+      ds_add_prod(acc[F::U], y, s);
+    }
   } else if (kind == DS_KIND_U) {
-    if constexpr (F::Q >= 0) return df_sub(df_mul_f(m[F::U], c), df_mul_f(m[F::Q], s));
+    if constexpr (F::Q >= 0) {
+      ds_add_prod(acc[F::Q], y, -s);
+      ds_add_prod(acc[F::U], y, c);
+    }
   } else {
-    if constexpr (F::I >= 0 && F::Q >= 0)
-      return df_add(m[F::I], df_add(df_mul_f(m[F::Q], c), df_mul_f(m[F::U], s)));
+    if constexpr (F::I >= 0 && F::Q >= 0) {
+      ds_add(acc[F::I], y);
+      ds_add_prod(acc[F::Q], y, c);
+      ds_add_prod(acc[F::U], y, s);
+    }
   }
-  return df{0.f, 0.f};
+}
+
+// acc -= w_kind . m for a double-float map m
+template <int NC>
+__device__ __forceinline__ void row_sub_dot_ds(int kind, float c, float s, const df (&m)[NC],
+                                               dsum& acc) {
+  using F = Frame<NC>;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) ds_add(acc, df_neg(m[F::I]));
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) {
+      ds_add_prod(acc, m[F::Q], -c);
+      ds_add_prod(acc, m[F::U], -s);
+    }
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) {
+      ds_add_prod(acc, m[F::Q], s);
+      ds_add_prod(acc, m[F::U], -c);
+    }
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0) {
+      ds_add(acc, df_neg(m[F::I]));
+      ds_add_prod(acc, m[F::Q], -c);
+      ds_add_prod(acc, m[F::U], -s);
+    }
+  }
 }
 
 __device__ __forceinline__ void load4_df(const int32_t* __restrict__ pix,
@@ -75,32 +115,38 @@ __device__ __forceinline__ void load4_df(const int32_t* __restrict__ pix,
 }
 
 template <int NC>
-__device__ __forceinline__ void flush_bins_df(double* __restrict__ bins, int p, const df (&acc)[NC]) {
+__device__ __forceinline__ void flush_bins_ds(double* __restrict__ bins, int p, const dsum (&acc)[NC]) {
   double* dst = bins + (int64_t)p * 4;
 #pragma unroll
-  for (int j = 0; j < NC; ++j) atomicAdd(dst + j, df_to_double(acc[j]));
+  for (int j = 0; j < NC; ++j) atomicAdd(dst + j, ds_to_double(acc[j]));
 }
 
+// Segmented sum across the warp of per-lane compensated partials keyed by
+// baseline (each key's lanes contiguous, -1 for none); the first lane of every
+// segment adds it to out[o][key] in float64.
 template <int NO>
-__device__ __forceinline__ void warp_segment_flush_df(int key, df (&val)[NO], int n_o,
+__device__ __forceinline__ void warp_segment_flush_ds(int key, dsum (&val)[NO], int n_o,
                                                       double* __restrict__ out, int64_t n_b) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 0; o < NO; ++o) ds_norm(val[o]);
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int k2 = __shfl_down_sync(full, key, d);
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
-      const df v2 = df_shfl_down(val[o], d);
-      if (lane + d < 32 && k2 == key) val[o] = df_add(val[o], v2);
+      const df v2 = df{__shfl_down_sync(full, val[o].hi, d), __shfl_down_sync(full, val[o].lo, d)};
+      if (lane + d < 32 && k2 == key) ds_add(val[o], v2);
     }
   }
   const int kp = __shfl_up_sync(full, key, 1);
   if (key >= 0 && (lane == 0 || kp != key)) {
 #pragma unroll
     for (int o = 0; o < NO; ++o)
-      if (o < n_o) atomicAdd(out + (int64_t)o * n_b + key, df_to_double(val[o]));
+      if (o < n_o) atomicAdd(out + (int64_t)o * n_b + key, ds_to_double(val[o]));
   }
 }
+
 
 }  // namespace ds

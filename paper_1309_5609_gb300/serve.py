@@ -63,11 +63,16 @@ class Request:
 
 
 def device_bytes(n_t: int, n_o: int, nside: int, baseline_len: int) -> int:
-    """Device footprint of one admitted request (request arrays + plan)."""
+    """Upper bound of the device footprint of one admitted request: its arrays and
+    its mixed-precision plan (the plan reports its exact figure once built)."""
     npix = 12 * nside * nside
-    n_u = n_o * (-(-n_t // baseline_len))
+    n_b = -(-n_t // baseline_len)
+    n_u = n_o * n_b
     arrays = n_t * (4 + 4 + 4 + 4 * n_o)          # pix, cos, sin, y (float32)
-    plan = n_t * 4 + npix * (4 + 1 + 8 * 6 + 8 * 4 + 4 * 4 * 3 + 8 * 4) + n_u * 8 * 6
+    per_pixel = 4 + 1 + 8 * 6 + 8 * 4 * 2 + 4 * 4 * 3   # hits, mask, M^-1, sums, maps
+    runs = int(0.6 * 36 * n_t)                     # run records (at most 0.6 runs per sample)
+    plan = (n_t * 4 + npix * per_pixel + n_u * (8 * 7 + 8 + 4) + n_b * 4 + runs
+            + (n_t // 512 + 1) * 8 + (1 << 16))  # per-baseline counts, scan tiles, scalars
     return int(arrays + plan)
 
 

@@ -441,3 +441,47 @@ def test_accurate_start_matches_oracle(case):
     ref = oracle.destripe(op, yo, tol=1e-10)
     assert np.abs(a.cpu().numpy() - ref["a"]).max() < 1e-4
     plan.close()
+
+
+@pytest.mark.parametrize("rounds", [1, 3, 16])
+@pytest.mark.parametrize("layout", [0, 2])
+@pytest.mark.parametrize("case", [CASES[1], CASES[3], CASES[6]], ids=["Iqu_flags", "I_L1", "I_iqu"])
+def test_carried_rescans_every_chunk_length(case, layout, rounds):
+    # the rescans keep per-lane baseline sums across rounds of a warp's chunk and
+    # flush them where a baseline ends: every chunk length, baselines of 1 to 50
+    # samples, flags, both operator layouts; the right-hand side, the map and the
+    # solve meet the float64 bars, the float32 operator its own
+    prob = case_problem(case)
+    op, d = oracle_plan(prob)
+    plan, g, y = gpu_plan(prob, "mixed")
+    ds.destripe_tune(plan, "layout", layout)
+    ds.destripe_tune(plan, "rescan_rounds", rounds)
+    yo = y.double().cpu().numpy().reshape(plan.n_o, plan.n_t)
+    b = torch.empty(plan.n_u, dtype=torch.float64, device=DEV)
+    ds.destripe_rhs(plan, y, b)
+    assert rel_rms(b.cpu().numpy(), oracle.rhs(op, yo)) < 1e-11
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(plan.n_u)
+    Ax = torch.empty(plan.n_u, dtype=torch.float64, device=DEV)
+    ds.destripe_apply_A(plan, torch.from_numpy(x).to(DEV), Ax)
+    assert rel_rms(Ax.cpu().numpy(), oracle.apply_A(op, x)) < 1e-5
+    a = torch.zeros(plan.n_u, dtype=torch.float64, device=DEV)
+    st, iters, rel = ds.destripe_solve(plan, y, a, tol=1e-10)
+    ref = oracle.destripe(op, yo, tol=1e-10)
+    assert st == ds.DS_OK and rel < 1e-9, (st, iters, rel)
+    assert rel_rms(a.cpu().numpy(), ref["a"]) < 1e-5
+    m = torch.zeros(plan.n_c * plan.npix, dtype=torch.float64, device=DEV)
+    ds.destripe_map(plan, y, a, m)
+    mref = oracle.bin_map(op, yo - oracle.expand(op, a.cpu().numpy()))
+    assert rel_rms(m.cpu().numpy(), mref) < 1e-11
+    plan.close()
+
+
+def test_rescan_rounds_key_bounds():
+    prob = case_problem(CASES[0])
+    plan, g, y = gpu_plan(prob, "mixed")
+    for bad in (-1, 17, 2.5):
+        with pytest.raises(ds.DestripeError):
+            ds.destripe_tune(plan, "rescan_rounds", bad)
+    ds.destripe_tune(plan, "rescan_rounds", 0)
+    plan.close()

@@ -102,3 +102,15 @@ def test_ill_posed_requests_never_return_garbage():
         assert np.isfinite(r.a.numpy()).all() and np.isfinite(r.rel_resid)
         if r.kinds == ("q", "u") and r.n_t >= 100_000:
             assert r.status == ds.DS_OK
+
+
+def test_footprint_estimate_bounds_the_plan():
+    for ns, kinds, L in ((16, ("q", "u"), 100), (64, ("q",), 25), (32, ("q", "u"), 3000)):
+        p = make_problem(200_000, ns, kinds, baseline_len=L, seed=2, device=DEV,
+                         y_dtype=torch.float32, keep_f64_trig=False)
+        plan = ds.destripe_plan(p.pix, p.c32, p.s32, None, nside=ns, kinds=kinds,
+                                baseline_len=L, precision="mixed")
+        held = ds.destripe_plan_info(plan)["device_bytes"]
+        arrays = p.n_t * (12 + 4 * len(kinds))
+        assert held + arrays <= device_bytes(p.n_t, len(kinds), ns, L)
+        plan.close()
