@@ -28,13 +28,6 @@ constexpr int kBlock = 256;
 // registers) spills and gains nothing more.
 constexpr int kDfMinBlocks = 3;
 
-// 4-sample groups per thread in k_bin_df.  Every run end among a thread's samples
-// costs one float64 atomic add per component (the pass's bound), so longer
-// stretches per thread would end fewer runs early; measured on the B-Machine-like
-// workload, 4 groups (16 samples) took 1.59 ms against 1.29 ms for one: the
-// warp's 16-byte loads then stride 64 bytes apart.
-constexpr int kDfGroups = 1;
-
 // x[i] -> (hi, lo) with hi = x rounded to float32, lo = the rest rounded to float32
 __global__ void __launch_bounds__(kBlock) k_split_df(const double* __restrict__ x,
                                                      float2* __restrict__ xs, int64_t n, Gate g) {
@@ -69,9 +62,14 @@ __device__ __forceinline__ void load_y4(const float* __restrict__ y, int n_o, in
 }
 
 // bins[p] += sum_o w_o(t) z_o(t), z = x[o][t/L] (ZY false) or y[o][t] - a[o][t/L] (ZY true);
-// the baselines come split into double-float pairs (xs, NULL for none).  A thread
-// takes kDfGroups x 4 consecutive samples; each run of equal pixels among them
-// is one compensated sum and one float64 atomic add per component.
+// the baselines come split into double-float pairs (xs, NULL for none).  A lane
+// takes 4 consecutive samples, a warp 128; each run of equal pixels is one
+// compensated sum per component and ends in one float64 atomic add per component
+// (the pass's bound).  A run that crosses from one lane's samples into the next
+// lane's is handed on instead of flushed twice: each lane keeps its first and last
+// run open, a segmented shuffle scan over the lanes carries every last run into
+// the next lane while that lane's first run has the same pixel (through lanes
+// whose samples are all on that pixel), and the lane where the run ends flushes it.
 template <int KS, bool ZY>
 __global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_bin_df(const int32_t* __restrict__ pix,
                                                    const float* __restrict__ cc,
@@ -85,31 +83,32 @@ __global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_bin_df(const int32_t* 
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
   const bool hasx = x != nullptr;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned upto = lane == 31 ? full : (2u << lane) - 1u;
   const int64_t nvec = (n_t + 3) >> 2;
-  const int64_t n_units = (nvec + kDfGroups - 1) / kDfGroups;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t u0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  BaselineCursor bc(u0 * 4 * kDfGroups, stride * 4 * kDfGroups, L);
-  for (int64_t u = u0; u < n_units; u += stride, bc.advance(L)) {
-    int64_t b = bc.b;
-    int64_t bend = bc.next_start(u * 4 * kDfGroups, L);
-    df zb[NO];
+  const int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  BaselineCursor bc(v0 << 2, stride << 2, L);
+  for (int64_t vb = v0 - lane; vb < nvec; vb += stride, bc.advance(L)) {
+    const int64_t v = vb + lane;
+    int head_p = -1, cur = -1, nruns = 0;
+    dsum head[NC], acc[NC];
 #pragma unroll
-    for (int o = 0; o < NO; ++o)
-      zb[o] = (o < n_o && hasx) ? df_ldg(x, o * n_b + b) : df{0.f, 0.f};
-    dsum acc[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = ds_zero();
-    int cur = -1;
-    for (int gi = 0; gi < kDfGroups; ++gi) {
-      const int64_t v = u * kDfGroups + gi;
-      if (v >= nvec) break;
+    for (int j = 0; j < NC; ++j) head[j] = acc[j] = ds_zero();
+    if (v < nvec) {
       int p[4];
       float c[4], s[4];
       load4_df(pix, cc, ss, v, n_t, p, c, s);
       float yv[NO][4];
       if constexpr (ZY) load_y4<NO>(y, n_o, n_t, v, yv);
       const int64_t t0 = v << 2;
+      int64_t b = bc.b;
+      int64_t bend = bc.next_start(t0, L);
+      df zb[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        zb[o] = (o < n_o && hasx) ? df_ldg(x, o * n_b + b) : df{0.f, 0.f};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int64_t t = t0 + k;
@@ -123,8 +122,17 @@ __global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_bin_df(const int32_t* 
         }
         if (p[k] < 0) continue;
         if (p[k] != cur) {
-          if (cur >= 0) flush_bins_ds<NC>(bins, cur, acc);
+          if (cur >= 0) {
+            if (nruns == 1) {  // the lane's first run stays open for the hand-off
+              head_p = cur;
+#pragma unroll
+              for (int j = 0; j < NC; ++j) head[j] = acc[j];
+            } else {
+              flush_bins_ds<NC>(bins, cur, acc);
+            }
+          }
           cur = p[k];
+          nruns += 1;
 #pragma unroll
           for (int j = 0; j < NC; ++j) acc[j] = ds_zero();
         }
@@ -148,7 +156,40 @@ __global__ void __launch_bounds__(kBlock, kDfMinBlocks) k_bin_df(const int32_t* 
 #pragma unroll
       for (int j = 0; j < NC; ++j) ds_norm(acc[j]);
     }
-    if (cur >= 0) flush_bins_ds<NC>(bins, cur, acc);
+    // acc is the lane's last run (pixel cur); with a single run it is also the first
+    const bool single = nruns == 1;
+    if (single) head_p = cur;
+    const int prev_tail = __shfl_up_sync(full, cur, 1);
+    const bool link = lane > 0 && head_p >= 0 && head_p == prev_tail;  // takes the previous lane's run
+    const bool through = single && link;
+    // out = the last run's sums including what flows in through single-run lanes
+    const unsigned starts = __ballot_sync(full, !through);  // lane 0 always starts a segment
+    const int seg0 = 31 - __clz(starts & upto);
+    const unsigned reach = __reduce_max_sync(full, (unsigned)(lane - seg0));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      if ((unsigned)d > reach) break;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const df o2 = df{__shfl_up_sync(full, acc[j].hi, d), __shfl_up_sync(full, acc[j].lo, d)};
+        if (lane - d >= seg0) ds_add(acc[j], o2);
+      }
+    }
+    dsum in[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const df o2 = df{__shfl_up_sync(full, acc[j].hi, 1), __shfl_up_sync(full, acc[j].lo, 1)};
+      in[j] = dsum{o2.hi, o2.lo};
+    }
+    const bool next_link = __shfl_down_sync(full, link, 1) && lane < 31;
+    if (!single && head_p >= 0) {
+      if (link) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) ds_add(head[j], ds_pair(in[j]));
+      }
+      flush_bins_ds<NC>(bins, head_p, head);
+    }
+    if (cur >= 0 && !next_link) flush_bins_ds<NC>(bins, cur, acc);
   }
 }
 
