@@ -38,9 +38,11 @@
  *    timelines y.  DS_PREC_MIXED takes float32 timelines y; the per-sample work
  *    of the CG iterations (expand, bin, rescan, baseline sums) runs in float32;
  *    the right-hand side, the residual refreshes that keep the iteration honest
- *    and the maps run in double-float (pairs of float32, about 48 significant
- *    bits) with float64 accumulators; pixel matrices, their inverses and rcond
- *    cut, pixel solves and the CG vectors and scalars are float64.
+ *    and the maps read their operands as double-float pairs (two float32, about
+ *    48 significant bits) and sum in compensated float32 (Sum2 / Dot2 of Ogita,
+ *    Rump and Oishi) flushed to float64 accumulators; pixel matrices, their
+ *    inverses and rcond cut, pixel solves and the CG vectors and scalars are
+ *    float64.
  */
 #ifndef DESTRIPE_H
 #define DESTRIPE_H
@@ -219,8 +221,9 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     (default), 0 = float64 pixel sums with scalar atomics
  *   "graph_iters"     1..64 CG iterations per captured graph replay (default 16)
  *   "accurate_df"     MIXED plans: 1 = the accurate passes (right-hand side, maps,
- *                     float64 residual refreshes) use double-float arithmetic on the
- *                     float32 pipes with float64 accumulators (default), 0 = float64
+ *                     float64 residual refreshes) use double-float operands and
+ *                     compensated float32 sums on the float32 pipes with float64
+ *                     accumulators (default), 0 = float64
  *   "stream_mode"     MIXED plans: 0 = streaming kernels read the pointing with vector
  *                     loads (default); 1 / 2 = TMA bulk copies stage it through a
  *                     shared-memory pipeline of 4 x 2048-sample stages at 2 blocks per SM

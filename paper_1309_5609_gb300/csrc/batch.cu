@@ -12,7 +12,7 @@
 //
 // Per problem the iteration is exactly the single-problem mixed-precision one:
 // float32 operator (vector atomics into float32 pixel sums), float64 CG vectors
-// and scalars, double-float residual refreshes gated per problem.  Per-problem
+// and scalars, compensated-sum residual refreshes gated per problem.  Per-problem
 // dot products are deterministic: every tile writes its partial and the last
 // tile of the problem (ticket counter) adds them in tile order.
 #include <cmath>

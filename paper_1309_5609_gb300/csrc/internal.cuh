@@ -167,7 +167,7 @@ struct Plan {
   int bin_mode;             // mixed binning: 0 = float64 atomics, 1 = float32 vector atomics
   int graph_iters_cfg;      // CG iterations per captured graph
   int blocks_per_sm;        // streaming-kernel blocks per SM
-  int accurate_df;          // mixed plans: accurate passes in double-float (1) or float64 (0)
+  int accurate_df;          // mixed plans: accurate passes in compensated float32 (1) or float64 (0)
   int stream_mode;          // mixed operator: 0 = direct vector loads, 1 = TMA-staged pipeline
   int refresh_max;          // mixed plans: float64 residual at least every this many iterations
   double drift_ratio;       // mixed plans: squared true / recursive residual ratio of the switch
@@ -234,7 +234,7 @@ void launch_bin_y(const Plan& P, cudaStream_t st, const void* y, const double* a
 void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_map, Gate g);
 void launch_rescan_x(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out, Gate g);
 void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g);
-// apply_df.cu: accurate passes of mixed plans in double-float arithmetic
+// apply_df.cu: accurate passes of mixed plans (double-float operands, compensated sums)
 // rounds of 32 work items per warp chunk of the carried-sum rescans over n_units items
 int rescan_rounds(const Plan& P, int64_t n_units, int grid);
 void launch_split_df(const Plan& P, cudaStream_t st, const double* x, Gate g);

@@ -1,6 +1,6 @@
-// Double-float helpers shared by the single-problem and batched accurate passes:
-// rows applied to double-float values, 4-sample loads, flushes into float64
-// pixel sums and the warp-segmented per-baseline sum.
+// Helpers shared by the single-problem and batched accurate passes: rows applied
+// to double-float values in compensated sums (df.cuh), 4-sample loads, flushes
+// into float64 pixel sums and the warp-segmented per-baseline sum.
 #pragma once
 
 #include "df.cuh"
