@@ -309,7 +309,7 @@ def run_ours(args):
         for k, v in tune.items():
             ds.destripe_tune(plan, k, v)
         info = ds.destripe_plan_info(plan)
-        layout.update(layout=info["layout"], n_runs=info["n_runs"])
+        layout.update(layout=info["layout"], n_runs=info["n_runs"], bin_order=info["bin_order"])
         if prof_acc is not None:
             ds.destripe_profile(plan, 1)
         st, iters, rel = ds.destripe_solve(plan, prob.y, a, tol=args.tol)
@@ -368,7 +368,8 @@ def run_ours(args):
     form = layout.get("layout", 0) if mixed else 0
     kname = {0: {"bin": "k_bin", "rescan": "k_rescan"},
              1: {"bin": "k_ck_bin", "rescan": "k_ck_rescan"},
-             2: {"bin": "k_rl_bin", "rescan": "k_rl_rescan"}}[form][dom]
+             2: {"bin": "k_pm_bin" if layout.get("bin_order") else "k_rl_bin",
+                 "rescan": "k_rl_rescan"}}[form][dom]
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
             "traffic": kernel_traffic(prob.n_t, kname, name),
@@ -386,7 +387,9 @@ def run_ours(args):
             "data": "synthetic (seeded scan, Gaussian sky, 1/f noise), resident in HBM",
             "config": dict(config_dict(args, name), tune=tune,
                            operator_layout={0: "time-ordered pixels", 1: "chunk-local pixel index",
-                                            2: "run-length records"}[form],
+                                            2: "run-length records"}[form]
+                           + (", pixel-major binning" if form == 2 and layout.get("bin_order")
+                              else ""),
                            runs_per_sample=layout.get("n_runs", 0) / prob.n_t), "roofline": roof,
             "iterations_per_step": iters_tot / args.steps,
             "rel_resid_max": max(rels) if rels else None,

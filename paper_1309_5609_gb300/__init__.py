@@ -48,7 +48,7 @@ class ds_info(ctypes.Structure):
                 ("n_good_pix", ctypes.c_int64), ("n_valid", ctypes.c_int64),
                 ("n_outputs", ctypes.c_int32), ("n_comp", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("layout", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32), ("n_runs", ctypes.c_int64)]
+                ("bin_order", ctypes.c_int32), ("n_runs", ctypes.c_int64)]
 
 
 class ds_profile(ctypes.Structure):

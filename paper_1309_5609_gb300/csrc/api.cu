@@ -105,7 +105,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->pm_off, P->pm_rec, P->pm_df, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a
@@ -301,6 +301,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->layout = 0;
   P->rescan_dedup = 1;
   P->rescan_rounds = 0;
+  P->bin_order = 1;
   P->samples_per_thread = 4;
   cudaError_t e = cudaSuccess;
 #define DS_ALLOC(ptr, n) \
@@ -375,6 +376,7 @@ ds_status destripe_plan_info(ds_plan_t plan, ds_info* info) {
   info->n_comp = P.n_c;
   info->device_bytes = P.device_bytes;
   info->layout = P.layout;
+  info->bin_order = (P.layout == 2 && pm_ready(P)) ? 1 : 0;
   info->n_runs = P.rl_rec != nullptr ? P.rl_n : 0;
   return DS_OK;
 }
@@ -594,6 +596,16 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
   } else if (k == "rescan_dedup") {
     if (value != 0.0 && value != 1.0) return DS_EINVAL;
     P.rescan_dedup = (int)value;
+  } else if (k == "bin_order") {
+    if (value != 0.0 && value != 1.0) return DS_EINVAL;
+    if (P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
+    if (value == 1.0 && P.pm_rec == nullptr && P.rl_rec != nullptr) {
+      clear_stale_error();
+      ds_status s = pm_build(P);
+      if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
+      if (s != DS_OK) return s;
+    }
+    P.bin_order = (int)value;
   } else if (k == "rescan_rounds") {
     if (!(value >= 0.0 && value <= 16.0) || (double)(int)value != value) return DS_EINVAL;
     P.rescan_rounds = (int)value;

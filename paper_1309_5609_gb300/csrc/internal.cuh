@@ -195,6 +195,14 @@ struct Plan {
   int64_t rl_n;
   int64_t* rl_tiles;        // runs per construction tile, between count and fill
   float4* rl_df;            // per run: (sum cos 2psi, sum sin 2psi) as double-float pairs
+  // pixel-major copy of the runs (runs_pm.cu): the runs of pixel p are
+  // pm_off[p] .. pm_off[p + 1] - 1, in no particular order
+  uint32_t* pm_off;         // [n_pix + 1]
+  float4* pm_rec;           // per run: (count, sum cos, sum sin, baseline as int bits)
+  float4* pm_df;            // per run: the double-float sums, as rl_df
+  float4* x4;               // [n_b] float32 baselines of every output, per baseline
+  float4* xd4;              // [2][n_b] split baselines: hi parts, then lo parts
+  int bin_order;            // run-length plans: 1 = bin pixel-major (default), 0 = in time order
 };
 
 // api.cu: device memory of a plan from the library's stream-ordered pool;
@@ -205,6 +213,11 @@ cudaError_t plan_alloc(Plan& P, void** ptr, size_t bytes, bool count);
 ds_status rl_count(Plan& P, int64_t* d_total);
 ds_status rl_fill(Plan& P, int64_t n_runs);
 ds_status rl_build(Plan& P);
+ds_status pm_build(Plan& P);
+// runs_pm.cu: the binning pass over the pixel-major copy (one warp per pixel, no atomics)
+bool pm_ready(const Plan& P);
+void launch_bin_pm(const Plan& P, cudaStream_t st, Gate g);
+void launch_bin_pm_df(const Plan& P, cudaStream_t st, Gate g);
 constexpr double kRunsPerSampleMax = 0.6;  // plans build run records at or below this ratio
 bool rl_ready(const Plan& P);
 void launch_bin_rl(const Plan& P, cudaStream_t st, Gate g);

@@ -120,31 +120,6 @@ __global__ void __launch_bounds__(kBlock) k_rl_rescan(const RunRec* __restrict__
 // Compensated sums throughout: the run sums C, S are exact double-float pairs,
 // the baselines come split (xdf), the map as (map_hi, map_lo).
 
-// acc += w_kind-run sums * z: I n z, q (C z, S z), u (-S z, C z)
-template <int NC>
-__device__ __forceinline__ void run_bin_ds(int kind, float n, df C, df S, df z, dsum (&acc)[NC]) {
-  using F = Frame<NC>;
-  if (kind == DS_KIND_I) {
-    if constexpr (F::I >= 0) ds_add_prod(acc[F::I], z, n);
-  } else if (kind == DS_KIND_Q) {
-    if constexpr (F::Q >= 0) {
-      ds_add_prod(acc[F::Q], z, C);
-      ds_add_prod(acc[F::U], z, S);
-    }
-  } else if (kind == DS_KIND_U) {
-    if constexpr (F::Q >= 0) {
-      ds_add_prod(acc[F::Q], z, df_neg(S));
-      ds_add_prod(acc[F::U], z, C);
-    }
-  } else {
-    if constexpr (F::I >= 0 && F::Q >= 0) {
-      ds_add_prod(acc[F::I], z, n);
-      ds_add_prod(acc[F::Q], z, C);
-      ds_add_prod(acc[F::U], z, S);
-    }
-  }
-}
-
 // acc -= (w_kind-run sums) . m
 template <int NC>
 __device__ __forceinline__ void run_sub_dot_ds(int kind, float n, df C, df S, const df (&m)[NC],
@@ -283,6 +258,10 @@ __global__ void __launch_bounds__(kBlock) k_rl_rescan_df(const RunRec* __restric
 bool rl_ready(const Plan& P) { return P.layout == 2 && P.rl_rec != nullptr && P.x32 != nullptr; }
 
 void launch_bin_rl(const Plan& P, cudaStream_t st, Gate g) {
+  if (pm_ready(P)) {
+    launch_bin_pm(P, st, g);
+    return;
+  }
   const int grid = stream_grid(P, P.rl_n, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
@@ -309,6 +288,10 @@ bool rl_df_ready(const Plan& P) { return P.layout == 2 && P.rl_df != nullptr && 
 
 // x must have been split into P.xdf (launch_split_df)
 void launch_bin_rl_df(const Plan& P, cudaStream_t st, Gate g) {
+  if (pm_ready(P)) {
+    launch_bin_pm_df(P, st, g);
+    return;
+  }
   const int grid = stream_grid(P, P.rl_n, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;

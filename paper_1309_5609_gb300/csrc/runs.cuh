@@ -3,6 +3,7 @@
 // enters every row of Sect. 3 through (n, C, S).
 #pragma once
 
+#include "df.cuh"
 #include "internal.cuh"
 #include "rows.cuh"
 
@@ -53,6 +54,31 @@ __device__ __forceinline__ float run_dot(int kind, float n, float C, float S, co
 __device__ __forceinline__ RunRec load_run(const RunRec* __restrict__ rec, int64_t i) {
   const int4 v = __ldcs(reinterpret_cast<const int4*>(rec) + i);
   return RunRec{v.x, __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w)};
+}
+
+// acc += w_kind-run sums * z: I n z, q (C z, S z), u (-S z, C z)
+template <int NC>
+__device__ __forceinline__ void run_bin_ds(int kind, float n, df C, df S, df z, dsum (&acc)[NC]) {
+  using F = Frame<NC>;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) ds_add_prod(acc[F::I], z, n);
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) {
+      ds_add_prod(acc[F::Q], z, C);
+      ds_add_prod(acc[F::U], z, S);
+    }
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) {
+      ds_add_prod(acc[F::Q], z, df_neg(S));
+      ds_add_prod(acc[F::U], z, C);
+    }
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0) {
+      ds_add_prod(acc[F::I], z, n);
+      ds_add_prod(acc[F::Q], z, C);
+      ds_add_prod(acc[F::U], z, S);
+    }
+  }
 }
 
 }  // namespace ds

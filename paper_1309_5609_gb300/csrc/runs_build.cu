@@ -257,6 +257,96 @@ __global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ 
   }
 }
 
+// ---- pixel-major copy of the records (runs_pm.cu bins from it) ------------------
+
+// Runs per pixel (cnt zeroed by the caller).
+__global__ void __launch_bounds__(kBlock) k_pm_hist(const RunRec* __restrict__ rec, int64_t n_runs,
+                                                    uint32_t* __restrict__ cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_runs; i += stride)
+    atomicAdd(cnt + __ldcs(reinterpret_cast<const int*>(rec + i)), 1u);
+}
+
+__device__ __forceinline__ int64_t block_sum(int64_t v, int64_t* sh) {
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  if (lane == 0) sh[wq] = v;
+  __syncthreads();
+  int64_t t = 0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+  __syncthreads();
+  return t;
+}
+
+// blk[j] = sum of cnt over block j's S consecutive pixels.
+__global__ void __launch_bounds__(kBlock) k_pm_scan_up(const uint32_t* __restrict__ cnt, int64_t n,
+                                                       int64_t S, int64_t* __restrict__ blk) {
+  __shared__ int64_t sh[kBlock / 32];
+  const int64_t lo = (int64_t)blockIdx.x * S, hi = lo + S < n ? lo + S : n;
+  int64_t v = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += cnt[i];
+  const int64_t t = block_sum(v, sh);
+  if (threadIdx.x == 0) blk[blockIdx.x] = t;
+}
+
+// off[p] = first run of pixel p: block j's offset (blk, made exclusive by k_rl_scan)
+// plus the prefix within the block, in tiles of blockDim pixels; cnt becomes the
+// scatter cursor (= off).  off[n] = the total.
+__global__ void __launch_bounds__(kBlock) k_pm_scan_down(uint32_t* __restrict__ cnt, int64_t n,
+                                                         int64_t S, const int64_t* __restrict__ blk,
+                                                         const int64_t* __restrict__ total,
+                                                         uint32_t* __restrict__ off) {
+  __shared__ int64_t wsum[kBlock / 32];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t lo = (int64_t)blockIdx.x * S, hi = lo + S < n ? lo + S : n;
+  int64_t carry = blk[blockIdx.x];
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < hi ? cnt[i] : 0;
+    int64_t inc = v;  // inclusive scan within the warp
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t u = __shfl_up_sync(full, inc, d);
+      if (lane >= d) inc += u;
+    }
+    if (lane == 31) wsum[wq] = inc;
+    __syncthreads();
+    int64_t before = 0, tile = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      if (q < wq) before += wsum[q];
+      tile += wsum[q];
+    }
+    if (i < hi) {
+      const uint32_t o = (uint32_t)(carry + before + inc - v);
+      off[i] = o;
+      cnt[i] = o;
+    }
+    carry += tile;
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) off[n] = (uint32_t)*total;
+}
+
+// Each run to its pixel's next slot: (count, sum cos, sum sin, baseline bits) and
+// the double-float sums.  The order of the runs within a pixel is arbitrary.
+__global__ void __launch_bounds__(kBlock) k_pm_scatter(const RunRec* __restrict__ rec,
+                                                       const int32_t* __restrict__ rb,
+                                                       const float4* __restrict__ rdf,
+                                                       int64_t n_runs, uint32_t* __restrict__ cursor,
+                                                       float4* __restrict__ pm_rec,
+                                                       float4* __restrict__ pm_df) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_runs; i += stride) {
+    const int4 r = __ldcs(reinterpret_cast<const int4*>(rec) + i);
+    const int b = __ldcs(rb + i);
+    const float4 cs = __ldcs(rdf + i);
+    const uint32_t slot = atomicAdd(cursor + r.x, 1u);
+    pm_rec[slot] = make_float4(__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w),
+                               __int_as_float(b));
+    pm_df[slot] = cs;
+  }
+}
+
 }  // namespace
 
 // Run records are built in two steps around the plan's synchronisation: the
@@ -303,10 +393,41 @@ ds_status rl_fill(Plan& P, int64_t n_runs) {
   DS_CUDA_TRY(cudaGetLastError());
   cudaFreeAsync(P.rl_tiles, P.stream);
   P.rl_tiles = nullptr;
-  return DS_OK;
+  return pm_build(P);
 }
 
 // On request after the plan exists (synchronises once).
+// The pixel-major copy of the records: runs per pixel, their prefix, a scatter
+// with one atomic cursor per pixel.  Stream-ordered; no host synchronisation.
+ds_status pm_build(Plan& P) {
+  if (P.rl_rec == nullptr || P.rl_n <= 0 || P.rl_n >= (int64_t)UINT32_MAX) return DS_OK;
+  const int64_t npix = P.npix;
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_off), sizeof(uint32_t) * (npix + 1), true));
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_rec), sizeof(float4) * P.rl_n, true));
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_df), sizeof(float4) * P.rl_n, true));
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.x4), sizeof(float4) * P.n_b, true));
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.xd4), sizeof(float4) * 2 * P.n_b, true));
+  const int64_t g = stream_grid(P, npix, kBlock, 8);
+  const int64_t S = (npix + g - 1) / g, G = (npix + S - 1) / S;
+  uint32_t* cnt = nullptr;
+  int64_t* blk = nullptr;
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false));
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * (G + 1), false));
+  cudaStream_t st = P.stream;
+  DS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st));
+  const int rgrid = stream_grid(P, P.rl_n, kBlock, 8);
+  k_pm_hist<<<rgrid, kBlock, 0, st>>>(P.rl_rec, P.rl_n, cnt);
+  k_pm_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk);
+  k_rl_scan<<<1, kScanThreads, 0, st>>>(blk, G, blk + G);
+  k_pm_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk, blk + G, P.pm_off);
+  k_pm_scatter<<<rgrid, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.rl_df, P.rl_n, cnt, P.pm_rec, P.pm_df);
+  P.launches += 5;
+  DS_CUDA_TRY(cudaGetLastError());
+  cudaFreeAsync(cnt, st);
+  cudaFreeAsync(blk, st);
+  return DS_OK;
+}
+
 ds_status rl_build(Plan& P) {
   int64_t* total = nullptr;
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&total), sizeof(int64_t), false));

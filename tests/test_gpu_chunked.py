@@ -100,18 +100,48 @@ def test_time_ordered_operator_variants(case, tune):
     check_apply(prob, None, layout=0, tune=tune)
 
 
+@pytest.mark.parametrize("bin_order", [0, 1], ids=["time_order", "pixel_major"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_run_length_operator_parity(case):
+def test_run_length_operator_parity(case, bin_order):
     kinds, nside, n_t, L, ff, scan = case
     prob = make_problem(n_t, nside, kinds, baseline_len=L, seed=23, scan=scan, flag_frac=ff,
                         flag_mean_len=200, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
-    check_apply(prob, None, layout=2)
+    check_apply(prob, None, layout=2, tune={"bin_order": bin_order})
 
 
+@pytest.mark.parametrize("bin_order", [0, 1], ids=["time_order", "pixel_major"])
 @pytest.mark.parametrize("kinds", [("q", "u"), ("iqu",), ("I",)])
-def test_run_length_operator_with_distinct_pixels(kinds):
+def test_run_length_operator_with_distinct_pixels(kinds, bin_order):
     # every run is a single sample
-    check_apply(random_pixel_problem(50_003, 128, kinds, 7, seed=4), None, layout=2)
+    check_apply(random_pixel_problem(50_003, 128, kinds, 7, seed=4), None, layout=2,
+                tune={"bin_order": bin_order})
+
+
+def test_pixel_major_binning_matches_time_order_and_reports_itself():
+    # the two binning orders of the run records give the same operator (float32
+    # summation order aside) and the same accurate solve; the plan reports the order
+    prob = make_problem(300_000, 32, ("I", "q", "u"), baseline_len=250, seed=8, flag_frac=0.01,
+                        flag_mean_len=300, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
+    gp = prob.to(DEV)
+    out = {}
+    for order in (0, 1):
+        plan = ds.destripe_plan(gp.pix, gp.c32, gp.s32, gp.valid, nside=prob.nside,
+                                kinds=prob.kinds, baseline_len=prob.baseline_len, precision="mixed")
+        ds.destripe_tune(plan, "layout", 2)
+        ds.destripe_tune(plan, "bin_order", order)
+        assert ds.destripe_plan_info(plan)["bin_order"] == order
+        x = torch.from_numpy(np.random.default_rng(3).standard_normal(plan.n_u)).to(DEV)
+        Ax = torch.empty(plan.n_u, dtype=torch.float64, device=DEV)
+        ds.destripe_apply_A(plan, x, Ax)
+        a = torch.zeros(plan.n_u, dtype=torch.float64, device=DEV)
+        st, it, rel = ds.destripe_solve(plan, gp.y.float().contiguous(), a, tol=1e-10)
+        assert st == ds.DS_OK, (order, st, it, rel)
+        out[order] = (Ax.cpu().numpy(), a.cpu().numpy())
+        with pytest.raises(ds.DestripeError):
+            ds.destripe_tune(plan, "bin_order", 2)
+        plan.close()
+    assert rel_err(out[1][0], out[0][0]) < 1e-6
+    assert np.abs(out[1][1] - out[0][1]).max() < 1e-5 * max(1.0, np.abs(out[0][1]).max())
 
 
 def test_run_length_solve_matches_oracle():
