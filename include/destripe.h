@@ -103,7 +103,8 @@ typedef struct {
   int32_t n_comp;        /* 1, 2 or 3 */
   int64_t device_bytes;  /* bytes the plan holds on the device */
   int32_t layout;        /* form of the float32 operator in use (tune key "layout") */
-  int32_t bin_order;     /* run-length operator: 1 = binning over the pixel-major copy */
+  int32_t bin_order;     /* run-length operator: 1 = binning over the pixel-major copy
+                            (built by the first solve or operator application) */
   int64_t n_runs;        /* run-length records held (0 if none) */
 } ds_info;
 
@@ -247,10 +248,11 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *   "samples_per_thread"  MIXED plans: 4 (default) or 8 consecutive samples per thread in
  *                     the float32 operator (8: two 16-byte loads per stream per thread)
  *   "bin_order"       MIXED plans with run-length records: 1 = the binning passes read a
- *                     pixel-major copy of the records (built with them: 32 more bytes per
- *                     run) with one warp per pixel and one plain store of its sums, no
+ *                     pixel-major copy of the records (24 more bytes per run, built on the
+ *                     plan's stream by the first destripe_solve or destripe_apply_A, or
+ *                     here) with one warp per pixel and one plain store of its sums, no
  *                     atomic updates (default); 0 = they read the records in time order
- *                     with one reduction per run.  Setting 1 builds the copy if missing.
+ *                     with one reduction per run.
  *   "rescan_rounds"   MIXED plans: rounds of 32 work items (runs, or 4-sample groups)
  *                     per warp chunk in the rescans that keep per-lane baseline sums
  *                     across rounds and flush them across the warp only where a baseline

@@ -105,7 +105,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->pm_off, P->pm_rec, P->pm_df, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a
@@ -376,7 +376,7 @@ ds_status destripe_plan_info(ds_plan_t plan, ds_info* info) {
   info->n_comp = P.n_c;
   info->device_bytes = P.device_bytes;
   info->layout = P.layout;
-  info->bin_order = (P.layout == 2 && pm_ready(P)) ? 1 : 0;
+  info->bin_order = (P.layout == 2 && P.bin_order == 1 && P.rl_rec != nullptr) ? 1 : 0;
   info->n_runs = P.rl_rec != nullptr ? P.rl_n : 0;
   return DS_OK;
 }
@@ -392,6 +392,8 @@ ds_status destripe_apply_A(ds_plan_t plan, const double* d_x, double* d_Ax) {
   if (plan == nullptr || d_x == nullptr || d_Ax == nullptr || d_x == d_Ax) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
   clear_stale_error();
+  const ds_status sp = pm_ensure(P);
+  if (sp != DS_OK) return sp;
   DS_CUDA_TRY(cudaMemsetAsync(d_Ax, 0, sizeof(double) * P.n_u, P.stream));
   enqueue_apply(P, P.stream, P.desc.precision == DS_PREC_FP64, d_x, d_Ax, Gate{nullptr, nullptr});
   P.launches += 3;
@@ -449,6 +451,8 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   Plan& P = *reinterpret_cast<Plan*>(plan);
   if (max_iter <= 0) max_iter = 10000;
   clear_stale_error();
+  const ds_status sp = pm_ensure(P);
+  if (sp != DS_OK) return sp;
   cudaStream_t st = P.stream;
   if (warm_start)
     DS_CUDA_TRY(cudaMemcpyAsync(P.x, d_a, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));

@@ -199,7 +199,7 @@ struct Plan {
   // pm_off[p] .. pm_off[p + 1] - 1, in no particular order
   uint32_t* pm_off;         // [n_pix + 1]
   float4* pm_rec;           // per run: (count, sum cos, sum sin, baseline as int bits)
-  float4* pm_df;            // per run: the double-float sums, as rl_df
+  float2* pm_lo;            // per run: low parts of the double-float sums (the record holds the high)
   float4* x4;               // [n_b] float32 baselines of every output, per baseline
   float4* xd4;              // [2][n_b] split baselines: hi parts, then lo parts
   int bin_order;            // run-length plans: 1 = bin pixel-major (default), 0 = in time order
@@ -214,6 +214,8 @@ ds_status rl_count(Plan& P, int64_t* d_total);
 ds_status rl_fill(Plan& P, int64_t n_runs);
 ds_status rl_build(Plan& P);
 ds_status pm_build(Plan& P);
+// builds the pixel-major copy before its first use if the plan bins from it
+ds_status pm_ensure(Plan& P);
 // runs_pm.cu: the binning pass over the pixel-major copy (one warp per pixel, no atomics)
 bool pm_ready(const Plan& P);
 void launch_bin_pm(const Plan& P, cudaStream_t st, Gate g);

@@ -328,13 +328,14 @@ __global__ void __launch_bounds__(kBlock) k_pm_scan_down(uint32_t* __restrict__ 
 }
 
 // Each run to its pixel's next slot: (count, sum cos, sum sin, baseline bits) and
-// the double-float sums.  The order of the runs within a pixel is arbitrary.
+// the low parts of the double-float sums (the record's sums are their high
+// parts).  The order of the runs within a pixel is arbitrary.
 __global__ void __launch_bounds__(kBlock) k_pm_scatter(const RunRec* __restrict__ rec,
                                                        const int32_t* __restrict__ rb,
                                                        const float4* __restrict__ rdf,
                                                        int64_t n_runs, uint32_t* __restrict__ cursor,
                                                        float4* __restrict__ pm_rec,
-                                                       float4* __restrict__ pm_df) {
+                                                       float2* __restrict__ pm_lo) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_runs; i += stride) {
     const int4 r = __ldcs(reinterpret_cast<const int4*>(rec) + i);
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(kBlock) k_pm_scatter(const RunRec* __restrict_
     const uint32_t slot = atomicAdd(cursor + r.x, 1u);
     pm_rec[slot] = make_float4(__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w),
                                __int_as_float(b));
-    pm_df[slot] = cs;
+    pm_lo[slot] = make_float2(cs.y, cs.w);
   }
 }
 
@@ -393,18 +394,20 @@ ds_status rl_fill(Plan& P, int64_t n_runs) {
   DS_CUDA_TRY(cudaGetLastError());
   cudaFreeAsync(P.rl_tiles, P.stream);
   P.rl_tiles = nullptr;
-  return pm_build(P);
+  return DS_OK;
 }
 
 // On request after the plan exists (synchronises once).
 // The pixel-major copy of the records: runs per pixel, their prefix, a scatter
 // with one atomic cursor per pixel.  Stream-ordered; no host synchronisation.
+// Built on first use by a single-problem solve or operator application (batched
+// problems bin with their own kernels and never need it).
 ds_status pm_build(Plan& P) {
   if (P.rl_rec == nullptr || P.rl_n <= 0 || P.rl_n >= (int64_t)UINT32_MAX) return DS_OK;
   const int64_t npix = P.npix;
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_off), sizeof(uint32_t) * (npix + 1), true));
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_rec), sizeof(float4) * P.rl_n, true));
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_df), sizeof(float4) * P.rl_n, true));
+  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_lo), sizeof(float2) * P.rl_n, true));
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.x4), sizeof(float4) * P.n_b, true));
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.xd4), sizeof(float4) * 2 * P.n_b, true));
   const int64_t g = stream_grid(P, npix, kBlock, 8);
@@ -420,12 +423,17 @@ ds_status pm_build(Plan& P) {
   k_pm_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk);
   k_rl_scan<<<1, kScanThreads, 0, st>>>(blk, G, blk + G);
   k_pm_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk, blk + G, P.pm_off);
-  k_pm_scatter<<<rgrid, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.rl_df, P.rl_n, cnt, P.pm_rec, P.pm_df);
+  k_pm_scatter<<<rgrid, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.rl_df, P.rl_n, cnt, P.pm_rec, P.pm_lo);
   P.launches += 5;
   DS_CUDA_TRY(cudaGetLastError());
   cudaFreeAsync(cnt, st);
   cudaFreeAsync(blk, st);
   return DS_OK;
+}
+
+ds_status pm_ensure(Plan& P) {
+  if (P.layout != 2 || P.bin_order != 1 || P.pm_rec != nullptr || P.rl_rec == nullptr) return DS_OK;
+  return pm_build(P);
 }
 
 ds_status rl_build(Plan& P) {

@@ -103,12 +103,13 @@ __global__ void __launch_bounds__(kBlock) k_pm_bin(const uint32_t* __restrict__ 
   }
 }
 
-// The accurate variant: double-float run sums and baselines, compensated sums
-// (renormalised every step), float64 pixel sums.
+// The accurate variant: double-float run sums (high parts from the record, low
+// parts beside it) and baselines, compensated sums (renormalised every step),
+// float64 pixel sums.
 template <int KS>
 __global__ void __launch_bounds__(kBlock) k_pm_bin_df(const uint32_t* __restrict__ off,
                                                       const float4* __restrict__ rec,
-                                                      const float4* __restrict__ rdf,
+                                                      const float2* __restrict__ lo,
                                                       const float4* __restrict__ xd4,
                                                       double* __restrict__ bins, int64_t npix,
                                                       int64_t n_b, KindsArg kk, Gate g) {
@@ -127,13 +128,13 @@ __global__ void __launch_bounds__(kBlock) k_pm_bin_df(const uint32_t* __restrict
     for (int j = 0; j < NC; ++j) acc[j] = ds_zero();
     for (uint32_t i = beg + lane; i < end; i += 32) {
       const float4 r = __ldcs(rec + i);
-      const float4 cs = __ldcs(rdf + i);
+      const float2 l = __ldcs(lo + i);
       const int b = __float_as_int(r.w);
       const float4 zh = __ldg(xd4 + b), zl = __ldg(xd4 + n_b + b);
 #pragma unroll
       for (int o = 0; o < NO; ++o)
         if (o < n_o)
-          run_bin_ds<NC>(K::kind(o, kk), r.x, df{cs.x, cs.y}, df{cs.z, cs.w},
+          run_bin_ds<NC>(K::kind(o, kk), r.x, df{r.y, l.x}, df{r.z, l.y},
                          df{f4_at(zh, o), f4_at(zl, o)}, acc);
 #pragma unroll
       for (int j = 0; j < NC; ++j) ds_norm(acc[j]);
@@ -176,7 +177,7 @@ void launch_bin_pm_df(const Plan& P, cudaStream_t st, Gate g) {
   const int grid = stream_grid(P, P.npix * 32, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_pm_bin_df<KS><<<grid, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pm_df, P.xd4, P.bins, P.npix,
+    k_pm_bin_df<KS><<<grid, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pm_lo, P.xd4, P.bins, P.npix,
                                              P.n_b, P.kinds, g);
   });
 }

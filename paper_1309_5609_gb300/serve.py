@@ -70,7 +70,7 @@ def device_bytes(n_t: int, n_o: int, nside: int, baseline_len: int) -> int:
     n_u = n_o * n_b
     arrays = n_t * (4 + 4 + 4 + 4 * n_o)          # pix, cos, sin, y (float32)
     per_pixel = 4 + 1 + 8 * 6 + 8 * 4 * 2 + 4 * 4 * 3 + 4   # hits, mask, M^-1, sums, maps, runs
-    runs = int(0.6 * (36 + 32) * n_t)              # run records, time- and pixel-major (<= 0.6/sample)
+    runs = int(0.6 * (36 + 24) * n_t)              # run records, time- and pixel-major (<= 0.6/sample)
     plan = (n_t * 4 + npix * per_pixel + n_u * (8 * 7 + 8 + 4) + n_b * (4 + 48) + runs
             + (n_t // 512 + 1) * 8 + (1 << 16))  # per-baseline counts and packed baselines, scalars
     return int(arrays + plan)
