@@ -403,19 +403,35 @@ ds_status rl_fill(Plan& P, int64_t n_runs) {
 // Built on first use by a single-problem solve or operator application (batched
 // problems bin with their own kernels and never need it).
 ds_status pm_build(Plan& P) {
-  if (P.rl_rec == nullptr || P.rl_n <= 0 || P.rl_n >= (int64_t)UINT32_MAX) return DS_OK;
+  // run offsets are 32-bit, with room for the binning loop's stride past the end
+  if (P.rl_rec == nullptr || P.rl_n <= 0 || P.rl_n > (int64_t)UINT32_MAX - 256) return DS_OK;
   const int64_t npix = P.npix;
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_off), sizeof(uint32_t) * (npix + 1), true));
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_rec), sizeof(float4) * P.rl_n, true));
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.pm_lo), sizeof(float2) * P.rl_n, true));
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.x4), sizeof(float4) * P.n_b, true));
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.xd4), sizeof(float4) * 2 * P.n_b, true));
   const int64_t g = stream_grid(P, npix, kBlock, 8);
   const int64_t S = (npix + g - 1) / g, G = (npix + S - 1) / S;
-  uint32_t* cnt = nullptr;
-  int64_t* blk = nullptr;
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false));
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * (G + 1), false));
+  uint32_t* cnt = nullptr;  // runs per pixel, then the scatter cursor (scratch)
+  int64_t* blk = nullptr;   // block totals and the total (scratch)
+  const int64_t held_before = P.device_bytes;
+  cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(&P.pm_off), sizeof(uint32_t) * (npix + 1), true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pm_rec), sizeof(float4) * P.rl_n, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pm_lo), sizeof(float2) * P.rl_n, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.x4), sizeof(float4) * P.n_b, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.xd4), sizeof(float4) * 2 * P.n_b, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * (G + 1), false);
+  if (e != cudaSuccess) {
+    // give back what was taken: without the copy the binning reads the runs in time order
+    void** held[] = {reinterpret_cast<void**>(&P.pm_off), reinterpret_cast<void**>(&P.pm_rec),
+                     reinterpret_cast<void**>(&P.pm_lo), reinterpret_cast<void**>(&P.x4),
+                     reinterpret_cast<void**>(&P.xd4), reinterpret_cast<void**>(&cnt),
+                     reinterpret_cast<void**>(&blk)};
+    for (void** h : held)
+      if (*h != nullptr) {
+        cudaFreeAsync(*h, P.stream);
+        *h = nullptr;
+      }
+    P.device_bytes = held_before;
+    return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
+  }
   cudaStream_t st = P.stream;
   DS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st));
   const int rgrid = stream_grid(P, P.rl_n, kBlock, 8);
@@ -433,7 +449,13 @@ ds_status pm_build(Plan& P) {
 
 ds_status pm_ensure(Plan& P) {
   if (P.layout != 2 || P.bin_order != 1 || P.pm_rec != nullptr || P.rl_rec == nullptr) return DS_OK;
-  return pm_build(P);
+  const ds_status s = pm_build(P);
+  if (s == DS_ENOMEM) {  // no room for the copy: bin the runs in time order instead
+    cudaGetLastError();
+    P.bin_order = 0;
+    return DS_OK;
+  }
+  return s;
 }
 
 ds_status rl_build(Plan& P) {
