@@ -229,3 +229,33 @@ def test_tune_rejects_bad_chunks():
         ds.destripe_tune(p64, "layout", 1)
     assert e.value.status == ds.DS_ESTATE
     p64.close()
+
+
+def runs_per_pixel_problem(counts, nside, kinds, L, seed):
+    """Pixel i of `counts` gets exactly counts[i] runs (2-4 samples each, random angles),
+    interleaved round-robin with a filler pixel so that no two runs merge."""
+    rng = np.random.default_rng(seed)
+    npix = 12 * nside * nside
+    pixels = rng.choice(npix - 1, size=len(counts), replace=False)
+    filler = npix - 1
+    seq = []
+    for r in range(max(counts)):
+        for p, k in zip(pixels, counts):
+            if r < k:
+                seq += [int(p)] * int(rng.integers(2, 5))
+                seq += [filler] * int(rng.integers(1, 3))
+    pix = torch.tensor(seq, dtype=torch.int32)
+    n_t = pix.numel()
+    psi = torch.from_numpy(rng.uniform(0, np.pi, n_t))
+    y = torch.from_numpy(rng.standard_normal((len(kinds), n_t)))
+    sky = torch.zeros((3, npix), dtype=torch.float64)
+    return Problem(n_t, nside, tuple(kinds), L, pix, torch.cos(2 * psi).float(),
+                   torch.sin(2 * psi).float(), y, sky)
+
+
+@pytest.mark.parametrize("kinds", [("q", "u"), ("I", "q", "u")])
+def test_pixel_major_binning_at_warp_step_boundaries(kinds):
+    # the pixel-major binning walks a pixel's runs 64 at a time (two per lane):
+    # pixels with 1, 31-33, 63-65 and 200 runs
+    prob = runs_per_pixel_problem([1, 31, 32, 33, 63, 64, 65, 200], 8, kinds, 997, seed=12)
+    check_apply(prob, None, layout=2, tune={"bin_order": 1})
