@@ -122,3 +122,38 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_batch_tune_profile_and_host_entry_points_reject_null_before_device_work(lib):
+    # every entry point checks its handles and pointers before touching the device
+    out = ctypes.c_void_p()
+    assert lib.destripe_batch_create(0, None, ctypes.byref(out)) == ds.DS_EINVAL
+    assert lib.destripe_batch_create(4097, None, ctypes.byref(out)) == ds.DS_EINVAL
+    assert lib.destripe_batch_create(8, None, None) == ds.DS_EINVAL
+    slot = ctypes.c_int32()
+    n = ctypes.c_int32()
+    assert lib.destripe_batch_add(None, None, None, None, 1e-10, 0, ctypes.byref(slot)) == ds.DS_EINVAL
+    assert lib.destripe_batch_step(None, 1, ctypes.byref(n)) == ds.DS_EINVAL
+    assert lib.destripe_batch_slot_status(None, 0, None, None, None) == ds.DS_EINVAL
+    assert lib.destripe_batch_retire(None, 0, None, None, None) == ds.DS_EINVAL
+    assert lib.destripe_batch_tune(None, b"tile_samples", 8192.0) == ds.DS_EINVAL
+    assert lib.destripe_batch_autotune(None, 4, None) == ds.DS_EINVAL
+    assert lib.destripe_batch_info(None, None, None) == ds.DS_EINVAL
+    lib.destripe_batch_destroy(None)
+    assert lib.destripe_tune(None, b"bin_order", 1.0) == ds.DS_EINVAL
+    assert lib.destripe_tune(None, b"rescan_rounds", 4.0) == ds.DS_EINVAL
+    assert lib.destripe_profile(None, 1, None) == ds.DS_EINVAL
+    d = _desc()
+    it = ctypes.c_int32()
+    rel = ctypes.c_double()
+    assert lib.destripe_run_host(ctypes.byref(d), None, None, None, None, None, 1e-10, 10,
+                                 None, None, None, None, ctypes.byref(it),
+                                 ctypes.byref(rel)) == ds.DS_EINVAL
+    bad = _desc(n_t=0)
+    ok = ctypes.c_void_p(256)
+    assert lib.destripe_run_host(ctypes.byref(bad), ok, ok, ok, None, ok, 1e-10, 10,
+                                 None, None, None, None, ctypes.byref(it),
+                                 ctypes.byref(rel)) == ds.DS_EINVAL
+    assert lib.destripe_bin_noalloc(None, ok, ok, ok, None, ok, ok, None, None) == ds.DS_EINVAL
+    assert lib.destripe_bin_noalloc(ctypes.byref(bad), ok, ok, ok, None, ok, ok, None,
+                                    None) == ds.DS_EINVAL
