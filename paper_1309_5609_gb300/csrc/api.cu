@@ -77,12 +77,16 @@ cudaError_t plan_pool(int device, cudaMemPool_t* out) {
 
 }  // namespace
 
-cudaError_t ds::plan_alloc(Plan& P, void** ptr, size_t bytes, bool count) {
+cudaError_t ds::plan_alloc_on(Plan& P, cudaStream_t st, void** ptr, size_t bytes, bool count) {
   if (count) P.device_bytes += (int64_t)bytes;
   cudaMemPool_t pool = nullptr;
   const cudaError_t e = plan_pool(P.device, &pool);
   if (e != cudaSuccess) return e;
-  return cudaMallocFromPoolAsync(ptr, bytes, pool, P.stream);
+  return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
+
+cudaError_t ds::plan_alloc(Plan& P, void** ptr, size_t bytes, bool count) {
+  return plan_alloc_on(P, P.stream, ptr, bytes, count);
 }
 
 namespace {
@@ -99,6 +103,7 @@ cudaError_t dalloc(Plan& P, T** ptr, int64_t count) {
 
 void plan_free(Plan* P) {
   if (P == nullptr) return;
+  if (P->side_stream) cudaStreamSynchronize(P->side_stream);  // a copy still being built
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
   if (P->graph_exec_acc) cudaGraphExecDestroy(P->graph_exec_acc);
   if (P->ev) {
@@ -116,6 +121,9 @@ void plan_free(Plan* P) {
   if (P->h_err) cudaFreeHost(P->h_err);
   if (P->h_scal) cudaFreeHost(P->h_scal);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  if (P->side_stream) cudaStreamDestroy(P->side_stream);
+  for (cudaEvent_t e : P->side_ev)
+    if (e) cudaEventDestroy(e);
   delete P;
 }
 
@@ -451,16 +459,20 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   Plan& P = *reinterpret_cast<Plan*>(plan);
   if (max_iter <= 0) max_iter = 10000;
   clear_stale_error();
-  const ds_status sp = pm_ensure(P);
-  if (sp != DS_OK) return sp;
   cudaStream_t st = P.stream;
   if (warm_start)
     DS_CUDA_TRY(cudaMemcpyAsync(P.x, d_a, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
   DS_CUDA_TRY(cudaMemsetAsync(P.b, 0, sizeof(double) * P.n_u, st));
+  // a first solve builds the pixel-major copy beside its right-hand side
+  bool pm_started = false;
+  const ds_status sp = pm_begin(P, &pm_started);
+  if (sp != DS_OK) return sp;
   enqueue_rhs(P, st, d_y, P.b, Gate{nullptr, nullptr});
   enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, warm_start ? 1 : 0);
   P.launches += 3 + 3 + (warm_start ? 3 : 0);
-  ds_status s = launch_status();
+  ds_status s = pm_join(P, pm_started);
+  if (s != DS_OK) return s;
+  s = launch_status();
   if (s != DS_OK) return s;
   s = build_graph(P);
   if (s != DS_OK) return s;
@@ -605,7 +617,7 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
     if (P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
     if (value == 1.0 && P.pm_rec == nullptr && P.rl_rec != nullptr) {
       clear_stale_error();
-      ds_status s = pm_build(P);
+      ds_status s = pm_build(P, P.stream);
       if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
       if (s != DS_OK) return s;
     }

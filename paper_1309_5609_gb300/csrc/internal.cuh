@@ -203,19 +203,28 @@ struct Plan {
   float4* x4;               // [n_b] float32 baselines of every output, per baseline
   float4* xd4;              // [2][n_b] split baselines: hi parts, then lo parts
   int bin_order;            // run-length plans: 1 = bin pixel-major (default), 0 = in time order
+  cudaStream_t side_stream; // builds the pixel-major copy beside the first right-hand side
+  cudaEvent_t side_ev[2];   // records ready (plan stream) / copy built (side stream)
 };
 
 // api.cu: device memory of a plan from the library's stream-ordered pool;
 // counted in device_bytes when count is set
 cudaError_t plan_alloc(Plan& P, void** ptr, size_t bytes, bool count);
+// the same, ordered on another stream of the plan
+cudaError_t plan_alloc_on(Plan& P, cudaStream_t st, void** ptr, size_t bytes, bool count);
 
 // runs.cu
 ds_status rl_count(Plan& P, int64_t* d_total);
 ds_status rl_fill(Plan& P, int64_t n_runs);
 ds_status rl_build(Plan& P);
-ds_status pm_build(Plan& P);
-// builds the pixel-major copy before its first use if the plan bins from it
+ds_status pm_build(Plan& P, cudaStream_t st);
+// builds the pixel-major copy on the plan's stream before its first use if the
+// plan bins from it
 ds_status pm_ensure(Plan& P);
+// the same on the plan's side stream, overlapping what the plan's stream does
+// next; pm_join makes the plan's stream wait for it
+ds_status pm_begin(Plan& P, bool* started);
+ds_status pm_join(Plan& P, bool started);
 // runs_pm.cu: the binning pass over the pixel-major copy (one warp per pixel, no atomics)
 bool pm_ready(const Plan& P);
 void launch_bin_pm(const Plan& P, cudaStream_t st, Gate g);

@@ -402,7 +402,7 @@ ds_status rl_fill(Plan& P, int64_t n_runs) {
 // with one atomic cursor per pixel.  Stream-ordered; no host synchronisation.
 // Built on first use by a single-problem solve or operator application (batched
 // problems bin with their own kernels and never need it).
-ds_status pm_build(Plan& P) {
+ds_status pm_build(Plan& P, cudaStream_t st) {
   // run offsets are 32-bit, with room for the binning loop's stride past the end
   if (P.rl_rec == nullptr || P.rl_n <= 0 || P.rl_n > (int64_t)UINT32_MAX - 256) return DS_OK;
   const int64_t npix = P.npix;
@@ -411,13 +411,13 @@ ds_status pm_build(Plan& P) {
   uint32_t* cnt = nullptr;  // runs per pixel, then the scatter cursor (scratch)
   int64_t* blk = nullptr;   // block totals and the total (scratch)
   const int64_t held_before = P.device_bytes;
-  cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(&P.pm_off), sizeof(uint32_t) * (npix + 1), true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pm_rec), sizeof(float4) * P.rl_n, true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pm_lo), sizeof(float2) * P.rl_n, true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.x4), sizeof(float4) * P.n_b, true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.xd4), sizeof(float4) * 2 * P.n_b, true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * (G + 1), false);
+  cudaError_t e = plan_alloc_on(P, st, reinterpret_cast<void**>(&P.pm_off), sizeof(uint32_t) * (npix + 1), true);
+  if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&P.pm_rec), sizeof(float4) * P.rl_n, true);
+  if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&P.pm_lo), sizeof(float2) * P.rl_n, true);
+  if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&P.x4), sizeof(float4) * P.n_b, true);
+  if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&P.xd4), sizeof(float4) * 2 * P.n_b, true);
+  if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false);
+  if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&blk), sizeof(int64_t) * (G + 1), false);
   if (e != cudaSuccess) {
     // give back what was taken: without the copy the binning reads the runs in time order
     void** held[] = {reinterpret_cast<void**>(&P.pm_off), reinterpret_cast<void**>(&P.pm_rec),
@@ -426,13 +426,12 @@ ds_status pm_build(Plan& P) {
                      reinterpret_cast<void**>(&blk)};
     for (void** h : held)
       if (*h != nullptr) {
-        cudaFreeAsync(*h, P.stream);
+        cudaFreeAsync(*h, st);
         *h = nullptr;
       }
     P.device_bytes = held_before;
     return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
   }
-  cudaStream_t st = P.stream;
   DS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st));
   const int rgrid = stream_grid(P, P.rl_n, kBlock, 8);
   k_pm_hist<<<rgrid, kBlock, 0, st>>>(P.rl_rec, P.rl_n, cnt);
@@ -447,15 +446,45 @@ ds_status pm_build(Plan& P) {
   return DS_OK;
 }
 
-ds_status pm_ensure(Plan& P) {
-  if (P.layout != 2 || P.bin_order != 1 || P.pm_rec != nullptr || P.rl_rec == nullptr) return DS_OK;
-  const ds_status s = pm_build(P);
-  if (s == DS_ENOMEM) {  // no room for the copy: bin the runs in time order instead
+static bool pm_needed(const Plan& P) {
+  return P.layout == 2 && P.bin_order == 1 && P.pm_rec == nullptr && P.rl_rec != nullptr;
+}
+
+// Without room for the copy the binning reads the runs in time order instead.
+static ds_status pm_outcome(Plan& P, ds_status s) {
+  if (s == DS_ENOMEM) {
     cudaGetLastError();
     P.bin_order = 0;
     return DS_OK;
   }
   return s;
+}
+
+ds_status pm_ensure(Plan& P) {
+  if (!pm_needed(P)) return DS_OK;
+  return pm_outcome(P, pm_build(P, P.stream));
+}
+
+ds_status pm_begin(Plan& P, bool* started) {
+  *started = false;
+  if (!pm_needed(P)) return DS_OK;
+  if (P.side_stream == nullptr) {
+    DS_CUDA_TRY(cudaStreamCreateWithFlags(&P.side_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : P.side_ev) DS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  // the run records come from the plan's stream
+  DS_CUDA_TRY(cudaEventRecord(P.side_ev[0], P.stream));
+  DS_CUDA_TRY(cudaStreamWaitEvent(P.side_stream, P.side_ev[0], 0));
+  const ds_status s = pm_build(P, P.side_stream);
+  if (s != DS_OK) return pm_outcome(P, s);
+  DS_CUDA_TRY(cudaEventRecord(P.side_ev[1], P.side_stream));
+  *started = true;
+  return DS_OK;
+}
+
+ds_status pm_join(Plan& P, bool started) {
+  if (started) DS_CUDA_TRY(cudaStreamWaitEvent(P.stream, P.side_ev[1], 0));
+  return DS_OK;
 }
 
 ds_status rl_build(Plan& P) {
