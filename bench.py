@@ -1,15 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 destriper on a synthetic scan shaped like the paper's
-30-day B-Machine channel (1.3e8 samples at 50 Hz; I, q, u outputs; nside 256;
-60 s baselines).
+12-month LATTE-like IQU radiometer (1.6e9 samples at 50 Hz; one I/Q/U output;
+nside 512; 1 s baselines; 2% flagged samples): the largest workload that fits
+one GPU.  --config 2 runs the 30-day B-Machine-like channel (1.3e8 samples;
+I, q, u outputs; nside 256; 60 s baselines).
 
 One step = the whole destriping job on inputs already resident in HBM: plan
 (hits, pixel matrices, rcond cut), right-hand side, CG to ||r||/||b|| < 1e-10,
 gauge, destriped map.  value = timestream samples x CG iterations / step time,
-summed over ranks and divided by the slowest rank's time.
+summed over ranks and divided by the slowest rank's time.  Beside it, outside
+the timed region: the plain float64 path on the same workload (fp64_path), the
+errors of the mixed result against it and against the float64 oracle on sampled
+pixels and baselines (error_vs_oracle), the end-to-end job from host buffers
+(e2e) and the oracle's own rate on the host cores (cpu_baseline).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config 2|4|1] [--precision mixed|fp64]
+                    [--config 4|2|1|3|5] [--precision mixed|fp64]
 
 N > 1 runs N independent replicas (one per GPU; the single-problem solve has
 no data-path exchange), launched with torch.distributed.run.  --impl reference
@@ -34,6 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "timestream samples/s per CG iteration (% HBM roofline); full-solve time; p50/p99"
 UNIT = "samples/s"
 BYTES_PER_SAMPLE_PASS = 12  # int32 pixel + float32 cos 2psi + float32 sin 2psi, per pass
+L2_BYTES = 129 * 10 ** 6
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -45,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--config", type=int, default=4, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--serve-seconds", type=float, default=30.0,
                     help="length of the request trace (config 5)")
     ap.add_argument("--serve-master", type=int, default=100_000_000,
@@ -55,6 +62,10 @@ def parse():
     ap.add_argument("--n-samples", type=int, default=None, help="cut the workload (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true",
+                    help="single-problem workloads: skip the plain float64 comparator")
+    ap.add_argument("--oracle-procs", type=int, default=0,
+                    help="processes of the all-core oracle timing (0 = every host core)")
     ap.add_argument("--oracle-samples", type=int, default=1_000_000)
     ap.add_argument("--oracle-iters", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true",
@@ -193,11 +204,15 @@ def config_dict(args, name=None):
     if name is None:
         name = WORKLOAD_NAMES[args.config] + (f"-prefix{args.n_samples}" if args.n_samples else "")
     n_b = -(-n_t // c["baseline_len"])
+    pointing = 12 * n_t
+    l2 = ("inputs larger than L2: the pointing streams from HBM every pass "
+          f"({pointing / 1e9:.2f} GB against a 129 MB L2)" if pointing > L2_BYTES else
+          f"L2-resident: {pointing / 1e6:.1f} MB of pointing fit the 129 MB L2, so this "
+          "workload measures parity and launch overheads, not HBM")
     return {"workload": name, "n_samples": n_t, "nside": c["nside"],
             "outputs": ",".join(c["kinds"]), "baseline_len": c["baseline_len"],
             "unknowns": len(c["kinds"]) * n_b, "precision": args.precision, "tol": args.tol,
-            "flagged_fraction": c.get("flag_frac", 0.0),
-            "l2": "inputs larger than L2 (pointing and timelines stream from HBM every pass)",
+            "flagged_fraction": c.get("flag_frac", 0.0), "l2": l2,
             "step": "plan + RHS + CG to tol + gauge + destriped map"}
 
 
@@ -220,6 +235,49 @@ def oracle_rate(prob_np, n_iters, tol=1e-10):
     if lim is not None:
         lim.unregister() if hasattr(lim, "unregister") else None
     return plan.n_t * max(iters, 1) / dt, iters, dt
+
+
+def host_cpu():
+    """Core count and CPU model of the host the oracle runs on."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() == "Model name" and val.strip():
+                info["model"] = val.strip()
+            elif key.strip() == "Vendor ID" and val.strip():
+                info["vendor"] = val.strip()
+    except Exception:
+        pass
+    return info
+
+
+def _oracle_worker_init():
+    # one thread per process: the all-core figure is processes x single-thread oracles
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+
+
+def _oracle_worker(job):
+    d, n_iters = job
+    t0 = time.perf_counter()
+    rate, it, dt = oracle_rate(d, n_iters)
+    return d["pix"].shape[0] * max(it, 1), t0, time.perf_counter()
+
+
+def oracle_all_cores(d, n_iters, procs):
+    """The oracle as it stands, one copy per host core on the same sample, run at
+    the same time (a spawned pool: the parent already holds a CUDA context).
+    Returns (sample-iterations per second over the wall time of the concurrent
+    runs, processes)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs, initializer=_oracle_worker_init) as pool:
+        res = pool.map(_oracle_worker, [(d, n_iters)] * procs, chunksize=1)
+    units = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return units / wall, procs
 
 
 def prefix_numpy(prob, n):
@@ -264,14 +322,21 @@ def run_reference(args):
     value = tot_si / tot_t
     sample = (f"prefix of {n} samples of {name}: plan + RHS + {iters_per_step} CG iterations "
               f"per step, float64 numpy, 1 thread")
-    cfg = config_dict(args) if args.config in (1, 2, 4) else {"workload": name, "n_samples": n}
+    if args.config in (1, 2, 4):
+        cfg = config_dict(args)
+        cfg.update(workload=f"{cfg['workload']}-prefix{n}", n_samples=n,
+                   unknowns=len(prob.kinds) * (-(-n // prob.baseline_len)),
+                   full_workload=config_dict(args)["workload"],
+                   full_n_samples=config_dict(args)["n_samples"])
+    else:
+        cfg = {"workload": name, "n_samples": n}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded scan, Gaussian sky, 1/f noise)", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -364,7 +429,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     dur_s = per_launch[dom] / 1e3
     achieved = alg_bytes / dur_s / 1e9 if dur_s > 0 else None
-    mixed = args.precision == "mixed" and tune.get("stream_mode", 0) == 0
+    mixed = args.precision == "mixed"
     form = layout.get("layout", 0) if mixed else 0
     kname = {0: {"bin": "k_bin", "rescan": "k_rescan"},
              1: {"bin": "k_ck_bin", "rescan": "k_ck_rescan"},
@@ -396,22 +461,184 @@ def run_ours(args):
             "gpu_launches": int(prof.get("kernel_launches", 0)),
             "clocks": clk.summary()}
 
+    # outside the timed region: the plain float64 path on the same workload, and the
+    # errors of the last timed job's result against it
+    sigma = float(prob.meta.get("sigma", 1.0))
+    if rank == 0 and not args.no_fp64_path and args.precision == "mixed":
+        line["fp64_path"], line["error_vs_fp64_path"] = fp64_path_leg(args, prob, ds, a, m,
+                                                                      n_c, sigma)
+    # sampled outputs of the mixed path for the oracle (taken on the GPU here; the
+    # oracle runs in the CPU leg below)
+    sampled = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sampled = gpu_sampled_outputs(args, prob, ds, a, m, n_c)
     # end to end through the C ABI with host buffers (copies inside the timed region)
     if not args.no_e2e:
         line["e2e"] = e2e_leg(args, prob, ds, world, dist if world > 1 else None)
     if rank == 0 and not args.no_cpu_baseline:
-        d, n = prefix_numpy(prob, args.oracle_samples)
-        rate, it, dt = oracle_rate(d, args.oracle_iters)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {n} samples of the same workload: oracle "
-                                          f"plan + RHS + {it} CG iterations in {dt:.1f} s "
-                                          f"(float64 numpy, 1 thread)"}
+        line["cpu_baseline"], line["error_vs_oracle"] = cpu_baseline_leg(args, prob, sampled,
+                                                                         sigma)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def rel_rms(a, b):
+    import numpy as np
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    den = float(np.sqrt(np.mean(b ** 2))) if b.size else 0.0
+    return float(np.sqrt(np.mean((a - b) ** 2)) / (den if den > 0 else 1.0)) if b.size else 0.0
+
+
+def fp64_path_leg(args, prob, ds, a_mixed, m_mixed, n_c, sigma):
+    """One job of the plain float64 single-problem path (float64 timelines, float64
+    per-sample work) on the same workload, timed with CUDA events; and the mixed
+    result's differences from it, plus the float64 residual of the mixed
+    baselines recomputed by this float64 plan."""
+    import torch
+    dev = prob.pix.device
+    y64 = prob.y.double().contiguous()  # promotion outside the timed region
+    a64 = torch.zeros_like(a_mixed)
+    m64 = torch.zeros_like(m_mixed)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    plan = ds.destripe_plan(prob.pix, prob.c32, prob.s32, prob.valid, nside=prob.nside,
+                            kinds=prob.kinds, baseline_len=prob.baseline_len, precision="fp64")
+    st, iters, rel = ds.destripe_solve(plan, y64, a64, tol=args.tol)
+    ds.destripe_map(plan, y64, a64, m64)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    # float64 residual of the mixed solution: ||b - A a|| / ||b|| with this plan
+    b = torch.empty_like(a64)
+    ds.destripe_rhs(plan, y64, b)
+    Aa = torch.empty_like(a64)
+    ds.destripe_apply_A(plan, a_mixed, Aa)
+    res_mixed = float(torch.linalg.norm(b - Aa) / torch.linalg.norm(b))
+    plan.close()
+    del y64, b, Aa
+    comp = {"value": prob.n_t * iters / (ms / 1e3), "unit": UNIT, "ms_per_job": ms,
+            "iterations": iters, "rel_resid": rel, "status": int(st),
+            "note": "float64 plan and timelines on the same workload, one job, outside the "
+                    "timed region (timelines promoted to float64 beforehand)"}
+    da = (a_mixed - a64).abs()
+    err = {"baselines_max_abs_over_sigma": float(da.max()) / sigma,
+           "baselines_rel_rms": rel_rms(a_mixed.cpu().numpy(), a64.cpu().numpy()),
+           "map_rel_rms": rel_rms(m_mixed.cpu().numpy(), m64.cpu().numpy()),
+           "mixed_solution_fp64_residual": res_mixed, "sigma_white": sigma}
+    del a64, m64
+    torch.cuda.empty_cache()
+    return comp, err
+
+
+def sampled_baselines(n_b, cfg, k):
+    import numpy as np
+    rng = np.random.default_rng(cfg)
+    return sorted(set(rng.integers(0, n_b, k).tolist()) | {0, n_b - 1})
+
+
+def gpu_sampled_outputs(args, prob, ds, a, m, n_c):
+    """The mixed path's outputs at the pixels touched by a few sampled baselines:
+    every sample on those pixels (renumbered) with the GPU's hits, mask, binned
+    map, destriped map (given the timed job's baselines) and the float32
+    operator's (A x) on the sampled baselines.  Host arrays for the oracle."""
+    import numpy as np
+    import torch
+    dev = prob.pix.device
+    L, n_t, n_b = prob.baseline_len, prob.n_t, prob.n_b
+    baselines = sampled_baselines(n_b, args.config, 6 if L >= 1000 else 12)
+    T = torch.cat([torch.arange(b * L, min((b + 1) * L, n_t), device=dev) for b in baselines])
+    P = torch.unique(prob.pix[T])
+    U = torch.nonzero(torch.isin(prob.pix, P)).squeeze(1)
+    plan = ds.destripe_plan(prob.pix, prob.c32, prob.s32, prob.valid, nside=prob.nside,
+                            kinds=prob.kinds, baseline_len=L, precision="mixed")
+    mb = torch.zeros_like(m)
+    hits = torch.zeros(prob.npix, dtype=torch.int32, device=dev)
+    mask = torch.zeros(prob.npix, dtype=torch.uint8, device=dev)
+    ds.destripe_bin(plan, prob.y, None, mb, hits, mask)
+    x = torch.randn(prob.n_o * n_b, dtype=torch.float64, device=dev,
+                    generator=torch.Generator(dev).manual_seed(3))
+    Ax = torch.empty_like(x)
+    ds.destripe_apply_A(plan, x, Ax)
+    plan.close()
+    cols = torch.tensor(baselines, device=dev)
+    out = {"baselines": np.array(baselines), "L": L, "nside": prob.nside, "kinds": prob.kinds,
+           "P": P.cpu().numpy(), "U": U.cpu().numpy(), "T": T.cpu().numpy(),
+           "pix": prob.pix[U].cpu().numpy(), "c": prob.c32[U].double().cpu().numpy(),
+           "s": prob.s32[U].double().cpu().numpy(),
+           "valid": None if prob.valid is None else prob.valid[U].cpu().numpy(),
+           "y": prob.y[:, U].double().cpu().numpy(),
+           "a": a.view(prob.n_o, n_b).cpu().numpy(),
+           "x": x.view(prob.n_o, n_b)[:, :].cpu().numpy(),
+           "hits": hits[P].cpu().numpy(), "mask": mask[P].cpu().numpy().astype(bool),
+           "bin_map": mb.view(n_c, prob.npix)[:, P].cpu().numpy(),
+           "map": m.view(n_c, prob.npix)[:, P].cpu().numpy(),
+           "Ax": Ax.view(prob.n_o, n_b)[:, cols].cpu().numpy()}
+    del mb, hits, mask, x, Ax
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_sampled_errors(g):
+    """The oracle on the sampled subset (every sample of the touched pixels, so
+    that their cut, map and the sampled baselines' (A x) are exact) against the
+    mixed path's outputs there."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    L, U, T = g["L"], g["U"], g["T"]
+    local = np.searchsorted(g["P"], g["pix"])
+    sub = oracle.make_plan(local, g["c"], g["s"], g["valid"], g["nside"], g["kinds"], L,
+                           npix=len(g["P"]))
+    bin_ref = oracle.bin_map(sub, g["y"])
+    map_ref = oracle.bin_map(sub, g["y"] - g["a"][:, U // L])
+    Zz = oracle.apply_Z(sub, g["x"][:, U // L])
+    pos = np.searchsorted(U, T)
+    idx = {b: i for i, b in enumerate(g["baselines"].tolist())}
+    col = np.array([idx[t // L] for t in T])
+    Ax_ref = np.stack([np.bincount(col, weights=Zz[o, pos], minlength=len(idx))
+                       for o in range(Zz.shape[0])])
+    return {"method": "sampled: the oracle on every sample of the pixels touched by "
+                      f"{len(idx)} sampled baselines (hits, mask, maps and (A x) there are "
+                      "exact on that subset)",
+            "sampled_baselines": len(idx), "sampled_pixels": int(len(g["P"])),
+            "sampled_samples": int(len(U)),
+            "hits_mask_bitexact": bool(np.array_equal(g["hits"], sub.hits)
+                                       and np.array_equal(g["mask"], sub.mask)),
+            "binned_map_rel_rms": rel_rms(g["bin_map"], bin_ref),
+            "destriped_map_rel_rms": rel_rms(g["map"], map_ref),
+            "operator_rel_rms": rel_rms(g["Ax"], Ax_ref),
+            "oracle_s": time.perf_counter() - t0}
+
+
+def cpu_baseline_leg(args, prob, sampled, sigma):
+    """The oracle on the host cores: its rate on a bounded prefix of the same
+    workload (one thread, then one copy per core at once), and the mixed path's
+    errors against it on the sampled subset."""
+    d, n = prefix_numpy(prob, args.oracle_samples)
+    rate1, it, dt = oracle_rate(d, args.oracle_iters)
+    host = host_cpu()
+    procs = args.oracle_procs or host.get("nproc") or 1
+    try:
+        rate_all, procs = oracle_all_cores(d, args.oracle_iters, procs)
+    except Exception as e:  # the one-thread figure still stands
+        rate_all, procs = None, 0
+        host["all_cores_error"] = str(e)[:200]
+    base = {"value": rate_all if rate_all else rate1, "unit": UNIT,
+            "cores": procs if rate_all else 1, "kind": "oracle",
+            "sample": f"first {n} samples of the same workload: oracle plan + RHS + {it} CG "
+                      f"iterations (float64 numpy; {dt:.1f} s on one thread); value = "
+                      + (f"{procs} single-thread copies run at once" if rate_all else
+                         "one thread"),
+            "one_thread": rate1, "all_cores": rate_all, "host": host}
+    err = oracle_sampled_errors(sampled) if sampled is not None else None
+    return base, err
 
 
 def e2e_leg(args, prob, ds, world, dist):

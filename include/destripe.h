@@ -62,7 +62,7 @@ typedef enum {
   DS_ENOMEM = 2,    /* device allocation failed */
   DS_ECUDA = 3,     /* a CUDA runtime call failed */
   DS_ENOCONV = 4,   /* CG reached max_iter; the best iterate is still written */
-  DS_ETIMEOUT = 5,  /* a bounded device wait gave up */
+  DS_ETIMEOUT = 5,  /* reserved: a bounded device wait gave up (no call waits on the device) */
   DS_ENAN = 6,      /* non-finite value met in the data or the iteration */
   DS_EPIX = 7,      /* a pixel index outside [0, 12 nside^2) */
   DS_ESTATE = 8     /* call not valid for this plan (e.g. precision mismatch) */
@@ -225,11 +225,6 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     float64 residual refreshes) use double-float operands and
  *                     compensated float32 sums on the float32 pipes with float64
  *                     accumulators (default), 0 = float64
- *   "stream_mode"     MIXED plans: 0 = streaming kernels read the pointing with vector
- *                     loads (default); 1 / 2 = TMA bulk copies stage it through a
- *                     shared-memory pipeline of 4 x 2048-sample stages at 2 blocks per SM
- *                     / 3 x 1024-sample stages at 3 blocks per SM (persistent blocks;
- *                     waits are bounded, DS_ETIMEOUT on expiry)
  *   "blocks_per_sm"   1..32 resident-block target of the streaming kernels (default 16)
  *   "layout"          MIXED plans: 0 = the float32 operator reads the time-ordered pixel
  *                     indices; 2 = run-length records: per run of consecutive samples on
@@ -278,7 +273,9 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value);
  * destripe_batch_create: room for max_slots (1..4096) problems.
  * destripe_batch_add:    computes the problem's right-hand side and CG start
  *     (d_a0: float64 [n_o][n_b] starting guess or NULL) and gives it a slot.
- *     DS_ESTATE if the batch is full, the plan is already in it, or it cannot join.
+ *     DS_ESTATE if the batch is full, the plan is already in it, or it cannot join;
+ *     DS_ENAN if the timelines hold a non-finite value on a valid sample (the problem
+ *     does not join).  Waits on the batch's stream for the problem's start.
  * destripe_batch_step:   runs CG iterations for every running problem, at least
  *     min_iters unless all have stopped; *n_running = problems not yet stopped.
  *     Synchronises the stream.

@@ -301,7 +301,6 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->graph_iters_cfg = 16;
   P->blocks_per_sm = 16;
   P->accurate_df = 1;
-  P->stream_mode = 0;
   P->refresh_max = 50;
   P->drift_ratio = 1e4;
   P->accurate_start = 0;
@@ -503,7 +502,6 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   DS_CUDA_TRY(cudaMemcpyAsync(P.h_state, P.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
   DS_CUDA_TRY(cudaMemcpyAsync(P.h_err, P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DS_CUDA_TRY(cudaStreamSynchronize(st));
-  if (*P.h_err & ERR_TIMEOUT) return DS_ETIMEOUT;
   const CgState H = *P.h_state;
   // Mixed plans that did not converge return the iterate with the smallest
   // float64 residual seen (a float32 operator can drift on ill-posed problems).
@@ -574,9 +572,6 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
   } else if (k == "refresh_max") {
     if (!(value >= 1.0 && value <= 1e6)) return DS_EINVAL;
     P.refresh_max = (int)value;
-  } else if (k == "stream_mode") {
-    if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
-    P.stream_mode = (int)value;
   } else if (k == "layout") {
     if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
     if (value != 0.0 && P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;

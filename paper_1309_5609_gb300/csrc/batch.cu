@@ -1131,6 +1131,12 @@ ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, cons
   enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, d_a0 ? 1 : 0);
   if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
   B->launches += 6 + (d_a0 ? 3 : 0);
+  // a non-finite value in the data reaches ||b||^2: such a problem is refused here
+  // instead of occupying a slot (the host waits for this problem's start only;
+  // steps run on the same stream and have all ended when the host admits)
+  DS_CUDA_TRY(cudaMemcpyAsync(P.h_scal + 7, &P.state->bb, sizeof(double), cudaMemcpyDeviceToHost, st));
+  DS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!std::isfinite(P.h_scal[7])) return DS_ENAN;
   B->nc = P.n_c;
   B->plans[sl] = &P;
   B->stopped[sl] = 0;

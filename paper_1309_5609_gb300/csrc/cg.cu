@@ -375,7 +375,7 @@ void enqueue_gauge(const Plan& P, cudaStream_t st, double* a) {
 int kernels_per_iteration(const Plan& P, bool accurate) {
   if (P.desc.precision != DS_PREC_MIXED) return 6;
   const bool df = P.accurate_df && P.maplo != nullptr;  // + the baseline split kernel
-  const bool f32 = P.x32 != nullptr && !accurate && P.stream_mode == 0 && P.layout != 1;
+  const bool f32 = P.x32 != nullptr && !accurate && P.layout != 1;
   // pixel-major binning packs the baselines per baseline first (one kernel per bin)
   const bool pm = P.layout == 2 && pm_ready(P);
   const int packs = pm ? (df ? 1 : 0) + (accurate ? (df ? 1 : 0) : (f32 ? 1 : 0)) : 0;

@@ -109,7 +109,7 @@ struct CgState {
   int stall_iters;     // stop when no 10x improvement for this many iterations (0 = never)
 };
 
-enum ErrBits { ERR_PIX = 1, ERR_NAN = 2, ERR_TIMEOUT = 4 };
+enum ErrBits { ERR_PIX = 1, ERR_NAN = 2 };
 
 struct Plan {
   ds_desc desc;
@@ -168,7 +168,6 @@ struct Plan {
   int graph_iters_cfg;      // CG iterations per captured graph
   int blocks_per_sm;        // streaming-kernel blocks per SM
   int accurate_df;          // mixed plans: accurate passes in compensated float32 (1) or float64 (0)
-  int stream_mode;          // mixed operator: 0 = direct vector loads, 1 = TMA-staged pipeline
   int refresh_max;          // mixed plans: float64 residual at least every this many iterations
   double drift_ratio;       // mixed plans: squared true / recursive residual ratio of the switch
   int accurate_start;       // mixed plans: 1 = accurate operator from the first iteration
@@ -203,6 +202,7 @@ struct Plan {
   float4* x4;               // [n_b] float32 baselines of every output, per baseline
   float4* xd4;              // [2][n_b] split baselines: hi parts, then lo parts
   int bin_order;            // run-length plans: 1 = bin pixel-major (default), 0 = in time order
+  int pm_pending;           // the copy is being built on the side stream: unusable until pm_join
   cudaStream_t side_stream; // builds the pixel-major copy beside the first right-hand side
   cudaEvent_t side_ev[2];   // records ready (plan stream) / copy built (side stream)
 };
@@ -266,10 +266,6 @@ void launch_bin_df(const Plan& P, cudaStream_t st, const double* x, const float*
 void launch_pixel_solve_df(const Plan& P, cudaStream_t st, double* out_map, Gate g);
 void launch_rescan_df(const Plan& P, cudaStream_t st, const double* x, const float* y,
                       double* out, Gate g);
-// apply_tma.cu: mixed operator with TMA-staged pointing streams
-bool tma_supported(const Plan& P);
-void launch_bin_tma(const Plan& P, cudaStream_t st, const double* x, Gate g);
-void launch_rescan_tma(const Plan& P, cudaStream_t st, const double* x, double* out, Gate g);
 // full operator pieces
 void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, double* out, Gate g,
                    cudaEvent_t* ev = nullptr);

@@ -418,8 +418,9 @@ ds_status pm_build(Plan& P, cudaStream_t st) {
   if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&P.xd4), sizeof(float4) * 2 * P.n_b, true);
   if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false);
   if (e == cudaSuccess) e = plan_alloc_on(P, st, reinterpret_cast<void**>(&blk), sizeof(int64_t) * (G + 1), false);
-  if (e != cudaSuccess) {
-    // give back what was taken: without the copy the binning reads the runs in time order
+  // On any failure give back what was taken and leave no half-built copy behind:
+  // without the copy the binning reads the runs in time order.
+  auto release = [&](cudaError_t err) {
     void** held[] = {reinterpret_cast<void**>(&P.pm_off), reinterpret_cast<void**>(&P.pm_rec),
                      reinterpret_cast<void**>(&P.pm_lo), reinterpret_cast<void**>(&P.x4),
                      reinterpret_cast<void**>(&P.xd4), reinterpret_cast<void**>(&cnt),
@@ -430,9 +431,11 @@ ds_status pm_build(Plan& P, cudaStream_t st) {
         *h = nullptr;
       }
     P.device_bytes = held_before;
-    return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
-  }
-  DS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st));
+    return err == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
+  };
+  if (e != cudaSuccess) return release(e);
+  e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st);
+  if (e != cudaSuccess) return release(e);
   const int rgrid = stream_grid(P, P.rl_n, kBlock, 8);
   k_pm_hist<<<rgrid, kBlock, 0, st>>>(P.rl_rec, P.rl_n, cnt);
   k_pm_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk);
@@ -440,10 +443,24 @@ ds_status pm_build(Plan& P, cudaStream_t st) {
   k_pm_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk, blk + G, P.pm_off);
   k_pm_scatter<<<rgrid, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.rl_df, P.rl_n, cnt, P.pm_rec, P.pm_lo);
   P.launches += 5;
-  DS_CUDA_TRY(cudaGetLastError());
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return release(e);
   cudaFreeAsync(cnt, st);
   cudaFreeAsync(blk, st);
   return DS_OK;
+}
+
+// Frees a pixel-major copy (built or not) ordered after the work on st.
+static void pm_release(Plan& P, cudaStream_t st) {
+  void** held[] = {reinterpret_cast<void**>(&P.pm_off), reinterpret_cast<void**>(&P.pm_rec),
+                   reinterpret_cast<void**>(&P.pm_lo), reinterpret_cast<void**>(&P.x4),
+                   reinterpret_cast<void**>(&P.xd4)};
+  for (void** h : held)
+    if (*h != nullptr) {
+      cudaFreeAsync(*h, st);
+      *h = nullptr;
+    }
+  P.pm_pending = 0;
 }
 
 static bool pm_needed(const Plan& P) {
@@ -477,13 +494,28 @@ ds_status pm_begin(Plan& P, bool* started) {
   DS_CUDA_TRY(cudaStreamWaitEvent(P.side_stream, P.side_ev[0], 0));
   const ds_status s = pm_build(P, P.side_stream);
   if (s != DS_OK) return pm_outcome(P, s);
-  DS_CUDA_TRY(cudaEventRecord(P.side_ev[1], P.side_stream));
+  // until pm_join orders the plan's stream after the build, nothing may bin from
+  // the copy (a warm start's first operator application comes before the join)
+  P.pm_pending = 1;
+  if (cudaEventRecord(P.side_ev[1], P.side_stream) != cudaSuccess) {
+    cudaStreamSynchronize(P.side_stream);
+    pm_release(P, P.side_stream);
+    return DS_ECUDA;
+  }
   *started = true;
   return DS_OK;
 }
 
 ds_status pm_join(Plan& P, bool started) {
-  if (started) DS_CUDA_TRY(cudaStreamWaitEvent(P.stream, P.side_ev[1], 0));
+  if (!started) return DS_OK;
+  if (cudaStreamWaitEvent(P.stream, P.side_ev[1], 0) != cudaSuccess) {
+    // the plan's stream cannot be ordered after the build: wait for it here
+    if (cudaStreamSynchronize(P.side_stream) != cudaSuccess) {
+      pm_release(P, P.side_stream);
+      return DS_ECUDA;
+    }
+  }
+  P.pm_pending = 0;
   return DS_OK;
 }
 

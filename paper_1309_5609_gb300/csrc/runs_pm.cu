@@ -159,7 +159,9 @@ __global__ void __launch_bounds__(kBlock) k_pm_bin_df(const uint32_t* __restrict
 
 }  // namespace
 
-bool pm_ready(const Plan& P) { return P.bin_order == 1 && P.pm_rec != nullptr; }
+bool pm_ready(const Plan& P) {
+  return P.bin_order == 1 && P.pm_rec != nullptr && !P.pm_pending;
+}
 
 // P.x32 holds the float32 baselines of this pass (k_to_f32)
 void launch_bin_pm(const Plan& P, cudaStream_t st, Gate g) {

@@ -27,7 +27,7 @@ from typing import Callable, List, Optional
 
 import numpy as np
 
-from . import (DS_OK, destripe_batch_add, destripe_batch_create, destripe_batch_info,
+from . import (DS_OK, DestripeError, destripe_batch_add, destripe_batch_create, destripe_batch_info,
                destripe_batch_retire, destripe_batch_slot_status, destripe_batch_step,
                destripe_plan, destripe_tune)
 
@@ -158,7 +158,16 @@ class Server:
         acc = req.accurate_start if req.accurate_start is not None else req.n_t < self.accurate_below
         if acc:
             destripe_tune(plan, "accurate_start", 1)
-        slot = destripe_batch_add(self.batch, plan, y, tol=req.tol)
+        try:
+            slot = destripe_batch_add(self.batch, plan, y, tol=req.tol)
+        except DestripeError as e:
+            # refused at admission (non-finite data): answered at once, no slot held
+            req.admitted = req.finished = self.now()
+            req.status, req.iters = e.status, 0
+            plan.close()
+            self.done.append(req)
+            self.stats.latencies.append(req.latency)
+            return True
         req.admitted = self.now()
         self.resident[slot] = (req, plan, (pix, c, s, y), need)
         self.used += need

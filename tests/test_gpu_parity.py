@@ -346,36 +346,6 @@ def test_mixed_accurate_passes_both_modes(accurate_df):
     assert rel_rms(a.cpu().numpy(), ref["a"]) < 1e-5
 
 
-TMA_CASES = CASES + [
-    (("q", "u"), 16, 2048 * 3 + 5, 64, 0.0, ScanParams()),   # ragged last tile
-    (("I", "q", "u"), 8, 3, 1, 0.0, ScanParams()),           # fewer samples than one vector
-]
-
-
-@pytest.mark.parametrize("case", TMA_CASES, ids=IDS + ["ragged_tile", "three_samples"])
-def test_tma_pipeline_operator_parity(case):
-    # mixed operator with the pointing staged by TMA bulk copies
-    prob = case_problem(case)
-    op, d = oracle_plan(prob)
-    plan, g, y = gpu_plan(prob, "mixed")
-    ds.destripe_tune(plan, "stream_mode", 1)
-    rng = np.random.default_rng(6)
-    for _ in range(2):  # twice: the pixel sums must come back cleared
-        x = rng.standard_normal(plan.n_u)
-        Ax = torch.empty(plan.n_u, dtype=torch.float64, device=DEV)
-        ds.destripe_apply_A(plan, torch.from_numpy(x).to(DEV), Ax)
-        ref = oracle.apply_A(op, x)
-        scale = max(1e-300, float(np.sqrt(np.mean(ref ** 2))))
-        err = float(np.sqrt(np.mean((Ax.cpu().numpy() - ref) ** 2))) / scale
-        assert err < 1e-5 or np.abs(ref).max() < 1e-9, err
-    a = torch.zeros(plan.n_u, dtype=torch.float64, device=DEV)
-    st, iters, rel = ds.destripe_solve(plan, y, a, tol=1e-10)
-    assert st == ds.DS_OK, st
-    yo = y.double().cpu().numpy().reshape(plan.n_o, plan.n_t)
-    ref = oracle.destripe(op, yo, tol=1e-10)
-    assert np.abs(a.cpu().numpy() - ref["a"]).max() < 1e-4
-
-
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", DEGENERATE, ids=["iqu", "I_iqu"])
 def test_degenerate_problems_drive_the_float64_residual_down(case, precision):
