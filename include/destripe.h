@@ -248,6 +248,21 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     here) with one warp per pixel and one plain store of its sums, no
  *                     atomic updates (default); 0 = they read the records in time order
  *                     with one reduction per run.
+ *   "rescan_samples"  MIXED plans with run-length records: 1 = the rescans read the
+ *                     time-ordered samples (12 bytes per sample) instead of the records
+ *                     (20 bytes per run); chosen when the records are requested above
+ *                     0.6 runs per sample
+ *   "precond"         preconditioner of the CG (no counterpart in the paper, which uses
+ *                     unpreconditioned Krylov solvers): 0 = none (default); 1 = D^-1, the
+ *                     valid samples of each baseline; 2 = two-level: D^-1 plus a coarse
+ *                     correction R E^+ R^T on a space of large-scale sky modes (cells of
+ *                     the sphere, "coarse_nside"), E = R^T A R built once per plan at its
+ *                     first solve (from the pixel-major run records, made for the purpose
+ *                     when the plan has none; synchronises).  The solution is the same;
+ *                     the iterations are fewer where short baselines leave slow
+ *                     sky-like modes
+ *   "coarse_nside"    two-level preconditioner: 12 coarse_nside^2 cells (power of two,
+ *                     1..64, default 8; at most the map's nside); a change rebuilds E
  *   "rescan_rounds"   MIXED plans: rounds of 32 work items (runs, or 4-sample groups)
  *                     per warp chunk in the rescans that keep per-lane baseline sums
  *                     across rounds and flush them across the warp only where a baseline

@@ -14,7 +14,7 @@ void enqueue_dot(const Plan& P, cudaStream_t st, const double* a, const double* 
 void enqueue_gauge(const Plan& P, cudaStream_t st, double* a);
 void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev, bool accurate);
 void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, double delta,
-                      int warm);
+                      int warm, bool precond);
 }  // namespace ds
 
 using namespace ds;
@@ -110,7 +110,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->pc_cell, P->pc_val, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a
@@ -310,6 +310,8 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->rescan_rounds = 0;
   P->bin_order = 1;
   P->samples_per_thread = 4;
+  P->precond = 0;
+  P->pc_nside = 8;
   cudaError_t e = cudaSuccess;
 #define DS_ALLOC(ptr, n) \
   if (e == cudaSuccess) e = dalloc(*P, &P->ptr, (n));
@@ -467,10 +469,15 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   const ds_status sp = pm_begin(P, &pm_started);
   if (sp != DS_OK) return sp;
   enqueue_rhs(P, st, d_y, P.b, Gate{nullptr, nullptr});
-  enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, warm_start ? 1 : 0);
-  P.launches += 3 + 3 + (warm_start ? 3 : 0);
   ds_status s = pm_join(P, pm_started);
   if (s != DS_OK) return s;
+  // the two-level preconditioner's coarse space, built once per plan
+  if (P.precond == 2 && !P.pc_built) {
+    s = pc_prepare(P);
+    if (s != DS_OK) return s;
+  }
+  enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, warm_start ? 1 : 0, true);
+  P.launches += 3 + 3 + (warm_start ? 3 : 0) + (P.precond ? 3 : 0);
   s = launch_status();
   if (s != DS_OK) return s;
   s = build_graph(P);
@@ -583,6 +590,8 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
       clear_stale_error();
       const ds_status s = rl_build(P);
       if (s != DS_OK) return s;
+      // records asked for above the automatic density: the rescans keep the samples
+      P.rescan_samples = (double)P.rl_n > kRunsPerSampleMax * (double)P.n_t ? 1 : 0;
     }
     P.layout = (int)value;
   } else if (k == "chunk") {
@@ -620,6 +629,20 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
   } else if (k == "rescan_rounds") {
     if (!(value >= 0.0 && value <= 16.0) || (double)(int)value != value) return DS_EINVAL;
     P.rescan_rounds = (int)value;
+  } else if (k == "rescan_samples") {
+    if (value != 0.0 && value != 1.0) return DS_EINVAL;
+    P.rescan_samples = (int)value;
+  } else if (k == "precond") {
+    if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
+    P.precond = (int)value;
+  } else if (k == "coarse_nside") {
+    const int nc = (int)value;
+    if ((double)nc != value || nc < 1 || nc > 64 || (nc & (nc - 1)) != 0) return DS_EINVAL;
+    if (nc != P.pc_nside) {
+      cudaStreamSynchronize(P.stream);
+      pc_free(P, P.stream);
+      P.pc_nside = nc;
+    }
   } else if (k == "blocks_per_sm") {
     if (!(value >= 1.0 && value <= 32.0)) return DS_EINVAL;
     P.blocks_per_sm = (int)value;

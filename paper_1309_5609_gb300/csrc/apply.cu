@@ -551,7 +551,7 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     launch_pixel_solve_df(P, st, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
-    if (runs) launch_rescan_rl_df(P, st, out, g);
+    if (runs && !P.rescan_samples) launch_rescan_rl_df(P, st, out, g);
     else launch_rescan_df(P, st, x, nullptr, out, g);
     if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
     return;
@@ -563,7 +563,8 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     launch_pixel_solve(P, st, false, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
-    launch_rescan_rl(P, st, out, g);
+    if (P.rescan_samples) launch_rescan_x(P, st, false, x, out, g);
+    else launch_rescan_rl(P, st, out, g);
     if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
     return;
   }

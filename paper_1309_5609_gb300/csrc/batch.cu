@@ -32,7 +32,7 @@
 namespace ds {
 void enqueue_gauge(const Plan& P, cudaStream_t st, double* a);
 void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, double delta,
-                      int warm);
+                      int warm, bool precond);
 }  // namespace ds
 
 namespace ds {
@@ -1128,7 +1128,7 @@ ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, cons
     DS_CUDA_TRY(cudaMemcpyAsync(P.x, d_a0, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
   DS_CUDA_TRY(cudaMemsetAsync(P.b, 0, sizeof(double) * P.n_u, st));
   enqueue_rhs(P, st, d_y, P.b, Gate{nullptr, nullptr});
-  enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, d_a0 ? 1 : 0);
+  enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, d_a0 ? 1 : 0, false);
   if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
   B->launches += 6 + (d_a0 ? 3 : 0);
   // a non-finite value in the data reaches ||b||^2: such a problem is refused here

@@ -62,6 +62,34 @@ __device__ bool finish_sum(double partial, double* __restrict__ red, unsigned* _
   return false;
 }
 
+// The same, returning true in every thread of the last block, with *total (the
+// sum of all partials in block order) valid in all of them.
+__device__ bool finish_sum_block(double partial, double* __restrict__ red,
+                                 unsigned* __restrict__ ticket, double* total) {
+  __shared__ bool last;
+  __shared__ double s_tot;
+  const double bs = block_sum(partial);
+  if (threadIdx.x == 0) {
+    red[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double v = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += ((volatile double*)red)[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    s_tot = v;
+  }
+  __syncthreads();
+  *total = s_tot;
+  return true;
+}
+
 // The vector kernels below read pairs of elements with one 16-byte load (the
 // vectors are 256-byte aligned allocations); with odd n, thread 0 of block 0 also
 // takes the last element.  Every thread's share is fixed, so sums stay
@@ -159,7 +187,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_alpha(const double* __restrict__ 
       st->status = 3;  // breakdown: the direction carries no curvature
       st->done = 1;
     } else {
-      st->alpha = st->rr / tot;
+      st->alpha = (st->precond ? st->rz : st->rr) / tot;
       if (!isfinite(st->alpha)) {
         st->status = 4;
         st->done = 1;
@@ -301,6 +329,157 @@ __global__ void __launch_bounds__(kBlock) k_cg_direction(double* __restrict__ p,
   }
 }
 
+// ---- preconditioned directions (precond.cu builds the coarse space) ----------------
+// z = D^-1 r (+ R E^+ R^T r), rz = r . z, p = z + beta p.  D^-1 is the float32
+// reciprocal of the valid samples of the unknown's baseline (0 without any), the
+// same in every kernel, so that the preconditioner is one fixed SPD operator.
+
+__device__ __forceinline__ double pc_dinv(int nv) {
+  return nv > 0 ? (double)__frcp_rn((float)nv) : 0.0;
+}
+
+// Sums of val over each segment of lanes with equal consecutive keys, left in the
+// segment's first lane (keys need not be sorted: a key that comes back later in
+// the warp starts a new segment).
+__device__ __forceinline__ double seg_sum_to_head(int key, double val) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int next = __shfl_down_sync(full, key, 1);
+  bool stop = lane == 31 || next != key;  // the segment ends within [lane, lane + w)
+#pragma unroll
+  for (int w = 1; w < 32; w <<= 1) {
+    const double v2 = __shfl_down_sync(full, val, w);
+    const bool s2 = __shfl_down_sync(full, stop, w);
+    if (!stop) {
+      val += v2;
+      stop = s2;
+    }
+  }
+  return val;
+}
+
+// u += R^T r (shared-memory sums per block, one flush per block) and
+// r . D^-1 r; mode 1 (no coarse space): rz = r . D^-1 r.
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_pc_restrict(const double* __restrict__ r,
+                                                        const int32_t* __restrict__ nvalid,
+                                                        const int32_t* __restrict__ cell,
+                                                        const float* __restrict__ val,
+                                                        int64_t n_b, int n_o, int n,
+                                                        double* __restrict__ u,
+                                                        double* __restrict__ red, unsigned* ticket,
+                                                        CgState* st) {
+  if (st->done) return;
+  extern __shared__ double s_u[];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_u[i] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int o = 0; o < n_o; ++o) {
+    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; bb < n_b;
+         bb += stride) {
+      const int64_t b = bb + lane;
+      const bool in = b < n_b;
+      const int64_t i = (int64_t)o * n_b + b;
+      const double ri = in ? r[i] : 0.0;
+      acc += ri * ri * (in ? pc_dinv(nvalid[b]) : 0.0);
+      if (n > 0) {
+#pragma unroll
+        for (int s = 0; s < kPcSlots; ++s) {
+          const int key = in ? cell[b * kPcSlots + s] : -1;
+          const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+          const bool head = key >= 0 && (lane == 0 || kprev != key);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const double v = key >= 0 ? (double)val[(i * kPcSlots + s) * NC + c] * ri : 0.0;
+            const double tot = seg_sum_to_head(key, v);
+            if (head) atomicAdd(s_u + key * NC + c, tot);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if (s_u[j] != 0.0) atomicAdd(u + j, s_u[j]);
+  double tot;
+  if (finish_sum(acc, red, ticket, &tot)) {
+    if (n > 0) {
+      st->rdr = tot;
+    } else {
+      st->rz_old = st->rz;
+      st->rz = tot;
+    }
+  }
+}
+
+// c = E^+ u (one warp per row), rz = r . D^-1 r + u . c; the last block clears u.
+__global__ void __launch_bounds__(kBlock) k_pc_coarse(const double* __restrict__ einv,
+                                                      double* __restrict__ u,
+                                                      double* __restrict__ c, int n,
+                                                      double* __restrict__ red, unsigned* ticket,
+                                                      CgState* st) {
+  if (st->done) return;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  double acc = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n;
+       row += warps) {
+    const double* e = einv + row * n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s = fma(e[j], u[j], s);
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(full, s, d);
+    if (lane == 0) {
+      c[row] = s;
+      acc = fma(s, u[row], acc);
+    }
+  }
+  double tot;
+  if (finish_sum_block(acc, red, ticket, &tot)) {
+    if (threadIdx.x == 0) {
+      st->rz_old = st->rz;
+      st->rz = st->rdr + tot;
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) u[j] = 0.0;
+  }
+}
+
+// p = D^-1 r + R c + beta p (beta = 0 at the start); q = 0.
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_pc_direction(double* __restrict__ p,
+                                                         const double* __restrict__ r,
+                                                         double* __restrict__ q,
+                                                         const int32_t* __restrict__ nvalid,
+                                                         const int32_t* __restrict__ cell,
+                                                         const float* __restrict__ val,
+                                                         const double* __restrict__ c,
+                                                         int64_t n_b, int n_o, int n,
+                                                         const CgState* st) {
+  if (st->done) return;
+  const double beta = st->iter == 0 ? 0.0 : st->rz / st->rz_old;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int o = 0; o < n_o; ++o) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += stride) {
+      const int64_t i = (int64_t)o * n_b + b;
+      double z = pc_dinv(nvalid[b]) * r[i];
+      if (n > 0) {
+#pragma unroll
+        for (int s = 0; s < kPcSlots; ++s) {
+          const int k = cell[b * kPcSlots + s];
+          if (k < 0) continue;
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc)
+            z = fma((double)val[(i * kPcSlots + s) * NC + cc], __ldg(c + k * NC + cc), z);
+        }
+      }
+      p[i] = fma(beta, p[i], z);
+      q[i] = 0.0;
+    }
+  }
+}
+
 // Gauge: mean over (I-carrying outputs, baselines with data) -> scal[0..1]
 __global__ void __launch_bounds__(kBlock) k_gauge_sum(const double* __restrict__ a,
                                                       const int32_t* __restrict__ nvalid,
@@ -343,8 +522,12 @@ __global__ void __launch_bounds__(kBlock) k_gauge_apply(double* __restrict__ a,
 
 __global__ void k_set_state(CgState* st, double tol, int max_iter, int mixed, double delta,
                             int refresh_max, double drift2, int accurate_start,
-                            int stall_iters) {
+                            int stall_iters, int precond) {
   st->tol2 = tol * tol * st->bb;
+  st->precond = precond;
+  st->rz = 0.0;
+  st->rz_old = 0.0;
+  st->rdr = 0.0;
   st->stall_iters = stall_iters;
   st->drift2 = drift2;
   st->accurate_start = mixed ? accurate_start : 0;
@@ -371,15 +554,36 @@ void enqueue_gauge(const Plan& P, cudaStream_t st, double* a) {
   k_gauge_apply<<<vec_grid(P, P.n_b), kBlock, 0, st>>>(a, P.nvalid, P.n_b, P.kinds, P.scal + 4);
 }
 
+void enqueue_precond_direction(const Plan& P, cudaStream_t st) {
+  const bool coarse = pc_ready(P);
+  const int n = coarse ? P.pc_n : 0;
+  const int vg = vec_grid(P, P.n_b);
+  auto go = [&](auto ncc) {
+    constexpr int NC = decltype(ncc)::value;
+    k_pc_restrict<NC><<<vg, kBlock, sizeof(double) * n, st>>>(
+        P.r, P.nvalid, P.pc_cell, P.pc_val, P.n_b, P.n_o, n, P.pc_u, P.red, P.counters + 4,
+        P.state);
+    if (coarse)
+      k_pc_coarse<<<stream_grid(P, (int64_t)n * 32, kBlock, 8), kBlock, 0, st>>>(
+          P.pc_einv, P.pc_u, P.pc_c, n, P.red, P.counters + 5, P.state);
+    k_pc_direction<NC><<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.nvalid, P.pc_cell, P.pc_val,
+                                             P.pc_c, P.n_b, P.n_o, n, P.state);
+  };
+  if (P.n_c == 1) go(std::integral_constant<int, 1>{});
+  else if (P.n_c == 2) go(std::integral_constant<int, 2>{});
+  else go(std::integral_constant<int, 3>{});
+}
+
 // accurate: the iteration applies the operator in the accurate arithmetic
 int kernels_per_iteration(const Plan& P, bool accurate) {
-  if (P.desc.precision != DS_PREC_MIXED) return 6;
+  const int pc = P.precond ? (pc_ready(P) ? 2 : 1) : 0;  // extra kernels of the direction
+  if (P.desc.precision != DS_PREC_MIXED) return 6 + pc;
   const bool df = P.accurate_df && P.maplo != nullptr;  // + the baseline split kernel
   const bool f32 = P.x32 != nullptr && !accurate && P.layout != 1;
   // pixel-major binning packs the baselines per baseline first (one kernel per bin)
   const bool pm = P.layout == 2 && pm_ready(P);
-  const int packs = pm ? (df ? 1 : 0) + (accurate ? (df ? 1 : 0) : (f32 ? 1 : 0)) : 0;
-  return 11 + (df ? 1 : 0) + (df && accurate ? 1 : 0) + (f32 ? 1 : 0) + packs;
+  const int packs = (pm && P.n_o > 1) ? (df ? 1 : 0) + (accurate ? (df ? 1 : 0) : (f32 ? 1 : 0)) : 0;
+  return 11 + (df ? 1 : 0) + (df && accurate ? 1 : 0) + (f32 ? 1 : 0) + packs + pc;
 }
 
 // One CG iteration (gated by state->done), used both directly and under capture.
@@ -404,23 +608,28 @@ void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev, bool acc
     k_cg_reliable<<<vg, kBlock, 0, st>>>(P.r, P.b, P.t, P.n_u, P.red, P.counters, P.state);
     k_cg_keep_best<<<vg, kBlock, 0, st>>>(P.x, P.x_best, P.n_u, P.state);
   }
-  k_cg_direction<<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.n_u, P.state);
+  if (P.precond)
+    enqueue_precond_direction(P, st);
+  else
+    k_cg_direction<<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.n_u, P.state);
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
 }
 
 void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, double delta,
-                      int warm) {
+                      int warm, bool precond) {
   const bool mixed = P.desc.precision == DS_PREC_MIXED;
   // bb = b . b
   enqueue_dot(P, st, P.b, P.b, P.n_u, &P.state->bb);
   k_set_state<<<1, 1, 0, st>>>(P.state, tol, max_iter, mixed ? 1 : 0, delta, P.refresh_max,
-                               P.drift_ratio, P.accurate_start, P.stall_iters);
+                               P.drift_ratio, P.accurate_start, P.stall_iters,
+                               precond && P.precond ? 1 : 0);
   if (warm) {
     cudaMemsetAsync(P.t, 0, sizeof(double) * P.n_u, st);
     enqueue_apply(P, st, true, P.x, P.t, Gate{nullptr, nullptr});
   }
   k_cg_start<<<vec_grid(P, P.n_u), kBlock, 0, st>>>(P.x, P.r, P.p, P.q, P.b, P.t, warm, P.n_u,
                                                      P.red, P.counters, P.state, P.x_best);
+  if (precond && P.precond) enqueue_precond_direction(P, st);  // the first direction z_0
 }
 
 }  // namespace ds

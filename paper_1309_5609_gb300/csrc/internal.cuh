@@ -107,9 +107,17 @@ struct CgState {
   double rr_progress;  // the residual at the last 10x improvement
   int progress_iter;   // ... and its iteration
   int stall_iters;     // stop when no 10x improvement for this many iterations (0 = never)
+  // preconditioned CG (z = the preconditioned residual)
+  int precond;         // 0: none (z = r); 1: D^-1; 2: D^-1 + coarse correction
+  int pad2;
+  double rz;           // r . z of the current residual
+  double rz_old;       // ... before the last update (for beta)
+  double rdr;          // r . D^-1 r (the coarse part is added by the coarse kernel)
 };
 
 enum ErrBits { ERR_PIX = 1, ERR_NAN = 2 };
+
+constexpr int kPcSlots = 2;  // coarse cells kept per baseline by the two-level preconditioner
 
 struct Plan {
   ds_desc desc;
@@ -203,6 +211,20 @@ struct Plan {
   float4* xd4;              // [2][n_b] split baselines: hi parts, then lo parts
   int bin_order;            // run-length plans: 1 = bin pixel-major (default), 0 = in time order
   int pm_pending;           // the copy is being built on the side stream: unusable until pm_join
+  int rescan_samples;       // run-length plans: the rescans read the time-ordered samples (dense
+                            // runs: a record per run costs more than 12 bytes per sample)
+  // preconditioner of the CG (precond.cu): 0 none, 1 D^-1 (valid samples per
+  // baseline), 2 two-level (D^-1 plus a coarse space of large-scale sky modes)
+  int precond;
+  int pc_nside;             // the coarse space has 12 pc_nside^2 cells
+  int pc_built;             // coarse space and E^+ built for this plan
+  int pc_n;                 // coarse columns (kept cells x n_c)
+  int pc_cells;             // kept cells
+  int32_t* pc_cell;         // [n_b][kPcSlots] kept-cell number of each slot, -1 = none
+  float* pc_val;            // [n_o][n_b][kPcSlots][n_c] entries of R
+  double* pc_einv;          // [pc_n][pc_n] generalised inverse of E = R^T A R
+  double* pc_u;             // [pc_n] R^T r, kept at zero between uses
+  double* pc_c;             // [pc_n] coarse correction E^+ R^T r
   cudaStream_t side_stream; // builds the pixel-major copy beside the first right-hand side
   cudaEvent_t side_ev[2];   // records ready (plan stream) / copy built (side stream)
 };
@@ -225,6 +247,8 @@ ds_status pm_ensure(Plan& P);
 // next; pm_join makes the plan's stream wait for it
 ds_status pm_begin(Plan& P, bool* started);
 ds_status pm_join(Plan& P, bool started);
+void pm_release(Plan& P, cudaStream_t st);
+void rl_release(Plan& P, cudaStream_t st);
 // runs_pm.cu: the binning pass over the pixel-major copy (one warp per pixel, no atomics)
 bool pm_ready(const Plan& P);
 void launch_bin_pm(const Plan& P, cudaStream_t st, Gate g);
@@ -274,6 +298,18 @@ void enqueue_map(const Plan& P, cudaStream_t st, const void* y, const double* a,
 
 // plan.cu
 ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid);
+
+// precond.cu: coarse space and coarse matrix of the two-level preconditioner
+__host__ __device__ int coarse_cell(int64_t p, int64_t nside, int64_t nc);
+ds_status pc_build(Plan& P);
+// builds the coarse space, first making (and afterwards freeing) the run records
+// and their pixel-major copy when the plan's operator does not keep them
+ds_status pc_prepare(Plan& P);
+void pc_free(Plan& P, cudaStream_t st);
+bool pc_ready(const Plan& P);
+// cg.cu: the preconditioner's kernels of one CG step (restrict, coarse solve,
+// new direction), gated by the CG state
+void enqueue_precond_direction(const Plan& P, cudaStream_t st);
 
 }  // namespace ds
 

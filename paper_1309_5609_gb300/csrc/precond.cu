@@ -1,0 +1,643 @@
+// Two-level preconditioner of the destriping CG: construction of the coarse
+// space and of its coarse matrix (the per-iteration kernels are in cg.cu).
+//
+// The paper solves the destriping equation (Sect. 3) with an unpreconditioned
+// Krylov method (GMRES in Sect. 4, CG named as the alternative).  With short
+// baselines the slow modes of A = F~^T Z F~ are baseline patterns that look like
+// large-scale sky: offsets a with F~ a close to A_p m for a map m that is smooth
+// over one baseline's sweep, which the map absorbs almost entirely.  A coarse
+// space spans them.  The sphere is cut into cells (coarse_cell below), and the
+// coarse column (k, c) holds, per baseline, the average over the baseline's
+// valid samples of row component c restricted to the samples in cell k:
+//
+//     R[(o,b), (k,c)] = (1 / n_b) sum_{t in b, cell(p(t)) = k} v(t) w_{o,c}(t),
+//
+// the best baseline fit of the map that is 1 on component c of cell k.  A
+// baseline keeps at most kPcSlots cells (the ones holding most of its samples;
+// any R gives a valid preconditioner, and the coarse matrix below is built from
+// the R actually stored).  The preconditioner is additive:
+//
+//     z = D^-1 r + R E^+ R^T r,   D = diag(n_b),   E = R^T A R,
+//
+// with E = R^T D R - (K R)^T M^-1 (K R), K = A_p^T V F~: the first term from one
+// pass over the baselines, the second from one pass over the pixel-major run
+// records (one warp per pixel sums (K R)_p in registers and adds
+// (K R)_p^T M_p^-1 (K R)_p into E).  E^+ is a generalised inverse by the sweep
+// operator, skipping pivots that have lost all but a 1e-10 share of their
+// diagonal; the I null mode (a common offset of the I-carrying outputs, which
+// R reproduces) gets a rank-one term so that it is swept like the rest.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+#include "rows.cuh"
+
+namespace ds {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kCand = 4;      // cells a baseline can hold while its samples are read
+constexpr int kWarpCells = 8; // cells of one pixel's baselines merged per warp
+
+// Floor of the square root of x >= 0 (exact for x < 2^52).
+__device__ __forceinline__ int64_t isqrt64(int64_t x) {
+  int64_t r = (int64_t)sqrtf((float)x);
+  while (r * r > x) --r;
+  while ((r + 1) * (r + 1) <= x) ++r;
+  return r;
+}
+
+}  // namespace
+
+// Coarse cell of a HEALPix RING pixel p at resolution nside.  Fine ring i goes
+// to the nearest of the 4 nc - 1 coarse rings (the coarse ring k lies at the
+// colatitude of fine ring k nside / nc), and within it to one of the coarse
+// ring's sectors of equal longitude width (4k, 4nc or 4(4nc - k) of them, as in
+// a HEALPix grid of resolution nc).  Cells are numbered ring by ring: 12 nc^2 in
+// all, compact regions of about (60 / nc) degrees.
+__host__ __device__ int coarse_cell(int64_t p, int64_t nside, int64_t nc) {
+  const int64_t N = nside, npix = 12 * N * N, ncap = 2 * N * (N - 1);
+  int64_t i, j, nring, twice_shift;
+  if (p < ncap) {  // north cap: ring i has 4 i pixels, centres at (j + 1/2) 2 pi / 4i
+#ifdef __CUDA_ARCH__
+    i = (1 + isqrt64(1 + 2 * p)) >> 1;
+#else
+    i = (1 + (int64_t)std::sqrt((double)(1 + 2 * p))) >> 1;
+    while (2 * i * (i - 1) > p) --i;
+    while (2 * (i + 1) * i <= p) ++i;
+#endif
+    j = p - 2 * i * (i - 1);
+    nring = 4 * i;
+    twice_shift = 1;
+  } else if (p < npix - ncap) {  // equatorial belt: 4N pixels, shift alternates
+    const int64_t q = p - ncap;
+    i = q / (4 * N) + N;
+    j = q - (i - N) * 4 * N;
+    nring = 4 * N;
+    twice_shift = (i - N + 1) & 1;
+  } else {  // south cap, mirrored
+    const int64_t q = npix - 1 - p;
+#ifdef __CUDA_ARCH__
+    const int64_t ii = (1 + isqrt64(1 + 2 * q)) >> 1;
+#else
+    int64_t ii = (1 + (int64_t)std::sqrt((double)(1 + 2 * q))) >> 1;
+    while (2 * ii * (ii - 1) > q) --ii;
+    while (2 * (ii + 1) * ii <= q) ++ii;
+#endif
+    i = 4 * N - ii;
+    j = 4 * ii - 1 - (q - 2 * ii * (ii - 1));
+    nring = 4 * ii;
+    twice_shift = 1;
+  }
+  int64_t k = (2 * i * nc + N) / (2 * N);
+  if (k < 1) k = 1;
+  if (k > 4 * nc - 1) k = 4 * nc - 1;
+  int64_t nk, off;
+  if (k < nc) {
+    nk = 4 * k;
+    off = 2 * k * (k - 1);
+  } else if (k <= 3 * nc) {
+    nk = 4 * nc;
+    off = 2 * nc * (nc - 1) + (k - nc) * 4 * nc;
+  } else {
+    const int64_t kk = 4 * nc - k;
+    nk = 4 * kk;
+    off = 12 * nc * nc - 2 * kk * (kk + 1);
+  }
+  int64_t sec = ((2 * j + twice_shift) * nk) / (2 * nring);
+  if (sec >= nk) sec = nk - 1;
+  return (int)(off + sec);
+}
+
+namespace {
+
+__global__ void __launch_bounds__(kBlock) k_pc_cell_table(int32_t* __restrict__ cell_of,
+                                                          int64_t npix, int64_t nside, int64_t nc) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride)
+    cell_of[p] = coarse_cell(p, nside, nc);
+}
+
+// One thread per baseline: the cells its valid samples fall in (up to kCand, in
+// order of appearance) with each output's row sums per cell; the kPcSlots cells
+// with most samples are kept, their sums divided by the baseline's valid count.
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ pix,
+                                                    const float* __restrict__ cc,
+                                                    const float* __restrict__ ss,
+                                                    const int32_t* __restrict__ cell_of,
+                                                    const int32_t* __restrict__ nvalid,
+                                                    int64_t n_t, int64_t L, int64_t n_b,
+                                                    KindsArg kk, int32_t* __restrict__ slot_cell,
+                                                    float* __restrict__ slot_val,
+                                                    int32_t* __restrict__ used) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += stride) {
+    int id[kCand];
+    int cnt[kCand];
+    float sum[kCand][NO][NC];
+#pragma unroll
+    for (int j = 0; j < kCand; ++j) {
+      id[j] = -1;
+      cnt[j] = 0;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) sum[j][o][c] = 0.f;
+    }
+    const int64_t t1 = (b + 1) * L < n_t ? (b + 1) * L : n_t;
+    for (int64_t t = b * L; t < t1; ++t) {
+      const int p = pix[t];
+      if (p < 0) continue;
+      const int k = __ldg(cell_of + p);
+      const float c = cc[t], s = ss[t];
+      bool placed = false;
+#pragma unroll
+      for (int j = 0; j < kCand; ++j) {
+        if (!placed && (id[j] == k || id[j] < 0)) {
+          id[j] = k;
+          cnt[j] += 1;
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+            if (o < n_o) row_bin<NC, float>(K::kind(o, kk), c, s, 1.f, sum[j][o]);
+          placed = true;
+        }
+      }
+    }
+    const int nv = nvalid[b];
+    const float inv = nv > 0 ? 1.f / (float)nv : 0.f;
+    // the kPcSlots cells with most samples, in decreasing order
+#pragma unroll
+    for (int s = 0; s < kPcSlots; ++s) {
+      int best = -1, bc = 0;
+#pragma unroll
+      for (int j = 0; j < kCand; ++j)
+        if (id[j] >= 0 && cnt[j] > bc) {
+          best = j;
+          bc = cnt[j];
+        }
+      int cell = -1;
+      float v[NO][NC];
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[o][c] = 0.f;
+#pragma unroll
+      for (int j = 0; j < kCand; ++j)
+        if (j == best) {
+          cell = id[j];
+          cnt[j] = 0;
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[o][c] = sum[j][o][c] * inv;
+        }
+      slot_cell[b * kPcSlots + s] = cell;
+      if (cell >= 0) used[cell] = 1;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < n_o)
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            slot_val[(((int64_t)o * n_b + b) * kPcSlots + s) * NC + c] = v[o][c];
+    }
+  }
+}
+
+// Cell numbers to kept-cell numbers (-1 stays -1).
+__global__ void __launch_bounds__(kBlock) k_pc_remap(int32_t* __restrict__ slot_cell, int64_t n,
+                                                     const int32_t* __restrict__ cmap) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int c = slot_cell[i];
+    slot_cell[i] = c >= 0 ? cmap[c] : -1;
+  }
+}
+
+// E += R^T D R: per unknown (o, b), n_b times the outer product of its R row.
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_pc_E_diag(const int32_t* __restrict__ slot_cell,
+                                                      const float* __restrict__ slot_val,
+                                                      const int32_t* __restrict__ nvalid,
+                                                      int64_t n_b, int n_o, int n,
+                                                      double* __restrict__ E) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_u = (int64_t)n_o * n_b;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_u; u += stride) {
+    const int64_t b = u % n_b;
+    const int nv = nvalid[b];
+    if (nv <= 0) continue;
+    int col[kPcSlots * NC];
+    double val[kPcSlots * NC];
+#pragma unroll
+    for (int s = 0; s < kPcSlots; ++s) {
+      const int cell = slot_cell[b * kPcSlots + s];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        col[s * NC + c] = cell >= 0 ? cell * NC + c : -1;
+        val[s * NC + c] = cell >= 0 ? (double)slot_val[(u * kPcSlots + s) * NC + c] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < kPcSlots * NC; ++a) {
+      if (col[a] < 0 || val[a] == 0.0) continue;
+#pragma unroll
+      for (int e = 0; e < kPcSlots * NC; ++e) {
+        if (col[e] < 0 || val[e] == 0.0) continue;
+        atomicAdd(E + (int64_t)col[a] * n + col[e], (double)nv * val[a] * val[e]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float f4_get(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// E -= (K R)^T M^-1 (K R), one warp per pixel over its pixel-major runs.  A run
+// (count n, sum cos, sum sin, baseline b) is one entry of K: the row sums k_o of
+// each output on the pixel's components.  (K R)_p[c'][(cell, c)] =
+// sum over runs and outputs of k_o[c'] R[(o,b), (cell, c)].  Each lane sums its
+// runs for up to kCand cells in registers; the warp merges the lanes' cells in
+// shared memory and adds the pixel's term into E.
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict__ off,
+                                                     const float4* __restrict__ rec,
+                                                     const int32_t* __restrict__ slot_cell,
+                                                     const float* __restrict__ slot_val,
+                                                     const double* __restrict__ minv,
+                                                     const uint8_t* __restrict__ mask,
+                                                     int64_t npix, int64_t n_b, KindsArg kk,
+                                                     int n, double* __restrict__ E) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO, NM = NC * (NC + 1) / 2;
+  const int n_o = K::n_o(kk);
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  __shared__ int s_id[kBlock / 32][kWarpCells];
+  __shared__ double s_kr[kBlock / 32][kWarpCells][NC][NC];
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; p < npix; p += warps) {
+    if (!mask[p]) continue;  // warp-uniform
+    const uint32_t beg = __ldg(off + p), end = __ldg(off + p + 1);
+    if (beg == end) continue;
+    int id[kCand];
+    float kr[kCand][NC][NC];
+#pragma unroll
+    for (int j = 0; j < kCand; ++j) {
+      id[j] = -1;
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) kr[j][a][c] = 0.f;
+    }
+    for (uint32_t i = beg + lane; i < end; i += 32) {
+      const float4 r = __ldg(rec + i);
+      const int64_t b = __float_as_int(r.w);
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        if (o >= n_o) continue;
+        float kv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) kv[c] = 0.f;
+        // the output's row summed over the run (z = 1)
+        {
+          using F = Frame<NC>;
+          const int kind = K::kind(o, kk);
+          if (kind == DS_KIND_I) {
+            if constexpr (F::I >= 0) kv[F::I] = r.x;
+          } else if (kind == DS_KIND_Q) {
+            if constexpr (F::Q >= 0) { kv[F::Q] = r.y; kv[F::U] = r.z; }
+          } else if (kind == DS_KIND_U) {
+            if constexpr (F::Q >= 0) { kv[F::Q] = -r.z; kv[F::U] = r.y; }
+          } else {
+            if constexpr (F::I >= 0 && F::Q >= 0) { kv[F::I] = r.x; kv[F::Q] = r.y; kv[F::U] = r.z; }
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < kPcSlots; ++s) {
+          const int cell = __ldg(slot_cell + b * kPcSlots + s);
+          if (cell < 0) continue;
+          float rv[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            rv[c] = __ldg(slot_val + (((int64_t)o * n_b + b) * kPcSlots + s) * NC + c);
+          bool placed = false;
+#pragma unroll
+          for (int j = 0; j < kCand; ++j) {
+            if (!placed && (id[j] == cell || id[j] < 0)) {
+              id[j] = cell;
+#pragma unroll
+              for (int a = 0; a < NC; ++a)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) kr[j][a][c] = fmaf(kv[a], rv[c], kr[j][a][c]);
+              placed = true;
+            }
+          }
+        }
+      }
+    }
+    // merge the lanes' cells: the warp's table of distinct cells
+    if (lane < kWarpCells) s_id[wib][lane] = -1;
+    __syncwarp();
+    int slot[kCand];
+#pragma unroll
+    for (int j = 0; j < kCand; ++j) {
+      slot[j] = -1;
+      if (id[j] < 0) continue;
+      for (int t = 0; t < kWarpCells; ++t) {
+        const int old = atomicCAS(&s_id[wib][t], -1, id[j]);
+        if (old == -1 || old == id[j]) {
+          slot[j] = t;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    int ncell = 0;
+    while (ncell < kWarpCells && s_id[wib][ncell] >= 0) ++ncell;
+    // warp sums of every (cell, a, c) entry
+    for (int t = 0; t < ncell; ++t) {
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          float v = 0.f;
+#pragma unroll
+          for (int j = 0; j < kCand; ++j)
+            if (slot[j] == t) v += kr[j][a][c];
+          for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(full, v, d);
+          if (lane == 0) s_kr[wib][t][a][c] = v;
+        }
+    }
+    __syncwarp();
+    // the pixel's M^-1 (packed symmetric)
+    double mi[NC][NC];
+    {
+      const double* mp = minv + p * NM;
+      if constexpr (NC == 1) {
+        mi[0][0] = mp[0];
+      } else if constexpr (NC == 2) {
+        mi[0][0] = mp[0]; mi[0][1] = mi[1][0] = mp[1]; mi[1][1] = mp[2];
+      } else {
+        mi[0][0] = mp[0]; mi[0][1] = mi[1][0] = mp[1]; mi[0][2] = mi[2][0] = mp[2];
+        mi[1][1] = mp[3]; mi[1][2] = mi[2][1] = mp[4]; mi[2][2] = mp[5];
+      }
+    }
+    const int m = ncell * NC;
+    for (int q = lane; q < m * m; q += 32) {
+      const int e1 = q / m, e2 = q - (q / m) * m;
+      const int t1 = e1 / NC, c1 = e1 - t1 * NC, t2 = e2 / NC, c2 = e2 - t2 * NC;
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int a2 = 0; a2 < NC; ++a2)
+          v += s_kr[wib][t1][a][c1] * mi[a][a2] * s_kr[wib][t2][a2][c2];
+      if (v != 0.0)
+        atomicAdd(E + (int64_t)(s_id[wib][t1] * NC + c1) * n + s_id[wib][t2] * NC + c2, -v);
+    }
+    __syncwarp();
+  }
+}
+
+// Rank-one term mu/m on every pair of the m I-component columns.
+__global__ void k_pc_null_term(double* __restrict__ E, int n, int nc, int ci, int cells, double mu) {
+  const int64_t total = (int64_t)cells * cells;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+    const int64_t a = q / cells, b = q - (q / cells) * cells;
+    E[(a * nc + ci) * n + b * nc + ci] += mu / (double)cells;
+  }
+}
+
+// One step of the sweep operator on pivot k (out = sweep_k(in)); a pivot whose
+// value has fallen to tol_rel of its original diagonal is skipped (in copied to
+// out) and flagged.
+__global__ void __launch_bounds__(kBlock) k_pc_sweep(const double* __restrict__ in,
+                                                     double* __restrict__ out, int n, int k,
+                                                     const double* __restrict__ diag0,
+                                                     double tol_rel, int32_t* __restrict__ skipped) {
+  __shared__ double s_inv;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    const double d = in[(int64_t)k * n + k];
+    s_skip = !(d > tol_rel * diag0[k]);
+    s_inv = s_skip ? 0.0 : 1.0 / d;
+    if (s_skip && blockIdx.x == 0) skipped[k] = 1;
+  }
+  __syncthreads();
+  const double inv = s_inv;
+  const bool skip = s_skip != 0;
+  const int64_t total = (int64_t)n * n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+    const int64_t i = q / n, j = q - (q / n) * n;
+    double v = in[q];
+    if (!skip) {
+      if (i == k && j == k) v = -inv;
+      else if (i == k || j == k) v = v * inv;
+      else v = v - in[i * n + k] * in[(int64_t)k * n + j] * inv;
+    }
+    out[q] = v;
+  }
+}
+
+// E^+ = -(swept matrix) with the rows and columns of skipped pivots set to 0.
+__global__ void __launch_bounds__(kBlock) k_pc_finish(const double* __restrict__ in,
+                                                      double* __restrict__ out, int n,
+                                                      const int32_t* __restrict__ skipped) {
+  const int64_t total = (int64_t)n * n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+    const int64_t i = q / n, j = q - (q / n) * n;
+    out[q] = (skipped[i] || skipped[j]) ? 0.0 : -in[q];
+  }
+}
+
+__global__ void k_pc_diag(const double* __restrict__ E, double* __restrict__ d, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    d[i] = E[(int64_t)i * n + i];
+}
+
+}  // namespace
+
+void pc_free(Plan& P, cudaStream_t st) {
+  void** held[] = {reinterpret_cast<void**>(&P.pc_cell), reinterpret_cast<void**>(&P.pc_val),
+                   reinterpret_cast<void**>(&P.pc_einv), reinterpret_cast<void**>(&P.pc_u),
+                   reinterpret_cast<void**>(&P.pc_c)};
+  for (void** h : held)
+    if (*h != nullptr) {
+      cudaFreeAsync(*h, st);
+      *h = nullptr;
+    }
+  P.pc_n = 0;
+  P.pc_cells = 0;
+  P.pc_built = 0;
+}
+
+bool pc_ready(const Plan& P) { return P.precond == 2 && P.pc_built && P.pc_n > 0; }
+
+// Builds the coarse space and E^+ on the plan's stream (synchronises it twice).
+// Needs the pixel-major copy of the run records (pm_ready).
+ds_status pc_build(Plan& P) {
+  if (P.pc_built) return DS_OK;
+  if (P.pm_rec == nullptr || P.pm_pending) {  // no pixel-major runs: D^-1 alone
+    P.pc_built = 1;
+    return DS_OK;
+  }
+  cudaStream_t st = P.stream;
+  const int64_t nc = P.pc_nside < P.desc.nside ? P.pc_nside : P.desc.nside;
+  const int64_t ncell = 12 * nc * nc;
+  int32_t *cell_of = nullptr, *used = nullptr, *cmap = nullptr, *skipped = nullptr;
+  double *E = nullptr, *E2 = nullptr, *diag0 = nullptr;
+  auto fail = [&](cudaError_t e) {
+    void* tmp[] = {cell_of, used, cmap, skipped, E, E2, diag0};
+    for (void* t : tmp)
+      if (t) cudaFreeAsync(t, st);
+    pc_free(P, st);
+    return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
+  };
+  cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(&cell_of), sizeof(int32_t) * P.npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&used), sizeof(int32_t) * ncell, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cmap), sizeof(int32_t) * ncell, false);
+  if (e == cudaSuccess)
+    e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_cell), sizeof(int32_t) * P.n_b * kPcSlots, true);
+  if (e == cudaSuccess)
+    e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_val),
+                   sizeof(float) * P.n_u * kPcSlots * P.n_c, true);
+  if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, sizeof(int32_t) * ncell, st);
+  if (e != cudaSuccess) return fail(e);
+  const int g_pix = stream_grid(P, P.npix, kBlock, 8);
+  k_pc_cell_table<<<g_pix, kBlock, 0, st>>>(cell_of, P.npix, P.desc.nside, nc);
+  const int g_b = stream_grid(P, P.n_b, kBlock, 8);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_pc_rows<KS><<<g_b, kBlock, 0, st>>>(P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b,
+                                          P.kinds, P.pc_cell, P.pc_val, used);
+  });
+  P.launches += 2;
+  e = cudaGetLastError();
+  // kept cells: numbered in cell order on the host
+  std::vector<int32_t> h_used(ncell), h_map(ncell, -1);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_used.data(), used, sizeof(int32_t) * ncell, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(e);
+  int kept = 0;
+  for (int64_t c = 0; c < ncell; ++c)
+    if (h_used[c]) h_map[c] = kept++;
+  const int n = kept * P.n_c;
+  if (n == 0) {  // nothing observed: the Jacobi part alone
+    void* tmp[] = {cell_of, used, cmap};
+    for (void* t : tmp) cudaFreeAsync(t, st);
+    pc_free(P, st);
+    P.pc_built = 1;
+    return DS_OK;
+  }
+  e = cudaMemcpyAsync(cmap, h_map.data(), sizeof(int32_t) * ncell, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_einv), sizeof(double) * n * n, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&E), sizeof(double) * n * n, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&E2), sizeof(double) * n * n, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&diag0), sizeof(double) * n, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&skipped), sizeof(int32_t) * n, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_u), sizeof(double) * n, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_c), sizeof(double) * n, true);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E, 0, sizeof(double) * n * n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.pc_u, 0, sizeof(double) * n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.pc_c, 0, sizeof(double) * n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(skipped, 0, sizeof(int32_t) * n, st);
+  if (e != cudaSuccess) return fail(e);
+  k_pc_remap<<<g_b, kBlock, 0, st>>>(P.pc_cell, P.n_b * kPcSlots, cmap);
+  const int g_u = stream_grid(P, P.n_u, kBlock, 8);
+  auto by_nc = [&](auto ncc) {
+    constexpr int NC = decltype(ncc)::value;
+    k_pc_E_diag<NC><<<g_u, kBlock, 0, st>>>(P.pc_cell, P.pc_val, P.nvalid, P.n_b, P.n_o, n, E);
+  };
+  if (P.n_c == 1) by_nc(std::integral_constant<int, 1>{});
+  else if (P.n_c == 2) by_nc(std::integral_constant<int, 2>{});
+  else by_nc(std::integral_constant<int, 3>{});
+  const int g_w = stream_grid(P, P.npix * 32, kBlock, 8);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_pc_E_pix<KS><<<g_w, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pc_cell, P.pc_val, P.minv,
+                                           P.mask, P.npix, P.n_b, P.kinds, n, E);
+  });
+  P.launches += 3;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(e);
+  // the I null mode: rank-one term at the mean diagonal, on the I-component columns
+  if (P.has_I_outputs) {
+    std::vector<double> hd(n);
+    k_pc_diag<<<(n + 255) / 256, 256, 0, st>>>(E, diag0, n);
+    e = cudaMemcpyAsync(hd.data(), diag0, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(e);
+    double mu = 0.0;
+    for (double v : hd) mu += v;
+    mu /= (double)n;
+    const int ci = 0;  // I is the first component whenever outputs carry I
+    k_pc_null_term<<<stream_grid(P, (int64_t)kept * kept, kBlock, 8), kBlock, 0, st>>>(
+        E, n, P.n_c, ci, kept, mu);
+    P.launches += 2;
+  }
+  k_pc_diag<<<(n + 255) / 256, 256, 0, st>>>(E, diag0, n);
+  // sweep every pivot, ping-ponging between E and E2
+  const int g_s = stream_grid(P, (int64_t)n * n, kBlock, 8);
+  double* a = E;
+  double* bbuf = E2;
+  for (int k = 0; k < n; ++k) {
+    k_pc_sweep<<<g_s, kBlock, 0, st>>>(a, bbuf, n, k, diag0, 1e-10, skipped);
+    double* t = a;
+    a = bbuf;
+    bbuf = t;
+  }
+  k_pc_finish<<<g_s, kBlock, 0, st>>>(a, P.pc_einv, n, skipped);
+  P.launches += n + 2;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(e);
+  void* tmp[] = {cell_of, used, cmap, skipped, E, E2, diag0};
+  for (void* t : tmp) cudaFreeAsync(t, st);
+  P.pc_n = n;
+  P.pc_cells = kept;
+  P.pc_built = 1;
+  return DS_OK;
+}
+
+ds_status pc_prepare(Plan& P) {
+  if (P.pc_built) return DS_OK;
+  cudaStream_t st = P.stream;
+  const bool runs_kept = P.layout == 2 && P.desc.precision == DS_PREC_MIXED;
+  bool made_runs = false, made_pm = false;
+  ds_status s = DS_OK;
+  if (P.pm_rec == nullptr) {
+    if (P.rl_rec == nullptr) {
+      s = rl_build(P);
+      made_runs = true;
+    }
+    if (s == DS_OK) {
+      s = pm_build(P, st);
+      made_pm = true;
+    }
+  }
+  if (s == DS_OK) s = pc_build(P);
+  // records the operator does not read are given back once E is built
+  if (made_pm && !(runs_kept && P.bin_order == 1)) pm_release(P, st);
+  if (made_runs && !runs_kept) rl_release(P, st);
+  if (s == DS_ENOMEM) {  // no room for the coarse space: D^-1 alone
+    cudaGetLastError();
+    pc_free(P, st);
+    P.pc_built = 1;
+    s = DS_OK;
+  }
+  if (s != DS_OK) return s;
+  return cudaStreamSynchronize(st) == cudaSuccess ? DS_OK : DS_ECUDA;
+}
+
+}  // namespace ds

@@ -451,7 +451,7 @@ ds_status pm_build(Plan& P, cudaStream_t st) {
 }
 
 // Frees a pixel-major copy (built or not) ordered after the work on st.
-static void pm_release(Plan& P, cudaStream_t st) {
+void pm_release(Plan& P, cudaStream_t st) {
   void** held[] = {reinterpret_cast<void**>(&P.pm_off), reinterpret_cast<void**>(&P.pm_rec),
                    reinterpret_cast<void**>(&P.pm_lo), reinterpret_cast<void**>(&P.x4),
                    reinterpret_cast<void**>(&P.xd4)};
@@ -517,6 +517,17 @@ ds_status pm_join(Plan& P, bool started) {
   }
   P.pm_pending = 0;
   return DS_OK;
+}
+
+void rl_release(Plan& P, cudaStream_t st) {
+  void** held[] = {reinterpret_cast<void**>(&P.rl_rec), reinterpret_cast<void**>(&P.rl_b),
+                   reinterpret_cast<void**>(&P.rl_df), reinterpret_cast<void**>(&P.rl_tiles)};
+  for (void** h : held)
+    if (*h != nullptr) {
+      cudaFreeAsync(*h, st);
+      *h = nullptr;
+    }
+  P.rl_n = 0;
 }
 
 ds_status rl_build(Plan& P) {

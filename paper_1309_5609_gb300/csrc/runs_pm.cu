@@ -53,12 +53,24 @@ __device__ __forceinline__ float f4_at(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+// Baselines of run record r: all outputs' packed per baseline (x4), or, with one
+// output, the float32 baselines themselves (4 bytes a gather instead of 16).
+template <bool ONE>
+__device__ __forceinline__ float4 pm_baselines(const void* __restrict__ xb, const float4& r) {
+  const int b = __float_as_int(r.w);
+  if constexpr (ONE) {
+    return make_float4(__ldg(static_cast<const float*>(xb) + b), 0.f, 0.f, 0.f);
+  } else {
+    return __ldg(static_cast<const float4*>(xb) + b);
+  }
+}
+
 // bins[p] = sum over the runs of p of (row sums) x[o][b], float32.  Each lane
 // takes two runs per step with both loads issued first.
-template <int KS>
+template <int KS, bool ONE>
 __global__ void __launch_bounds__(kBlock) k_pm_bin(const uint32_t* __restrict__ off,
                                                    const float4* __restrict__ rec,
-                                                   const float4* __restrict__ x4,
+                                                   const void* __restrict__ xb,
                                                    float* __restrict__ bins, int64_t npix,
                                                    KindsArg kk, Gate g) {
   if (gate_closed(g)) return;
@@ -79,8 +91,8 @@ __global__ void __launch_bounds__(kBlock) k_pm_bin(const uint32_t* __restrict__ 
       const bool two = i + 32 < end;
       const float4 r0 = __ldcs(rec + i);
       const float4 r1 = two ? __ldcs(rec + i + 32) : zero;
-      const float4 z0 = __ldg(x4 + __float_as_int(r0.w));
-      const float4 z1 = two ? __ldg(x4 + __float_as_int(r1.w)) : zero;
+      const float4 z0 = pm_baselines<ONE>(xb, r0);
+      const float4 z1 = two ? pm_baselines<ONE>(xb, r1) : zero;
 #pragma unroll
       for (int o = 0; o < NO; ++o)
         if (o < n_o) run_bin<NC>(K::kind(o, kk), r0.x, r0.y, r0.z, f4_at(z0, o), acc);
@@ -105,12 +117,14 @@ __global__ void __launch_bounds__(kBlock) k_pm_bin(const uint32_t* __restrict__ 
 
 // The accurate variant: double-float run sums (high parts from the record, low
 // parts beside it) and baselines, compensated sums (renormalised every step),
-// float64 pixel sums.
-template <int KS>
+// float64 pixel sums.  Baselines: hi parts xd4[b], lo parts xd4[n_b + b]; with one
+// output (ONE), the split pairs xdf[b] themselves.
+template <int KS, bool ONE>
 __global__ void __launch_bounds__(kBlock) k_pm_bin_df(const uint32_t* __restrict__ off,
                                                       const float4* __restrict__ rec,
                                                       const float2* __restrict__ lo,
                                                       const float4* __restrict__ xd4,
+                                                      const float2* __restrict__ xdf,
                                                       double* __restrict__ bins, int64_t npix,
                                                       int64_t n_b, KindsArg kk, Gate g) {
   if (gate_closed(g)) return;
@@ -130,7 +144,15 @@ __global__ void __launch_bounds__(kBlock) k_pm_bin_df(const uint32_t* __restrict
       const float4 r = __ldcs(rec + i);
       const float2 l = __ldcs(lo + i);
       const int b = __float_as_int(r.w);
-      const float4 zh = __ldg(xd4 + b), zl = __ldg(xd4 + n_b + b);
+      float4 zh, zl;
+      if constexpr (ONE) {
+        const float2 z = __ldg(xdf + b);
+        zh = make_float4(z.x, 0.f, 0.f, 0.f);
+        zl = make_float4(z.y, 0.f, 0.f, 0.f);
+      } else {
+        zh = __ldg(xd4 + b);
+        zl = __ldg(xd4 + n_b + b);
+      }
 #pragma unroll
       for (int o = 0; o < NO; ++o)
         if (o < n_o)
@@ -165,22 +187,36 @@ bool pm_ready(const Plan& P) {
 
 // P.x32 holds the float32 baselines of this pass (k_to_f32)
 void launch_bin_pm(const Plan& P, cudaStream_t st, Gate g) {
-  k_pm_pack_x<<<stream_grid(P, P.n_b, kBlock, 8), kBlock, 0, st>>>(P.x32, P.x4, P.n_b, P.n_o, g);
+  const bool one = P.n_o == 1;
+  if (!one)
+    k_pm_pack_x<<<stream_grid(P, P.n_b, kBlock, 8), kBlock, 0, st>>>(P.x32, P.x4, P.n_b, P.n_o, g);
   const int grid = stream_grid(P, P.npix * 32, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_pm_bin<KS><<<grid, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.x4, P.bins32, P.npix, P.kinds, g);
+    if (one)
+      k_pm_bin<KS, true><<<grid, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.x32, P.bins32, P.npix,
+                                                  P.kinds, g);
+    else
+      k_pm_bin<KS, false><<<grid, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.x4, P.bins32, P.npix,
+                                                   P.kinds, g);
   });
 }
 
 // P.xdf holds the split baselines of this pass (launch_split_df)
 void launch_bin_pm_df(const Plan& P, cudaStream_t st, Gate g) {
-  k_pm_pack_xdf<<<stream_grid(P, P.n_b, kBlock, 8), kBlock, 0, st>>>(P.xdf, P.xd4, P.n_b, P.n_o, g);
+  const bool one = P.n_o == 1;
+  if (!one)
+    k_pm_pack_xdf<<<stream_grid(P, P.n_b, kBlock, 8), kBlock, 0, st>>>(P.xdf, P.xd4, P.n_b,
+                                                                       P.n_o, g);
   const int grid = stream_grid(P, P.npix * 32, kBlock, P.blocks_per_sm);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_pm_bin_df<KS><<<grid, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pm_lo, P.xd4, P.bins, P.npix,
-                                             P.n_b, P.kinds, g);
+    if (one)
+      k_pm_bin_df<KS, true><<<grid, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pm_lo, P.xd4, P.xdf,
+                                                     P.bins, P.npix, P.n_b, P.kinds, g);
+    else
+      k_pm_bin_df<KS, false><<<grid, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pm_lo, P.xd4, P.xdf,
+                                                      P.bins, P.npix, P.n_b, P.kinds, g);
   });
 }
 
