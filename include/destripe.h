@@ -182,6 +182,45 @@ ds_status destripe_run_host(const ds_desc* desc, const int32_t* h_pix, const flo
                             int32_t* h_hits, uint8_t* h_mask, int32_t* iters,
                             double* rel_resid);
 
+/* White-noise gap filling (Sect. 2, data description: flagged and missing samples
+ * are replaced by Gaussian white noise with the mean and standard deviation of the
+ * good samples of each day), in place, so that the destriper can run on a
+ * timeline of constant sampling with every sample valid.
+ *   desc       n_samples, n_outputs, precision (type of y) and stream are used
+ *   d_valid    uint8 [n_t], 1 = good sample, 0 = flagged (required)
+ *   block_len  samples per day (>= 1; the last block may be shorter)
+ *   seed       key of the random draws
+ *   d_y        [n_o][n_t] float64 (DS_PREC_FP64) or float32 (DS_PREC_MIXED), in/out:
+ *              each flagged sample of output o in day d becomes
+ *              mean + std * z (population statistics of the good samples of that
+ *              output and day; 0 when the day has none), z standard normal from
+ *              Philox4x32-10 (Salmon et al. 2011) with counter (t mod 2^32,
+ *              t div 2^32, o, 0) and key (seed mod 2^32, seed div 2^32), Box-Muller of
+ *              its first two words u0, u1: sqrt(-2 ln u0') cos(2 pi u1'), u' =
+ *              (u + 1/2) 2^-32.  Good samples are not written.
+ * Asynchronous on desc->stream; allocates a small table of day statistics. */
+ds_status destripe_gapfill(const ds_desc* desc, const uint8_t* d_valid, int64_t block_len,
+                           uint64_t seed, void* d_y);
+
+/* Amplitude spectra of the timelines y (d_a NULL) or of the baseline-removed
+ * y - F~ a (Sect. 6, frequency domain), per output.  The timeline is cut into
+ * floor(n_t / seg_len) segments of seg_len samples (the tail is dropped); the
+ * one-sided power spectral density P_k = 2 |X_k|^2 / (f_samp seg_len), averaged
+ * over segments (k = 0 and k = seg_len / 2 not doubled), gives the amplitude
+ * sqrt(P_k), averaged over n_bins bins of linearly growing length: with
+ * K = seg_len / 2, bin j (0-based) holds k = e_j + 1 .. e_{j+1},
+ * e_j = floor(K j (j + 1) / (n_bins (n_bins + 1))).  Samples are used as given
+ * (fill gaps first, destripe_gapfill).
+ *   d_y      timelines as for destripe_bin;  d_a  float64 [n_o][n_b] or NULL
+ *   seg_len  2 .. n_t;  n_bins >= 1 with n_bins (n_bins + 1) / 2 <= seg_len / 2
+ *   f_samp   sampling rate (Hz)
+ *   d_freq   float64 [n_bins] mean frequency of each bin, or NULL
+ *   d_amp    float64 [n_o][n_bins] mean amplitude (units of y per sqrt(Hz))
+ * Uses cuFFT; takes its work buffers from the plan's memory pool.  Synchronises
+ * the plan's stream. */
+ds_status destripe_spectrum(ds_plan_t plan, const void* d_y, const double* d_a, int64_t seg_len,
+                            int32_t n_bins, double f_samp, double* d_freq, double* d_amp);
+
 /* Kernel timing and launch counts of a plan (no counterpart in the paper; it
  * exists to measure the kernels against the HBM roofline).  While profiling is
  * enabled, the captured CG graph records CUDA events around the binning and
@@ -253,14 +292,16 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     (20 bytes per run); chosen when the records are requested above
  *                     0.6 runs per sample
  *   "precond"         preconditioner of the CG (no counterpart in the paper, which uses
- *                     unpreconditioned Krylov solvers): 0 = none (default); 1 = D^-1, the
- *                     valid samples of each baseline; 2 = two-level: D^-1 plus a coarse
- *                     correction R E^+ R^T on a space of large-scale sky modes (cells of
- *                     the sphere, "coarse_nside"), E = R^T A R built once per plan at its
- *                     first solve (from the pixel-major run records, made for the purpose
- *                     when the plan has none; synchronises).  The solution is the same;
- *                     the iterations are fewer where short baselines leave slow
- *                     sky-like modes
+ *                     unpreconditioned Krylov solvers): 0 = none; 1 = D^-1, the valid
+ *                     samples of each baseline; 2 = two-level (default): D^-1 plus a
+ *                     coarse correction R E^+ R^T on a space of large-scale sky modes
+ *                     (cells of the sphere, "coarse_nside"), E = R^T A R built once per
+ *                     plan at its first solve (from the pixel-major run records, made
+ *                     for the purpose when the plan has none; synchronises).  Where
+ *                     baselines sweep more than two cells for over a fifth of the valid
+ *                     samples (long baselines) the coarse space is not built and D^-1
+ *                     alone applies.  The solution is the same; the iterations are
+ *                     fewer where short baselines leave slow sky-like modes
  *   "coarse_nside"    two-level preconditioner: 12 coarse_nside^2 cells (power of two,
  *                     1..64, default 8; at most the map's nside); a change rebuilds E
  *   "rescan_rounds"   MIXED plans: rounds of 32 work items (runs, or 4-sample groups)

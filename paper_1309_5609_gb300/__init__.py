@@ -24,6 +24,7 @@ __all__ = [
     "Batch", "destripe_batch_create", "destripe_batch_add", "destripe_batch_step",
     "destripe_batch_slot_status", "destripe_batch_retire", "destripe_batch_tune",
     "destripe_batch_info", "destripe_batch_destroy", "destripe_batch_autotune", "components",
+    "destripe_gapfill", "destripe_spectrum",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -106,6 +107,10 @@ _SIGS = {
     "destripe_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ds_batch_tuning)]),
     "destripe_bin_noalloc": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P, _P, _P,
                                             _P]),
+    "destripe_gapfill": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, ctypes.c_int64,
+                                        ctypes.c_uint64, _P]),
+    "destripe_spectrum": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_double, _P, _P]),
     "destripe_run_host": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P,
                                          ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P,
                                          ctypes.POINTER(ctypes.c_int32),
@@ -321,6 +326,42 @@ def destripe_solve(plan: Plan, y, a, tol: float = 1e-10, max_iter: int = 10000,
     if st not in (DS_OK, DS_ENOCONV):
         raise DestripeError(st, "destripe_solve")
     return st, it.value, rr.value
+
+
+def destripe_gapfill(y, valid, *, block_len: int, seed: int, stream=None):
+    """Fill the flagged samples of y ([n_o, n_t] float32 or float64 CUDA tensor, in
+    place) with white noise of each day's good-sample mean and deviation."""
+    import torch
+    if y.dim() != 2:
+        raise ValueError("y must be [n_outputs, n_samples]")
+    n_o, n_t = y.shape
+    _check(valid, torch.uint8, n_t, "valid", y.device)
+    if y.dtype not in (torch.float32, torch.float64) or not y.is_contiguous() or not y.is_cuda:
+        raise TypeError("y must be a contiguous float32 or float64 CUDA tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream(y.device).cuda_stream
+    prec = "fp64" if y.dtype == torch.float64 else "mixed"
+    desc = _make_desc(n_t, 1, ("q",) * n_o, 1, prec, 0.0, stream)
+    st = load_library().destripe_gapfill(ctypes.byref(desc), _ptr(valid), int(block_len),
+                                         int(seed) & ((1 << 64) - 1), _ptr(y))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_gapfill")
+
+
+def destripe_spectrum(plan: Plan, y, a, *, seg_len: int, n_bins: int, f_samp: float):
+    """Binned amplitude spectra of y (a None) or y - F~ a; returns (freq [n_bins],
+    amp [n_o, n_bins]) float64 CUDA tensors."""
+    import torch
+    _check(y, plan.y_dtype, plan.n_o * plan.n_t, "y", plan.device)
+    if a is not None:
+        _check(a, torch.float64, plan.n_u, "a", plan.device)
+    freq = torch.empty(n_bins, dtype=torch.float64, device=plan.device)
+    amp = torch.empty((plan.n_o, n_bins), dtype=torch.float64, device=plan.device)
+    st = load_library().destripe_spectrum(plan.handle, _ptr(y), _ptr(a), int(seg_len),
+                                          int(n_bins), float(f_samp), _ptr(freq), _ptr(amp))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_spectrum")
+    return freq, amp
 
 
 def destripe_gauge(plan: Plan, a):

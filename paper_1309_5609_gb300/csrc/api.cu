@@ -310,7 +310,7 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->rescan_rounds = 0;
   P->bin_order = 1;
   P->samples_per_thread = 4;
-  P->precond = 0;
+  P->precond = 2;
   P->pc_nside = 8;
   cudaError_t e = cudaSuccess;
 #define DS_ALLOC(ptr, n) \

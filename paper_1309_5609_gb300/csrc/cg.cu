@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "cg_state.cuh"
+#include "df.cuh"
 #include "internal.cuh"
 
 namespace ds {
@@ -332,23 +333,26 @@ __global__ void __launch_bounds__(kBlock) k_cg_direction(double* __restrict__ p,
 // ---- preconditioned directions (precond.cu builds the coarse space) ----------------
 // z = D^-1 r (+ R E^+ R^T r), rz = r . z, p = z + beta p.  D^-1 is the float32
 // reciprocal of the valid samples of the unknown's baseline (0 without any), the
-// same in every kernel, so that the preconditioner is one fixed SPD operator.
+// same in every kernel.  The coarse part runs in float32 (R is stored in float32;
+// the residual enters R^T r rounded to float32, the correction R c is summed in
+// float32 and added to the float64 D^-1 r): GB300's float64 pipe is narrow, and
+// the float64 work of these kernels is kept to the few operations that feed r . z.
 
 __device__ __forceinline__ double pc_dinv(int nv) {
-  return nv > 0 ? (double)__frcp_rn((float)nv) : 0.0;
+  return nv > 0 ? f64_of_f32(__frcp_rn((float)nv)) : 0.0;
 }
 
 // Sums of val over each segment of lanes with equal consecutive keys, left in the
 // segment's first lane (keys need not be sorted: a key that comes back later in
 // the warp starts a new segment).
-__device__ __forceinline__ double seg_sum_to_head(int key, double val) {
+__device__ __forceinline__ float seg_sum_to_head(int key, float val) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int next = __shfl_down_sync(full, key, 1);
   bool stop = lane == 31 || next != key;  // the segment ends within [lane, lane + w)
 #pragma unroll
   for (int w = 1; w < 32; w <<= 1) {
-    const double v2 = __shfl_down_sync(full, val, w);
+    const float v2 = __shfl_down_sync(full, val, w);
     const bool s2 = __shfl_down_sync(full, stop, w);
     if (!stop) {
       val += v2;
@@ -383,8 +387,9 @@ __global__ void __launch_bounds__(kBlock) k_pc_restrict(const double* __restrict
       const bool in = b < n_b;
       const int64_t i = (int64_t)o * n_b + b;
       const double ri = in ? r[i] : 0.0;
-      acc += ri * ri * (in ? pc_dinv(nvalid[b]) : 0.0);
+      if (in) acc = fma(ri * pc_dinv(nvalid[b]), ri, acc);
       if (n > 0) {
+        const float rf = __double2float_rn(ri);
 #pragma unroll
         for (int s = 0; s < kPcSlots; ++s) {
           const int key = in ? cell[b * kPcSlots + s] : -1;
@@ -392,9 +397,9 @@ __global__ void __launch_bounds__(kBlock) k_pc_restrict(const double* __restrict
           const bool head = key >= 0 && (lane == 0 || kprev != key);
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            const double v = key >= 0 ? (double)val[(i * kPcSlots + s) * NC + c] * ri : 0.0;
-            const double tot = seg_sum_to_head(key, v);
-            if (head) atomicAdd(s_u + key * NC + c, tot);
+            const float v = key >= 0 ? val[(i * kPcSlots + s) * NC + c] * rf : 0.f;
+            const float tot = seg_sum_to_head(key, v);
+            if (head) atomicAdd(s_u + key * NC + c, f64_of_f32(tot));
           }
         }
       }
@@ -414,10 +419,11 @@ __global__ void __launch_bounds__(kBlock) k_pc_restrict(const double* __restrict
   }
 }
 
-// c = E^+ u (one warp per row), rz = r . D^-1 r + u . c; the last block clears u.
+// c = E^+ u (one warp per row; also rounded to float32 for the direction kernel),
+// rz = r . D^-1 r + u . c; the last block clears u.
 __global__ void __launch_bounds__(kBlock) k_pc_coarse(const double* __restrict__ einv,
                                                       double* __restrict__ u,
-                                                      double* __restrict__ c, int n,
+                                                      float* __restrict__ c, int n,
                                                       double* __restrict__ red, unsigned* ticket,
                                                       CgState* st) {
   if (st->done) return;
@@ -432,7 +438,7 @@ __global__ void __launch_bounds__(kBlock) k_pc_coarse(const double* __restrict__
     for (int j = lane; j < n; j += 32) s = fma(e[j], u[j], s);
     for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(full, s, d);
     if (lane == 0) {
-      c[row] = s;
+      c[row] = __double2float_rn(s);
       acc = fma(s, u[row], acc);
     }
   }
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(kBlock) k_pc_direction(double* __restrict__ p,
                                                          const int32_t* __restrict__ nvalid,
                                                          const int32_t* __restrict__ cell,
                                                          const float* __restrict__ val,
-                                                         const double* __restrict__ c,
+                                                         const float* __restrict__ c,
                                                          int64_t n_b, int n_o, int n,
                                                          const CgState* st) {
   if (st->done) return;
@@ -465,14 +471,16 @@ __global__ void __launch_bounds__(kBlock) k_pc_direction(double* __restrict__ p,
       const int64_t i = (int64_t)o * n_b + b;
       double z = pc_dinv(nvalid[b]) * r[i];
       if (n > 0) {
+        float zc = 0.f;
 #pragma unroll
         for (int s = 0; s < kPcSlots; ++s) {
           const int k = cell[b * kPcSlots + s];
           if (k < 0) continue;
 #pragma unroll
           for (int cc = 0; cc < NC; ++cc)
-            z = fma((double)val[(i * kPcSlots + s) * NC + cc], __ldg(c + k * NC + cc), z);
+            zc = fmaf(val[(i * kPcSlots + s) * NC + cc], __ldg(c + k * NC + cc), zc);
         }
+        z += f64_of_f32(zc);
       }
       p[i] = fma(beta, p[i], z);
       q[i] = 0.0;

@@ -224,7 +224,7 @@ struct Plan {
   float* pc_val;            // [n_o][n_b][kPcSlots][n_c] entries of R
   double* pc_einv;          // [pc_n][pc_n] generalised inverse of E = R^T A R
   double* pc_u;             // [pc_n] R^T r, kept at zero between uses
-  double* pc_c;             // [pc_n] coarse correction E^+ R^T r
+  float* pc_c;              // [pc_n] coarse correction E^+ R^T r, rounded to float32
   cudaStream_t side_stream; // builds the pixel-major copy beside the first right-hand side
   cudaEvent_t side_ev[2];   // records ready (plan stream) / copy built (side stream)
 };
@@ -301,7 +301,7 @@ ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid);
 
 // precond.cu: coarse space and coarse matrix of the two-level preconditioner
 __host__ __device__ int coarse_cell(int64_t p, int64_t nside, int64_t nc);
-ds_status pc_build(Plan& P);
+ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm);
 // builds the coarse space, first making (and afterwards freeing) the run records
 // and their pixel-major copy when the plan's operator does not keep them
 ds_status pc_prepare(Plan& P);

@@ -40,6 +40,7 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kCand = 4;      // cells a baseline can hold while its samples are read
 constexpr int kWarpCells = 8; // cells of one pixel's baselines merged per warp
+constexpr double kPcKeptMin = 0.8;  // share of valid samples the kept slots must hold
 
 // Floor of the square root of x >= 0 (exact for x < 2^52).
 __device__ __forceinline__ int64_t isqrt64(int64_t x) {
@@ -132,11 +133,13 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
                                                     int64_t n_t, int64_t L, int64_t n_b,
                                                     KindsArg kk, int32_t* __restrict__ slot_cell,
                                                     float* __restrict__ slot_val,
-                                                    int32_t* __restrict__ used) {
+                                                    int32_t* __restrict__ used,
+                                                    unsigned long long* __restrict__ kept_total) {
   using K = KSet<KS>;
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long kept_all = 0, valid_all = 0;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += stride) {
     int id[kCand];
     int cnt[kCand];
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
           bc = cnt[j];
         }
       int cell = -1;
+      kept_all += (unsigned long long)bc;
       float v[NO][NC];
 #pragma unroll
       for (int o = 0; o < NO; ++o)
@@ -206,6 +210,15 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
           for (int c = 0; c < NC; ++c)
             slot_val[(((int64_t)o * n_b + b) * kPcSlots + s) * NC + c] = v[o][c];
     }
+    valid_all += (unsigned long long)(nv > 0 ? nv : 0);
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    kept_all += __shfl_down_sync(0xffffffffu, kept_all, d);
+    valid_all += __shfl_down_sync(0xffffffffu, valid_all, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(kept_total, kept_all);
+    atomicAdd(kept_total + 1, valid_all);
   }
 }
 
@@ -483,21 +496,21 @@ void pc_free(Plan& P, cudaStream_t st) {
 
 bool pc_ready(const Plan& P) { return P.precond == 2 && P.pc_built && P.pc_n > 0; }
 
-// Builds the coarse space and E^+ on the plan's stream (synchronises it twice).
-// Needs the pixel-major copy of the run records (pm_ready).
-ds_status pc_build(Plan& P) {
+// Builds the coarse space and E^+ on the plan's stream (synchronises it).  The
+// second term of E reads the pixel-major copy of the run records; a plan whose
+// operator does not keep one gets it for the purpose (made_runs / made_pm) and
+// gives it back afterwards.
+ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
+  *made_runs = *made_pm = false;
   if (P.pc_built) return DS_OK;
-  if (P.pm_rec == nullptr || P.pm_pending) {  // no pixel-major runs: D^-1 alone
-    P.pc_built = 1;
-    return DS_OK;
-  }
   cudaStream_t st = P.stream;
   const int64_t nc = P.pc_nside < P.desc.nside ? P.pc_nside : P.desc.nside;
   const int64_t ncell = 12 * nc * nc;
   int32_t *cell_of = nullptr, *used = nullptr, *cmap = nullptr, *skipped = nullptr;
+  unsigned long long* kept = nullptr;  // samples in kept slots, valid samples
   double *E = nullptr, *E2 = nullptr, *diag0 = nullptr;
   auto fail = [&](cudaError_t e) {
-    void* tmp[] = {cell_of, used, cmap, skipped, E, E2, diag0};
+    void* tmp[] = {cell_of, used, cmap, skipped, E, E2, diag0, kept};
     for (void* t : tmp)
       if (t) cudaFreeAsync(t, st);
     pc_free(P, st);
@@ -511,7 +524,9 @@ ds_status pc_build(Plan& P) {
   if (e == cudaSuccess)
     e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_val),
                    sizeof(float) * P.n_u * kPcSlots * P.n_c, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&kept), sizeof(unsigned long long) * 2, false);
   if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, sizeof(int32_t) * ncell, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(kept, 0, sizeof(unsigned long long) * 2, st);
   if (e != cudaSuccess) return fail(e);
   const int g_pix = stream_grid(P, P.npix, kBlock, 8);
   k_pc_cell_table<<<g_pix, kBlock, 0, st>>>(cell_of, P.npix, P.desc.nside, nc);
@@ -519,26 +534,52 @@ ds_status pc_build(Plan& P) {
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     k_pc_rows<KS><<<g_b, kBlock, 0, st>>>(P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b,
-                                          P.kinds, P.pc_cell, P.pc_val, used);
+                                          P.kinds, P.pc_cell, P.pc_val, used, kept);
   });
   P.launches += 2;
   e = cudaGetLastError();
   // kept cells: numbered in cell order on the host
   std::vector<int32_t> h_used(ncell), h_map(ncell, -1);
+  unsigned long long h_kept[2] = {0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_used.data(), used, sizeof(int32_t) * ncell, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_kept, kept, sizeof(h_kept), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(e);
-  int kept = 0;
+  int n_kept = 0;
   for (int64_t c = 0; c < ncell; ++c)
-    if (h_used[c]) h_map[c] = kept++;
-  const int n = kept * P.n_c;
-  if (n == 0) {  // nothing observed: the Jacobi part alone
-    void* tmp[] = {cell_of, used, cmap};
+    if (h_used[c]) h_map[c] = n_kept++;
+  const int n = n_kept * P.n_c;
+  // Baselines that sweep many cells (long baselines) keep only part of their
+  // samples in kPcSlots cells; such a coarse space spans the slow modes badly
+  // and costs more than it saves, so the plan keeps D^-1 alone.
+  const bool spans = h_kept[1] > 0 && (double)h_kept[0] >= kPcKeptMin * (double)h_kept[1];
+  if (n == 0 || !spans) {
+    void* tmp[] = {cell_of, used, cmap, kept};
     for (void* t : tmp) cudaFreeAsync(t, st);
     pc_free(P, st);
     P.pc_built = 1;
     return DS_OK;
+  }
+  // the pixel-major runs for the second term of E
+  if (P.pm_rec == nullptr) {
+    ds_status sr = DS_OK;
+    if (P.rl_rec == nullptr) {
+      sr = rl_build(P);
+      *made_runs = true;
+    }
+    if (sr == DS_OK) {
+      sr = pm_build(P, st);
+      *made_pm = true;
+    }
+    if (sr != DS_OK || P.pm_rec == nullptr) {  // no room or too many runs: D^-1 alone
+      void* tmp[] = {cell_of, used, cmap, kept};
+      for (void* t : tmp) cudaFreeAsync(t, st);
+      pc_free(P, st);
+      P.pc_built = 1;
+      return sr == DS_ENOMEM ? DS_OK : sr;
+    }
   }
   e = cudaMemcpyAsync(cmap, h_map.data(), sizeof(int32_t) * ncell, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -548,10 +589,10 @@ ds_status pc_build(Plan& P) {
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&diag0), sizeof(double) * n, false);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&skipped), sizeof(int32_t) * n, false);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_u), sizeof(double) * n, true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_c), sizeof(double) * n, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_c), sizeof(float) * n, true);
   if (e == cudaSuccess) e = cudaMemsetAsync(E, 0, sizeof(double) * n * n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.pc_u, 0, sizeof(double) * n, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.pc_c, 0, sizeof(double) * n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.pc_c, 0, sizeof(float) * n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(skipped, 0, sizeof(int32_t) * n, st);
   if (e != cudaSuccess) return fail(e);
   k_pc_remap<<<g_b, kBlock, 0, st>>>(P.pc_cell, P.n_b * kPcSlots, cmap);
@@ -583,8 +624,8 @@ ds_status pc_build(Plan& P) {
     for (double v : hd) mu += v;
     mu /= (double)n;
     const int ci = 0;  // I is the first component whenever outputs carry I
-    k_pc_null_term<<<stream_grid(P, (int64_t)kept * kept, kBlock, 8), kBlock, 0, st>>>(
-        E, n, P.n_c, ci, kept, mu);
+    k_pc_null_term<<<stream_grid(P, (int64_t)n_kept * n_kept, kBlock, 8), kBlock, 0, st>>>(
+        E, n, P.n_c, ci, n_kept, mu);
     P.launches += 2;
   }
   k_pc_diag<<<(n + 255) / 256, 256, 0, st>>>(E, diag0, n);
@@ -602,10 +643,10 @@ ds_status pc_build(Plan& P) {
   P.launches += n + 2;
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(e);
-  void* tmp[] = {cell_of, used, cmap, skipped, E, E2, diag0};
+  void* tmp[] = {cell_of, used, cmap, skipped, E, E2, diag0, kept};
   for (void* t : tmp) cudaFreeAsync(t, st);
   P.pc_n = n;
-  P.pc_cells = kept;
+  P.pc_cells = n_kept;
   P.pc_built = 1;
   return DS_OK;
 }
@@ -615,18 +656,7 @@ ds_status pc_prepare(Plan& P) {
   cudaStream_t st = P.stream;
   const bool runs_kept = P.layout == 2 && P.desc.precision == DS_PREC_MIXED;
   bool made_runs = false, made_pm = false;
-  ds_status s = DS_OK;
-  if (P.pm_rec == nullptr) {
-    if (P.rl_rec == nullptr) {
-      s = rl_build(P);
-      made_runs = true;
-    }
-    if (s == DS_OK) {
-      s = pm_build(P, st);
-      made_pm = true;
-    }
-  }
-  if (s == DS_OK) s = pc_build(P);
+  ds_status s = pc_build(P, &made_runs, &made_pm);
   // records the operator does not read are given back once E is built
   if (made_pm && !(runs_kept && P.bin_order == 1)) pm_release(P, st);
   if (made_runs && !runs_kept) rl_release(P, st);

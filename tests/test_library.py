@@ -157,3 +157,18 @@ def test_batch_tune_profile_and_host_entry_points_reject_null_before_device_work
     assert lib.destripe_bin_noalloc(None, ok, ok, ok, None, ok, ok, None, None) == ds.DS_EINVAL
     assert lib.destripe_bin_noalloc(ctypes.byref(bad), ok, ok, ok, None, ok, ok, None,
                                     None) == ds.DS_EINVAL
+
+
+def test_gapfill_and_spectrum_reject_bad_arguments_before_device_work(lib):
+    ok = ctypes.c_void_p(256)
+    d = _desc()
+    assert lib.destripe_gapfill(None, ok, 100, 1, ok) == ds.DS_EINVAL
+    assert lib.destripe_gapfill(ctypes.byref(d), None, 100, 1, ok) == ds.DS_EINVAL
+    assert lib.destripe_gapfill(ctypes.byref(d), ok, 0, 1, ok) == ds.DS_EINVAL
+    assert lib.destripe_gapfill(ctypes.byref(d), ok, 100, 1, None) == ds.DS_EINVAL
+    bad = _desc(n_t=0)
+    assert lib.destripe_gapfill(ctypes.byref(bad), ok, 100, 1, ok) == ds.DS_EINVAL
+    assert lib.destripe_spectrum(None, ok, None, 64, 4, 50.0, None, ok) == ds.DS_EINVAL
+    # the preconditioner's tune keys exist (a null plan is still refused first)
+    assert lib.destripe_tune(None, b"precond", 2.0) == ds.DS_EINVAL
+    assert lib.destripe_tune(None, b"coarse_nside", 8.0) == ds.DS_EINVAL
