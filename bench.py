@@ -57,6 +57,10 @@ def parse():
                     help="length of the request trace (config 5)")
     ap.add_argument("--serve-master", type=int, default=100_000_000,
                     help="samples of the host-resident master scans (config 5)")
+    ap.add_argument("--serve-comparator", type=int, default=0,
+                    help="config 5: requests of the measured float64 FIFO (0 = all)")
+    ap.add_argument("--serve-cap", type=float, default=0.0,
+                    help="config 5: cap on the samples of the admitted requests (0 = none)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--n-samples", type=int, default=None, help="cut the workload (testing)")
@@ -863,38 +867,37 @@ def run_serve(args):
     warm = Server(max_slots=64, hbm_budget=200 << 30)
     warm.run([Request(**{**r.__dict__, "arrival": 0.0}) for r in reqs[:3]])
     warm.close()
-    srv = Server(max_slots=64, hbm_budget=200 << 30, iters_per_step=8)
+    cap = int(args.serve_cap) if args.serve_cap > 0 else None
+    srv = Server(max_slots=64, hbm_budget=200 << 30, iters_per_step=8, max_resident_samples=cap)
     with Clocks(local) as clk:
         stats = srv.run(reqs)
     srv.close()
     summ = stats.summary()
     ok = sum(r.status == ds.DS_OK for r in reqs)
-    # comparator: sequential plain float64 solves; service time measured on a
-    # sample of requests and modelled as c0 + c1 * samples * iterations
-    rng = np.random.default_rng(7)
-    sample = rng.choice(len(reqs), size=min(10, len(reqs)), replace=False)
-    xs, ts = [], []
-    for i in sample:
-        r = reqs[i]
-        g = [t.to(dev) for t in (r.pix, r.cos2psi, r.sin2psi)]
-        y64 = torch.stack([row.to(dev) for row in r.y]).double().contiguous()
+    # comparator: the same requests served one after the other by plain float64
+    # solves (copies to the device, plan, solve, baselines back), each request's
+    # service time measured, the FIFO latencies computed from the arrivals
+    svc, seq_units = [], 0.0
+    limit = args.serve_comparator if args.serve_comparator > 0 else len(reqs)
+    for r in reqs[:limit]:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        g = [t.to(dev) for t in (r.pix, r.cos2psi, r.sin2psi)]
+        y64 = torch.stack([row.to(dev) for row in r.y]).double().contiguous()
         pl = ds.destripe_plan(g[0], g[1], g[2], None, nside=r.nside, kinds=r.kinds,
                               baseline_len=r.baseline_len, precision="fp64")
         a = torch.empty(pl.n_u, dtype=torch.float64, device=dev)
-        st, it, rel = ds.destripe_solve(pl, y64, a, tol=args.tol)
+        try:
+            st, it, rel = ds.destripe_solve(pl, y64, a, tol=args.tol)
+        except ds.DestripeError:
+            it = 0
         a_h = a.cpu()
-        dt = time.perf_counter() - t0
+        svc.append(time.perf_counter() - t0)
+        seq_units += r.n_t * it
         pl.close()
-        xs.append(r.n_t * max(it, 1))
-        ts.append(dt)
-    A = np.vstack([np.ones(len(xs)), xs]).T
-    c0, c1 = np.linalg.lstsq(A, np.array(ts), rcond=None)[0]
-    c0, c1 = max(c0, 0.0), max(c1, 1e-15)
-    svc = [c0 + c1 * r.n_t * max(r.iters, 1) for r in reqs]
-    seq_lat = fifo_latencies([r.arrival for r in reqs], svc)
-    seq_wall = max(r.arrival + l for r, l in zip(reqs, seq_lat))
+        del g, y64, a
+    seq_lat = fifo_latencies([r.arrival for r in reqs[:limit]], svc)
+    seq_wall = max(r.arrival + l for r, l in zip(reqs[:limit], seq_lat))
     units = float(stats.sample_iters)
     t_s = stats.wall
     if dist is not None:
@@ -910,16 +913,18 @@ def run_serve(args):
                        "requests": len(reqs), "rate_per_s": 20.0,
                        "lengths": f"log-uniform 1e5..{min(2e8, n_master):.0e}",
                        "nside": list(nsides), "baselines_s": [0.5, 60.0], "outputs": "q or q,u",
-                       "precision": "mixed", "tol": args.tol, "max_slots": 64},
+                       "precision": "mixed", "tol": args.tol, "max_slots": 64,
+                       "max_resident_samples": cap},
             "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "mean_latency_s": summ["mean_s"],
             "iterations": iteration_stats(reqs, ds.DS_OK),
             "samples_per_s": summ["samples_per_s"], "converged": int(ok),
             "host_time_s": {k: summ[k] for k in ("host_admit_s", "host_step_s", "host_retire_s")},
             "max_resident": summ["max_resident"], "gpu_launches": summ["kernel_launches"],
-            "sequential_fp64_model": {
+            "sequential_fp64_fifo": {
                 "p50_s": float(np.percentile(seq_lat, 50)), "p99_s": float(np.percentile(seq_lat, 99)),
-                "value": units / seq_wall, "unit": UNIT,
-                "service_model": f"{c0:.3e} s + {c1:.3e} s per sample-iteration (fit on {len(xs)} measured float64 solves)"},
+                "value": seq_units / seq_wall, "unit": UNIT, "requests": limit,
+                "note": "every request's float64 solve timed one after the other on the same "
+                        "GPU (copies, plan, solve, copy back); FIFO latencies from the arrivals"},
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

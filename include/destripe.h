@@ -120,6 +120,10 @@ typedef struct {
 ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* d_cos2psi,
                         const float* d_sin2psi, const uint8_t* d_valid, ds_plan_t* out);
 
+/* Sizes and state of a plan (Sect. 3: the numbers of samples, baselines and
+ * map pixels that fix the shapes of F~, P and the maps; the pixels kept by the
+ * cut and the weight-1 samples).  info: host struct, filled on DS_OK; no device
+ * work. */
 ds_status destripe_plan_info(ds_plan_t plan, ds_info* info);
 
 /* Binned map m = M^-1 sum_t sum_o v w_o(t) (y_o(t) - a_o[t / L]) (Eqs. mapQ/mapU
@@ -139,7 +143,11 @@ ds_status destripe_bin(ds_plan_t plan, const void* d_y, const double* d_a, doubl
  * Uses the plan's precision for the per-sample work. */
 ds_status destripe_apply_A(ds_plan_t plan, const double* d_x, double* d_Ax);
 
-/* Right-hand side d_b = F~^T Z y (float64 accumulation). */
+/* Right-hand side of the destriping equation (Sect. 3), d_b = F~^T Z y: bin y,
+ * solve each pixel, rescan the map and sum y minus the rescan per baseline.
+ *   d_y  timelines as for destripe_bin;  d_b  float64 [n_o][n_b] output
+ * Float64 accumulation (compensated float32 sums flushed to float64 in MIXED
+ * plans).  Asynchronous on the plan's stream. */
 ds_status destripe_rhs(ds_plan_t plan, const void* d_y, double* d_b);
 
 /* Solve the destriping equation by conjugate gradient (Sect. 3 names CG; the
@@ -163,7 +171,11 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
 ds_status destripe_map(ds_plan_t plan, const void* d_y, const double* d_a, double* d_map,
                        int32_t* d_hits, uint8_t* d_mask);
 
-/* Remove the I null mode from d_a in place (see destripe_solve). */
+/* Remove the I null mode from d_a in place (see destripe_solve).  The paper's
+ * polarimeter case (q, u outputs, Sect. 3) has no such mode; outputs that carry I
+ * leave a common offset of all their baselines undetermined (the I map absorbs
+ * it), fixed here by a zero mean over the baselines with data; baselines without
+ * data are set to 0.  d_a float64 [n_o][n_b]; asynchronous on the plan's stream. */
 ds_status destripe_gauge(ds_plan_t plan, double* d_a);
 
 void destripe_destroy(ds_plan_t plan);

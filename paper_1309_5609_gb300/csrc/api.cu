@@ -110,7 +110,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->pc_cell, P->pc_val, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->tl_rec, P->tl_off, P->pc_cell, P->pc_val, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a
@@ -580,7 +580,7 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
     if (!(value >= 1.0 && value <= 1e6)) return DS_EINVAL;
     P.refresh_max = (int)value;
   } else if (k == "layout") {
-    if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
+    if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0) return DS_EINVAL;
     if (value != 0.0 && P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
     if (value == 1.0 && P.lid == nullptr) {
       const ds_status s = chunk_index(P, ck_default_chunk(P.n_t, P.num_sms));
@@ -592,6 +592,13 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
       if (s != DS_OK) return s;
       // records asked for above the automatic density: the rescans keep the samples
       P.rescan_samples = (double)P.rl_n > kRunsPerSampleMax * (double)P.n_t ? 1 : 0;
+    }
+    if (value == 3.0 && P.tl_rec == nullptr) {
+      clear_stale_error();
+      ds_status s = P.rl_rec == nullptr ? rl_build(P) : DS_OK;
+      if (s == DS_OK) s = tl_build(P);
+      if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
+      if (s != DS_OK) return s;
     }
     P.layout = (int)value;
   } else if (k == "chunk") {

@@ -568,6 +568,17 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
     return;
   }
+  if (!fp64 && P.bin_mode == 1 && tl_ready(P)) {
+    k_to_f32<<<stream_grid(P, P.n_u, kBlock, 8), kBlock, 0, st>>>(x, P.x32, P.n_u, g);
+    if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+    launch_bin_tl(P, st, g);
+    if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+    launch_pixel_solve(P, st, false, nullptr, g);
+    if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+    launch_rescan_tl(P, st, out, g);
+    if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+    return;
+  }
   if (!fp64 && P.bin_mode == 1 && ck_ready(P)) {
     if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
     launch_bin_ck(P, st, x, g);

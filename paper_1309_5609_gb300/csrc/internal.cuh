@@ -181,7 +181,7 @@ struct Plan {
   int accurate_start;       // mixed plans: 1 = accurate operator from the first iteration
   int stall_iters;          // stop a solve whose residual has not dropped 10x in this many iterations
   int layout;               // mixed operator: 0 = time-ordered pixels, 1 = chunk-local index,
-                            // 2 = run-length records
+                            // 2 = run-length records, 3 = time-tiled pixel-sorted records
   int rescan_dedup;         // float32 rescan: reuse the map value of a repeated pixel
   int rescan_rounds;        // rounds per warp chunk of the carried-sum rescans (0: automatic)
   int samples_per_thread;   // float32 operator: 4 or 8 consecutive samples per thread
@@ -211,6 +211,13 @@ struct Plan {
   float4* xd4;              // [2][n_b] split baselines: hi parts, then lo parts
   int bin_order;            // run-length plans: 1 = bin pixel-major (default), 0 = in time order
   int pm_pending;           // the copy is being built on the side stream: unusable until pm_join
+  // time-tiled, pixel-sorted run records (tiles.cu; layout 3)
+  int4* tl_rec;             // [runs] (pixel, n << 24 | baseline in tile, sum cos, sum sin)
+  int64_t* tl_off;          // [tiles + 1] first record of each tile
+  int64_t tl_tiles;         // tiles of tl_tb consecutive baselines
+  int64_t tl_tb;
+  int tl_bin_blocks;        // resident blocks per SM of the two passes
+  int tl_rescan_blocks;
   int rescan_samples;       // run-length plans: the rescans read the time-ordered samples (dense
                             // runs: a record per run costs more than 12 bytes per sample)
   // preconditioner of the CG (precond.cu): 0 none, 1 D^-1 (valid samples per
@@ -255,6 +262,11 @@ void launch_bin_pm(const Plan& P, cudaStream_t st, Gate g);
 void launch_bin_pm_df(const Plan& P, cudaStream_t st, Gate g);
 constexpr double kRunsPerSampleMax = 0.6;  // plans build run records at or below this ratio
 bool rl_ready(const Plan& P);
+// tiles.cu: time-tiled, pixel-sorted run records (layout 3)
+ds_status tl_build(Plan& P);
+bool tl_ready(const Plan& P);
+void launch_bin_tl(const Plan& P, cudaStream_t st, Gate g);
+void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g);
 void launch_bin_rl(const Plan& P, cudaStream_t st, Gate g);
 void launch_rescan_rl(const Plan& P, cudaStream_t st, double* out, Gate g);
 bool rl_df_ready(const Plan& P);

@@ -23,9 +23,10 @@
 // pass over the baselines, the second from one pass over the pixel-major run
 // records (one warp per pixel sums (K R)_p in registers and adds
 // (K R)_p^T M_p^-1 (K R)_p into E).  E^+ is a generalised inverse by the sweep
-// operator, skipping pivots that have lost all but a 1e-10 share of their
-// diagonal; the I null mode (a common offset of the I-carrying outputs, which
-// R reproduces) gets a rank-one term so that it is swept like the rest.
+// operator, skipping pivots that hold less than a 1e-6 share of their direction's
+// R^T D R (null modes of A, where E is rounding noise); the I null mode (a common
+// offset of the I-carrying outputs, which R reproduces) gets a rank-one term so
+// that it is swept like the rest.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -41,6 +42,7 @@ constexpr int kBlock = 256;
 constexpr int kCand = 4;      // cells a baseline can hold while its samples are read
 constexpr int kWarpCells = 8; // cells of one pixel's baselines merged per warp
 constexpr double kPcKeptMin = 0.8;  // share of valid samples the kept slots must hold
+constexpr double kPcPivotMin = 1e-6;  // share of diag(R^T D R) below which a pivot is skipped
 
 // Floor of the square root of x >= 0 (exact for x < 2^52).
 __device__ __forceinline__ int64_t isqrt64(int64_t x) {
@@ -300,14 +302,14 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict_
     const uint32_t beg = __ldg(off + p), end = __ldg(off + p + 1);
     if (beg == end) continue;
     int id[kCand];
-    float kr[kCand][NC][NC];
+    double kr[kCand][NC][NC];
 #pragma unroll
     for (int j = 0; j < kCand; ++j) {
       id[j] = -1;
 #pragma unroll
       for (int a = 0; a < NC; ++a)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) kr[j][a][c] = 0.f;
+        for (int c = 0; c < NC; ++c) kr[j][a][c] = 0.0;
     }
     for (uint32_t i = beg + lane; i < end; i += 32) {
       const float4 r = __ldg(rec + i);
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict_
 #pragma unroll
               for (int a = 0; a < NC; ++a)
 #pragma unroll
-                for (int c = 0; c < NC; ++c) kr[j][a][c] = fmaf(kv[a], rv[c], kr[j][a][c]);
+                for (int c = 0; c < NC; ++c) kr[j][a][c] = fma((double)kv[a], (double)rv[c], kr[j][a][c]);
               placed = true;
             }
           }
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict_
       for (int a = 0; a < NC; ++a)
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          float v = 0.f;
+          double v = 0.0;
 #pragma unroll
           for (int j = 0; j < kCand; ++j)
             if (slot[j] == t) v += kr[j][a][c];
@@ -604,6 +606,8 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   if (P.n_c == 1) by_nc(std::integral_constant<int, 1>{});
   else if (P.n_c == 2) by_nc(std::integral_constant<int, 2>{});
   else by_nc(std::integral_constant<int, 3>{});
+  // the scale of each coarse direction: diag(R^T D R), before the pixel term
+  k_pc_diag<<<(n + 255) / 256, 256, 0, st>>>(E, diag0, n);
   const int g_w = stream_grid(P, P.npix * 32, kBlock, 8);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
@@ -613,10 +617,10 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   P.launches += 3;
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(e);
-  // the I null mode: rank-one term at the mean diagonal, on the I-component columns
+  // the I null mode: rank-one term at the mean diagonal of R^T D R, on the
+  // I-component columns
   if (P.has_I_outputs) {
     std::vector<double> hd(n);
-    k_pc_diag<<<(n + 255) / 256, 256, 0, st>>>(E, diag0, n);
     e = cudaMemcpyAsync(hd.data(), diag0, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(e);
@@ -628,13 +632,15 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
         E, n, P.n_c, ci, n_kept, mu);
     P.launches += 2;
   }
-  k_pc_diag<<<(n + 255) / 256, 256, 0, st>>>(E, diag0, n);
-  // sweep every pivot, ping-ponging between E and E2
+  // sweep every pivot, ping-ponging between E and E2; a pivot is skipped when it
+  // holds less than kPcPivotMin of its direction's R^T D R: the direction is
+  // (numerically) a null mode of A, and E is known there only to the float32
+  // rounding of R and of the run sums
   const int g_s = stream_grid(P, (int64_t)n * n, kBlock, 8);
   double* a = E;
   double* bbuf = E2;
   for (int k = 0; k < n; ++k) {
-    k_pc_sweep<<<g_s, kBlock, 0, st>>>(a, bbuf, n, k, diag0, 1e-10, skipped);
+    k_pc_sweep<<<g_s, kBlock, 0, st>>>(a, bbuf, n, k, diag0, kPcPivotMin, skipped);
     double* t = a;
     a = bbuf;
     bbuf = t;

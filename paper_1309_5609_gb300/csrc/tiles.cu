@@ -1,0 +1,420 @@
+// Time-tiled, pixel-sorted run records: the float32 operator of plans whose runs
+// are short (about one pixel per sample, e.g. nside 512 at 50 Hz), where neither
+// the time-ordered samples nor the pixel-major copy pays.
+//
+// The runs of consecutive samples on one pixel within a baseline (runs_build.cu)
+// are cut into tiles of Tb consecutive baselines, and within each tile sorted by
+// pixel (one counting sort per tile at plan time).  A record is 16 bytes:
+//     (pixel, n << 24 | baseline - first baseline of the tile, sum cos 2psi, sum sin 2psi)
+// with n <= 255 samples (plans with longer runs keep the other forms).
+//
+// Both passes of an iteration give each tile to one block, which streams the
+// tile's records once (Sect. 3 operator, exact reformulation: only the float32
+// rounding order changes):
+//  * binning (P~^T R^T F~ x): the tile's baselines are staged in shared memory;
+//    a warp walks a contiguous share of the tile's records in rounds of 32, sums
+//    the contributions of equal pixels across the lanes (a segmented sum over the
+//    sorted keys) and carries the last pixel's sums into its next round, so that
+//    one vector reduction (red.global.add.v4.f32) is issued per pixel and warp
+//    share instead of one per run;
+//  * rescan and per-baseline sums (F~^T (z - R P~ m)): the tile's baseline sums
+//    live in shared memory (float32 atomics; the runs of one pixel lie in
+//    different baselines, so lanes rarely collide); the map row of a pixel is
+//    gathered by every lane of its run group at one address; the block stores
+//    its baselines' sums once (each baseline belongs to one tile: no atomics in
+//    global memory).
+#include "internal.cuh"
+#include "rows.cuh"
+#include "runs.cuh"
+#include "stream_common.cuh"
+
+namespace ds {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kTileThreads = 512;
+constexpr int kTileFloats = 12288;  // shared floats per block: baselines x outputs of a tile
+
+// ---- construction ------------------------------------------------------------------
+
+// tile_off[t] = first run of tile t (runs are in baseline order), t = 0 .. n_tiles.
+__global__ void k_tl_bounds(const int32_t* __restrict__ rb, int64_t n_runs, int64_t n_tiles,
+                            int64_t Tb, int64_t* __restrict__ tile_off) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= n_tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t * Tb;
+    int64_t lo = 0, hi = n_runs;  // first run with baseline >= b
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)rb[mid] < b) lo = mid + 1;
+      else hi = mid;
+    }
+    tile_off[t] = lo;
+  }
+}
+
+// *longest = the largest sample count of any run
+__global__ void __launch_bounds__(kBlock) k_tl_longest(const RunRec* __restrict__ rec,
+                                                       int64_t n_runs, int* __restrict__ longest) {
+  int m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_runs;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)rec[i].n);
+  for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, d));
+  if ((threadIdx.x & 31) == 0) atomicMax(longest, m);
+}
+
+// Runs per pixel within tile t (cnt zeroed before).
+__global__ void __launch_bounds__(kBlock) k_tl_hist(const RunRec* __restrict__ rec,
+                                                    const int64_t* __restrict__ tile_off, int64_t t,
+                                                    uint32_t* __restrict__ cnt) {
+  const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
+  for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(cnt + rec[i].pix, 1u);
+}
+
+// Exclusive scan of cnt[0 .. n) into run positions, in three steps: block sums
+// (each block S consecutive pixels), their scan from the tile's first run, and
+// the positions within each block.  cnt becomes the scatter cursor.
+__global__ void __launch_bounds__(kBlock) k_tl_scan_up(const uint32_t* __restrict__ cnt, int64_t n,
+                                                       int64_t S, int64_t* __restrict__ blk) {
+  __shared__ int64_t sh[kBlock / 32];
+  const int64_t lo = (int64_t)blockIdx.x * S, hi = lo + S < n ? lo + S : n;
+  int64_t v = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += cnt[i];
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int q = 0; q < kBlock / 32; ++q) t += sh[q];
+    blk[blockIdx.x] = t;
+  }
+}
+
+// blk[j] = tile start + sum of blk[0 .. j) (one thread; G is at most a few thousand)
+__global__ void k_tl_scan_top(int64_t* __restrict__ blk, int64_t G,
+                              const int64_t* __restrict__ tile_off, int64_t t) {
+  int64_t run = tile_off[t];
+  for (int64_t j = 0; j < G; ++j) {
+    const int64_t x = blk[j];
+    blk[j] = run;
+    run += x;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_tl_scan_down(uint32_t* __restrict__ cnt, int64_t n,
+                                                         int64_t S, const int64_t* __restrict__ blk,
+                                                         int64_t* __restrict__ pos) {
+  __shared__ int64_t wsum[kBlock / 32];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t lo = (int64_t)blockIdx.x * S, hi = lo + S < n ? lo + S : n;
+  int64_t carry = blk[blockIdx.x];
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < hi ? cnt[i] : 0;
+    int64_t inc = v;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t u = __shfl_up_sync(full, inc, d);
+      if (lane >= d) inc += u;
+    }
+    if (lane == 31) wsum[wq] = inc;
+    __syncthreads();
+    int64_t before = 0, tile = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      if (q < wq) before += wsum[q];
+      tile += wsum[q];
+    }
+    if (i < hi) pos[i] = carry + before + inc - v;
+    carry += tile;
+    __syncthreads();
+  }
+}
+
+// Each run of tile t to its pixel's next slot, as a 16-byte record.
+__global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict__ rec,
+                                                       const int32_t* __restrict__ rb,
+                                                       const int64_t* __restrict__ tile_off,
+                                                       int64_t t, int64_t Tb,
+                                                       unsigned long long* __restrict__ cursor,
+                                                       int4* __restrict__ out) {
+  const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
+  const int64_t b0 = t * Tb;
+  for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const RunRec r = rec[i];
+    const unsigned bl = (unsigned)((int64_t)rb[i] - b0);
+    const unsigned long long slot = atomicAdd(cursor + r.pix, 1ull);
+    out[slot] = make_int4(r.pix, (int)(((unsigned)r.n << 24) | bl), __float_as_int(r.c),
+                          __float_as_int(r.s));
+  }
+}
+
+// ---- the operator's passes --------------------------------------------------------
+
+struct TileRun {
+  int pix;
+  float n, c, s;
+  int bl;
+};
+
+__device__ __forceinline__ TileRun load_tile_run(const int4* __restrict__ rec, int64_t i) {
+  const int4 v = __ldcs(rec + i);
+  return TileRun{v.x, (float)((unsigned)v.y >> 24), __int_as_float(v.z), __int_as_float(v.w),
+                 (int)((unsigned)v.y & 0xFFFFFFu)};
+}
+
+// bins[p] += sum over the tile's runs on p of the rows summed over the run times
+// the run's baselines (float32).
+template <int KS>
+__global__ void __launch_bounds__(kTileThreads) k_tl_bin(const int4* __restrict__ rec,
+                                                         const int64_t* __restrict__ tile_off,
+                                                         int64_t n_tiles, int64_t Tb,
+                                                         const float* __restrict__ x,
+                                                         float* __restrict__ bins, int64_t n_b,
+                                                         KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  extern __shared__ float xs[];  // [n_o][Tb]
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t b0 = t * Tb;
+    const int64_t nb = b0 + Tb < n_b ? Tb : n_b - b0;
+    for (int o = 0; o < n_o; ++o)
+      for (int64_t j = threadIdx.x; j < nb; j += blockDim.x) xs[o * Tb + j] = __ldg(x + o * n_b + b0 + j);
+    __syncthreads();
+    const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
+    // warp wq takes a contiguous share of the tile's runs, whole rounds of 32
+    const int64_t per = ((r1 - r0 + nw - 1) / nw + 31) & ~int64_t(31);
+    const int64_t lo = r0 + wq * per;
+    const int64_t hi = lo + per < r1 ? lo + per : r1;
+    int ckey = -1;  // the pixel whose sums are carried from the previous round
+    float carry[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) carry[j] = 0.f;
+    for (int64_t base = lo; base < hi; base += 32) {
+      const int64_t i = base + lane;
+      float acc[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+      int key = -1;
+      if (i < hi) {
+        const TileRun r = load_tile_run(rec, i);
+        key = r.pix;
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o) run_bin<NC>(K::kind(o, kk), r.n, r.c, r.s, xs[o * Tb + r.bl], acc);
+      }
+      // the carried pixel joins lane 0 if the round starts on it, else it is flushed
+      if (lane == 0 && ckey >= 0) {
+        if (key == ckey) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) acc[j] += carry[j];
+        } else {
+          flush_bins<NC, float>(bins, ckey, carry);
+        }
+      }
+      // segmented sums over the lanes: each segment's total lands in its first lane
+      const int nxt = __shfl_down_sync(full, key, 1);
+      bool stop = lane == 31 || nxt != key;
+#pragma unroll
+      for (int w = 1; w < 32; w <<= 1) {
+        float v2[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) v2[j] = __shfl_down_sync(full, acc[j], w);
+        const bool s2 = __shfl_down_sync(full, stop, w);
+        if (!stop) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) acc[j] += v2[j];
+          stop = s2;
+        }
+      }
+      const int prv = __shfl_up_sync(full, key, 1);
+      const bool head = key >= 0 && (lane == 0 || prv != key);
+      // the last segment of the round is carried into the next one
+      const unsigned heads = __ballot_sync(full, head);
+      const int last = heads ? 31 - __clz(heads) : -1;
+      const int lkey = __shfl_sync(full, key, 31);
+      const bool carry_last = last >= 0 && __shfl_sync(full, key, last) == lkey && lkey >= 0;
+      if (head && !(carry_last && lane == last)) flush_bins<NC, float>(bins, key, acc);
+      ckey = carry_last ? lkey : -1;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) carry[j] = __shfl_sync(full, acc[j], last >= 0 ? last : 0);
+    }
+    if (lane == 0 && ckey >= 0) flush_bins<NC, float>(bins, ckey, carry);
+    __syncthreads();
+  }
+}
+
+// out[o][b] = sum over the tile's runs in baseline b of n x[o][b] - (row sums) . m_p
+// (float32 sums in shared memory, one float64 store per baseline).
+template <int KS>
+__global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restrict__ rec,
+                                                            const int64_t* __restrict__ tile_off,
+                                                            int64_t n_tiles, int64_t Tb,
+                                                            const float* __restrict__ x,
+                                                            const float* __restrict__ map,
+                                                            double* __restrict__ out, int64_t n_b,
+                                                            KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  extern __shared__ float sums[];  // [n_o][Tb]
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t b0 = t * Tb;
+    const int64_t nb = b0 + Tb < n_b ? Tb : n_b - b0;
+    for (int64_t j = threadIdx.x; j < (int64_t)n_o * Tb; j += blockDim.x) sums[j] = 0.f;
+    __syncthreads();
+    const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const TileRun r = load_tile_run(rec, i);
+      float m[NC];
+      load_map<NC, float>(map, r.pix, m);
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        if (o < n_o) {
+          const float z = __ldg(x + o * n_b + b0 + r.bl);
+          const float v = fmaf(r.n, z, -run_dot<NC>(K::kind(o, kk), r.n, r.c, r.s, m));
+          atomicAdd(sums + o * Tb + r.bl, v);
+        }
+      }
+    }
+    __syncthreads();
+    for (int o = 0; o < n_o; ++o)
+      for (int64_t j = threadIdx.x; j < nb; j += blockDim.x)
+        out[o * n_b + b0 + j] = to_f64(sums[o * Tb + j]);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+bool tl_ready(const Plan& P) { return P.layout == 3 && P.tl_rec != nullptr && P.x32 != nullptr; }
+
+static int tl_grid(const Plan& P, int per_sm) {
+  const int64_t g = (int64_t)P.num_sms * (per_sm > 0 ? per_sm : 1);
+  return (int)(P.tl_tiles < g ? P.tl_tiles : g);
+}
+
+void launch_bin_tl(const Plan& P, cudaStream_t st, Gate g) {
+  const size_t smem = sizeof(float) * (size_t)P.n_o * P.tl_tb;
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_tl_bin<KS><<<tl_grid(P, P.tl_bin_blocks), kTileThreads, smem, st>>>(
+        P.tl_rec, P.tl_off, P.tl_tiles, P.tl_tb, P.x32, P.bins32, P.n_b, P.kinds, g);
+  });
+}
+
+void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g) {
+  const size_t smem = sizeof(float) * (size_t)P.n_o * P.tl_tb;
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_tl_rescan<KS><<<tl_grid(P, P.tl_rescan_blocks), kTileThreads, smem, st>>>(
+        P.tl_rec, P.tl_off, P.tl_tiles, P.tl_tb, P.x32, P.map32, out, P.n_b, P.kinds, g);
+  });
+}
+
+// Builds the tiled records from the time-ordered run records (stream-ordered on
+// the plan's stream, one host synchronisation for the longest run).  Returns
+// DS_ESTATE, leaving nothing behind, when a run is longer than 255 samples.
+ds_status tl_build(Plan& P) {
+  if (P.rl_rec == nullptr || P.rl_n <= 0) return DS_ESTATE;
+  cudaStream_t st = P.stream;
+  int64_t Tb = kTileFloats / P.n_o;
+  if (Tb > P.n_b) Tb = P.n_b;
+  const int64_t n_tiles = (P.n_b + Tb - 1) / Tb;
+  const int64_t npix = P.npix;
+  const int64_t g = stream_grid(P, npix, kBlock, 8);
+  const int64_t S = (npix + g - 1) / g, G = (npix + S - 1) / S;
+  int* longest = nullptr;
+  uint32_t* cnt = nullptr;
+  int64_t *blk = nullptr, *pos = nullptr;
+  auto release = [&](cudaError_t e) {
+    void* tmp[] = {longest, cnt, blk, pos, P.tl_rec, P.tl_off};
+    for (void* t : tmp)
+      if (t) cudaFreeAsync(t, st);
+    P.tl_rec = nullptr;
+    P.tl_off = nullptr;
+    return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
+  };
+  cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(&longest), sizeof(int), false);
+  if (e == cudaSuccess) e = cudaMemsetAsync(longest, 0, sizeof(int), st);
+  if (e != cudaSuccess) return release(e);
+  k_tl_longest<<<stream_grid(P, P.rl_n, kBlock, 8), kBlock, 0, st>>>(P.rl_rec, P.rl_n, longest);
+  int h_longest = 0;
+  e = cudaMemcpyAsync(&h_longest, longest, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return release(e);
+  if (h_longest > 255) {
+    release(cudaSuccess);
+    return DS_ESTATE;
+  }
+  const int64_t held_before = P.device_bytes;
+  e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_rec), sizeof(int4) * P.rl_n, true);
+  if (e == cudaSuccess)
+    e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_off), sizeof(int64_t) * (n_tiles + 1), true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * G, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&pos), sizeof(int64_t) * npix, false);
+  if (e != cudaSuccess) {
+    P.device_bytes = held_before;
+    return release(e);
+  }
+  k_tl_bounds<<<(unsigned)((n_tiles + 1 + 127) / 128), 128, 0, st>>>(P.rl_b, P.rl_n, n_tiles, Tb,
+                                                                     P.tl_off);
+  const int rg = stream_grid(P, (P.rl_n + n_tiles - 1) / n_tiles, kBlock, 8);
+  for (int64_t t = 0; t < n_tiles && e == cudaSuccess; ++t) {
+    e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st);
+    if (e != cudaSuccess) break;
+    k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, P.tl_off, t, cnt);
+    k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk);
+    k_tl_scan_top<<<1, 1, 0, st>>>(blk, G, P.tl_off, t);
+    k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk, pos);
+    k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.tl_off, t, Tb,
+                                        reinterpret_cast<unsigned long long*>(pos), P.tl_rec);
+    P.launches += 5;
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    P.device_bytes = held_before;
+    return release(e);
+  }
+  for (void* t : {(void*)longest, (void*)cnt, (void*)blk, (void*)pos}) cudaFreeAsync(t, st);
+  P.tl_tiles = n_tiles;
+  P.tl_tb = Tb;
+  // shared arrays above 48 KB need the kernels' opt-in; resident blocks per SM
+  const size_t smem = sizeof(float) * (size_t)P.n_o * Tb;
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tl_bin<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tl_rescan<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.tl_bin_blocks, k_tl_bin<KS>,
+                                                        kTileThreads, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.tl_rescan_blocks, k_tl_rescan<KS>,
+                                                        kTileThreads, smem);
+  });
+  if (e != cudaSuccess || P.tl_bin_blocks < 1 || P.tl_rescan_blocks < 1) {
+    P.device_bytes = held_before;
+    void* mine[] = {P.tl_rec, P.tl_off};
+    for (void* t : mine)
+      if (t) cudaFreeAsync(t, st);
+    P.tl_rec = nullptr;
+    P.tl_off = nullptr;
+    return e == cudaSuccess ? DS_ESTATE : DS_ECUDA;
+  }
+  return DS_OK;
+}
+
+}  // namespace ds

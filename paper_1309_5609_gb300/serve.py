@@ -106,11 +106,17 @@ class Server:
     Requests shorter than accurate_below samples iterate with the accurate
     operator from the start: on small, ill-conditioned problems the float32
     operator costs CG its conjugacy and several times the iterations, while their
-    accurate iterations are cheap."""
+    accurate iterations are cheap.
+
+    max_resident_samples (optional) caps the samples of the admitted problems: the
+    batch shares the GPU among everything admitted, so an unbounded resident set
+    stretches every request; with a cap, arrivals wait in the queue (in arrival
+    order) while the admitted ones finish sooner.  A request larger than the cap
+    is admitted when nothing else is resident."""
 
     def __init__(self, max_slots: int = 64, hbm_budget: int = 64 << 30,
                  iters_per_step: int = 8, clock: Callable[[], float] = time.perf_counter,
-                 accurate_below: int = 3_000_000):
+                 accurate_below: int = 3_000_000, max_resident_samples: Optional[int] = None):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
@@ -123,6 +129,8 @@ class Server:
         self.accurate_below = accurate_below
         self.clock = clock
         self.used = 0
+        self.max_resident_samples = max_resident_samples
+        self.resident_samples = 0
         self.queue: List[Request] = []       # arrived, not admitted
         self.resident = {}                   # slot -> (request, plan, device tensors, bytes)
         self.done: List[Request] = []
@@ -138,6 +146,9 @@ class Server:
         if need > self.budget:
             raise ValueError(f"request {req.rid} needs {need} bytes, above the HBM budget")
         if self.used + need > self.budget or len(self.resident) >= self.max_slots:
+            return False
+        if (self.max_resident_samples is not None and self.resident
+                and self.resident_samples + req.n_t > self.max_resident_samples):
             return False
         rows = list(req.y) if isinstance(req.y, (list, tuple)) else [req.y[o] for o in range(len(req.kinds))]
         with torch.cuda.stream(self.copy_stream):
@@ -171,6 +182,7 @@ class Server:
         req.admitted = self.now()
         self.resident[slot] = (req, plan, (pix, c, s, y), need)
         self.used += need
+        self.resident_samples += req.n_t
         self.stats.max_resident = max(self.stats.max_resident, len(self.resident))
         return True
 
@@ -188,6 +200,7 @@ class Server:
             req.iters, req.rel_resid, req.status = it, rel, st
             plan.close()
             self.used -= need
+            self.resident_samples -= req.n_t
             self.done.append(req)
             self.stats.latencies.append(req.latency)
             self.stats.samples += req.n_t
