@@ -438,7 +438,10 @@ def run_ours(args):
     kname = {0: {"bin": "k_bin", "rescan": "k_rescan"},
              1: {"bin": "k_ck_bin", "rescan": "k_ck_rescan"},
              2: {"bin": "k_pm_bin" if layout.get("bin_order") else "k_rl_bin",
-                 "rescan": "k_rl_rescan"}}[form][dom]
+                 "rescan": "k_rescan" if (tune.get("rescan_samples", 0) or
+                                        layout.get("n_runs", 0) > 0.6 * prob.n_t)
+                 else "k_rl_rescan"},
+             3: {"bin": "k_tl_bin", "rescan": "k_tl_rescan"}}[form][dom]
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
             "traffic": kernel_traffic(prob.n_t, kname, name),
@@ -456,7 +459,8 @@ def run_ours(args):
             "data": "synthetic (seeded scan, Gaussian sky, 1/f noise), resident in HBM",
             "config": dict(config_dict(args, name), tune=tune,
                            operator_layout={0: "time-ordered pixels", 1: "chunk-local pixel index",
-                                            2: "run-length records"}[form]
+                                            2: "run-length records",
+                                            3: "time-tiled pixel-sorted run records"}[form]
                            + (", pixel-major binning" if form == 2 and layout.get("bin_order")
                               else ""),
                            runs_per_sample=layout.get("n_runs", 0) / prob.n_t), "roofline": roof,

@@ -233,6 +233,37 @@ ds_status destripe_gapfill(const ds_desc* desc, const uint8_t* d_valid, int64_t 
 ds_status destripe_spectrum(ds_plan_t plan, const void* d_y, const double* d_a, int64_t seg_len,
                             int32_t n_bins, double f_samp, double* d_freq, double* d_amp);
 
+/* Pointing of an analytic ground scan, computed on the device (Sect. 5, scanning
+ * strategy: a spin about the vertical axis at fixed elevation, the sky turning with
+ * the Earth; Sect. 3: the parallactic angle psi orients the polarimeter; HEALPix
+ * RING pixels as cited in Sect. 3).  For sample k = first_sample + i:
+ *   t = k / f_samp, az = az0 + 2 pi t / spin_period, lst = lst0 + 2 pi t / sidereal_day,
+ *   sin dec = sin el sin lat + cos el cos lat cos az,
+ *   H = atan2(-sin az cos el, sin el cos lat - cos el sin lat cos az), RA = lst - H mod 2 pi,
+ *   psi = atan2(sin H, tan lat cos dec - sin dec cos H) + 2 pi t / pol_rotation_period
+ * (no modulator term when pol_rotation_period is 0); d_pix[i] = RING pixel of
+ * (pi/2 - dec, RA) at nside, d_cos2psi[i] / d_sin2psi[i] = cos 2psi / sin 2psi rounded
+ * to float32.  Each step is one float64 operation in this order (no fused
+ * multiply-adds), so that the output is reproducible bit for bit.
+ *   d_pix int32 [n], d_cos2psi / d_sin2psi float [n]: device outputs (caller-owned)
+ * Asynchronous on stream.  Runs on the float64 pipe: on GB300 it is slower than
+ * copying precomputed pointing from the host, and it serves plan-time generation
+ * of simulated scans. */
+typedef struct {
+  double f_samp;               /* Hz */
+  double spin_period;          /* s per azimuth revolution */
+  double elevation_deg;
+  double latitude_deg;
+  double az0;                  /* rad, azimuth at t = 0 (north through east) */
+  double lst0;                 /* rad, local sidereal time at t = 0 */
+  double sidereal_day;         /* s */
+  double pol_rotation_period;  /* s; 0 = no modulator */
+} ds_scan;
+
+ds_status destripe_scan_pointing(const ds_scan* scan, int64_t first_sample, int64_t n_samples,
+                                 int32_t nside, int32_t* d_pix, float* d_cos2psi,
+                                 float* d_sin2psi, void* stream);
+
 /* Kernel timing and launch counts of a plan (no counterpart in the paper; it
  * exists to measure the kernels against the HBM roofline).  While profiling is
  * enabled, the captured CG graph records CUDA events around the binning and
@@ -312,8 +343,12 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     for the purpose when the plan has none; synchronises).  Where
  *                     baselines sweep more than two cells for over a fifth of the valid
  *                     samples (long baselines) the coarse space is not built and D^-1
- *                     alone applies.  The solution is the same; the iterations are
- *                     fewer where short baselines leave slow sky-like modes
+ *                     alone applies.  A solve that breaks down or stalls with the
+ *                     coarse correction (a nearly singular system whose slow modes
+ *                     the iteration's arithmetic cannot resolve) continues from its
+ *                     best iterate with D^-1 alone, which the plan keeps afterwards.
+ *                     The solution is the same; the iterations are fewer where short
+ *                     baselines leave slow sky-like modes
  *   "coarse_nside"    two-level preconditioner: 12 coarse_nside^2 cells (power of two,
  *                     1..64, default 8; at most the map's nside); a change rebuilds E
  *   "rescan_rounds"   MIXED plans: rounds of 32 work items (runs, or 4-sample groups)
@@ -393,14 +428,66 @@ ds_status destripe_batch_autotune(ds_batch_t batch, int32_t max_trials, ds_batch
 ds_status destripe_batch_info(ds_batch_t batch, int32_t* n_slots_used, int64_t* kernel_launches);
 void destripe_batch_destroy(ds_batch_t batch);
 
+/* ---- Time-sharded solves ----------------------------------------------------------
+ * Sect. 4 distributes the data over processes by time (Epetra maps over the
+ * samples and baselines) and exchanges pixel-domain quantities once per operator
+ * application (Export / Import).  Here each rank (one process per GPU) holds a
+ * contiguous time slice of the timeline that starts on a baseline boundary, with
+ * its pointing, its data and its slice of the baselines, and the library calls the
+ * caller's all-reduce at every exchange point:
+ *   - the plan's hits (int32 [n_pix]) and pixel matrices (float64 [n_pix][n_m],
+ *     n_m = 1, 3 or 6), before the rcond cut, so that every rank cuts alike;
+ *   - the pixel sums of every operator application, right-hand side and map,
+ *     between the binning and the per-pixel solve (float32 [n_pix][4] in the float32
+ *     iteration, float64 [n_pix][4] otherwise);
+ *   - the CG scalars (dot products; the gauge's sum and count), float64.
+ * allreduce(d_buf, count, dtype, stream, user) must replace the count values at
+ * d_buf (device memory of this rank) by their sum over all ranks, ordered after the
+ * work enqueued on stream (a cudaStream_t) and before the work enqueued after the
+ * call returns (an NCCL all-reduce enqueued on stream does both; a host-side
+ * all-reduce synchronises stream first).  It returns 0 on success; any other value
+ * ends the library call with DS_ECUDA.  Every rank must make the same sequence of
+ * calls.  A sharded plan works with destripe_rhs, destripe_apply_A (this rank's
+ * rows), destripe_bin / destripe_map (the global map on every rank) and
+ * destripe_solve_sharded; destripe_solve, the preconditioner and batches refuse
+ * it (DS_ESTATE). */
+typedef enum { DS_DT_F64 = 0, DS_DT_F32 = 1, DS_DT_I32 = 2 } ds_dtype;
+typedef int32_t (*ds_allreduce_fn)(void* d_buf, int64_t count, int32_t dtype, void* stream,
+                                   void* user);
+typedef struct {
+  ds_allreduce_fn allreduce;  /* required */
+  void* user;                 /* passed through */
+} ds_exchange;
+
+/* A plan on this rank's slice (desc->n_samples: the slice's samples; the slice
+ * starts on a baseline boundary of the global timeline, so that every rank's
+ * baselines are whole, the last one possibly short on the last rank).  Arguments
+ * as for destripe_plan; the exchange is called for the hits and pixel matrices.
+ * Synchronises desc->stream. */
+ds_status destripe_plan_sharded(const ds_desc* desc, const ds_exchange* ex, const int32_t* d_pix,
+                                const float* d_cos2psi, const float* d_sin2psi,
+                                const uint8_t* d_valid, ds_plan_t* out);
+
+/* CG on the sharded destriping equation (no counterpart beyond Sect. 4's
+ * distributed Krylov solver: every rank holds its slice of the vectors; dot
+ * products and the pixel sums are exchanged).  Arguments as for destripe_solve,
+ * with d_a this rank's slice [n_o][n_b_local].  The iteration runs from the host
+ * (no captured graph): the operator in the plan's precision, and in MIXED plans the
+ * float64 residual refreshes of destripe_solve; the gauge uses the global mean.
+ * Synchronises the plan's stream. */
+ds_status destripe_solve_sharded(ds_plan_t plan, const void* d_y, double* d_a, double tol,
+                                 int32_t max_iter, int32_t warm_start, int32_t* iters,
+                                 double* rel_resid);
+
 /* Binned map without any device allocation (no counterpart in the paper: it
  * serves callers that cannot allocate device memory when they need a map, such
  * as processes whose device memory is owned by another allocator and loops that
  * forbid allocation after start-up).  Same result as destripe_plan followed by
  * destripe_bin(plan, d_y, NULL, ...), from the pointing and data directly.
  *   desc        as for destripe_plan (desc->baseline_len is not used)
- *   d_pix, d_cos2psi, d_sin2psi, d_valid   pointing as for destripe_plan (no
- *               alignment requirement)
+ *   d_pix, d_cos2psi, d_sin2psi, d_valid   pointing as for destripe_plan (cos and sin
+ *               16-byte aligned); hits, pixel matrices, cut and inverses are those a
+ *               plan of the same descriptor computes
  *   d_y         [n_o][n_t] float64 (DS_PREC_FP64) or float32 (DS_PREC_MIXED)
  *   d_map       float64 [n_c][n_pix] output; d_hits, d_mask optional outputs
  * Intermediate sums live in one fixed device array declared by the library

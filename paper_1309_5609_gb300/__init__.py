@@ -24,7 +24,8 @@ __all__ = [
     "Batch", "destripe_batch_create", "destripe_batch_add", "destripe_batch_step",
     "destripe_batch_slot_status", "destripe_batch_retire", "destripe_batch_tune",
     "destripe_batch_info", "destripe_batch_destroy", "destripe_batch_autotune", "components",
-    "destripe_gapfill", "destripe_spectrum",
+    "destripe_gapfill", "destripe_spectrum", "destripe_plan_sharded", "destripe_solve_sharded",
+    "torch_allreduce", "destripe_scan_pointing",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,6 +42,22 @@ class ds_desc(ctypes.Structure):
                 ("baseline_len", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("rcond_min", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
+
+
+# int32 allreduce(void* d_buf, int64 count, int32 dtype, void* stream, void* user)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_void_p, ctypes.c_void_p)
+DS_DT_F64, DS_DT_F32, DS_DT_I32 = 0, 1, 2
+
+
+class ds_exchange(ctypes.Structure):
+    _fields_ = [("allreduce", ALLREDUCE_FN), ("user", ctypes.c_void_p)]
+
+
+class ds_scan(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in (
+        "f_samp", "spin_period", "elevation_deg", "latitude_deg", "az0", "lst0", "sidereal_day",
+        "pol_rotation_period")]
 
 
 class ds_info(ctypes.Structure):
@@ -107,6 +124,13 @@ _SIGS = {
     "destripe_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ds_batch_tuning)]),
     "destripe_bin_noalloc": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, _P, _P, _P, _P, _P, _P,
                                             _P]),
+    "destripe_scan_pointing": (ctypes.c_int, [ctypes.POINTER(ds_scan), ctypes.c_int64,
+                                              ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P]),
+    "destripe_plan_sharded": (ctypes.c_int, [ctypes.POINTER(ds_desc), ctypes.POINTER(ds_exchange),
+                                             _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "destripe_solve_sharded": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_double)]),
     "destripe_gapfill": (ctypes.c_int, [ctypes.POINTER(ds_desc), _P, ctypes.c_int64,
                                         ctypes.c_uint64, _P]),
     "destripe_spectrum": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32,
@@ -362,6 +386,114 @@ def destripe_spectrum(plan: Plan, y, a, *, seg_len: int, n_bins: int, f_samp: fl
     if st != DS_OK:
         raise DestripeError(st, "destripe_spectrum")
     return freq, amp
+
+
+class _DeviceView:
+    """A zero-copy view of count values of a device buffer (CUDA array interface)."""
+
+    _TYPESTR = {DS_DT_F64: "<f8", DS_DT_F32: "<f4", DS_DT_I32: "<i4"}
+
+    def __init__(self, ptr, count, dtype):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": self._TYPESTR[dtype],
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def torch_allreduce(group=None):
+    """An all-reduce (sum) over a torch.distributed group for the sharded calls:
+    with the NCCL backend it is enqueued on the library's stream on the buffer
+    itself; with other backends the stream is synchronised and the values are
+    summed through host memory."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(ptr, count, dtype, stream):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        view = torch.as_tensor(_DeviceView(ptr, count, dtype), device=dev)
+        s = torch.cuda.ExternalStream(stream, device=dev) if stream else torch.cuda.default_stream(dev)
+        with torch.cuda.stream(s):
+            if dist.get_backend(group) == "nccl":
+                dist.all_reduce(view, group=group)
+            else:
+                s.synchronize()
+                h = view.cpu()
+                dist.all_reduce(h, group=group)
+                view.copy_(h)
+        return 0
+
+    return fn
+
+
+def destripe_plan_sharded(pix, cos2psi, sin2psi, valid=None, *, nside: int, kinds=("q", "u"),
+                          baseline_len: int, precision="mixed", allreduce, rcond_min: float = 1e-3,
+                          stream=None) -> Plan:
+    """Plan on this rank's time slice (starting on a baseline boundary); allreduce(ptr,
+    count, dtype, stream) sums count values at a device pointer over the ranks, in
+    place (torch_allreduce() gives one over torch.distributed)."""
+    import torch
+    lib = load_library()
+    n_t = pix.numel()
+    dev = pix.device
+    _check(pix, torch.int32, n_t, "pix")
+    _check(cos2psi, torch.float32, n_t, "cos2psi", dev)
+    _check(sin2psi, torch.float32, n_t, "sin2psi", dev)
+    if valid is not None:
+        _check(valid, torch.uint8, n_t, "valid", dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def cb(ptr, count, dtype, st, user):
+        try:
+            return int(allreduce(ptr, count, dtype, st) or 0)
+        except Exception:
+            return 1
+
+    cfn = ALLREDUCE_FN(cb)
+    ex = ds_exchange(cfn, None)
+    desc = _make_desc(n_t, nside, kinds, baseline_len, precision, rcond_min, stream)
+    h = _P()
+    st = lib.destripe_plan_sharded(ctypes.byref(desc), ctypes.byref(ex), _ptr(pix), _ptr(cos2psi),
+                                   _ptr(sin2psi), _ptr(valid), ctypes.byref(h))
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_plan_sharded")
+    # the plan calls back into cfn until destroyed: keep it alive with the plan
+    return Plan(h, desc, kinds, nside, (cos2psi, sin2psi, cfn, ex), dev)
+
+
+def destripe_solve_sharded(plan: Plan, y, a, tol: float = 1e-10, max_iter: int = 10000,
+                           warm_start: bool = False):
+    """CG over all ranks; a is this rank's slice.  Returns (status, iterations,
+    relative residual); raises on errors other than DS_ENOCONV."""
+    import torch
+    _check(y, plan.y_dtype, plan.n_o * plan.n_t, "y", plan.device)
+    _check(a, torch.float64, plan.n_u, "a", plan.device)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    st = load_library().destripe_solve_sharded(plan.handle, _ptr(y), _ptr(a), float(tol),
+                                               int(max_iter), 1 if warm_start else 0,
+                                               ctypes.byref(it), ctypes.byref(rr))
+    if st not in (DS_OK, DS_ENOCONV):
+        raise DestripeError(st, "destripe_solve_sharded")
+    return st, it.value, rr.value
+
+
+def destripe_scan_pointing(scan, first_sample: int, n_samples: int, nside: int, device=None,
+                           stream=None):
+    """Pointing of an analytic scan on the device: (pix int32, cos 2psi float32,
+    sin 2psi float32) tensors of n_samples.  scan: an object with the ds_scan fields
+    as attributes (e.g. synth.ScanParams)."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    sc = ds_scan(*(float(getattr(scan, f)) for f, _ in ds_scan._fields_))
+    pix = torch.empty(n_samples, dtype=torch.int32, device=dev)
+    c = torch.empty(n_samples, dtype=torch.float32, device=dev)
+    s = torch.empty(n_samples, dtype=torch.float32, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    st = load_library().destripe_scan_pointing(ctypes.byref(sc), int(first_sample), int(n_samples),
+                                               int(nside), _ptr(pix), _ptr(c), _ptr(s), stream)
+    if st != DS_OK:
+        raise DestripeError(st, "destripe_scan_pointing")
+    return pix, c, s
 
 
 def destripe_gauge(plan: Plan, a):

@@ -34,7 +34,9 @@ int n_comp_of(const int* kinds, int n_o, int* has_i_out) {
   return (I && P) ? 3 : (P ? 2 : 1);
 }
 
-int kindset_of(const int* k, int n_o, int n_c) {
+}  // namespace
+
+int ds::kindset_of(const int* k, int n_o, int n_c) {
   if (n_o == 2 && k[0] == DS_KIND_Q && k[1] == DS_KIND_U) return KS_QU;
   if (n_o == 3 && k[0] == DS_KIND_I && k[1] == DS_KIND_Q && k[2] == DS_KIND_U) return KS_IQU3;
   if (n_o == 1 && k[0] == DS_KIND_IQU) return KS_IQU1;
@@ -42,6 +44,8 @@ int kindset_of(const int* k, int n_o, int n_c) {
   if (n_c == 2 && n_o <= 2) return KS_QU12;  // q and u outputs only, at most two
   return n_c == 1 ? KS_GEN1 : (n_c == 2 ? KS_GEN2 : KS_GEN3);
 }
+
+namespace {
 
 // Plan memory comes from one stream-ordered pool per device, owned by the library:
 // freeing a plan needs no device-wide synchronisation (cudaFree has one), and a
@@ -264,11 +268,20 @@ const char* destripe_strerror(ds_status s) {
 
 ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* d_cos2psi,
                         const float* d_sin2psi, const uint8_t* d_valid, ds_plan_t* out) {
+  return plan_create(desc, nullptr, d_pix, d_cos2psi, d_sin2psi, d_valid, out);
+}
+
+}  // extern "C"
+
+ds_status ds::plan_create(const ds_desc* desc, const ds_exchange* ex, const int32_t* d_pix,
+                          const float* d_cos2psi, const float* d_sin2psi,
+                          const uint8_t* d_valid, ds_plan_t* out) {
   if (out == nullptr) return DS_EINVAL;
   *out = nullptr;
   ds_status s = check_desc(desc);
   if (s != DS_OK) return s;
   if (d_pix == nullptr || d_cos2psi == nullptr || d_sin2psi == nullptr) return DS_EINVAL;
+  if (ex != nullptr && ex->allreduce == nullptr) return DS_EINVAL;
   if ((reinterpret_cast<uintptr_t>(d_cos2psi) & 15) || (reinterpret_cast<uintptr_t>(d_sin2psi) & 15))
     return DS_EINVAL;
   Plan* P = new (std::nothrow) Plan();
@@ -312,6 +325,11 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   P->samples_per_thread = 4;
   P->precond = 2;
   P->pc_nside = 8;
+  if (ex != nullptr) {
+    P->shard_allreduce = ex->allreduce;
+    P->shard_user = ex->user;
+    P->precond = 1;  // the coarse matrix would need every rank's pixel terms
+  }
   cudaError_t e = cudaSuccess;
 #define DS_ALLOC(ptr, n) \
   if (e == cudaSuccess) e = dalloc(*P, &P->ptr, (n));
@@ -371,6 +389,8 @@ ds_status destripe_plan(const ds_desc* desc, const int32_t* d_pix, const float* 
   *out = reinterpret_cast<ds_plan_t>(P);
   return DS_OK;
 }
+
+extern "C" {
 
 ds_status destripe_plan_info(ds_plan_t plan, ds_info* info) {
   if (plan == nullptr || info == nullptr) return DS_EINVAL;
@@ -458,6 +478,7 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   if (plan == nullptr || d_y == nullptr || d_a == nullptr) return DS_EINVAL;
   if (!(tol >= 0.0) || !std::isfinite(tol)) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (P.shard_allreduce != nullptr) return DS_ESTATE;  // destripe_solve_sharded
   if (max_iter <= 0) max_iter = 10000;
   clear_stale_error();
   cudaStream_t st = P.stream;
@@ -514,6 +535,27 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   // float64 residual seen (a float32 operator can drift on ill-posed problems).
   const bool use_best = P.x_best != nullptr && H.status != 1 && !(H.rr_true <= H.rr_best);
   double* result = use_best ? P.x_best : P.x;
+  // The coarse correction boosts the slow sky-like modes.  Where A is nearly
+  // singular along them, the iteration's arithmetic cannot resolve them and CG
+  // breaks down (no curvature, non-finite values) or stalls.  Such a solve goes on
+  // without the coarse correction from its best iterate, and the plan keeps D^-1
+  // alone from then on.
+  const bool broke = (H.status == 3 && !(H.rr_true <= H.tol2)) || H.status == 4 || H.status == 5;
+  if (broke && pc_ready(P) && std::isfinite(H.bb) && H.iter < max_iter) {
+    P.pc_fallback = 1;
+    for (cudaGraphExec_t* gx : {&P.graph_exec, &P.graph_exec_acc})
+      if (*gx) {
+        cudaGraphExecDestroy(*gx);
+        *gx = nullptr;
+      }
+    const bool from_zero = !use_best && H.status == 4;  // float64 plan with non-finite x
+    if (from_zero) DS_CUDA_TRY(cudaMemsetAsync(d_a, 0, sizeof(double) * P.n_u, st));
+    else DS_CUDA_TRY(cudaMemcpyAsync(d_a, result, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
+    int32_t it2 = 0;
+    const ds_status s2 = destripe_solve(plan, d_y, d_a, tol, max_iter - H.iter, 1, &it2, rel_resid);
+    if (iters) *iters = H.iter + it2;
+    return s2;
+  }
   enqueue_gauge(P, st, result);
   P.launches += 2;
   DS_CUDA_TRY(cudaMemcpyAsync(d_a, result, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
@@ -641,6 +683,7 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
     P.rescan_samples = (int)value;
   } else if (k == "precond") {
     if (value != 0.0 && value != 1.0 && value != 2.0) return DS_EINVAL;
+    if (value == 2.0 && P.shard_allreduce != nullptr) return DS_ESTATE;
     P.precond = (int)value;
   } else if (k == "coarse_nside") {
     const int nc = (int)value;

@@ -533,6 +533,15 @@ void launch_rescan_y(const Plan& P, cudaStream_t st, const void* y, double* out,
   });
 }
 
+// The pixel sums the next pixel solve reads: float32 [n_pix][4] for the float32
+// operator with vector reductions, float64 [n_pix][4] otherwise.  A sharded plan
+// sums them over the ranks here (the Export / Import step of Sect. 4).
+static void exchange_sums(const Plan& P, cudaStream_t st, bool f32) {
+  if (P.shard_allreduce == nullptr) return;
+  if (f32) shard_exchange(P, st, P.bins32, P.npix * 4, DS_DT_F32);
+  else shard_exchange(P, st, P.bins, P.npix * 4, DS_DT_F64);
+}
+
 static bool use_df(const Plan& P) {
   return P.desc.precision == DS_PREC_MIXED && P.accurate_df && P.maplo != nullptr;
 }
@@ -548,6 +557,7 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     launch_split_df(P, st, x, g);
     if (runs) launch_bin_rl_df(P, st, g);
     else launch_bin_df(P, st, x, nullptr, g);
+    exchange_sums(P, st, false);
     if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     launch_pixel_solve_df(P, st, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
@@ -560,6 +570,7 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     k_to_f32<<<stream_grid(P, P.n_u, kBlock, 8), kBlock, 0, st>>>(x, P.x32, P.n_u, g);
     if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
     launch_bin_rl(P, st, g);
+    exchange_sums(P, st, true);
     if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     launch_pixel_solve(P, st, false, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
@@ -572,6 +583,7 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     k_to_f32<<<stream_grid(P, P.n_u, kBlock, 8), kBlock, 0, st>>>(x, P.x32, P.n_u, g);
     if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
     launch_bin_tl(P, st, g);
+    exchange_sums(P, st, true);
     if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     launch_pixel_solve(P, st, false, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
@@ -582,6 +594,7 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
   if (!fp64 && P.bin_mode == 1 && ck_ready(P)) {
     if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
     launch_bin_ck(P, st, x, g);
+    exchange_sums(P, st, true);
     if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     launch_pixel_solve(P, st, false, nullptr, g);
     if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
@@ -594,6 +607,7 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     k_to_f32<<<stream_grid(P, P.n_u, kBlock, 8), kBlock, 0, st>>>(x, P.x32, P.n_u, g);
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   launch_bin_x(P, st, fp64, x, g);
+  exchange_sums(P, st, f32_bins(P, fp64));
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
   launch_pixel_solve(P, st, fp64, nullptr, g);
   if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
@@ -604,11 +618,13 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
 void enqueue_rhs(const Plan& P, cudaStream_t st, const void* y, double* out, Gate g) {
   if (use_df(P)) {
     launch_bin_df(P, st, nullptr, static_cast<const float*>(y), g);
+    exchange_sums(P, st, false);
     launch_pixel_solve_df(P, st, nullptr, g);
     launch_rescan_df(P, st, nullptr, static_cast<const float*>(y), out, g);
     return;
   }
   launch_bin_y(P, st, y, nullptr, g);
+  exchange_sums(P, st, false);
   launch_pixel_solve(P, st, true, nullptr, g);
   launch_rescan_y(P, st, y, out, g);
 }
@@ -618,10 +634,12 @@ void enqueue_map(const Plan& P, cudaStream_t st, const void* y, const double* a,
   if (use_df(P)) {
     if (a != nullptr) launch_split_df(P, st, a, g);
     launch_bin_df(P, st, a, static_cast<const float*>(y), g);
+    exchange_sums(P, st, false);
     launch_pixel_solve_df(P, st, out_map, g);
     return;
   }
   launch_bin_y(P, st, y, a, g);
+  exchange_sums(P, st, false);
   launch_pixel_solve(P, st, true, out_map, g);
 }
 

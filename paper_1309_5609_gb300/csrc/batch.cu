@@ -1111,6 +1111,7 @@ ds_status destripe_batch_add(ds_batch_t B, ds_plan_t plan, const void* d_y, cons
   if (B == nullptr || plan == nullptr || d_y == nullptr || slot_out == nullptr) return DS_EINVAL;
   if (!(tol >= 0.0)) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
+  if (P.shard_allreduce != nullptr) return DS_ESTATE;  // a slice of a sharded problem
   if (P.desc.precision != DS_PREC_MIXED || P.bins32 == nullptr || P.maplo == nullptr ||
       P.xdf == nullptr || P.x32 == nullptr || !P.accurate_df || P.bin_mode != 1)
     return DS_ESTATE;

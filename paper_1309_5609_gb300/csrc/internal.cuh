@@ -225,6 +225,7 @@ struct Plan {
   int precond;
   int pc_nside;             // the coarse space has 12 pc_nside^2 cells
   int pc_built;             // coarse space and E^+ built for this plan
+  int pc_fallback;          // a solve broke down with the coarse correction: D^-1 alone
   int pc_n;                 // coarse columns (kept cells x n_c)
   int pc_cells;             // kept cells
   int32_t* pc_cell;         // [n_b][kPcSlots] kept-cell number of each slot, -1 = none
@@ -232,6 +233,12 @@ struct Plan {
   double* pc_einv;          // [pc_n][pc_n] generalised inverse of E = R^T A R
   double* pc_u;             // [pc_n] R^T r, kept at zero between uses
   float* pc_c;              // [pc_n] coarse correction E^+ R^T r, rounded to float32
+  // time-sharded plans (shard.cu): the caller's all-reduce over the ranks, called
+  // at every exchange point (plan matrices, pixel sums, CG scalars); its first
+  // failure is kept in shard_err and ends the call in progress
+  ds_allreduce_fn shard_allreduce;
+  void* shard_user;
+  mutable int shard_err;
   cudaStream_t side_stream; // builds the pixel-major copy beside the first right-hand side
   cudaEvent_t side_ev[2];   // records ready (plan stream) / copy built (side stream)
 };
@@ -310,6 +317,25 @@ void enqueue_map(const Plan& P, cudaStream_t st, const void* y, const double* a,
 
 // plan.cu
 ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid);
+// hits and M_p of the samples (M packed [n_pix][NM], both accumulated: zero them
+// first); df: compensated float32 sums of the mixed plans
+void launch_plan_matrices(int kindset, bool df, int grid, cudaStream_t st, const int32_t* pix,
+                          const float* c, const float* s, const uint8_t* valid, int32_t* hits,
+                          double* mm, int64_t n_t, int64_t npix, KindsArg kk, int32_t* err);
+// rcond cut and M_p^-1 in place, mask, kept-pixel count (accumulated into n_good)
+void launch_pixel_invert(int n_c, int grid, cudaStream_t st, double* mm, const int32_t* hits,
+                         uint8_t* mask, int64_t npix, double rcond_min,
+                         unsigned long long* n_good);
+// api.cu: kernel specialisation of a set of output kinds
+int kindset_of(const int* kinds, int n_o, int n_c);
+
+// shard.cu: the caller's all-reduce (sum) of count values at d_buf, ordered on st;
+// a no-op for plans that are not sharded
+void shard_exchange(const Plan& P, cudaStream_t st, void* d_buf, int64_t count, int32_t dtype);
+// api.cu: a plan on the given pointing, sharded when ex is not NULL
+ds_status plan_create(const ds_desc* desc, const ds_exchange* ex, const int32_t* d_pix,
+                      const float* d_cos2psi, const float* d_sin2psi, const uint8_t* d_valid,
+                      ds_plan_t* out);
 
 // precond.cu: coarse space and coarse matrix of the two-level preconditioner
 __host__ __device__ int coarse_cell(int64_t p, int64_t nside, int64_t nc);

@@ -9,7 +9,10 @@
 // moment.  This entry point serves them: the caller passes inputs and outputs,
 // and all intermediate per-pixel sums live in one fixed array in device global
 // memory that the library declares at file scope.  Every GPU that loads the
-// library holds that array (4.2 MB) until the process exits.
+// library holds that array (4.2 MB) until the process exits.  The hits, the
+// pixel matrices, the rcond cut and the inverses come from the very kernels a plan
+// of the same descriptor uses (plan.cu, pixmat.cuh), written into that array, so
+// that every pixel is kept or cut exactly as destripe_plan keeps or cuts it.
 //
 // Limits and sharing rules:
 //  - maps of at most DS_NOALLOC_MAX_PIX pixels (nside <= 64);
@@ -31,12 +34,14 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int64_t kMaxPix = DS_NOALLOC_MAX_PIX;
-// Layout (in doubles): sums [kMaxPix][4] | normal matrices [kMaxPix][6] |
-// hits int32 [kMaxPix] | error word.
+// Layout (in doubles): sums [kMaxPix][4] | normal matrices, then their inverses,
+// packed [kMaxPix][NM <= 6] | hits int32 [kMaxPix] | mask uint8 [kMaxPix] |
+// error word and kept-pixel count.
 constexpr int64_t kSumOff = 0;
 constexpr int64_t kMatOff = kSumOff + 4 * kMaxPix;
 constexpr int64_t kHitOff = kMatOff + 6 * kMaxPix;
-constexpr int64_t kErrOff = kHitOff + kMaxPix / 2;
+constexpr int64_t kMaskOff = kHitOff + kMaxPix / 2;
+constexpr int64_t kErrOff = kMaskOff + kMaxPix / 8;
 constexpr int64_t kScratchDoubles = kErrOff + 32;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -67,165 +72,77 @@ __global__ void __launch_bounds__(kBlock) k_na_clear(double* __restrict__ scratc
   int32_t* hits = reinterpret_cast<int32_t*>(scratch + kHitOff);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride)
     hits[i] = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) reinterpret_cast<int32_t*>(scratch + kErrOff)[0] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < 32) scratch[kErrOff + threadIdx.x] = 0.0;
 }
 
-template <int NC>
-__device__ __forceinline__ constexpr int na_sym(int i, int j) {
-  if (i > j) { int t = i; i = j; j = t; }
-  return i * NC - i * (i - 1) / 2 + (j - i);
-}
-
-// One pass over the samples: hits, normal matrices and sums of w_o(t) y_o(t).
+// One pass over the samples: sums of w_o(t) y_o(t) on the kept pixels.
 template <int KS, typename YT>
-__global__ void __launch_bounds__(kBlock) k_na_accum(const int32_t* __restrict__ pix,
-                                                     const float* __restrict__ cc,
-                                                     const float* __restrict__ ss,
-                                                     const uint8_t* __restrict__ valid,
-                                                     const YT* __restrict__ y,
-                                                     double* __restrict__ scratch, int64_t n_t,
-                                                     int64_t npix, KindsArg kk) {
+__global__ void __launch_bounds__(kBlock) k_na_sums(const int32_t* __restrict__ pix,
+                                                    const float* __restrict__ cc,
+                                                    const float* __restrict__ ss,
+                                                    const uint8_t* __restrict__ valid,
+                                                    const YT* __restrict__ y,
+                                                    double* __restrict__ scratch, int64_t n_t,
+                                                    int64_t npix, KindsArg kk) {
   using K = KSet<KS>;
-  constexpr int NC = K::NC, NO = K::NO, NM = NC * (NC + 1) / 2;
+  constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
-  int32_t* hits = reinterpret_cast<int32_t*>(scratch + kHitOff);
-  int32_t* err = reinterpret_cast<int32_t*>(scratch + kErrOff);
+  const uint8_t* mask = reinterpret_cast<const uint8_t*>(scratch + kMaskOff);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_t; t += stride) {
     if (valid != nullptr && valid[t] == 0) continue;
     const int p = pix[t];
-    if (p < 0 || p >= npix) {
-      atomicOr(err, 1);
-      continue;
-    }
+    if (p < 0 || p >= npix || !mask[p]) continue;  // out of range: flagged by the matrix pass
     const double c = cc[t], s = ss[t];
-    double sum[NC], mat[NM];
+    double sum[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) sum[j] = 0.0;
 #pragma unroll
-    for (int j = 0; j < NM; ++j) mat[j] = 0.0;
-#pragma unroll
-    for (int o = 0; o < NO; ++o) {
-      if (o < n_o) {
-        double row[NC];
-#pragma unroll
-        for (int j = 0; j < NC; ++j) row[j] = 0.0;
-        row_bin<NC, double>(K::kind(o, kk), c, s, 1.0, row);
-        const double yo = (double)y[(int64_t)o * n_t + t];
-#pragma unroll
-        for (int i = 0; i < NC; ++i) {
-          sum[i] += row[i] * yo;
-#pragma unroll
-          for (int j = i; j < NC; ++j) mat[na_sym<NC>(i, j)] += row[i] * row[j];
-        }
-      }
-    }
-    atomicAdd(hits + p, 1);
+    for (int o = 0; o < NO; ++o)
+      if (o < n_o) row_bin<NC, double>(K::kind(o, kk), c, s, (double)y[(int64_t)o * n_t + t], sum);
 #pragma unroll
     for (int j = 0; j < NC; ++j) atomicAdd(scratch + kSumOff + 4 * (int64_t)p + j, sum[j]);
-#pragma unroll
-    for (int j = 0; j < NM; ++j) atomicAdd(scratch + kMatOff + 6 * (int64_t)p + j, mat[j]);
   }
 }
 
-// Per pixel: rcond = lambda_min / lambda_max of M_p in closed form, the cut, and
-// m_p = M_p^-1 s_p on kept pixels (0 elsewhere).
+// Per pixel: m_p = M_p^-1 s_p on kept pixels (0 elsewhere), hits and mask out.
 template <int NC>
-__global__ void __launch_bounds__(kBlock) k_na_finish(const double* __restrict__ scratch,
-                                                      int64_t npix, double rcond_min,
-                                                      double* __restrict__ map,
-                                                      int32_t* __restrict__ hits_out,
-                                                      uint8_t* __restrict__ mask_out) {
+__global__ void __launch_bounds__(kBlock) k_na_map(const double* __restrict__ scratch,
+                                                   int64_t npix, double* __restrict__ map,
+                                                   int32_t* __restrict__ hits_out,
+                                                   uint8_t* __restrict__ mask_out) {
   constexpr int NM = NC * (NC + 1) / 2;
   const int32_t* hits = reinterpret_cast<const int32_t*>(scratch + kHitOff);
+  const uint8_t* mask = reinterpret_cast<const uint8_t*>(scratch + kMaskOff);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
-    double a[NM], s[NC], m[NC];
+    double mi[NM], s[NC], m[NC];
 #pragma unroll
-    for (int j = 0; j < NM; ++j) a[j] = scratch[kMatOff + 6 * p + j];
+    for (int j = 0; j < NM; ++j) mi[j] = scratch[kMatOff + NM * p + j];
 #pragma unroll
     for (int j = 0; j < NC; ++j) s[j] = scratch[kSumOff + 4 * p + j];
-    const int h = hits[p];
-    double rc = 0.0;
-    if (h > 0) {
-      if constexpr (NC == 1) {
-        rc = a[0] > 0.0 ? 1.0 : 0.0;
-      } else if constexpr (NC == 2) {
-        const double mid = 0.5 * (a[0] + a[2]), half = 0.5 * (a[0] - a[2]);
-        const double lmax = mid + sqrt(half * half + a[1] * a[1]);
-        rc = lmax > 0.0 ? ((a[0] * a[2] - a[1] * a[1]) / lmax) / lmax : 0.0;
-      } else {
-        const double p1 = a[1] * a[1] + a[2] * a[2] + a[4] * a[4];
-        double e1, e3;
-        if (p1 == 0.0) {
-          e1 = fmax(a[0], fmax(a[3], a[5]));
-          e3 = fmin(a[0], fmin(a[3], a[5]));
-        } else {
-          const double q = (a[0] + a[3] + a[5]) / 3.0;
-          const double d0 = a[0] - q, d1 = a[3] - q, d2 = a[5] - q;
-          const double pp = sqrt((d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1) / 6.0);
-          const double ip = 1.0 / pp;
-          const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip;
-          const double b01 = a[1] * ip, b02 = a[2] * ip, b12 = a[4] * ip;
-          double r = 0.5 * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
-                            b02 * (b01 * b12 - b11 * b02));
-          r = fmin(1.0, fmax(-1.0, r));
-          const double phi = acos(r) / 3.0;
-          e1 = q + 2.0 * pp * cos(phi);
-          e3 = q + 2.0 * pp * cos(phi + 2.0943951023931954923);
-        }
-        rc = e1 > 0.0 ? e3 / e1 : 0.0;
-      }
-    }
-    const bool keep = h > 0 && rc >= rcond_min;
+    const bool keep = mask[p] != 0;
     if (keep) {
-      if constexpr (NC == 1) {
-        m[0] = s[0] / a[0];
-      } else if constexpr (NC == 2) {
-        const double det = a[0] * a[2] - a[1] * a[1];
-        m[0] = (a[2] * s[0] - a[1] * s[1]) / det;
-        m[1] = (a[0] * s[1] - a[1] * s[0]) / det;
-      } else {
-        const double c00 = a[3] * a[5] - a[4] * a[4], c01 = a[2] * a[4] - a[1] * a[5];
-        const double c02 = a[1] * a[4] - a[2] * a[3], c11 = a[0] * a[5] - a[2] * a[2];
-        const double c12 = a[1] * a[2] - a[0] * a[4], c22 = a[0] * a[3] - a[1] * a[1];
-        const double id = 1.0 / (a[0] * c00 + a[1] * c01 + a[2] * c02);
-        m[0] = (c00 * s[0] + c01 * s[1] + c02 * s[2]) * id;
-        m[1] = (c01 * s[0] + c11 * s[1] + c12 * s[2]) * id;
-        m[2] = (c02 * s[0] + c12 * s[1] + c22 * s[2]) * id;
-      }
+      sym_mul<NC>(mi, s, m);
     } else {
 #pragma unroll
       for (int j = 0; j < NC; ++j) m[j] = 0.0;
     }
 #pragma unroll
     for (int j = 0; j < NC; ++j) map[(int64_t)j * npix + p] = m[j];
-    if (hits_out) hits_out[p] = h;
+    if (hits_out) hits_out[p] = hits[p];
     if (mask_out) mask_out[p] = keep ? 1 : 0;
   }
 }
 
-int na_kindset(const int* k, int n_o, int n_c) {
-  if (n_o == 2 && k[0] == DS_KIND_Q && k[1] == DS_KIND_U) return KS_QU;
-  if (n_o == 3 && k[0] == DS_KIND_I && k[1] == DS_KIND_Q && k[2] == DS_KIND_U) return KS_IQU3;
-  if (n_o == 1 && k[0] == DS_KIND_IQU) return KS_IQU1;
-  if (n_o == 1 && k[0] == DS_KIND_I) return KS_I;
-  return n_c == 1 ? KS_GEN1 : (n_c == 2 ? KS_GEN2 : KS_GEN3);
-}
-
 template <typename YT>
-void na_launch_accum(int ks, int grid, cudaStream_t st, const int32_t* pix, const float* c,
-                     const float* s, const uint8_t* valid, const YT* y, double* scratch,
-                     int64_t n_t, int64_t npix, KindsArg kk) {
-  switch (ks) {
-    case KS_QU: k_na_accum<KS_QU, YT><<<grid, kBlock, 0, st>>>(pix, c, s, valid, y, scratch, n_t, npix, kk); break;
-    case KS_IQU3: k_na_accum<KS_IQU3, YT><<<grid, kBlock, 0, st>>>(pix, c, s, valid, y, scratch, n_t, npix, kk); break;
-    case KS_IQU1: k_na_accum<KS_IQU1, YT><<<grid, kBlock, 0, st>>>(pix, c, s, valid, y, scratch, n_t, npix, kk); break;
-    case KS_I: k_na_accum<KS_I, YT><<<grid, kBlock, 0, st>>>(pix, c, s, valid, y, scratch, n_t, npix, kk); break;
-    case KS_GEN1: k_na_accum<KS_GEN1, YT><<<grid, kBlock, 0, st>>>(pix, c, s, valid, y, scratch, n_t, npix, kk); break;
-    case KS_GEN2: k_na_accum<KS_GEN2, YT><<<grid, kBlock, 0, st>>>(pix, c, s, valid, y, scratch, n_t, npix, kk); break;
-    default: k_na_accum<KS_GEN3, YT><<<grid, kBlock, 0, st>>>(pix, c, s, valid, y, scratch, n_t, npix, kk); break;
-  }
+void na_launch_sums(int ks, int grid, cudaStream_t st, const int32_t* pix, const float* c,
+                    const float* s, const uint8_t* valid, const YT* y, double* scratch,
+                    int64_t n_t, int64_t npix, KindsArg kk) {
+  with_kindset(ks, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_na_sums<KS, YT><<<grid, kBlock, 0, st>>>(pix, c, s, valid, y, scratch, n_t, npix, kk);
+  });
 }
 
 }  // namespace
@@ -247,6 +164,9 @@ extern "C" ds_status destripe_bin_noalloc(const ds_desc* desc, const int32_t* d_
   if (desc->reserved != 0) return DS_EINVAL;
   const int64_t npix = int64_t(12) * desc->nside * desc->nside;
   if (npix > kMaxPix) return DS_EINVAL;  // map larger than the fixed scratch array
+  // the matrix pass is the plan's own (vector loads of cos / sin)
+  if ((reinterpret_cast<uintptr_t>(d_cos2psi) & 15) || (reinterpret_cast<uintptr_t>(d_sin2psi) & 15))
+    return DS_EINVAL;
   bool has_i = false, has_p = false;
   KindsArg kk{};
   kk.n_o = desc->n_outputs;
@@ -273,22 +193,30 @@ extern "C" ds_status destripe_bin_noalloc(const ds_desc* desc, const int32_t* d_
     return (int)(g < 1 ? 1 : (g < cap ? g : cap));
   };
   k_na_clear<<<grid_for(10 * npix), kBlock, 0, st>>>(scratch, npix);
-  const int ks = na_kindset(desc->kinds, desc->n_outputs, n_c);
+  const int ks = kindset_of(desc->kinds, desc->n_outputs, n_c);
+  int32_t* hits = reinterpret_cast<int32_t*>(scratch + kHitOff);
+  uint8_t* mask = reinterpret_cast<uint8_t*>(scratch + kMaskOff);
+  int32_t* err = reinterpret_cast<int32_t*>(scratch + kErrOff);
+  // hits, M_p, the cut and M_p^-1 exactly as a plan of this descriptor builds them
+  launch_plan_matrices(ks, desc->precision == DS_PREC_MIXED, grid_for((n_t + 3) / 4), st, d_pix,
+                       d_cos2psi, d_sin2psi, d_valid, hits, scratch + kMatOff, n_t, npix, kk, err);
+  launch_pixel_invert(n_c, grid_for(npix), st, scratch + kMatOff, hits, mask, npix, rcond_min,
+                      reinterpret_cast<unsigned long long*>(scratch + kErrOff + 1));
   if (desc->precision == DS_PREC_FP64)
-    na_launch_accum<double>(ks, grid_for(n_t), st, d_pix, d_cos2psi, d_sin2psi, d_valid,
-                            static_cast<const double*>(d_y), scratch, n_t, npix, kk);
+    na_launch_sums<double>(ks, grid_for(n_t), st, d_pix, d_cos2psi, d_sin2psi, d_valid,
+                           static_cast<const double*>(d_y), scratch, n_t, npix, kk);
   else
-    na_launch_accum<float>(ks, grid_for(n_t), st, d_pix, d_cos2psi, d_sin2psi, d_valid,
-                           static_cast<const float*>(d_y), scratch, n_t, npix, kk);
+    na_launch_sums<float>(ks, grid_for(n_t), st, d_pix, d_cos2psi, d_sin2psi, d_valid,
+                          static_cast<const float*>(d_y), scratch, n_t, npix, kk);
   const int pg = grid_for(npix);
-  if (n_c == 1) k_na_finish<1><<<pg, kBlock, 0, st>>>(scratch, npix, rcond_min, d_map, d_hits, d_mask);
-  else if (n_c == 2) k_na_finish<2><<<pg, kBlock, 0, st>>>(scratch, npix, rcond_min, d_map, d_hits, d_mask);
-  else k_na_finish<3><<<pg, kBlock, 0, st>>>(scratch, npix, rcond_min, d_map, d_hits, d_mask);
+  if (n_c == 1) k_na_map<1><<<pg, kBlock, 0, st>>>(scratch, npix, d_map, d_hits, d_mask);
+  else if (n_c == 2) k_na_map<2><<<pg, kBlock, 0, st>>>(scratch, npix, d_map, d_hits, d_mask);
+  else k_na_map<3><<<pg, kBlock, 0, st>>>(scratch, npix, d_map, d_hits, d_mask);
   if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
-  int32_t err = 0;
-  if (cudaMemcpyAsync(&err, scratch + kErrOff, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+  int32_t err_h = 0;
+  if (cudaMemcpyAsync(&err_h, scratch + kErrOff, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return DS_ECUDA;
-  return err ? DS_EPIX : DS_OK;
+  return (err_h & ERR_PIX) ? DS_EPIX : DS_OK;
 }

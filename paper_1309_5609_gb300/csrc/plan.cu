@@ -7,6 +7,7 @@
 
 #include "df.cuh"
 #include "internal.cuh"
+#include "pixmat.cuh"
 #include "rows.cuh"
 
 namespace ds {
@@ -205,72 +206,6 @@ __global__ void __launch_bounds__(kBlock) k_plan_accum(const int32_t* __restrict
   }
 }
 
-// Closed-form eigenvalues of a packed symmetric matrix; rcond = lambda_min / lambda_max.
-// 2x2: mid +- radius.  3x3: the trigonometric solution of the characteristic cubic.
-template <int NC>
-__device__ double rcond_of(const double (&a)[NC * (NC + 1) / 2]) {
-  if constexpr (NC == 1) {
-    return a[0] > 0.0 ? 1.0 : 0.0;
-  } else if constexpr (NC == 2) {
-    const double mid = 0.5 * (a[0] + a[2]);
-    const double half = 0.5 * (a[0] - a[2]);
-    const double rad = sqrt(half * half + a[1] * a[1]);
-    const double lmax = mid + rad;
-    if (!(lmax > 0.0)) return 0.0;
-    const double det = a[0] * a[2] - a[1] * a[1];
-    return (det / lmax) / lmax;  // lambda_min = det / lambda_max
-  } else {
-    const double a00 = a[0], a01 = a[1], a02 = a[2], a11 = a[3], a12 = a[4], a22 = a[5];
-    const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
-    double e1, e3;
-    if (p1 == 0.0) {
-      e1 = fmax(a00, fmax(a11, a22));
-      e3 = fmin(a00, fmin(a11, a22));
-    } else {
-      const double q = (a00 + a11 + a22) / 3.0;
-      const double d0 = a00 - q, d1 = a11 - q, d2 = a22 - q;
-      const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
-      const double pp = sqrt(p2 / 6.0);
-      const double ip = 1.0 / pp;
-      const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip;
-      const double b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
-      const double detb = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
-                          b02 * (b01 * b12 - b11 * b02);
-      double r = 0.5 * detb;
-      r = fmin(1.0, fmax(-1.0, r));
-      const double phi = acos(r) / 3.0;
-      e1 = q + 2.0 * pp * cos(phi);
-      e3 = q + 2.0 * pp * cos(phi + 2.0943951023931954923);  // + 2 pi / 3
-    }
-    if (!(e1 > 0.0)) return 0.0;
-    return e3 / e1;
-  }
-}
-
-template <int NC>
-__device__ void sym_inverse(const double (&a)[NC * (NC + 1) / 2], double (&inv)[NC * (NC + 1) / 2]) {
-  if constexpr (NC == 1) {
-    inv[0] = 1.0 / a[0];
-  } else if constexpr (NC == 2) {
-    const double det = a[0] * a[2] - a[1] * a[1];
-    inv[0] = a[2] / det;
-    inv[1] = -a[1] / det;
-    inv[2] = a[0] / det;
-  } else {
-    const double a00 = a[0], a01 = a[1], a02 = a[2], a11 = a[3], a12 = a[4], a22 = a[5];
-    const double c00 = a11 * a22 - a12 * a12;
-    const double c01 = a02 * a12 - a01 * a22;
-    const double c02 = a01 * a12 - a02 * a11;
-    const double c11 = a00 * a22 - a02 * a02;
-    const double c12 = a01 * a02 - a00 * a12;
-    const double c22 = a00 * a11 - a01 * a01;
-    const double det = a00 * c00 + a01 * c01 + a02 * c02;
-    const double id = 1.0 / det;
-    inv[0] = c00 * id; inv[1] = c01 * id; inv[2] = c02 * id;
-    inv[3] = c11 * id; inv[4] = c12 * id; inv[5] = c22 * id;
-  }
-}
-
 // Per pixel: rcond cut and M_p^-1 (in place over M), mask, good-pixel count.
 template <int NC>
 __global__ void __launch_bounds__(kBlock) k_pixel_invert(double* __restrict__ mm,
@@ -359,6 +294,29 @@ __global__ void __launch_bounds__(kBlock) k_plan_weights(const int32_t* __restri
 
 }  // namespace
 
+void launch_plan_matrices(int kindset, bool df, int grid, cudaStream_t st, const int32_t* pix,
+                          const float* c, const float* s, const uint8_t* valid, int32_t* hits,
+                          double* mm, int64_t n_t, int64_t npix, KindsArg kk, int32_t* err) {
+  with_kindset(kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (df)
+      k_plan_accum_df<KS><<<grid, kBlock, 0, st>>>(pix, c, s, valid, hits, mm, n_t, npix, kk, err);
+    else
+      k_plan_accum<KS><<<grid, kBlock, 0, st>>>(pix, c, s, valid, hits, mm, n_t, npix, kk, err);
+  });
+}
+
+void launch_pixel_invert(int n_c, int grid, cudaStream_t st, double* mm, const int32_t* hits,
+                         uint8_t* mask, int64_t npix, double rcond_min,
+                         unsigned long long* n_good) {
+  if (n_c == 1)
+    k_pixel_invert<1><<<grid, kBlock, 0, st>>>(mm, hits, mask, npix, rcond_min, n_good);
+  else if (n_c == 2)
+    k_pixel_invert<2><<<grid, kBlock, 0, st>>>(mm, hits, mask, npix, rcond_min, n_good);
+  else
+    k_pixel_invert<3><<<grid, kBlock, 0, st>>>(mm, hits, mask, npix, rcond_min, n_good);
+}
+
 ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid) {
   cudaStream_t st = P.stream;
   const int nm = P.nm;
@@ -368,24 +326,16 @@ ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid) {
   DS_CUDA_TRY(cudaMemsetAsync(P.err, 0, sizeof(int32_t), st));
   DS_CUDA_TRY(cudaMemsetAsync(P.scal, 0, sizeof(double) * 8, st));
   const int grid = stream_grid(P, (P.n_t + 3) / 4, kBlock, 8);
-  with_kindset(P.kindset, [&](auto ksc) {
-    constexpr int KS = decltype(ksc)::value;
-    if (P.desc.precision == DS_PREC_MIXED && P.accurate_df)
-      k_plan_accum_df<KS><<<grid, kBlock, 0, st>>>(d_pix, P.c, P.s, d_valid, P.hits, P.minv,
-                                                    P.n_t, P.npix, P.kinds, P.err);
-    else
-      k_plan_accum<KS><<<grid, kBlock, 0, st>>>(d_pix, P.c, P.s, d_valid, P.hits, P.minv, P.n_t,
-                                                 P.npix, P.kinds, P.err);
-  });
+  launch_plan_matrices(P.kindset, P.desc.precision == DS_PREC_MIXED && P.accurate_df, grid, st,
+                       d_pix, P.c, P.s, d_valid, P.hits, P.minv, P.n_t, P.npix, P.kinds, P.err);
   DS_CUDA_TRY(cudaGetLastError());
+  // a sharded plan cuts on the hits and matrices of all ranks
+  shard_exchange(P, st, P.hits, P.npix, DS_DT_I32);
+  shard_exchange(P, st, P.minv, P.npix * nm, DS_DT_F64);
+  if (P.shard_err) return DS_ECUDA;
   unsigned long long* counts = reinterpret_cast<unsigned long long*>(P.scal);
   const int pgrid = stream_grid(P, P.npix, kBlock, 8);
-  if (P.n_c == 1)
-    k_pixel_invert<1><<<pgrid, kBlock, 0, st>>>(P.minv, P.hits, P.mask, P.npix, P.desc.rcond_min, counts);
-  else if (P.n_c == 2)
-    k_pixel_invert<2><<<pgrid, kBlock, 0, st>>>(P.minv, P.hits, P.mask, P.npix, P.desc.rcond_min, counts);
-  else
-    k_pixel_invert<3><<<pgrid, kBlock, 0, st>>>(P.minv, P.hits, P.mask, P.npix, P.desc.rcond_min, counts);
+  launch_pixel_invert(P.n_c, pgrid, st, P.minv, P.hits, P.mask, P.npix, P.desc.rcond_min, counts);
   DS_CUDA_TRY(cudaGetLastError());
   k_plan_weights<<<grid, kBlock, 0, st>>>(d_pix, d_valid, P.mask, P.pix, P.nvalid, P.n_t, P.npix,
                                           P.L, counts + 1);

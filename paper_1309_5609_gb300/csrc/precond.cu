@@ -494,9 +494,12 @@ void pc_free(Plan& P, cudaStream_t st) {
   P.pc_n = 0;
   P.pc_cells = 0;
   P.pc_built = 0;
+  P.pc_fallback = 0;
 }
 
-bool pc_ready(const Plan& P) { return P.precond == 2 && P.pc_built && P.pc_n > 0; }
+bool pc_ready(const Plan& P) {
+  return P.precond == 2 && P.pc_built && P.pc_n > 0 && !P.pc_fallback;
+}
 
 // Builds the coarse space and E^+ on the plan's stream (synchronises it).  The
 // second term of E reads the pixel-major copy of the run records; a plan whose

@@ -172,3 +172,18 @@ def test_gapfill_and_spectrum_reject_bad_arguments_before_device_work(lib):
     # the preconditioner's tune keys exist (a null plan is still refused first)
     assert lib.destripe_tune(None, b"precond", 2.0) == ds.DS_EINVAL
     assert lib.destripe_tune(None, b"coarse_nside", 8.0) == ds.DS_EINVAL
+
+
+def test_sharded_entry_points_reject_bad_arguments_before_device_work(lib):
+    ok = ctypes.c_void_p(256)
+    d = _desc()
+    out = ctypes.c_void_p()
+    assert lib.destripe_plan_sharded(ctypes.byref(d), None, ok, ok, ok, None,
+                                     ctypes.byref(out)) == ds.DS_EINVAL
+    ex = ds.ds_exchange(ds.ALLREDUCE_FN(0), None)
+    assert lib.destripe_plan_sharded(ctypes.byref(d), ctypes.byref(ex), ok, ok, ok, None,
+                                     ctypes.byref(out)) == ds.DS_EINVAL
+    it = ctypes.c_int32()
+    rel = ctypes.c_double()
+    assert lib.destripe_solve_sharded(None, ok, ok, 1e-10, 10, 0, ctypes.byref(it),
+                                      ctypes.byref(rel)) == ds.DS_EINVAL

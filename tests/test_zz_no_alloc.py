@@ -85,3 +85,23 @@ def test_noalloc_rejects_maps_above_the_limit():
                                   prob.s32.data_ptr(), None, prob.y.data_ptr(), m.data_ptr(),
                                   None, None)
     assert st == ds.DS_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_noalloc_bin_matches_the_oracle(precision):
+    # hits and mask bit-exact, the binned map at the float64 bar of the parity tests
+    import oracle
+    dev = torch.device("cuda:0")
+    prob = make_problem(120_001, 32, ("I", "q", "u"), baseline_len=500, seed=23, flag_frac=0.04,
+                        sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
+    ydt = torch.float64 if precision == "fp64" else torch.float32
+    y = prob.y.to(ydt).contiguous()
+    d = prob.numpy()
+    op = oracle.make_plan(d["pix"], d["c"], d["s"], d["valid"], prob.nside, prob.kinds,
+                          prob.baseline_len)
+    ref = oracle.bin_map(op, y.double().numpy())
+    g = prob.to(dev)
+    st, m, h, k = call_c_abi(g, y.to(dev), precision)
+    assert st == ds.DS_OK
+    assert np.array_equal(h, op.hits) and np.array_equal(k.astype(bool), op.mask)
+    assert rel_rms(m.reshape(op.n_c, -1), ref) < 1e-11
