@@ -237,7 +237,7 @@ ds_status destripe_spectrum(ds_plan_t plan, const void* d_y, const double* d_a, 
  * strategy: a spin about the vertical axis at fixed elevation, the sky turning with
  * the Earth; Sect. 3: the parallactic angle psi orients the polarimeter; HEALPix
  * RING pixels as cited in Sect. 3).  For sample k = first_sample + i:
- *   t = k / f_samp, az = az0 + 2 pi t / spin_period, lst = lst0 + 2 pi t / sidereal_day,
+ *   t = k (1 / f_samp), az = az0 + 2 pi t / spin_period, lst = lst0 + 2 pi t / sidereal_day,
  *   sin dec = sin el sin lat + cos el cos lat cos az,
  *   H = atan2(-sin az cos el, sin el cos lat - cos el sin lat cos az), RA = lst - H mod 2 pi,
  *   psi = atan2(sin H, tan lat cos dec - sin dec cos H) + 2 pi t / pol_rotation_period

@@ -4,7 +4,7 @@
 // (Sect. 3, the polarimeter's orientation), an optional polarisation modulator, and
 // the HEALPix RING pixel of each sample (Gorski et al. 2005, as cited in Sect. 3).
 //
-//     t        = k / f_samp
+//     t        = k (1 / f_samp)
 //     az       = az0 + (2 pi / T_spin) t,    lst = lst0 + (2 pi / T_sidereal) t
 //     sin dec  = sin el sin lat + cos el cos lat cos az
 //     H        = atan2(-sin az cos el, sin el cos lat - cos el sin lat cos az)
@@ -32,7 +32,7 @@ namespace {
 constexpr int kBlock = 256;
 
 struct ScanConst {
-  double f_samp;
+  double inv_fs;                // 1 / f_samp
   double w_spin, w_sid, w_mod;  // 2 pi / period (w_mod = 0: no modulator)
   double az0, lst0;
   double a_sd, b_sd;            // sin el sin lat, cos el cos lat
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kBlock) k_scan_pointing(ScanConst k, int64_t f
                                                           float* __restrict__ s2) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double t = __ddiv_rn((double)(first + i), k.f_samp);
+    const double t = __dmul_rn((double)(first + i), k.inv_fs);
     const double az = __dadd_rn(k.az0, __dmul_rn(k.w_spin, t));
     const double lst = __dadd_rn(k.lst0, __dmul_rn(k.w_sid, t));
     const double cos_az = cos(az), sin_az = sin(az);
@@ -131,7 +131,7 @@ extern "C" ds_status destripe_scan_pointing(const ds_scan* scan, int64_t first_s
   if (n_samples == 0) return DS_OK;
   const double pi = 3.141592653589793;
   ScanConst k{};
-  k.f_samp = scan->f_samp;
+  k.inv_fs = 1.0 / scan->f_samp;
   k.w_spin = 2.0 * pi / scan->spin_period;
   k.w_sid = 2.0 * pi / scan->sidereal_day;
   k.w_mod = scan->pol_rotation_period > 0.0 ? 2.0 * pi / scan->pol_rotation_period : 0.0;

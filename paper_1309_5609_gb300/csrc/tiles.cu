@@ -155,20 +155,54 @@ __global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict_
 
 // ---- the operator's passes --------------------------------------------------------
 
-struct TileRun {
-  int pix;
-  float n, c, s;
-  int bl;
-};
+constexpr int kUnroll = 4;  // records per lane loaded before any is used (bytes in flight)
 
-__device__ __forceinline__ TileRun load_tile_run(const int4* __restrict__ rec, int64_t i) {
-  const int4 v = __ldcs(rec + i);
-  return TileRun{v.x, (float)((unsigned)v.y >> 24), __int_as_float(v.z), __int_as_float(v.w),
-                 (int)((unsigned)v.y & 0xFFFFFFu)};
+// One round of 32 records of a warp's share: lane sums of equal pixels (the
+// records are sorted by pixel within the tile), the carried pixel of the previous
+// round joined to lane 0, one reduction per other segment, the last segment
+// carried on.
+template <int NC>
+__device__ __forceinline__ void tl_bin_round(int key, float (&acc)[NC], int& ckey,
+                                             float (&carry)[NC], float* __restrict__ bins) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0 && ckey >= 0) {
+    if (key == ckey) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] += carry[j];
+    } else {
+      flush_bins<NC, float>(bins, ckey, carry);
+    }
+  }
+  const int nxt = __shfl_down_sync(full, key, 1);
+  bool stop = lane == 31 || nxt != key;
+#pragma unroll
+  for (int w = 1; w < 32; w <<= 1) {
+    float v2[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) v2[j] = __shfl_down_sync(full, acc[j], w);
+    const bool s2 = __shfl_down_sync(full, stop, w);
+    if (!stop) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] += v2[j];
+      stop = s2;
+    }
+  }
+  const int prv = __shfl_up_sync(full, key, 1);
+  const bool head = key >= 0 && (lane == 0 || prv != key);
+  const unsigned heads = __ballot_sync(full, head);
+  const int last = heads ? 31 - __clz(heads) : -1;
+  const int lkey = __shfl_sync(full, key, 31);
+  const bool carry_last = last >= 0 && __shfl_sync(full, key, last) == lkey && lkey >= 0;
+  if (head && !(carry_last && lane == last)) flush_bins<NC, float>(bins, key, acc);
+  ckey = carry_last ? lkey : -1;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) carry[j] = __shfl_sync(full, acc[j], last >= 0 ? last : 0);
 }
 
 // bins[p] += sum over the tile's runs on p of the rows summed over the run times
-// the run's baselines (float32).
+// the run's baselines (float32).  A warp takes kUnroll rounds of 32 records at a
+// time: all their loads are issued before the first round is summed.
 template <int KS>
 __global__ void __launch_bounds__(kTileThreads) k_tl_bin(const int4* __restrict__ rec,
                                                          const int64_t* __restrict__ tile_off,
@@ -181,7 +215,6 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_bin(const int4* __restrict_
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
   extern __shared__ float xs[];  // [n_o][Tb]
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t b0 = t * Tb;
@@ -198,54 +231,30 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_bin(const int4* __restrict_
     float carry[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) carry[j] = 0.f;
-    for (int64_t base = lo; base < hi; base += 32) {
-      const int64_t i = base + lane;
-      float acc[NC];
+    for (int64_t base = lo; base < hi; base += 32 * kUnroll) {
+      int4 v[kUnroll];
 #pragma unroll
-      for (int j = 0; j < NC; ++j) acc[j] = 0.f;
-      int key = -1;
-      if (i < hi) {
-        const TileRun r = load_tile_run(rec, i);
-        key = r.pix;
-#pragma unroll
-        for (int o = 0; o < NO; ++o)
-          if (o < n_o) run_bin<NC>(K::kind(o, kk), r.n, r.c, r.s, xs[o * Tb + r.bl], acc);
+      for (int u = 0; u < kUnroll; ++u) {
+        const int64_t i = base + 32 * u + lane;
+        v[u] = i < hi ? __ldcs(rec + i) : make_int4(-1, 0, 0, 0);
       }
-      // the carried pixel joins lane 0 if the round starts on it, else it is flushed
-      if (lane == 0 && ckey >= 0) {
-        if (key == ckey) {
 #pragma unroll
-          for (int j = 0; j < NC; ++j) acc[j] += carry[j];
-        } else {
-          flush_bins<NC, float>(bins, ckey, carry);
+      for (int u = 0; u < kUnroll; ++u) {
+        if (base + 32 * u >= hi) break;  // warp-uniform
+        float acc[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+        const int key = v[u].x;
+        if (key >= 0) {
+          const float n = (float)((unsigned)v[u].y >> 24);
+          const int bl = (int)((unsigned)v[u].y & 0xFFFFFFu);
+          const float c = __int_as_float(v[u].z), sn = __int_as_float(v[u].w);
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+            if (o < n_o) run_bin<NC>(K::kind(o, kk), n, c, sn, xs[o * Tb + bl], acc);
         }
+        tl_bin_round<NC>(key, acc, ckey, carry, bins);
       }
-      // segmented sums over the lanes: each segment's total lands in its first lane
-      const int nxt = __shfl_down_sync(full, key, 1);
-      bool stop = lane == 31 || nxt != key;
-#pragma unroll
-      for (int w = 1; w < 32; w <<= 1) {
-        float v2[NC];
-#pragma unroll
-        for (int j = 0; j < NC; ++j) v2[j] = __shfl_down_sync(full, acc[j], w);
-        const bool s2 = __shfl_down_sync(full, stop, w);
-        if (!stop) {
-#pragma unroll
-          for (int j = 0; j < NC; ++j) acc[j] += v2[j];
-          stop = s2;
-        }
-      }
-      const int prv = __shfl_up_sync(full, key, 1);
-      const bool head = key >= 0 && (lane == 0 || prv != key);
-      // the last segment of the round is carried into the next one
-      const unsigned heads = __ballot_sync(full, head);
-      const int last = heads ? 31 - __clz(heads) : -1;
-      const int lkey = __shfl_sync(full, key, 31);
-      const bool carry_last = last >= 0 && __shfl_sync(full, key, last) == lkey && lkey >= 0;
-      if (head && !(carry_last && lane == last)) flush_bins<NC, float>(bins, key, acc);
-      ckey = carry_last ? lkey : -1;
-#pragma unroll
-      for (int j = 0; j < NC; ++j) carry[j] = __shfl_sync(full, acc[j], last >= 0 ? last : 0);
     }
     if (lane == 0 && ckey >= 0) flush_bins<NC, float>(bins, ckey, carry);
     __syncthreads();
@@ -253,7 +262,9 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_bin(const int4* __restrict_
 }
 
 // out[o][b] = sum over the tile's runs in baseline b of n x[o][b] - (row sums) . m_p
-// (float32 sums in shared memory, one float64 store per baseline).
+// (float32 sums in shared memory, one float64 store per baseline).  Each thread
+// issues the loads of kUnroll records, then their map rows and baselines, before
+// any sum.
 template <int KS>
 __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restrict__ rec,
                                                             const int64_t* __restrict__ tile_off,
@@ -273,17 +284,35 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
     for (int64_t j = threadIdx.x; j < (int64_t)n_o * Tb; j += blockDim.x) sums[j] = 0.f;
     __syncthreads();
     const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      const TileRun r = load_tile_run(rec, i);
-      float m[NC];
-      load_map<NC, float>(map, r.pix, m);
+    for (int64_t base = r0 + threadIdx.x; base < r1; base += (int64_t)kUnroll * blockDim.x) {
+      int4 v[kUnroll];
 #pragma unroll
-      for (int o = 0; o < NO; ++o) {
-        if (o < n_o) {
-          const float z = __ldg(x + o * n_b + b0 + r.bl);
-          const float v = fmaf(r.n, z, -run_dot<NC>(K::kind(o, kk), r.n, r.c, r.s, m));
-          atomicAdd(sums + o * Tb + r.bl, v);
+      for (int u = 0; u < kUnroll; ++u) {
+        const int64_t i = base + (int64_t)u * blockDim.x;
+        v[u] = i < r1 ? __ldcs(rec + i) : make_int4(-1, 0, 0, 0);
+      }
+      float m[kUnroll][NC];
+      float z[kUnroll][NO];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int bl = (int)((unsigned)v[u].y & 0xFFFFFFu);
+        if (v[u].x >= 0) {
+          load_map<NC, float>(map, v[u].x, m[u]);
+#pragma unroll
+          for (int o = 0; o < NO; ++o) z[u][o] = o < n_o ? __ldg(x + o * n_b + b0 + bl) : 0.f;
         }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (v[u].x < 0) continue;
+        const float n = (float)((unsigned)v[u].y >> 24);
+        const int bl = (int)((unsigned)v[u].y & 0xFFFFFFu);
+        const float c = __int_as_float(v[u].z), sn = __int_as_float(v[u].w);
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o)
+            atomicAdd(sums + o * Tb + bl,
+                      fmaf(n, z[u][o], -run_dot<NC>(K::kind(o, kk), n, c, sn, m[u])));
       }
     }
     __syncthreads();
