@@ -465,6 +465,8 @@ def run_ours(args):
                               else ""),
                            runs_per_sample=layout.get("n_runs", 0) / prob.n_t), "roofline": roof,
             "iterations_per_step": iters_tot / args.steps,
+            "full_solve_s": t_ms_all / args.steps / 1e3,
+            "timeline_samples_per_s": float(prob.n_t) * world / (t_ms_all / args.steps / 1e3),
             "rel_resid_max": max(rels) if rels else None,
             "gpu_launches": int(prof.get("kernel_launches", 0)),
             "clocks": clk.summary()}

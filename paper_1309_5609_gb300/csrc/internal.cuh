@@ -218,6 +218,10 @@ struct Plan {
   int64_t tl_tb;
   int tl_bin_blocks;        // resident blocks per SM of the two passes
   int tl_rescan_blocks;
+  int4* tl2_rec;            // the same records sorted by pixel within long tiles (binning)
+  int64_t* tl2_off;         // [tiles + 1]
+  int64_t* tl2_chunk;       // [tiles + 1] first warp chunk of each long tile
+  int64_t tl2_tiles, tl2_tb, tl2_chunks;
   int rescan_samples;       // run-length plans: the rescans read the time-ordered samples (dense
                             // runs: a record per run costs more than 12 bytes per sample)
   // preconditioner of the CG (precond.cu): 0 none, 1 D^-1 (valid samples per

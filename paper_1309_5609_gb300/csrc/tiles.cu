@@ -23,6 +23,8 @@
 //    gathered by every lane of its run group at one address; the block stores
 //    its baselines' sums once (each baseline belongs to one tile: no atomics in
 //    global memory).
+#include <vector>
+
 #include "internal.cuh"
 #include "rows.cuh"
 #include "runs.cuh"
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict_
 // ---- the operator's passes --------------------------------------------------------
 
 constexpr int kUnroll = 4;  // records per lane loaded before any is used (bytes in flight)
+constexpr int64_t kChunk = 32 * kUnroll * 16;  // records per warp chunk of the long-tile binning
 
 // One round of 32 records of a warp's share: lane sums of equal pixels (the
 // records are sorted by pixel within the tile), the carried pixel of the previous
@@ -323,6 +326,71 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
   }
 }
 
+// The binning over long tiles (many days: each pixel's runs of a tile are summed
+// in registers, so that reductions are few): warps take chunks of kChunk records
+// of one tile, gather the baselines from L2 (the tile's baselines span a few MB),
+// and carry their last pixel across rounds as k_tl_bin does.
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_tl_bin_long(const int4* __restrict__ rec,
+                                                        const int64_t* __restrict__ tile_off,
+                                                        const int64_t* __restrict__ chunk_first,
+                                                        int64_t n_tiles, int64_t n_chunks,
+                                                        int64_t Tb, const float* __restrict__ x,
+                                                        float* __restrict__ bins, int64_t n_b,
+                                                        KindsArg kk, Gate g) {
+  if (gate_closed(g)) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t ch = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < n_chunks;
+       ch += warps) {
+    int64_t t = 0;  // the chunk's tile: few tiles, a linear walk
+    while (t + 1 < n_tiles && chunk_first[t + 1] <= ch) ++t;
+    const int64_t lo = tile_off[t] + (ch - chunk_first[t]) * kChunk;
+    const int64_t hi = lo + kChunk < tile_off[t + 1] ? lo + kChunk : tile_off[t + 1];
+    const float* xb = x + t * Tb;
+    int ckey = -1;
+    float carry[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) carry[j] = 0.f;
+    for (int64_t base = lo; base < hi; base += 32 * kUnroll) {
+      int4 v[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int64_t i = base + 32 * u + lane;
+        v[u] = i < hi ? __ldcs(rec + i) : make_int4(-1, 0, 0, 0);
+      }
+      float z[kUnroll][NO];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int bl = (int)((unsigned)v[u].y & 0xFFFFFFu);
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          z[u][o] = (o < n_o && v[u].x >= 0) ? __ldg(xb + o * n_b + bl) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (base + 32 * u >= hi) break;  // warp-uniform
+        float acc[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+        const int key = v[u].x;
+        if (key >= 0) {
+          const float n = (float)((unsigned)v[u].y >> 24);
+          const float c = __int_as_float(v[u].z), sn = __int_as_float(v[u].w);
+#pragma unroll
+          for (int o = 0; o < NO; ++o)
+            if (o < n_o) run_bin<NC>(K::kind(o, kk), n, c, sn, z[u][o], acc);
+        }
+        tl_bin_round<NC>(key, acc, ckey, carry, bins);
+      }
+    }
+    if (lane == 0 && ckey >= 0) flush_bins<NC, float>(bins, ckey, carry);
+  }
+}
+
 }  // namespace
 
 bool tl_ready(const Plan& P) { return P.layout == 3 && P.tl_rec != nullptr && P.x32 != nullptr; }
@@ -333,6 +401,15 @@ static int tl_grid(const Plan& P, int per_sm) {
 }
 
 void launch_bin_tl(const Plan& P, cudaStream_t st, Gate g) {
+  if (P.tl2_rec != nullptr) {
+    with_kindset(P.kindset, [&](auto ksc) {
+      constexpr int KS = decltype(ksc)::value;
+      k_tl_bin_long<KS><<<stream_grid(P, P.tl2_chunks * 32, kBlock, 8), kBlock, 0, st>>>(
+          P.tl2_rec, P.tl2_off, P.tl2_chunk, P.tl2_tiles, P.tl2_chunks, P.tl2_tb, P.x32, P.bins32,
+          P.n_b, P.kinds, g);
+    });
+    return;
+  }
   const size_t smem = sizeof(float) * (size_t)P.n_o * P.tl_tb;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
@@ -350,27 +427,78 @@ void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g) {
   });
 }
 
-// Builds the tiled records from the time-ordered run records (stream-ordered on
-// the plan's stream, one host synchronisation for the longest run).  Returns
-// DS_ESTATE, leaving nothing behind, when a run is longer than 255 samples.
+// Sorts the time-ordered runs by pixel within tiles of Tb baselines into *out_rec
+// (16-byte records), with the tiles' first records in *out_off (stream-ordered on
+// the plan's stream; one counting sort per tile over the pixels).
+static cudaError_t tl_sort(Plan& P, int64_t Tb, int4** out_rec, int64_t** out_off) {
+  cudaStream_t st = P.stream;
+  const int64_t n_tiles = (P.n_b + Tb - 1) / Tb;
+  const int64_t npix = P.npix;
+  const int64_t g = stream_grid(P, npix, kBlock, 8);
+  const int64_t S = (npix + g - 1) / g, G = (npix + S - 1) / S;
+  uint32_t* cnt = nullptr;
+  int64_t *blk = nullptr, *pos = nullptr;
+  cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(out_rec), sizeof(int4) * P.rl_n, true);
+  if (e == cudaSuccess)
+    e = plan_alloc(P, reinterpret_cast<void**>(out_off), sizeof(int64_t) * (n_tiles + 1), true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * G, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&pos), sizeof(int64_t) * npix, false);
+  if (e == cudaSuccess) {
+    k_tl_bounds<<<(unsigned)((n_tiles + 1 + 127) / 128), 128, 0, st>>>(P.rl_b, P.rl_n, n_tiles,
+                                                                       Tb, *out_off);
+    const int rg = stream_grid(P, (P.rl_n + n_tiles - 1) / n_tiles, kBlock, 8);
+    for (int64_t t = 0; t < n_tiles && e == cudaSuccess; ++t) {
+      e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st);
+      if (e != cudaSuccess) break;
+      k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, *out_off, t, cnt);
+      k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk);
+      k_tl_scan_top<<<1, 1, 0, st>>>(blk, G, *out_off, t);
+      k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk, pos);
+      k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, *out_off, t, Tb,
+                                          reinterpret_cast<unsigned long long*>(pos), *out_rec);
+      P.launches += 5;
+      e = cudaGetLastError();
+    }
+  }
+  for (void* t : {(void*)cnt, (void*)blk, (void*)pos})
+    if (t) cudaFreeAsync(t, st);
+  return e;
+}
+
+static void tl_free(Plan& P) {
+  void* mine[] = {P.tl_rec, P.tl_off, P.tl2_rec, P.tl2_off, P.tl2_chunk};
+  for (void* t : mine)
+    if (t) cudaFreeAsync(t, P.stream);
+  P.tl_rec = nullptr;
+  P.tl_off = nullptr;
+  P.tl2_rec = nullptr;
+  P.tl2_off = nullptr;
+  P.tl2_chunk = nullptr;
+}
+
+// Builds the tiled records from the time-ordered run records: tiles of a few
+// hours for the rescan (their baseline sums fit in shared memory), and tiles of
+// about 2^26 samples for the binning (each pixel's runs of many days summed in
+// registers).  One host synchronisation for the longest run, one for the chunk
+// table.  Returns DS_ESTATE, leaving nothing behind, when a run is longer than
+// 255 samples.
 ds_status tl_build(Plan& P) {
   if (P.rl_rec == nullptr || P.rl_n <= 0) return DS_ESTATE;
   cudaStream_t st = P.stream;
   int64_t Tb = kTileFloats / P.n_o;
   if (Tb > P.n_b) Tb = P.n_b;
-  const int64_t n_tiles = (P.n_b + Tb - 1) / Tb;
-  const int64_t npix = P.npix;
-  const int64_t g = stream_grid(P, npix, kBlock, 8);
-  const int64_t S = (npix + g - 1) / g, G = (npix + S - 1) / S;
+  int64_t Tb2 = (int64_t(1) << 26) / P.L;
+  if (Tb2 > (int64_t(1) << 24) - 1) Tb2 = (int64_t(1) << 24) - 1;
+  if (Tb2 < Tb) Tb2 = Tb;
+  if (Tb2 > P.n_b) Tb2 = P.n_b;
+  const int64_t n_tiles = (P.n_b + Tb - 1) / Tb, n_tiles2 = (P.n_b + Tb2 - 1) / Tb2;
   int* longest = nullptr;
-  uint32_t* cnt = nullptr;
-  int64_t *blk = nullptr, *pos = nullptr;
+  const int64_t held_before = P.device_bytes;
   auto release = [&](cudaError_t e) {
-    void* tmp[] = {longest, cnt, blk, pos, P.tl_rec, P.tl_off};
-    for (void* t : tmp)
-      if (t) cudaFreeAsync(t, st);
-    P.tl_rec = nullptr;
-    P.tl_off = nullptr;
+    if (longest) cudaFreeAsync(longest, st);
+    tl_free(P);
+    P.device_bytes = held_before;
     return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
   };
   cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(&longest), sizeof(int), false);
@@ -381,41 +509,36 @@ ds_status tl_build(Plan& P) {
   e = cudaMemcpyAsync(&h_longest, longest, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return release(e);
+  cudaFreeAsync(longest, st);
+  longest = nullptr;
   if (h_longest > 255) {
     release(cudaSuccess);
     return DS_ESTATE;
   }
-  const int64_t held_before = P.device_bytes;
-  e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_rec), sizeof(int4) * P.rl_n, true);
-  if (e == cudaSuccess)
-    e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_off), sizeof(int64_t) * (n_tiles + 1), true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * G, false);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&pos), sizeof(int64_t) * npix, false);
-  if (e != cudaSuccess) {
-    P.device_bytes = held_before;
-    return release(e);
+  e = tl_sort(P, Tb, &P.tl_rec, &P.tl_off);
+  if (e != cudaSuccess) return release(e);
+  // the long tiles and their chunk table (tile t's chunks start at chunk_first[t])
+  if (n_tiles2 < n_tiles) {
+    e = tl_sort(P, Tb2, &P.tl2_rec, &P.tl2_off);
+    std::vector<int64_t> off(n_tiles2 + 1), first(n_tiles2 + 1);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(off.data(), P.tl2_off, sizeof(int64_t) * (n_tiles2 + 1),
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return release(e);
+    first[0] = 0;
+    for (int64_t t = 0; t < n_tiles2; ++t)
+      first[t + 1] = first[t] + (off[t + 1] - off[t] + kChunk - 1) / kChunk;
+    e = plan_alloc(P, reinterpret_cast<void**>(&P.tl2_chunk), sizeof(int64_t) * (n_tiles2 + 1), true);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P.tl2_chunk, first.data(), sizeof(int64_t) * (n_tiles2 + 1),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // first[] leaves scope
+    if (e != cudaSuccess) return release(e);
+    P.tl2_tiles = n_tiles2;
+    P.tl2_tb = Tb2;
+    P.tl2_chunks = first[n_tiles2];
   }
-  k_tl_bounds<<<(unsigned)((n_tiles + 1 + 127) / 128), 128, 0, st>>>(P.rl_b, P.rl_n, n_tiles, Tb,
-                                                                     P.tl_off);
-  const int rg = stream_grid(P, (P.rl_n + n_tiles - 1) / n_tiles, kBlock, 8);
-  for (int64_t t = 0; t < n_tiles && e == cudaSuccess; ++t) {
-    e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st);
-    if (e != cudaSuccess) break;
-    k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, P.tl_off, t, cnt);
-    k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk);
-    k_tl_scan_top<<<1, 1, 0, st>>>(blk, G, P.tl_off, t);
-    k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk, pos);
-    k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, P.tl_off, t, Tb,
-                                        reinterpret_cast<unsigned long long*>(pos), P.tl_rec);
-    P.launches += 5;
-    e = cudaGetLastError();
-  }
-  if (e != cudaSuccess) {
-    P.device_bytes = held_before;
-    return release(e);
-  }
-  for (void* t : {(void*)longest, (void*)cnt, (void*)blk, (void*)pos}) cudaFreeAsync(t, st);
   P.tl_tiles = n_tiles;
   P.tl_tb = Tb;
   // shared arrays above 48 KB need the kernels' opt-in; resident blocks per SM
@@ -435,12 +558,8 @@ ds_status tl_build(Plan& P) {
                                                         kTileThreads, smem);
   });
   if (e != cudaSuccess || P.tl_bin_blocks < 1 || P.tl_rescan_blocks < 1) {
+    tl_free(P);
     P.device_bytes = held_before;
-    void* mine[] = {P.tl_rec, P.tl_off};
-    for (void* t : mine)
-      if (t) cudaFreeAsync(t, st);
-    P.tl_rec = nullptr;
-    P.tl_off = nullptr;
     return e == cudaSuccess ? DS_ESTATE : DS_ECUDA;
   }
   return DS_OK;
