@@ -317,7 +317,17 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     consecutive samples: the sorted distinct pixels and a 16-bit rank per
  *                     sample), bins into shared memory and stages the chunk's map in
  *                     shared memory.  The index is built on the plan's stream when first
- *                     requested (6 bytes per sample of device memory; synchronises)
+ *                     requested (6 bytes per sample of device memory; synchronises);
+ *                     3 = time-tiled, pixel-sorted run records (runs of at most 255
+ *                     samples; 32 bytes per run of device memory, built on request,
+ *                     synchronises): the binning reads the runs sorted by pixel within
+ *                     long tiles ("bin_tile_samples"), each lane summing consecutive
+ *                     runs of one pixel in registers with about one vector reduction per
+ *                     pixel and tile; the rescan reads them sorted within tiles of a few
+ *                     hours whose baseline sums stay in shared memory
+ *   "bin_tile_samples"  layout 3: samples per long tile of the binning (default 2^26,
+ *                     about two weeks at 50 Hz); set before the layout is built, else
+ *                     DS_ESTATE
  *   "chunk"           MIXED plans: rebuild the chunk-local index with this many samples
  *                     per chunk (2048, 4096, 8192 or 16384; synchronises)
  *   "rescan_dedup"    MIXED plans: 1 = the float32 rescan reads the map once per run of

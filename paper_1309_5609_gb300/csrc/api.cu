@@ -114,7 +114,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->tl_rec, P->tl_off, P->tl2_rec, P->tl2_off, P->tl2_chunk, P->pc_cell, P->pc_val, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->tl_rec, P->tl_off, P->tl2_rec, P->tl2_off, P->tl2_chunk, P->tl_x4, P->pc_slot, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a
@@ -325,6 +325,7 @@ ds_status ds::plan_create(const ds_desc* desc, const ds_exchange* ex, const int3
   P->samples_per_thread = 4;
   P->precond = 2;
   P->pc_nside = 8;
+  P->tl_bin_samples = int64_t(1) << 26;
   if (ex != nullptr) {
     P->shard_allreduce = ex->allreduce;
     P->shard_user = ex->user;
@@ -693,6 +694,10 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
       pc_free(P, P.stream);
       P.pc_nside = nc;
     }
+  } else if (k == "bin_tile_samples") {
+    if (!(value >= 1.0 && value <= 1e15) || (double)(int64_t)value != value) return DS_EINVAL;
+    if (P.tl_rec != nullptr) return DS_ESTATE;  // the long tiles are already built
+    P.tl_bin_samples = (int64_t)value;
   } else if (k == "blocks_per_sm") {
     if (!(value >= 1.0 && value <= 32.0)) return DS_EINVAL;
     P.blocks_per_sm = (int)value;

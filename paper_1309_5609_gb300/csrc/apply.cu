@@ -580,7 +580,7 @@ void enqueue_apply(const Plan& P, cudaStream_t st, bool fp64, const double* x, d
     return;
   }
   if (!fp64 && P.bin_mode == 1 && tl_ready(P)) {
-    k_to_f32<<<stream_grid(P, P.n_u, kBlock, 8), kBlock, 0, st>>>(x, P.x32, P.n_u, g);
+    launch_pack_tl(P, st, x, g);
     if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
     launch_bin_tl(P, st, g);
     exchange_sums(P, st, true);

@@ -14,6 +14,7 @@
 #include "cg_state.cuh"
 #include "df.cuh"
 #include "internal.cuh"
+#include "rows.cuh"
 
 namespace ds {
 
@@ -342,65 +343,81 @@ __device__ __forceinline__ double pc_dinv(int nv) {
   return nv > 0 ? f64_of_f32(__frcp_rn((float)nv)) : 0.0;
 }
 
-// Sums of val over each segment of lanes with equal consecutive keys, left in the
-// segment's first lane (keys need not be sorted: a key that comes back later in
-// the warp starts a new segment).
-__device__ __forceinline__ float seg_sum_to_head(int key, float val) {
+// Sums of the NC values over each segment of lanes with equal consecutive keys,
+// left in the segment's first lane (keys need not be sorted: a key that comes
+// back later in the warp starts a new segment).
+template <int NC>
+__device__ __forceinline__ void seg_sum_to_head(int key, float (&val)[NC]) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int next = __shfl_down_sync(full, key, 1);
   bool stop = lane == 31 || next != key;  // the segment ends within [lane, lane + w)
 #pragma unroll
   for (int w = 1; w < 32; w <<= 1) {
-    const float v2 = __shfl_down_sync(full, val, w);
     const bool s2 = __shfl_down_sync(full, stop, w);
-    if (!stop) {
-      val += v2;
-      stop = s2;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float v2 = __shfl_down_sync(full, val[c], w);
+      if (!stop) val[c] += v2;
     }
+    if (!stop) stop = s2;
   }
-  return val;
 }
 
 // u += R^T r (shared-memory sums per block, one flush per block) and
-// r . D^-1 r; mode 1 (no coarse space): rz = r . D^-1 r.
-template <int NC>
+// r . D^-1 r; mode 1 (no coarse space): rz = r . D^-1 r.  One thread per
+// baseline: its outputs' residuals meet the slot's moments in registers.
+template <int KS>
 __global__ void __launch_bounds__(kBlock) k_pc_restrict(const double* __restrict__ r,
                                                         const int32_t* __restrict__ nvalid,
-                                                        const int32_t* __restrict__ cell,
-                                                        const float* __restrict__ val,
-                                                        int64_t n_b, int n_o, int n,
+                                                        const float4* __restrict__ slot,
+                                                        int64_t n_b, KindsArg kk, int n,
                                                         double* __restrict__ u,
                                                         double* __restrict__ red, unsigned* ticket,
                                                         CgState* st) {
   if (st->done) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
   extern __shared__ double s_u[];
   for (int i = threadIdx.x; i < n; i += blockDim.x) s_u[i] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
-  for (int o = 0; o < n_o; ++o) {
-    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; bb < n_b;
-         bb += stride) {
-      const int64_t b = bb + lane;
-      const bool in = b < n_b;
-      const int64_t i = (int64_t)o * n_b + b;
-      const double ri = in ? r[i] : 0.0;
-      if (in) acc = fma(ri * pc_dinv(nvalid[b]), ri, acc);
-      if (n > 0) {
-        const float rf = __double2float_rn(ri);
+  for (int64_t bb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; bb < n_b;
+       bb += stride) {
+    const int64_t b = bb + lane;
+    const bool in = b < n_b;
+    const double dinv = in ? pc_dinv(nvalid[b]) : 0.0;
+    float rf[NO];
 #pragma unroll
-        for (int s = 0; s < kPcSlots; ++s) {
-          const int key = in ? cell[b * kPcSlots + s] : -1;
-          const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-          const bool head = key >= 0 && (lane == 0 || kprev != key);
+    for (int o = 0; o < NO; ++o) {
+      const double ri = (in && o < n_o) ? r[(int64_t)o * n_b + b] : 0.0;
+      acc = fma(ri * dinv, ri, acc);
+      rf[o] = __double2float_rn(ri);
+    }
+    if (n > 0) {
 #pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            const float v = key >= 0 ? val[(i * kPcSlots + s) * NC + c] * rf : 0.f;
-            const float tot = seg_sum_to_head(key, v);
-            if (head) atomicAdd(s_u + key * NC + c, f64_of_f32(tot));
-          }
+      for (int s = 0; s < kPcSlots; ++s) {
+        const float4 m = in ? slot[b * kPcSlots + s] : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+        const int key = __float_as_int(m.x);
+        float v[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c] = 0.f;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          if (o >= n_o) continue;
+          float w[NC];
+          row_moments<NC>(K::kind(o, kk), m.y, m.z, m.w, w);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[c] = fmaf(w[c], rf[o], v[c]);
+        }
+        seg_sum_to_head<NC>(key, v);
+        const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+        if (key >= 0 && (lane == 0 || kprev != key)) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) atomicAdd(s_u + key * NC + c, f64_of_f32(v[c]));
         }
       }
     }
@@ -452,33 +469,47 @@ __global__ void __launch_bounds__(kBlock) k_pc_coarse(const double* __restrict__
   }
 }
 
-// p = D^-1 r + R c + beta p (beta = 0 at the start); q = 0.
-template <int NC>
+// p = D^-1 r + R c + beta p (beta = 0 at the start); q = 0.  One thread per
+// baseline and all its outputs.
+template <int KS>
 __global__ void __launch_bounds__(kBlock) k_pc_direction(double* __restrict__ p,
                                                          const double* __restrict__ r,
                                                          double* __restrict__ q,
                                                          const int32_t* __restrict__ nvalid,
-                                                         const int32_t* __restrict__ cell,
-                                                         const float* __restrict__ val,
+                                                         const float4* __restrict__ slot,
                                                          const float* __restrict__ c,
-                                                         int64_t n_b, int n_o, int n,
+                                                         int64_t n_b, KindsArg kk, int n,
                                                          const CgState* st) {
   if (st->done) return;
+  using K = KSet<KS>;
+  constexpr int NC = K::NC, NO = K::NO;
+  const int n_o = K::n_o(kk);
   const double beta = st->iter == 0 ? 0.0 : st->rz / st->rz_old;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int o = 0; o < n_o; ++o) {
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += stride) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += stride) {
+    const double dinv = pc_dinv(nvalid[b]);
+    float4 m[kPcSlots];
+    float cv[kPcSlots][NC];
+#pragma unroll
+    for (int s = 0; s < kPcSlots; ++s) {
+      m[s] = n > 0 ? slot[b * kPcSlots + s] : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+      const int k = __float_as_int(m[s].x);
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) cv[s][cc] = k >= 0 ? __ldg(c + k * NC + cc) : 0.f;
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      if (o >= n_o) continue;
       const int64_t i = (int64_t)o * n_b + b;
-      double z = pc_dinv(nvalid[b]) * r[i];
+      double z = dinv * r[i];
       if (n > 0) {
         float zc = 0.f;
 #pragma unroll
         for (int s = 0; s < kPcSlots; ++s) {
-          const int k = cell[b * kPcSlots + s];
-          if (k < 0) continue;
+          float w[NC];
+          row_moments<NC>(K::kind(o, kk), m[s].y, m[s].z, m[s].w, w);
 #pragma unroll
-          for (int cc = 0; cc < NC; ++cc)
-            zc = fmaf(val[(i * kPcSlots + s) * NC + cc], __ldg(c + k * NC + cc), zc);
+          for (int cc = 0; cc < NC; ++cc) zc = fmaf(w[cc], cv[s][cc], zc);
         }
         z += f64_of_f32(zc);
       }
@@ -566,20 +597,16 @@ void enqueue_precond_direction(const Plan& P, cudaStream_t st) {
   const bool coarse = pc_ready(P);
   const int n = coarse ? P.pc_n : 0;
   const int vg = vec_grid(P, P.n_b);
-  auto go = [&](auto ncc) {
-    constexpr int NC = decltype(ncc)::value;
-    k_pc_restrict<NC><<<vg, kBlock, sizeof(double) * n, st>>>(
-        P.r, P.nvalid, P.pc_cell, P.pc_val, P.n_b, P.n_o, n, P.pc_u, P.red, P.counters + 4,
-        P.state);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_pc_restrict<KS><<<vg, kBlock, sizeof(double) * n, st>>>(
+        P.r, P.nvalid, P.pc_slot, P.n_b, P.kinds, n, P.pc_u, P.red, P.counters + 4, P.state);
     if (coarse)
       k_pc_coarse<<<stream_grid(P, (int64_t)n * 32, kBlock, 8), kBlock, 0, st>>>(
           P.pc_einv, P.pc_u, P.pc_c, n, P.red, P.counters + 5, P.state);
-    k_pc_direction<NC><<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.nvalid, P.pc_cell, P.pc_val,
-                                             P.pc_c, P.n_b, P.n_o, n, P.state);
-  };
-  if (P.n_c == 1) go(std::integral_constant<int, 1>{});
-  else if (P.n_c == 2) go(std::integral_constant<int, 2>{});
-  else go(std::integral_constant<int, 3>{});
+    k_pc_direction<KS><<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.nvalid, P.pc_slot, P.pc_c, P.n_b,
+                                             P.kinds, n, P.state);
+  });
 }
 
 // accurate: the iteration applies the operator in the accurate arithmetic

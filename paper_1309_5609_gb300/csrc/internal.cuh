@@ -222,6 +222,8 @@ struct Plan {
   int64_t* tl2_off;         // [tiles + 1]
   int64_t* tl2_chunk;       // [tiles + 1] first warp chunk of each long tile
   int64_t tl2_tiles, tl2_tb, tl2_chunks;
+  int64_t tl_bin_samples;   // samples per long tile (tune key "bin_tile_samples")
+  float4* tl_x4;            // [n_b] float32 baselines of every output, per baseline
   int rescan_samples;       // run-length plans: the rescans read the time-ordered samples (dense
                             // runs: a record per run costs more than 12 bytes per sample)
   // preconditioner of the CG (precond.cu): 0 none, 1 D^-1 (valid samples per
@@ -232,8 +234,9 @@ struct Plan {
   int pc_fallback;          // a solve broke down with the coarse correction: D^-1 alone
   int pc_n;                 // coarse columns (kept cells x n_c)
   int pc_cells;             // kept cells
-  int32_t* pc_cell;         // [n_b][kPcSlots] kept-cell number of each slot, -1 = none
-  float* pc_val;            // [n_o][n_b][kPcSlots][n_c] entries of R
+  float4* pc_slot;          // [n_b][kPcSlots] per slot: x = kept-cell number (int bits, -1 =
+                            // none); y, z, w = the cell's share of the baseline's valid
+                            // samples and their cos 2psi, sin 2psi sums over the valid count
   double* pc_einv;          // [pc_n][pc_n] generalised inverse of E = R^T A R
   double* pc_u;             // [pc_n] R^T r, kept at zero between uses
   float* pc_c;              // [pc_n] coarse correction E^+ R^T r, rounded to float32
@@ -276,6 +279,7 @@ bool rl_ready(const Plan& P);
 // tiles.cu: time-tiled, pixel-sorted run records (layout 3)
 ds_status tl_build(Plan& P);
 bool tl_ready(const Plan& P);
+void launch_pack_tl(const Plan& P, cudaStream_t st, const double* x, Gate g);
 void launch_bin_tl(const Plan& P, cudaStream_t st, Gate g);
 void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g);
 void launch_bin_rl(const Plan& P, cudaStream_t st, Gate g);

@@ -15,7 +15,10 @@
 // the best baseline fit of the map that is 1 on component c of cell k.  A
 // baseline keeps at most kPcSlots cells (the ones holding most of its samples;
 // any R gives a valid preconditioner, and the coarse matrix below is built from
-// the R actually stored).  The preconditioner is additive:
+// the R actually stored).  Every row w_o is linear in (1, cos 2psi, sin 2psi), so
+// a slot stores three numbers shared by all outputs (the cell's share of the
+// baseline's valid samples and their cos and sin sums over the valid count) and
+// each output's entries follow from its kind.  The preconditioner is additive:
 //
 //     z = D^-1 r + R E^+ R^T r,   D = diag(n_b),   E = R^T A R,
 //
@@ -126,34 +129,26 @@ __global__ void __launch_bounds__(kBlock) k_pc_cell_table(int32_t* __restrict__ 
 // One thread per baseline: the cells its valid samples fall in (up to kCand, in
 // order of appearance) with each output's row sums per cell; the kPcSlots cells
 // with most samples are kept, their sums divided by the baseline's valid count.
-template <int KS>
 __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ pix,
                                                     const float* __restrict__ cc,
                                                     const float* __restrict__ ss,
                                                     const int32_t* __restrict__ cell_of,
                                                     const int32_t* __restrict__ nvalid,
                                                     int64_t n_t, int64_t L, int64_t n_b,
-                                                    KindsArg kk, int32_t* __restrict__ slot_cell,
-                                                    float* __restrict__ slot_val,
+                                                    float4* __restrict__ slot,
                                                     int32_t* __restrict__ used,
                                                     unsigned long long* __restrict__ kept_total) {
-  using K = KSet<KS>;
-  constexpr int NC = K::NC, NO = K::NO;
-  const int n_o = K::n_o(kk);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long kept_all = 0, valid_all = 0;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += stride) {
     int id[kCand];
     int cnt[kCand];
-    float sum[kCand][NO][NC];
+    float sc[kCand], sn[kCand];  // sums of cos 2psi and sin 2psi per candidate cell
 #pragma unroll
     for (int j = 0; j < kCand; ++j) {
       id[j] = -1;
       cnt[j] = 0;
-#pragma unroll
-      for (int o = 0; o < NO; ++o)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) sum[j][o][c] = 0.f;
+      sc[j] = sn[j] = 0.f;
     }
     const int64_t t1 = (b + 1) * L < n_t ? (b + 1) * L : n_t;
     for (int64_t t = b * L; t < t1; ++t) {
@@ -167,9 +162,8 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
         if (!placed && (id[j] == k || id[j] < 0)) {
           id[j] = k;
           cnt[j] += 1;
-#pragma unroll
-          for (int o = 0; o < NO; ++o)
-            if (o < n_o) row_bin<NC, float>(K::kind(o, kk), c, s, 1.f, sum[j][o]);
+          sc[j] += c;
+          sn[j] += s;
           placed = true;
         }
       }
@@ -186,31 +180,18 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
           best = j;
           bc = cnt[j];
         }
-      int cell = -1;
       kept_all += (unsigned long long)bc;
-      float v[NO][NC];
-#pragma unroll
-      for (int o = 0; o < NO; ++o)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) v[o][c] = 0.f;
+      int cell = -1;
+      float4 v = make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < kCand; ++j)
         if (j == best) {
           cell = id[j];
+          v = make_float4(__int_as_float(id[j]), (float)cnt[j] * inv, sc[j] * inv, sn[j] * inv);
           cnt[j] = 0;
-#pragma unroll
-          for (int o = 0; o < NO; ++o)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) v[o][c] = sum[j][o][c] * inv;
         }
-      slot_cell[b * kPcSlots + s] = cell;
+      slot[b * kPcSlots + s] = v;
       if (cell >= 0) used[cell] = 1;
-#pragma unroll
-      for (int o = 0; o < NO; ++o)
-        if (o < n_o)
-#pragma unroll
-          for (int c = 0; c < NC; ++c)
-            slot_val[(((int64_t)o * n_b + b) * kPcSlots + s) * NC + c] = v[o][c];
     }
     valid_all += (unsigned long long)(nv > 0 ? nv : 0);
   }
@@ -225,37 +206,42 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
 }
 
 // Cell numbers to kept-cell numbers (-1 stays -1).
-__global__ void __launch_bounds__(kBlock) k_pc_remap(int32_t* __restrict__ slot_cell, int64_t n,
+__global__ void __launch_bounds__(kBlock) k_pc_remap(float4* __restrict__ slot, int64_t n,
                                                      const int32_t* __restrict__ cmap) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int c = slot_cell[i];
-    slot_cell[i] = c >= 0 ? cmap[c] : -1;
+    const int c = __float_as_int(slot[i].x);
+    slot[i].x = __int_as_float(c >= 0 ? cmap[c] : -1);
   }
 }
 
 // E += R^T D R: per unknown (o, b), n_b times the outer product of its R row.
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_pc_E_diag(const int32_t* __restrict__ slot_cell,
-                                                      const float* __restrict__ slot_val,
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_pc_E_diag(const float4* __restrict__ slot,
                                                       const int32_t* __restrict__ nvalid,
-                                                      int64_t n_b, int n_o, int n,
+                                                      int64_t n_b, KindsArg kk, int n,
                                                       double* __restrict__ E) {
+  using K = KSet<KS>;
+  constexpr int NC = K::NC;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n_u = (int64_t)n_o * n_b;
+  const int64_t n_u = (int64_t)K::n_o(kk) * n_b;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_u; u += stride) {
     const int64_t b = u % n_b;
+    const int kind = K::kind((int)(u / n_b), kk);
     const int nv = nvalid[b];
     if (nv <= 0) continue;
     int col[kPcSlots * NC];
     double val[kPcSlots * NC];
 #pragma unroll
     for (int s = 0; s < kPcSlots; ++s) {
-      const int cell = slot_cell[b * kPcSlots + s];
+      const float4 m = slot[b * kPcSlots + s];
+      const int cell = __float_as_int(m.x);
+      float v[NC];
+      row_moments<NC>(kind, m.y, m.z, m.w, v);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         col[s * NC + c] = cell >= 0 ? cell * NC + c : -1;
-        val[s * NC + c] = cell >= 0 ? (double)slot_val[(u * kPcSlots + s) * NC + c] : 0.0;
+        val[s * NC + c] = cell >= 0 ? (double)v[c] : 0.0;
       }
     }
 #pragma unroll
@@ -270,10 +256,6 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_diag(const int32_t* __restrict_
   }
 }
 
-__device__ __forceinline__ float f4_get(const float4& v, int i) {
-  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-}
-
 // E -= (K R)^T M^-1 (K R), one warp per pixel over its pixel-major runs.  A run
 // (count n, sum cos, sum sin, baseline b) is one entry of K: the row sums k_o of
 // each output on the pixel's components.  (K R)_p[c'][(cell, c)] =
@@ -283,8 +265,7 @@ __device__ __forceinline__ float f4_get(const float4& v, int i) {
 template <int KS>
 __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict__ off,
                                                      const float4* __restrict__ rec,
-                                                     const int32_t* __restrict__ slot_cell,
-                                                     const float* __restrict__ slot_val,
+                                                     const float4* __restrict__ slot,
                                                      const double* __restrict__ minv,
                                                      const uint8_t* __restrict__ mask,
                                                      int64_t npix, int64_t n_b, KindsArg kk,
@@ -336,12 +317,11 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict_
         }
 #pragma unroll
         for (int s = 0; s < kPcSlots; ++s) {
-          const int cell = __ldg(slot_cell + b * kPcSlots + s);
+          const float4 m = __ldg(slot + b * kPcSlots + s);
+          const int cell = __float_as_int(m.x);
           if (cell < 0) continue;
           float rv[NC];
-#pragma unroll
-          for (int c = 0; c < NC; ++c)
-            rv[c] = __ldg(slot_val + (((int64_t)o * n_b + b) * kPcSlots + s) * NC + c);
+          row_moments<NC>(K::kind(o, kk), m.y, m.z, m.w, rv);
           bool placed = false;
 #pragma unroll
           for (int j = 0; j < kCand; ++j) {
@@ -483,8 +463,7 @@ __global__ void k_pc_diag(const double* __restrict__ E, double* __restrict__ d, 
 }  // namespace
 
 void pc_free(Plan& P, cudaStream_t st) {
-  void** held[] = {reinterpret_cast<void**>(&P.pc_cell), reinterpret_cast<void**>(&P.pc_val),
-                   reinterpret_cast<void**>(&P.pc_einv), reinterpret_cast<void**>(&P.pc_u),
+  void** held[] = {reinterpret_cast<void**>(&P.pc_slot), reinterpret_cast<void**>(&P.pc_einv), reinterpret_cast<void**>(&P.pc_u),
                    reinterpret_cast<void**>(&P.pc_c)};
   for (void** h : held)
     if (*h != nullptr) {
@@ -525,10 +504,7 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&used), sizeof(int32_t) * ncell, false);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cmap), sizeof(int32_t) * ncell, false);
   if (e == cudaSuccess)
-    e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_cell), sizeof(int32_t) * P.n_b * kPcSlots, true);
-  if (e == cudaSuccess)
-    e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_val),
-                   sizeof(float) * P.n_u * kPcSlots * P.n_c, true);
+    e = plan_alloc(P, reinterpret_cast<void**>(&P.pc_slot), sizeof(float4) * P.n_b * kPcSlots, true);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&kept), sizeof(unsigned long long) * 2, false);
   if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, sizeof(int32_t) * ncell, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(kept, 0, sizeof(unsigned long long) * 2, st);
@@ -536,11 +512,8 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   const int g_pix = stream_grid(P, P.npix, kBlock, 8);
   k_pc_cell_table<<<g_pix, kBlock, 0, st>>>(cell_of, P.npix, P.desc.nside, nc);
   const int g_b = stream_grid(P, P.n_b, kBlock, 8);
-  with_kindset(P.kindset, [&](auto ksc) {
-    constexpr int KS = decltype(ksc)::value;
-    k_pc_rows<KS><<<g_b, kBlock, 0, st>>>(P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b,
-                                          P.kinds, P.pc_cell, P.pc_val, used, kept);
-  });
+  k_pc_rows<<<g_b, kBlock, 0, st>>>(P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b,
+                                    P.pc_slot, used, kept);
   P.launches += 2;
   e = cudaGetLastError();
   // kept cells: numbered in cell order on the host
@@ -600,21 +573,18 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   if (e == cudaSuccess) e = cudaMemsetAsync(P.pc_c, 0, sizeof(float) * n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(skipped, 0, sizeof(int32_t) * n, st);
   if (e != cudaSuccess) return fail(e);
-  k_pc_remap<<<g_b, kBlock, 0, st>>>(P.pc_cell, P.n_b * kPcSlots, cmap);
+  k_pc_remap<<<g_b, kBlock, 0, st>>>(P.pc_slot, P.n_b * kPcSlots, cmap);
   const int g_u = stream_grid(P, P.n_u, kBlock, 8);
-  auto by_nc = [&](auto ncc) {
-    constexpr int NC = decltype(ncc)::value;
-    k_pc_E_diag<NC><<<g_u, kBlock, 0, st>>>(P.pc_cell, P.pc_val, P.nvalid, P.n_b, P.n_o, n, E);
-  };
-  if (P.n_c == 1) by_nc(std::integral_constant<int, 1>{});
-  else if (P.n_c == 2) by_nc(std::integral_constant<int, 2>{});
-  else by_nc(std::integral_constant<int, 3>{});
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    k_pc_E_diag<KS><<<g_u, kBlock, 0, st>>>(P.pc_slot, P.nvalid, P.n_b, P.kinds, n, E);
+  });
   // the scale of each coarse direction: diag(R^T D R), before the pixel term
   k_pc_diag<<<(n + 255) / 256, 256, 0, st>>>(E, diag0, n);
   const int g_w = stream_grid(P, P.npix * 32, kBlock, 8);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_pc_E_pix<KS><<<g_w, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pc_cell, P.pc_val, P.minv,
+    k_pc_E_pix<KS><<<g_w, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pc_slot, P.minv,
                                            P.mask, P.npix, P.n_b, P.kinds, n, E);
   });
   P.launches += 3;

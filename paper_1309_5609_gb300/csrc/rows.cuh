@@ -45,6 +45,26 @@ __device__ __forceinline__ void row_bin(int kind, T c, T s, T z, T (&acc)[NC]) {
   }
 }
 
+// The row of output `kind` averaged over some samples, from their moments
+// (m1 = the samples' share, mc and ms = their cos 2psi and sin 2psi sums, all
+// divided by the same count): every row is linear in (1, c, s), so these three
+// numbers give the average row of each output kind.
+template <int NC>
+__device__ __forceinline__ void row_moments(int kind, float m1, float mc, float ms, float (&v)[NC]) {
+  using F = Frame<NC>;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) v[j] = 0.f;
+  if (kind == DS_KIND_I) {
+    if constexpr (F::I >= 0) v[F::I] = m1;
+  } else if (kind == DS_KIND_Q) {
+    if constexpr (F::Q >= 0) { v[F::Q] = mc; v[F::U] = ms; }
+  } else if (kind == DS_KIND_U) {
+    if constexpr (F::Q >= 0) { v[F::Q] = -ms; v[F::U] = mc; }
+  } else {
+    if constexpr (F::I >= 0 && F::Q >= 0) { v[F::I] = m1; v[F::Q] = mc; v[F::U] = ms; }
+  }
+}
+
 // w_kind . m  (what rescanning the map gives for this output)
 template <int NC, typename T>
 __device__ __forceinline__ T row_dot(int kind, T c, T s, const T (&m)[NC]) {

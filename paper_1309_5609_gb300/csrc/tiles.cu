@@ -3,26 +3,23 @@
 // the time-ordered samples nor the pixel-major copy pays.
 //
 // The runs of consecutive samples on one pixel within a baseline (runs_build.cu)
-// are cut into tiles of Tb consecutive baselines, and within each tile sorted by
+// are cut into tiles of consecutive baselines, and within each tile sorted by
 // pixel (one counting sort per tile at plan time).  A record is 16 bytes:
 //     (pixel, n << 24 | baseline - first baseline of the tile, sum cos 2psi, sum sin 2psi)
-// with n <= 255 samples (plans with longer runs keep the other forms).
-//
-// Both passes of an iteration give each tile to one block, which streams the
-// tile's records once (Sect. 3 operator, exact reformulation: only the float32
-// rounding order changes):
-//  * binning (P~^T R^T F~ x): the tile's baselines are staged in shared memory;
-//    a warp walks a contiguous share of the tile's records in rounds of 32, sums
-//    the contributions of equal pixels across the lanes (a segmented sum over the
-//    sorted keys) and carries the last pixel's sums into its next round, so that
-//    one vector reduction (red.global.add.v4.f32) is issued per pixel and warp
-//    share instead of one per run;
-//  * rescan and per-baseline sums (F~^T (z - R P~ m)): the tile's baseline sums
-//    live in shared memory (float32 atomics; the runs of one pixel lie in
-//    different baselines, so lanes rarely collide); the map row of a pixel is
-//    gathered by every lane of its run group at one address; the block stores
-//    its baselines' sums once (each baseline belongs to one tile: no atomics in
-//    global memory).
+// with n <= 255 samples (plans with longer runs keep the other forms).  Two
+// copies are kept, sorted within tiles of two lengths (Sect. 3 operator, exact
+// reformulation: only the float32 rounding order changes):
+//  * binning (P~^T R^T F~ x) reads long tiles (about two weeks of data): a pixel
+//    is revisited every sidereal day, so its runs of a tile are many and
+//    contiguous.  Each lane sums consecutive records of one pixel in registers,
+//    gathering each run's baselines as one 16-byte vector (all outputs packed per
+//    baseline), and about one vector reduction per pixel and tile reaches L2,
+//    instead of one per run as in time order;
+//  * rescan and per-baseline sums (F~^T (z - R P~ m)) read short tiles (a few
+//    hours): each block keeps its tile's baseline sums in shared memory (float32
+//    atomics; the runs of one pixel lie in different baselines, so lanes rarely
+//    collide), gathers the map row of each run, and stores its baselines' sums
+//    once (each baseline belongs to one tile: no atomics in global memory).
 #include <vector>
 
 #include "internal.cuh"
@@ -67,14 +64,78 @@ __global__ void __launch_bounds__(kBlock) k_tl_longest(const RunRec* __restrict_
   if ((threadIdx.x & 31) == 0) atomicMax(longest, m);
 }
 
-// Runs per pixel within tile t (cnt zeroed before).
+// Order of the pixels within a tile: by first visit.  first[p] = the first run on
+// p (first zeroed to all ones before); rank[p] = how many pixels were visited
+// before p first was.  A pixel's neighbours along the scan then sit next to it in
+// the sorted records, and their runs share baselines (the baseline gathers of the
+// passes hit in L1).
+__global__ void __launch_bounds__(kBlock) k_tl_first(const RunRec* __restrict__ rec,
+                                                     int64_t n_runs, uint32_t* __restrict__ first) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_runs;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = rec[i].pix;
+    if (i == 0 || rec[i - 1].pix != p) atomicMin(first + p, (uint32_t)i);
+  }
+}
+
+// Pixels first visited in runs [g S, (g + 1) S) -> cnt[g]
+__global__ void __launch_bounds__(kBlock) k_tl_rank_count(const RunRec* __restrict__ rec,
+                                                          int64_t n_runs,
+                                                          const uint32_t* __restrict__ first,
+                                                          int64_t S, int64_t* __restrict__ cnt) {
+  __shared__ int64_t sh[kBlock / 32];
+  const int64_t lo = (int64_t)blockIdx.x * S, hi = lo + S < n_runs ? lo + S : n_runs;
+  int64_t c = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    c += first[rec[i].pix] == (uint32_t)i ? 1 : 0;
+  for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t s = 0;
+    for (int q = 0; q < kBlock / 32; ++q) s += sh[q];
+    cnt[blockIdx.x] = s;
+  }
+}
+
+// rank[p] for the pixels first visited in runs [g S, (g + 1) S), in run order from
+// the block's offset off[g]
+__global__ void __launch_bounds__(kBlock) k_tl_rank_write(const RunRec* __restrict__ rec,
+                                                          int64_t n_runs,
+                                                          const uint32_t* __restrict__ first,
+                                                          int64_t S, const int64_t* __restrict__ off,
+                                                          int32_t* __restrict__ rank) {
+  __shared__ int wsum[kBlock / 32];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t lo = (int64_t)blockIdx.x * S, hi = lo + S < n_runs ? lo + S : n_runs;
+  int64_t base = off[blockIdx.x];
+  for (int64_t b0 = lo; b0 < hi; b0 += blockDim.x) {
+    const int64_t i = b0 + threadIdx.x;
+    const int p = i < hi ? rec[i].pix : -1;
+    const bool mark = i < hi && first[p] == (uint32_t)i;
+    const unsigned bal = __ballot_sync(0xffffffffu, mark);
+    if (lane == 0) wsum[wq] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      if (q < wq) before += wsum[q];
+      total += wsum[q];
+    }
+    if (mark) rank[p] = (int32_t)(base + before + __popc(bal & ((1u << lane) - 1u)));
+    base += total;
+    __syncthreads();
+  }
+}
+
+// Runs per pixel rank (rank == nullptr: per pixel) within tile t (cnt zeroed before).
 __global__ void __launch_bounds__(kBlock) k_tl_hist(const RunRec* __restrict__ rec,
+                                                    const int32_t* __restrict__ rank,
                                                     const int64_t* __restrict__ tile_off, int64_t t,
                                                     uint32_t* __restrict__ cnt) {
   const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
   for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
        i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(cnt + rec[i].pix, 1u);
+    atomicAdd(cnt + (rank != nullptr ? rank[rec[i].pix] : rec[i].pix), 1u);
 }
 
 // Exclusive scan of cnt[0 .. n) into run positions, in three steps: block sums
@@ -96,11 +157,29 @@ __global__ void __launch_bounds__(kBlock) k_tl_scan_up(const uint32_t* __restric
   }
 }
 
-// blk[j] = tile start + sum of blk[0 .. j) (one thread; G is at most a few thousand)
-__global__ void k_tl_scan_top(int64_t* __restrict__ blk, int64_t G,
-                              const int64_t* __restrict__ tile_off, int64_t t) {
-  int64_t run = tile_off[t];
-  for (int64_t j = 0; j < G; ++j) {
+// blk[j] = start + sum of blk[0 .. j), start = tile_off[t] (or 0 without tile_off):
+// one block of kScanTop threads, each over a contiguous share of the G entries.
+constexpr int kScanTop = 1024;
+__global__ void __launch_bounds__(kScanTop) k_tl_scan_top(int64_t* __restrict__ blk, int64_t G,
+                                                          const int64_t* __restrict__ tile_off,
+                                                          int64_t t) {
+  __shared__ int64_t sh[kScanTop / 32];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t per = (G + kScanTop - 1) / kScanTop;
+  const int64_t lo = (int64_t)threadIdx.x * per, hi = lo + per < G ? lo + per : G;
+  int64_t s = 0;
+  for (int64_t j = lo; j < hi; ++j) s += blk[j];
+  int64_t inc = s;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int64_t u = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += u;
+  }
+  if (lane == 31) sh[wq] = inc;
+  __syncthreads();
+  int64_t before = tile_off != nullptr ? tile_off[t] : 0;
+  for (int q = 0; q < wq; ++q) before += sh[q];
+  int64_t run = before + inc - s;
+  for (int64_t j = lo; j < hi; ++j) {
     const int64_t x = blk[j];
     blk[j] = run;
     run += x;
@@ -139,6 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_tl_scan_down(uint32_t* __restrict__ 
 // Each run of tile t to its pixel's next slot, as a 16-byte record.
 __global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict__ rec,
                                                        const int32_t* __restrict__ rb,
+                                                       const int32_t* __restrict__ rank,
                                                        const int64_t* __restrict__ tile_off,
                                                        int64_t t, int64_t Tb,
                                                        unsigned long long* __restrict__ cursor,
@@ -149,7 +229,7 @@ __global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict_
        i += (int64_t)gridDim.x * blockDim.x) {
     const RunRec r = rec[i];
     const unsigned bl = (unsigned)((int64_t)rb[i] - b0);
-    const unsigned long long slot = atomicAdd(cursor + r.pix, 1ull);
+    const unsigned long long slot = atomicAdd(cursor + (rank != nullptr ? rank[r.pix] : r.pix), 1ull);
     out[slot] = make_int4(r.pix, (int)(((unsigned)r.n << 24) | bl), __float_as_int(r.c),
                           __float_as_int(r.s));
   }
@@ -157,110 +237,202 @@ __global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict_
 
 // ---- the operator's passes --------------------------------------------------------
 
-constexpr int kUnroll = 4;  // records per lane loaded before any is used (bytes in flight)
-constexpr int64_t kChunk = 32 * kUnroll * 16;  // records per warp chunk of the long-tile binning
+constexpr int kUnroll = 4;     // records per thread loaded before any is used (rescan)
+constexpr int kLaneRecs = 8;   // consecutive records a lane sums per round (binning)
+constexpr int kRound = 32 * kLaneRecs;  // records per warp round
+constexpr int kBinWarps = 8;   // warps per block of the binning
+constexpr int64_t kChunk = kRound * 8;  // records per warp chunk of the binning
 
-// One round of 32 records of a warp's share: lane sums of equal pixels (the
-// records are sorted by pixel within the tile), the carried pixel of the previous
-// round joined to lane 0, one reduction per other segment, the last segment
-// carried on.
-template <int NC>
-__device__ __forceinline__ void tl_bin_round(int key, float (&acc)[NC], int& ckey,
-                                             float (&carry)[NC], float* __restrict__ bins) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  if (lane == 0 && ckey >= 0) {
-    if (key == ckey) {
+// x32[o][b] = x[o][b] rounded to float32, and x4[b] = every output's baseline b
+// (one 16-byte gather per run record in the tiled passes).
+__global__ void __launch_bounds__(kBlock) k_tl_pack(const double* __restrict__ x,
+                                                    float* __restrict__ x32,
+                                                    float4* __restrict__ x4, int64_t n_b, int n_o,
+                                                    Gate g) {
+  if (gate_closed(g)) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += stride) {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int j = 0; j < NC; ++j) acc[j] += carry[j];
-    } else {
-      flush_bins<NC, float>(bins, ckey, carry);
-    }
+    for (int o = 0; o < 4; ++o)
+      if (o < n_o) {
+        v[o] = (float)x[o * n_b + b];
+        x32[o * n_b + b] = v[o];
+      }
+    x4[b] = make_float4(v[0], v[1], v[2], v[3]);
   }
-  const int nxt = __shfl_down_sync(full, key, 1);
-  bool stop = lane == 31 || nxt != key;
-#pragma unroll
-  for (int w = 1; w < 32; w <<= 1) {
-    float v2[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) v2[j] = __shfl_down_sync(full, acc[j], w);
-    const bool s2 = __shfl_down_sync(full, stop, w);
-    if (!stop) {
-#pragma unroll
-      for (int j = 0; j < NC; ++j) acc[j] += v2[j];
-      stop = s2;
-    }
-  }
-  const int prv = __shfl_up_sync(full, key, 1);
-  const bool head = key >= 0 && (lane == 0 || prv != key);
-  const unsigned heads = __ballot_sync(full, head);
-  const int last = heads ? 31 - __clz(heads) : -1;
-  const int lkey = __shfl_sync(full, key, 31);
-  const bool carry_last = last >= 0 && __shfl_sync(full, key, last) == lkey && lkey >= 0;
-  if (head && !(carry_last && lane == last)) flush_bins<NC, float>(bins, key, acc);
-  ckey = carry_last ? lkey : -1;
-#pragma unroll
-  for (int j = 0; j < NC; ++j) carry[j] = __shfl_sync(full, acc[j], last >= 0 ? last : 0);
 }
 
-// bins[p] += sum over the tile's runs on p of the rows summed over the run times
-// the run's baselines (float32).  A warp takes kUnroll rounds of 32 records at a
-// time: all their loads are issued before the first round is summed.
+// The baselines of every output at baseline b.
+template <int NO>
+__device__ __forceinline__ void tl_gather(const float* __restrict__ x32,
+                                          const float4* __restrict__ x4, int64_t b,
+                                          float (&z)[NO]) {
+  if constexpr (NO == 1) {
+    z[0] = __ldg(x32 + b);
+  } else {
+    const float4 q = __ldg(x4 + b);
+    const float a[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int o = 0; o < NO; ++o) z[o] = a[o];
+  }
+}
+
+// Shared-memory slot of record j of a warp's round: an XOR swizzle over the eight
+// 16-byte bank groups, so that both the coalesced stores (lane = j mod 32) and the
+// lane-sequential loads (lane = j / kLaneRecs) are free of bank conflicts.
+__device__ __forceinline__ int tl_swz(int j) { return j ^ ((j >> 3) & 7); }
+
+// bins[p] += sum over the runs on p of the rows summed over the run times the
+// run's baselines (float32), over long tiles whose records are sorted by pixel
+// (pixels in first-visit order).  A warp takes chunks of kChunk records of one
+// tile in rounds of kRound: the round is loaded with coalesced 16-byte loads,
+// staged in shared memory, and each lane then sums kLaneRecs consecutive records
+// in registers (one 16-byte baseline gather per record, issued for all its
+// records first).  A pixel's records are contiguous, so a lane issues a
+// reduction only for a pixel that starts and ends within its records; pixels
+// that cross lanes are joined by one segmented scan over the lanes per round, and
+// the round's last pixel is carried into the next round.  About one vector
+// reduction per pixel and tile remains.
 template <int KS>
-__global__ void __launch_bounds__(kTileThreads) k_tl_bin(const int4* __restrict__ rec,
-                                                         const int64_t* __restrict__ tile_off,
-                                                         int64_t n_tiles, int64_t Tb,
-                                                         const float* __restrict__ x,
-                                                         float* __restrict__ bins, int64_t n_b,
-                                                         KindsArg kk, Gate g) {
+__global__ void __launch_bounds__(32 * kBinWarps) k_tl_bin_lanes(
+    const int4* __restrict__ rec, const int64_t* __restrict__ tile_off,
+    const int64_t* __restrict__ chunk_first, int64_t n_tiles, int64_t n_chunks, int64_t Tb,
+    const float* __restrict__ x32, const float4* __restrict__ x4, float* __restrict__ bins,
+    KindsArg kk, Gate g) {
   if (gate_closed(g)) return;
   using K = KSet<KS>;
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
-  extern __shared__ float xs[];  // [n_o][Tb]
-  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  const unsigned full = 0xffffffffu;
+  __shared__ int4 stage[kBinWarps][kRound];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  int4* st = stage[wq];
+  const int64_t warps = (int64_t)gridDim.x * kBinWarps;
+  for (int64_t ch = (int64_t)blockIdx.x * kBinWarps + wq; ch < n_chunks; ch += warps) {
+    int64_t t = 0, tb = n_tiles - 1;  // the chunk's tile: last t with chunk_first[t] <= ch
+    while (t < tb) {
+      const int64_t mid = (t + tb + 1) >> 1;
+      if (__ldg(chunk_first + mid) <= ch) t = mid;
+      else tb = mid - 1;
+    }
+    const int64_t lo = __ldg(tile_off + t) + (ch - __ldg(chunk_first + t)) * kChunk;
+    const int64_t end = __ldg(tile_off + t + 1);
+    const int64_t hi = lo + kChunk < end ? lo + kChunk : end;
     const int64_t b0 = t * Tb;
-    const int64_t nb = b0 + Tb < n_b ? Tb : n_b - b0;
-    for (int o = 0; o < n_o; ++o)
-      for (int64_t j = threadIdx.x; j < nb; j += blockDim.x) xs[o * Tb + j] = __ldg(x + o * n_b + b0 + j);
-    __syncthreads();
-    const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
-    // warp wq takes a contiguous share of the tile's runs, whole rounds of 32
-    const int64_t per = ((r1 - r0 + nw - 1) / nw + 31) & ~int64_t(31);
-    const int64_t lo = r0 + wq * per;
-    const int64_t hi = lo + per < r1 ? lo + per : r1;
-    int ckey = -1;  // the pixel whose sums are carried from the previous round
+    int ckey = -1;  // the pixel carried from the previous round, and its sums
     float carry[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) carry[j] = 0.f;
-    for (int64_t base = lo; base < hi; base += 32 * kUnroll) {
-      int4 v[kUnroll];
+    for (int64_t base = lo; base < hi; base += kRound) {
+      int4 v[kLaneRecs];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
+      for (int u = 0; u < kLaneRecs; ++u) {
         const int64_t i = base + 32 * u + lane;
         v[u] = i < hi ? __ldcs(rec + i) : make_int4(-1, 0, 0, 0);
       }
+      __syncwarp();  // the previous round's shared reads are done
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        if (base + 32 * u >= hi) break;  // warp-uniform
-        float acc[NC];
+      for (int u = 0; u < kLaneRecs; ++u) st[tl_swz(32 * u + lane)] = v[u];
+      __syncwarp();
 #pragma unroll
-        for (int j = 0; j < NC; ++j) acc[j] = 0.f;
-        const int key = v[u].x;
-        if (key >= 0) {
-          const float n = (float)((unsigned)v[u].y >> 24);
-          const int bl = (int)((unsigned)v[u].y & 0xFFFFFFu);
-          const float c = __int_as_float(v[u].z), sn = __int_as_float(v[u].w);
+      for (int k = 0; k < kLaneRecs; ++k) v[k] = st[tl_swz(kLaneRecs * lane + k)];
+      float z[kLaneRecs][NO];
 #pragma unroll
-          for (int o = 0; o < NO; ++o)
-            if (o < n_o) run_bin<NC>(K::kind(o, kk), n, c, sn, xs[o * Tb + bl], acc);
+      for (int k = 0; k < kLaneRecs; ++k) {
+        if (v[k].x >= 0) {
+          tl_gather<NO>(x32, x4, b0 + (int64_t)((unsigned)v[k].y & 0xFFFFFFu), z[k]);
+        } else {
+#pragma unroll
+          for (int o = 0; o < NO; ++o) z[k][o] = 0.f;
         }
-        tl_bin_round<NC>(key, acc, ckey, carry, bins);
       }
+      // the lane's records: its first pixel (head, when another follows), complete
+      // pixels in between (reduced at once), and its last pixel (tail)
+      int cur = -1, hkey = -1;
+      bool has_head = false;
+      float acc[NC], hacc[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] = hacc[j] = 0.f;
+#pragma unroll
+      for (int k = 0; k < kLaneRecs; ++k) {
+        const int key = v[k].x;
+        if (key < 0) continue;  // past the chunk's end
+        float w[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) w[j] = 0.f;
+        const float n = (float)((unsigned)v[k].y >> 24);
+        const float c = __int_as_float(v[k].z), sn = __int_as_float(v[k].w);
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o < n_o) run_bin<NC>(K::kind(o, kk), n, c, sn, z[k][o], w);
+        if (key != cur) {
+          if (cur >= 0) {
+            if (!has_head) {
+              has_head = true;
+              hkey = cur;
+#pragma unroll
+              for (int j = 0; j < NC; ++j) hacc[j] = acc[j];
+            } else {
+              flush_bins<NC, float>(bins, cur, acc);
+            }
+          }
+          cur = key;
+#pragma unroll
+          for (int j = 0; j < NC; ++j) acc[j] = w[j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) acc[j] += w[j];
+        }
+      }
+      const int first = has_head ? hkey : cur;
+      // the carried pixel joins lane 0's first pixel, or is complete
+      if (lane == 0 && ckey >= 0) {
+        if (first == ckey) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) {
+            if (has_head) hacc[j] += carry[j];
+            else acc[j] += carry[j];
+          }
+        } else {
+          flush_bins<NC, float>(bins, ckey, carry);
+        }
+      }
+      // segmented inclusive scan of the tails over the lanes: a segment starts at
+      // a lane whose tail began inside it (it has a head) or whose tail pixel
+      // differs from the previous lane's
+      const int prev = __shfl_up_sync(full, cur, 1);
+      bool f = lane == 0 || has_head || prev != cur;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const bool fu = __shfl_up_sync(full, f, d);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          const float su = __shfl_up_sync(full, acc[j], d);
+          if (lane >= d && !f) acc[j] += su;
+        }
+        if (lane >= d && !f) f = fu;
+      }
+      // a head completes the pixel of the previous lanes' tails
+      float before[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) before[j] = __shfl_up_sync(full, acc[j], 1);
+      if (has_head) {
+        if (lane > 0 && prev == hkey) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) hacc[j] += before[j];
+        }
+        flush_bins<NC, float>(bins, hkey, hacc);
+      }
+      // a tail is complete unless the next lane starts with the same pixel; the
+      // last lane's tail is carried
+      const int next_first = __shfl_down_sync(full, first, 1);
+      if (lane < 31 && cur >= 0 && next_first != cur) flush_bins<NC, float>(bins, cur, acc);
+      ckey = __shfl_sync(full, cur, 31);
+#pragma unroll
+      for (int j = 0; j < NC; ++j) carry[j] = __shfl_sync(full, acc[j], 31);
     }
     if (lane == 0 && ckey >= 0) flush_bins<NC, float>(bins, ckey, carry);
-    __syncthreads();
   }
 }
 
@@ -272,7 +444,8 @@ template <int KS>
 __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restrict__ rec,
                                                             const int64_t* __restrict__ tile_off,
                                                             int64_t n_tiles, int64_t Tb,
-                                                            const float* __restrict__ x,
+                                                            const float* __restrict__ x32,
+                                                            const float4* __restrict__ x4,
                                                             const float* __restrict__ map,
                                                             double* __restrict__ out, int64_t n_b,
                                                             KindsArg kk, Gate g) {
@@ -301,8 +474,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
         const int bl = (int)((unsigned)v[u].y & 0xFFFFFFu);
         if (v[u].x >= 0) {
           load_map<NC, float>(map, v[u].x, m[u]);
-#pragma unroll
-          for (int o = 0; o < NO; ++o) z[u][o] = o < n_o ? __ldg(x + o * n_b + b0 + bl) : 0.f;
+          tl_gather<NO>(x32, x4, b0 + bl, z[u]);
         }
       }
 #pragma unroll
@@ -326,136 +498,74 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
   }
 }
 
-// The binning over long tiles (many days: each pixel's runs of a tile are summed
-// in registers, so that reductions are few): warps take chunks of kChunk records
-// of one tile, gather the baselines from L2 (the tile's baselines span a few MB),
-// and carry their last pixel across rounds as k_tl_bin does.
-template <int KS>
-__global__ void __launch_bounds__(kBlock) k_tl_bin_long(const int4* __restrict__ rec,
-                                                        const int64_t* __restrict__ tile_off,
-                                                        const int64_t* __restrict__ chunk_first,
-                                                        int64_t n_tiles, int64_t n_chunks,
-                                                        int64_t Tb, const float* __restrict__ x,
-                                                        float* __restrict__ bins, int64_t n_b,
-                                                        KindsArg kk, Gate g) {
-  if (gate_closed(g)) return;
-  using K = KSet<KS>;
-  constexpr int NC = K::NC, NO = K::NO;
-  const int n_o = K::n_o(kk);
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t ch = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < n_chunks;
-       ch += warps) {
-    int64_t t = 0;  // the chunk's tile: few tiles, a linear walk
-    while (t + 1 < n_tiles && chunk_first[t + 1] <= ch) ++t;
-    const int64_t lo = tile_off[t] + (ch - chunk_first[t]) * kChunk;
-    const int64_t hi = lo + kChunk < tile_off[t + 1] ? lo + kChunk : tile_off[t + 1];
-    const float* xb = x + t * Tb;
-    int ckey = -1;
-    float carry[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) carry[j] = 0.f;
-    for (int64_t base = lo; base < hi; base += 32 * kUnroll) {
-      int4 v[kUnroll];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int64_t i = base + 32 * u + lane;
-        v[u] = i < hi ? __ldcs(rec + i) : make_int4(-1, 0, 0, 0);
-      }
-      float z[kUnroll][NO];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int bl = (int)((unsigned)v[u].y & 0xFFFFFFu);
-#pragma unroll
-        for (int o = 0; o < NO; ++o)
-          z[u][o] = (o < n_o && v[u].x >= 0) ? __ldg(xb + o * n_b + bl) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        if (base + 32 * u >= hi) break;  // warp-uniform
-        float acc[NC];
-#pragma unroll
-        for (int j = 0; j < NC; ++j) acc[j] = 0.f;
-        const int key = v[u].x;
-        if (key >= 0) {
-          const float n = (float)((unsigned)v[u].y >> 24);
-          const float c = __int_as_float(v[u].z), sn = __int_as_float(v[u].w);
-#pragma unroll
-          for (int o = 0; o < NO; ++o)
-            if (o < n_o) run_bin<NC>(K::kind(o, kk), n, c, sn, z[u][o], acc);
-        }
-        tl_bin_round<NC>(key, acc, ckey, carry, bins);
-      }
-    }
-    if (lane == 0 && ckey >= 0) flush_bins<NC, float>(bins, ckey, carry);
-  }
-}
-
 }  // namespace
 
-bool tl_ready(const Plan& P) { return P.layout == 3 && P.tl_rec != nullptr && P.x32 != nullptr; }
+bool tl_ready(const Plan& P) {
+  return P.layout == 3 && P.tl_rec != nullptr && P.tl2_rec != nullptr && P.x32 != nullptr &&
+         P.tl_x4 != nullptr;
+}
 
-static int tl_grid(const Plan& P, int per_sm) {
-  const int64_t g = (int64_t)P.num_sms * (per_sm > 0 ? per_sm : 1);
-  return (int)(P.tl_tiles < g ? P.tl_tiles : g);
+void launch_pack_tl(const Plan& P, cudaStream_t st, const double* x, Gate g) {
+  k_tl_pack<<<stream_grid(P, P.n_b, kBlock, 8), kBlock, 0, st>>>(x, P.x32, P.tl_x4, P.n_b, P.n_o,
+                                                                  g);
 }
 
 void launch_bin_tl(const Plan& P, cudaStream_t st, Gate g) {
-  if (P.tl2_rec != nullptr) {
-    with_kindset(P.kindset, [&](auto ksc) {
-      constexpr int KS = decltype(ksc)::value;
-      k_tl_bin_long<KS><<<stream_grid(P, P.tl2_chunks * 32, kBlock, 8), kBlock, 0, st>>>(
-          P.tl2_rec, P.tl2_off, P.tl2_chunk, P.tl2_tiles, P.tl2_chunks, P.tl2_tb, P.x32, P.bins32,
-          P.n_b, P.kinds, g);
-    });
-    return;
-  }
-  const size_t smem = sizeof(float) * (size_t)P.n_o * P.tl_tb;
+  const int64_t warps = (int64_t)P.num_sms * P.tl_bin_blocks * kBinWarps;
+  const int64_t need = (P.tl2_chunks + kBinWarps - 1) / kBinWarps;
+  int grid = (int)(need < warps / kBinWarps ? need : warps / kBinWarps);
+  if (grid < 1) grid = 1;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_tl_bin<KS><<<tl_grid(P, P.tl_bin_blocks), kTileThreads, smem, st>>>(
-        P.tl_rec, P.tl_off, P.tl_tiles, P.tl_tb, P.x32, P.bins32, P.n_b, P.kinds, g);
+    k_tl_bin_lanes<KS><<<grid, 32 * kBinWarps, 0, st>>>(P.tl2_rec, P.tl2_off, P.tl2_chunk,
+                                                        P.tl2_tiles, P.tl2_chunks, P.tl2_tb, P.x32,
+                                                        P.tl_x4, P.bins32, P.kinds, g);
   });
 }
 
 void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g) {
+  const int64_t per_sm = P.tl_rescan_blocks > 0 ? P.tl_rescan_blocks : 1;
+  const int64_t cap = (int64_t)P.num_sms * per_sm;
+  const int grid = (int)(P.tl_tiles < cap ? P.tl_tiles : cap);
   const size_t smem = sizeof(float) * (size_t)P.n_o * P.tl_tb;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_tl_rescan<KS><<<tl_grid(P, P.tl_rescan_blocks), kTileThreads, smem, st>>>(
-        P.tl_rec, P.tl_off, P.tl_tiles, P.tl_tb, P.x32, P.map32, out, P.n_b, P.kinds, g);
+    k_tl_rescan<KS><<<grid, kTileThreads, smem, st>>>(P.tl_rec, P.tl_off, P.tl_tiles, P.tl_tb,
+                                                      P.x32, P.tl_x4, P.map32, out, P.n_b,
+                                                      P.kinds, g);
   });
 }
 
-// Sorts the time-ordered runs by pixel within tiles of Tb baselines into *out_rec
-// (16-byte records), with the tiles' first records in *out_off (stream-ordered on
-// the plan's stream; one counting sort per tile over the pixels).
-static cudaError_t tl_sort(Plan& P, int64_t Tb, int4** out_rec, int64_t** out_off) {
+// Sorts the time-ordered runs by pixel rank (first-visit order, nkeys ranks; or,
+// with rank == nullptr, by pixel over nkeys = n_pix) within tiles of Tb baselines
+// into *out_rec (16-byte records), with the tiles' first records in *out_off
+// (stream-ordered on the plan's stream; one counting sort per tile).
+static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nkeys,
+                           int4** out_rec, int64_t** out_off) {
   cudaStream_t st = P.stream;
   const int64_t n_tiles = (P.n_b + Tb - 1) / Tb;
-  const int64_t npix = P.npix;
-  const int64_t g = stream_grid(P, npix, kBlock, 8);
-  const int64_t S = (npix + g - 1) / g, G = (npix + S - 1) / S;
+  const int64_t g = stream_grid(P, nkeys, kBlock, 8);
+  const int64_t S = (nkeys + g - 1) / g, G = (nkeys + S - 1) / S;
   uint32_t* cnt = nullptr;
   int64_t *blk = nullptr, *pos = nullptr;
   cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(out_rec), sizeof(int4) * P.rl_n, true);
   if (e == cudaSuccess)
     e = plan_alloc(P, reinterpret_cast<void**>(out_off), sizeof(int64_t) * (n_tiles + 1), true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * nkeys, false);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * G, false);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&pos), sizeof(int64_t) * npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&pos), sizeof(int64_t) * nkeys, false);
   if (e == cudaSuccess) {
     k_tl_bounds<<<(unsigned)((n_tiles + 1 + 127) / 128), 128, 0, st>>>(P.rl_b, P.rl_n, n_tiles,
                                                                        Tb, *out_off);
     const int rg = stream_grid(P, (P.rl_n + n_tiles - 1) / n_tiles, kBlock, 8);
     for (int64_t t = 0; t < n_tiles && e == cudaSuccess; ++t) {
-      e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * npix, st);
+      e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nkeys, st);
       if (e != cudaSuccess) break;
-      k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, *out_off, t, cnt);
-      k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk);
-      k_tl_scan_top<<<1, 1, 0, st>>>(blk, G, *out_off, t);
-      k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, npix, S, blk, pos);
-      k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, *out_off, t, Tb,
+      k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, rank, *out_off, t, cnt);
+      k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, nkeys, S, blk);
+      k_tl_scan_top<<<1, kScanTop, 0, st>>>(blk, G, *out_off, t);
+      k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, nkeys, S, blk, pos);
+      k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, rank, *out_off, t, Tb,
                                           reinterpret_cast<unsigned long long*>(pos), *out_rec);
       P.launches += 5;
       e = cudaGetLastError();
@@ -466,8 +576,39 @@ static cudaError_t tl_sort(Plan& P, int64_t Tb, int4** out_rec, int64_t** out_of
   return e;
 }
 
+// rank[p] = first-visit order of the observed pixels (*nkeys of them); stream-
+// ordered, one host synchronisation for the count.
+static cudaError_t tl_rank(Plan& P, int32_t** rank, int64_t* nkeys) {
+  cudaStream_t st = P.stream;
+  const int64_t g = stream_grid(P, P.rl_n, kBlock, 8);
+  const int64_t S = (P.rl_n + g - 1) / g, G = (P.rl_n + S - 1) / S;
+  uint32_t* first = nullptr;
+  int64_t* blk = nullptr;
+  cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(&first), sizeof(uint32_t) * P.npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(rank), sizeof(int32_t) * P.npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * (G + 1), false);
+  if (e == cudaSuccess) e = cudaMemsetAsync(first, 0xFF, sizeof(uint32_t) * P.npix, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(blk + G, 0, sizeof(int64_t), st);
+  int64_t h_total = 0;
+  if (e == cudaSuccess) {
+    k_tl_first<<<stream_grid(P, P.rl_n, kBlock, 8), kBlock, 0, st>>>(P.rl_rec, P.rl_n, first);
+    k_tl_rank_count<<<(unsigned)G, kBlock, 0, st>>>(P.rl_rec, P.rl_n, first, S, blk);
+    k_tl_scan_top<<<1, kScanTop, 0, st>>>(blk, G + 1, nullptr, 0);  // blk[G] = the total
+    k_tl_rank_write<<<(unsigned)G, kBlock, 0, st>>>(P.rl_rec, P.rl_n, first, S, blk, *rank);
+    P.launches += 4;
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&h_total, blk + G, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  for (void* t : {(void*)first, (void*)blk})
+    if (t) cudaFreeAsync(t, st);
+  *nkeys = h_total;
+  return e;
+}
+
 static void tl_free(Plan& P) {
-  void* mine[] = {P.tl_rec, P.tl_off, P.tl2_rec, P.tl2_off, P.tl2_chunk};
+  void* mine[] = {P.tl_rec, P.tl_off, P.tl2_rec, P.tl2_off, P.tl2_chunk, P.tl_x4};
   for (void* t : mine)
     if (t) cudaFreeAsync(t, P.stream);
   P.tl_rec = nullptr;
@@ -475,28 +616,33 @@ static void tl_free(Plan& P) {
   P.tl2_rec = nullptr;
   P.tl2_off = nullptr;
   P.tl2_chunk = nullptr;
+  P.tl_x4 = nullptr;
 }
 
 // Builds the tiled records from the time-ordered run records: tiles of a few
 // hours for the rescan (their baseline sums fit in shared memory), and tiles of
-// about 2^26 samples for the binning (each pixel's runs of many days summed in
-// registers).  One host synchronisation for the longest run, one for the chunk
-// table.  Returns DS_ESTATE, leaving nothing behind, when a run is longer than
-// 255 samples.
+// P.tl_bin_samples samples (2^26 by default, about two weeks at 50 Hz) for the
+// binning, so that each pixel's runs of many days are summed in registers.  One
+// host synchronisation for the longest run, one for the chunk table.  Returns
+// DS_ESTATE, leaving nothing behind, when a run is longer than 255 samples (or
+// there are 2^32 - 1 runs or more).
 ds_status tl_build(Plan& P) {
-  if (P.rl_rec == nullptr || P.rl_n <= 0) return DS_ESTATE;
+  // run indices are ranked as 32-bit numbers
+  if (P.rl_rec == nullptr || P.rl_n <= 0 || P.rl_n >= (int64_t)0xFFFFFFFF) return DS_ESTATE;
   cudaStream_t st = P.stream;
   int64_t Tb = kTileFloats / P.n_o;
   if (Tb > P.n_b) Tb = P.n_b;
-  int64_t Tb2 = (int64_t(1) << 26) / P.L;
+  int64_t Tb2 = P.tl_bin_samples / P.L;
+  if (Tb2 < 1) Tb2 = 1;
   if (Tb2 > (int64_t(1) << 24) - 1) Tb2 = (int64_t(1) << 24) - 1;
-  if (Tb2 < Tb) Tb2 = Tb;
   if (Tb2 > P.n_b) Tb2 = P.n_b;
   const int64_t n_tiles = (P.n_b + Tb - 1) / Tb, n_tiles2 = (P.n_b + Tb2 - 1) / Tb2;
   int* longest = nullptr;
+  int32_t* rank = nullptr;
   const int64_t held_before = P.device_bytes;
   auto release = [&](cudaError_t e) {
     if (longest) cudaFreeAsync(longest, st);
+    if (rank) cudaFreeAsync(rank, st);
     tl_free(P);
     P.device_bytes = held_before;
     return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
@@ -515,44 +661,51 @@ ds_status tl_build(Plan& P) {
     release(cudaSuccess);
     return DS_ESTATE;
   }
-  e = tl_sort(P, Tb, &P.tl_rec, &P.tl_off);
+  e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_x4), sizeof(float4) * P.n_b, true);
+  int64_t nkeys = 0;
+  if (e == cudaSuccess) e = tl_rank(P, &rank, &nkeys);
+  if (e == cudaSuccess && nkeys <= 0) e = cudaErrorInvalidValue;
+  // the rescan's tiles in pixel order: the runs of neighbouring pixels along the
+  // scan share baselines, and would collide on the tile's shared baseline sums
+  if (e == cudaSuccess) e = tl_sort(P, Tb, nullptr, P.npix, &P.tl_rec, &P.tl_off);
   if (e != cudaSuccess) return release(e);
   // the long tiles and their chunk table (tile t's chunks start at chunk_first[t])
-  if (n_tiles2 < n_tiles) {
-    e = tl_sort(P, Tb2, &P.tl2_rec, &P.tl2_off);
-    std::vector<int64_t> off(n_tiles2 + 1), first(n_tiles2 + 1);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(off.data(), P.tl2_off, sizeof(int64_t) * (n_tiles2 + 1),
-                          cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return release(e);
-    first[0] = 0;
-    for (int64_t t = 0; t < n_tiles2; ++t)
-      first[t + 1] = first[t] + (off[t + 1] - off[t] + kChunk - 1) / kChunk;
-    e = plan_alloc(P, reinterpret_cast<void**>(&P.tl2_chunk), sizeof(int64_t) * (n_tiles2 + 1), true);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(P.tl2_chunk, first.data(), sizeof(int64_t) * (n_tiles2 + 1),
-                          cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // first[] leaves scope
-    if (e != cudaSuccess) return release(e);
-    P.tl2_tiles = n_tiles2;
-    P.tl2_tb = Tb2;
-    P.tl2_chunks = first[n_tiles2];
+  e = tl_sort(P, Tb2, rank, nkeys, &P.tl2_rec, &P.tl2_off);
+  if (e == cudaSuccess) {
+    cudaFreeAsync(rank, st);
+    rank = nullptr;
   }
+  std::vector<int64_t> off(n_tiles2 + 1), first(n_tiles2 + 1);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(off.data(), P.tl2_off, sizeof(int64_t) * (n_tiles2 + 1),
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return release(e);
+  first[0] = 0;
+  for (int64_t t = 0; t < n_tiles2; ++t)
+    first[t + 1] = first[t] + (off[t + 1] - off[t] + kChunk - 1) / kChunk;
+  e = plan_alloc(P, reinterpret_cast<void**>(&P.tl2_chunk), sizeof(int64_t) * (n_tiles2 + 1), true);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P.tl2_chunk, first.data(), sizeof(int64_t) * (n_tiles2 + 1),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // first[] leaves scope
+  if (e != cudaSuccess) return release(e);
+  P.tl2_tiles = n_tiles2;
+  P.tl2_tb = Tb2;
+  P.tl2_chunks = first[n_tiles2];
   P.tl_tiles = n_tiles;
   P.tl_tb = Tb;
-  // shared arrays above 48 KB need the kernels' opt-in; resident blocks per SM
+  // the rescan's shared array above 48 KB needs the kernel's opt-in; resident
+  // blocks per SM of both passes
   const size_t smem = sizeof(float) * (size_t)P.n_o * Tb;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tl_bin<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_tl_rescan<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.tl_bin_blocks, k_tl_bin<KS>,
-                                                        kTileThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.tl_bin_blocks, k_tl_bin_lanes<KS>,
+                                                        32 * kBinWarps, 0);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.tl_rescan_blocks, k_tl_rescan<KS>,
                                                         kTileThreads, smem);

@@ -47,13 +47,15 @@ def random_pixel_problem(n_t, nside, kinds, L, seed):
     return Problem(n_t, nside, tuple(kinds), L, pix, c32, s32, y, sky)
 
 
-def check_apply(prob, chunk, layout=1, reps=2, tune=None):
+def check_apply(prob, chunk, layout=1, reps=2, tune=None, before=None):
     d = prob.numpy()
     op = oracle.make_plan(d["pix"], d["c"], d["s"], d["valid"], prob.nside, prob.kinds,
                           prob.baseline_len)
     gp = prob.to(DEV)
     plan = ds.destripe_plan(gp.pix, gp.c32, gp.s32, gp.valid, nside=prob.nside,
                             kinds=prob.kinds, baseline_len=prob.baseline_len, precision="mixed")
+    for k, v in (before or {}).items():  # keys that shape the layout's build
+        ds.destripe_tune(plan, k, v)
     ds.destripe_tune(plan, "layout", layout)
     if chunk is not None:
         ds.destripe_tune(plan, "chunk", chunk)
@@ -280,7 +282,21 @@ def test_tiled_operator_tile_edges(L):
     check_apply(prob, None, layout=3)
 
 
+@pytest.mark.parametrize("tiles", [1, 7, 64, 0])
+@pytest.mark.parametrize("case", [CASES[2], CASES[1], CASES[0]], ids=["iqu_sky", "Iqu", "qu"])
+def test_tiled_binning_long_tile_lengths(case, tiles):
+    # baselines per long tile of the binning: 1 (a tile per baseline), 7, 64, or the
+    # default (one tile).  On the small IQU sky every pixel holds hundreds of runs
+    # per tile, so pixels cross lanes, rounds of 256 records and warp chunks
+    kinds, nside, n_t, L, ff, scan = case
+    prob = make_problem(n_t, nside, kinds, baseline_len=L, seed=25, scan=scan, flag_frac=ff,
+                        flag_mean_len=200, y_dtype=torch.float64)
+    before = {"bin_tile_samples": tiles * L} if tiles else None
+    check_apply(prob, None, layout=3, before=before)
+
+
 def test_tiled_operator_on_random_pixels():
     # every sample on its own pixel: one run per sample, groups of one run
     prob = random_pixel_problem(200_003, 64, ("q", "u"), 25, seed=5)
     check_apply(prob, None, layout=3)
+    check_apply(prob, None, layout=3, before={"bin_tile_samples": 25 * 3})
