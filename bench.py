@@ -441,7 +441,7 @@ def run_ours(args):
                  "rescan": "k_rescan" if (tune.get("rescan_samples", 0) or
                                         layout.get("n_runs", 0) > 0.6 * prob.n_t)
                  else "k_rl_rescan"},
-             3: {"bin": "k_tl_bin", "rescan": "k_tl_rescan"}}[form][dom]
+             3: {"bin": "k_tl_bin_lanes", "rescan": "k_tl_rescan"}}[form][dom]
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
             "traffic": kernel_traffic(prob.n_t, kname, name),

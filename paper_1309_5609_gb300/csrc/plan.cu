@@ -354,13 +354,26 @@ ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid) {
   P.n_good = (int64_t)hc[0];
   P.n_valid = (int64_t)hc[1];
   if (*P.h_err & ERR_PIX) return DS_EPIX;
-  // the records pay when runs are long enough (short runs: the time-ordered passes)
+  // the records pay when runs are long enough; with short runs, long problems
+  // (a tile of the binning or more) sort their runs by pixel within time tiles,
+  // and the others keep the time-ordered passes
   if (runs) {
     const int64_t n_runs = (int64_t)hc[2];
     if ((double)n_runs <= kRunsPerSampleMax * (double)P.n_t) {
       const ds_status s = rl_fill(P, n_runs);
       if (s != DS_OK) return s;
       P.layout = 2;
+    } else if (P.n_t >= P.tl_bin_samples) {
+      ds_status s = rl_fill(P, n_runs);
+      if (s == DS_OK) s = tl_build(P);
+      if (s == DS_OK) {
+        P.layout = 3;
+      } else if (s == DS_ESTATE || s == DS_ENOMEM) {  // runs too long, or no room
+        cudaGetLastError();
+        rl_release(P, st);
+      } else {
+        return s;
+      }
     } else {
       cudaFreeAsync(P.rl_tiles, st);
       P.rl_tiles = nullptr;

@@ -295,7 +295,7 @@ __device__ __forceinline__ int tl_swz(int j) { return j ^ ((j >> 3) & 7); }
 // the round's last pixel is carried into the next round.  About one vector
 // reduction per pixel and tile remains.
 template <int KS>
-__global__ void __launch_bounds__(32 * kBinWarps) k_tl_bin_lanes(
+__global__ void __launch_bounds__(32 * kBinWarps, 3) k_tl_bin_lanes(
     const int4* __restrict__ rec, const int64_t* __restrict__ tile_off,
     const int64_t* __restrict__ chunk_first, int64_t n_tiles, int64_t n_chunks, int64_t Tb,
     const float* __restrict__ x32, const float4* __restrict__ x4, float* __restrict__ bins,
