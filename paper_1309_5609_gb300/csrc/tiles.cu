@@ -16,10 +16,11 @@
 //    baseline), and about one vector reduction per pixel and tile reaches L2,
 //    instead of one per run as in time order;
 //  * rescan and per-baseline sums (F~^T (z - R P~ m)) read short tiles (a few
-//    hours): each block keeps its tile's baseline sums in shared memory (float32
-//    atomics; the runs of one pixel lie in different baselines, so lanes rarely
-//    collide), gathers the map row of each run, and stores its baselines' sums
-//    once (each baseline belongs to one tile: no atomics in global memory).
+//    hours): each block keeps its tile's map-term sums per baseline in shared
+//    memory (float32 atomics; the runs of one pixel lie in different baselines, so
+//    lanes rarely collide), gathers the map row of each run, and stores each
+//    baseline's valid samples times its baseline minus that sum once (each
+//    baseline belongs to one tile: no atomics in global memory).
 #include <vector>
 
 #include "internal.cuh"
@@ -127,15 +128,25 @@ __global__ void __launch_bounds__(kBlock) k_tl_rank_write(const RunRec* __restri
   }
 }
 
-// Runs per pixel rank (rank == nullptr: per pixel) within tile t (cnt zeroed before).
+// Sort key of run i within a batch of tiles [t0, ..): (tile - t0) x nkeys + the
+// pixel's rank (rank == nullptr: the pixel)
+__device__ __forceinline__ int64_t tl_key(const RunRec& r, int32_t b, const int32_t* rank,
+                                          int64_t Tb, int64_t t0, int64_t nkeys) {
+  const int64_t k = rank != nullptr ? rank[r.pix] : r.pix;
+  return ((int64_t)b / Tb - t0) * nkeys + k;
+}
+
+// Runs per key over the runs of tiles [t0, t1) (cnt zeroed before).
 __global__ void __launch_bounds__(kBlock) k_tl_hist(const RunRec* __restrict__ rec,
+                                                    const int32_t* __restrict__ rb,
                                                     const int32_t* __restrict__ rank,
-                                                    const int64_t* __restrict__ tile_off, int64_t t,
-                                                    uint32_t* __restrict__ cnt) {
-  const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
+                                                    const int64_t* __restrict__ tile_off,
+                                                    int64_t t0, int64_t t1, int64_t Tb,
+                                                    int64_t nkeys, uint32_t* __restrict__ cnt) {
+  const int64_t r0 = tile_off[t0], r1 = tile_off[t1];
   for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
        i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(cnt + (rank != nullptr ? rank[rec[i].pix] : rec[i].pix), 1u);
+    atomicAdd(cnt + tl_key(rec[i], rb[i], rank, Tb, t0, nkeys), 1u);
 }
 
 // Exclusive scan of cnt[0 .. n) into run positions, in three steps: block sums
@@ -187,8 +198,7 @@ __global__ void __launch_bounds__(kScanTop) k_tl_scan_top(int64_t* __restrict__ 
 }
 
 __global__ void __launch_bounds__(kBlock) k_tl_scan_down(uint32_t* __restrict__ cnt, int64_t n,
-                                                         int64_t S, const int64_t* __restrict__ blk,
-                                                         int64_t* __restrict__ pos) {
+                                                         int64_t S, const int64_t* __restrict__ blk) {
   __shared__ int64_t wsum[kBlock / 32];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
@@ -209,27 +219,28 @@ __global__ void __launch_bounds__(kBlock) k_tl_scan_down(uint32_t* __restrict__ 
       if (q < wq) before += wsum[q];
       tile += wsum[q];
     }
-    if (i < hi) pos[i] = carry + before + inc - v;
+    if (i < hi) cnt[i] = (uint32_t)(carry + before + inc - v);
     carry += tile;
     __syncthreads();
   }
 }
 
-// Each run of tile t to its pixel's next slot, as a 16-byte record.
+// Each run of tiles [t0, t1) to its key's next slot (cursors relative to the
+// batch's first run), as a 16-byte record with the baseline relative to its tile.
 __global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict__ rec,
                                                        const int32_t* __restrict__ rb,
                                                        const int32_t* __restrict__ rank,
                                                        const int64_t* __restrict__ tile_off,
-                                                       int64_t t, int64_t Tb,
-                                                       unsigned long long* __restrict__ cursor,
+                                                       int64_t t0, int64_t t1, int64_t Tb,
+                                                       int64_t nkeys, uint32_t* __restrict__ cursor,
                                                        int4* __restrict__ out) {
-  const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
-  const int64_t b0 = t * Tb;
+  const int64_t r0 = tile_off[t0], r1 = tile_off[t1];
   for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
        i += (int64_t)gridDim.x * blockDim.x) {
     const RunRec r = rec[i];
-    const unsigned bl = (unsigned)((int64_t)rb[i] - b0);
-    const unsigned long long slot = atomicAdd(cursor + (rank != nullptr ? rank[r.pix] : r.pix), 1ull);
+    const int32_t b = rb[i];
+    const unsigned bl = (unsigned)((int64_t)b % Tb);
+    const int64_t slot = r0 + atomicAdd(cursor + tl_key(r, b, rank, Tb, t0, nkeys), 1u);
     out[slot] = make_int4(r.pix, (int)(((unsigned)r.n << 24) | bl), __float_as_int(r.c),
                           __float_as_int(r.s));
   }
@@ -436,16 +447,17 @@ __global__ void __launch_bounds__(32 * kBinWarps, 3) k_tl_bin_lanes(
   }
 }
 
-// out[o][b] = sum over the tile's runs in baseline b of n x[o][b] - (row sums) . m_p
-// (float32 sums in shared memory, one float64 store per baseline).  Each thread
-// issues the loads of kUnroll records, then their map rows and baselines, before
-// any sum.
+// out[o][b] = nvalid[b] x[o][b] - sum over the tile's runs in baseline b of
+// (row sums) . m_p: the baseline term of every run of b adds up to the valid
+// samples of b times x, so only the map term is summed per run (float32 sums in
+// shared memory, one float64 store per baseline).  Each thread issues the loads
+// of kUnroll records, then their map rows, before any sum.
 template <int KS>
 __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restrict__ rec,
                                                             const int64_t* __restrict__ tile_off,
                                                             int64_t n_tiles, int64_t Tb,
                                                             const float* __restrict__ x32,
-                                                            const float4* __restrict__ x4,
+                                                            const int32_t* __restrict__ nvalid,
                                                             const float* __restrict__ map,
                                                             double* __restrict__ out, int64_t n_b,
                                                             KindsArg kk, Gate g) {
@@ -468,15 +480,9 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
         v[u] = i < r1 ? __ldcs(rec + i) : make_int4(-1, 0, 0, 0);
       }
       float m[kUnroll][NC];
-      float z[kUnroll][NO];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int bl = (int)((unsigned)v[u].y & 0xFFFFFFu);
-        if (v[u].x >= 0) {
-          load_map<NC, float>(map, v[u].x, m[u]);
-          tl_gather<NO>(x32, x4, b0 + bl, z[u]);
-        }
-      }
+      for (int u = 0; u < kUnroll; ++u)
+        if (v[u].x >= 0) load_map<NC, float>(map, v[u].x, m[u]);
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         if (v[u].x < 0) continue;
@@ -485,15 +491,15 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
         const float c = __int_as_float(v[u].z), sn = __int_as_float(v[u].w);
 #pragma unroll
         for (int o = 0; o < NO; ++o)
-          if (o < n_o)
-            atomicAdd(sums + o * Tb + bl,
-                      fmaf(n, z[u][o], -run_dot<NC>(K::kind(o, kk), n, c, sn, m[u])));
+          if (o < n_o) atomicAdd(sums + o * Tb + bl, -run_dot<NC>(K::kind(o, kk), n, c, sn, m[u]));
       }
     }
     __syncthreads();
     for (int o = 0; o < n_o; ++o)
-      for (int64_t j = threadIdx.x; j < nb; j += blockDim.x)
-        out[o * n_b + b0 + j] = to_f64(sums[o * Tb + j]);
+      for (int64_t j = threadIdx.x; j < nb; j += blockDim.x) {
+        const int64_t i = o * n_b + b0 + j;
+        out[i] = to_f64(fmaf((float)nvalid[b0 + j], x32[i], sums[o * Tb + j]));
+      }
     __syncthreads();
   }
 }
@@ -531,48 +537,62 @@ void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g) {
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     k_tl_rescan<KS><<<grid, kTileThreads, smem, st>>>(P.tl_rec, P.tl_off, P.tl_tiles, P.tl_tb,
-                                                      P.x32, P.tl_x4, P.map32, out, P.n_b,
+                                                      P.x32, P.nvalid, P.map32, out, P.n_b,
                                                       P.kinds, g);
   });
 }
 
 // Sorts the time-ordered runs by pixel rank (first-visit order, nkeys ranks; or,
 // with rank == nullptr, by pixel over nkeys = n_pix) within tiles of Tb baselines
-// into *out_rec (16-byte records), with the tiles' first records in *out_off
-// (stream-ordered on the plan's stream; one counting sort per tile).
+// into *out_rec (16-byte records), with the tiles' first records in *out_off.  One
+// counting sort per batch of tiles over the keys (tile, rank): the batch's counts
+// fit kSortCounts entries and its runs 32-bit cursors.  One host synchronisation
+// for the tile offsets; the rest is stream-ordered on the plan's stream.
 static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nkeys,
                            int4** out_rec, int64_t** out_off) {
+  constexpr int64_t kSortCounts = int64_t(1) << 30;  // 4 GB of uint32 counts per batch
   cudaStream_t st = P.stream;
   const int64_t n_tiles = (P.n_b + Tb - 1) / Tb;
-  const int64_t g = stream_grid(P, nkeys, kBlock, 8);
-  const int64_t S = (nkeys + g - 1) / g, G = (nkeys + S - 1) / S;
   uint32_t* cnt = nullptr;
-  int64_t *blk = nullptr, *pos = nullptr;
+  int64_t* blk = nullptr;
+  const int64_t per = kSortCounts / nkeys > 0 ? kSortCounts / nkeys : 1;  // tiles per batch
+  const int64_t cap = (per < n_tiles ? per : n_tiles) * nkeys;
+  const int64_t gmax = stream_grid(P, cap, kBlock, 8);
   cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(out_rec), sizeof(int4) * P.rl_n, true);
   if (e == cudaSuccess)
     e = plan_alloc(P, reinterpret_cast<void**>(out_off), sizeof(int64_t) * (n_tiles + 1), true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * nkeys, false);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * G, false);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&pos), sizeof(int64_t) * nkeys, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * cap, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * gmax, false);
+  std::vector<int64_t> off(n_tiles + 1);
   if (e == cudaSuccess) {
     k_tl_bounds<<<(unsigned)((n_tiles + 1 + 127) / 128), 128, 0, st>>>(P.rl_b, P.rl_n, n_tiles,
                                                                        Tb, *out_off);
-    const int rg = stream_grid(P, (P.rl_n + n_tiles - 1) / n_tiles, kBlock, 8);
-    for (int64_t t = 0; t < n_tiles && e == cudaSuccess; ++t) {
-      e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nkeys, st);
-      if (e != cudaSuccess) break;
-      k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, rank, *out_off, t, cnt);
-      k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, nkeys, S, blk);
-      k_tl_scan_top<<<1, kScanTop, 0, st>>>(blk, G, *out_off, t);
-      k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, nkeys, S, blk, pos);
-      k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, rank, *out_off, t, Tb,
-                                          reinterpret_cast<unsigned long long*>(pos), *out_rec);
-      P.launches += 5;
-      e = cudaGetLastError();
-    }
+    e = cudaMemcpyAsync(off.data(), *out_off, sizeof(int64_t) * (n_tiles + 1),
+                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
-  for (void* t : {(void*)cnt, (void*)blk, (void*)pos})
+  for (int64_t t0 = 0; t0 < n_tiles && e == cudaSuccess;) {
+    int64_t t1 = t0 + 1;  // the batch: at most `per` tiles and fewer than 2^32 runs
+    while (t1 < n_tiles && t1 - t0 < per && off[t1 + 1] - off[t0] < (int64_t)0xFFFFFFFF) ++t1;
+    const int64_t n = (t1 - t0) * nkeys;
+    const int64_t g = stream_grid(P, n, kBlock, 8);
+    const int64_t S = (n + g - 1) / g, G = (n + S - 1) / S;
+    const int rg = stream_grid(P, off[t1] - off[t0], kBlock, 8);
+    e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n, st);
+    if (e != cudaSuccess) break;
+    k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, rank, *out_off, t0, t1, Tb, nkeys, cnt);
+    k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, n, S, blk);
+    k_tl_scan_top<<<1, kScanTop, 0, st>>>(blk, G, nullptr, 0);
+    k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, n, S, blk);
+    k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, rank, *out_off, t0, t1, Tb, nkeys, cnt,
+                                        *out_rec);
+    P.launches += 5;
+    e = cudaGetLastError();
+    t0 = t1;
+  }
+  for (void* t : {(void*)cnt, (void*)blk})
     if (t) cudaFreeAsync(t, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // off[] leaves scope
   return e;
 }
 
