@@ -377,11 +377,11 @@ def run_ours(args):
                                 precision=args.precision)
         for k, v in tune.items():
             ds.destripe_tune(plan, k, v)
-        info = ds.destripe_plan_info(plan)
-        layout.update(layout=info["layout"], n_runs=info["n_runs"], bin_order=info["bin_order"])
         if prof_acc is not None:
             ds.destripe_profile(plan, 1)
         st, iters, rel = ds.destripe_solve(plan, prob.y, a, tol=args.tol)
+        info = ds.destripe_plan_info(plan)  # after the solve: records built by it count
+        layout.update(layout=info["layout"], n_runs=info["n_runs"], bin_order=info["bin_order"])
         ds.destripe_map(plan, prob.y, a, m, hits, mask)
         if prof_acc is not None:
             p = ds.destripe_profile(plan, -1)

@@ -422,7 +422,8 @@ ds_status destripe_apply_A(ds_plan_t plan, const double* d_x, double* d_Ax) {
   if (plan == nullptr || d_x == nullptr || d_Ax == nullptr || d_x == d_Ax) return DS_EINVAL;
   Plan& P = *reinterpret_cast<Plan*>(plan);
   clear_stale_error();
-  const ds_status sp = pm_ensure(P);
+  ds_status sp = tl_ensure(P);
+  if (sp == DS_OK) sp = pm_ensure(P);
   if (sp != DS_OK) return sp;
   DS_CUDA_TRY(cudaMemsetAsync(d_Ax, 0, sizeof(double) * P.n_u, P.stream));
   enqueue_apply(P, P.stream, P.desc.precision == DS_PREC_FP64, d_x, d_Ax, Gate{nullptr, nullptr});
@@ -486,7 +487,10 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   if (warm_start)
     DS_CUDA_TRY(cudaMemcpyAsync(P.x, d_a, sizeof(double) * P.n_u, cudaMemcpyDeviceToDevice, st));
   DS_CUDA_TRY(cudaMemsetAsync(P.b, 0, sizeof(double) * P.n_u, st));
-  // a first solve builds the pixel-major copy beside its right-hand side
+  // a first solve builds the tiled records the plan chose, and the pixel-major copy
+  // beside its right-hand side
+  const ds_status stl = tl_ensure(P);
+  if (stl != DS_OK) return stl;
   bool pm_started = false;
   const ds_status sp = pm_begin(P, &pm_started);
   if (sp != DS_OK) return sp;
@@ -625,6 +629,7 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
   } else if (k == "layout") {
     if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0) return DS_EINVAL;
     if (value != 0.0 && P.desc.precision != DS_PREC_MIXED) return DS_ESTATE;
+    P.tl_pending = 0;  // an explicit choice replaces the plan's own
     if (value == 1.0 && P.lid == nullptr) {
       const ds_status s = chunk_index(P, ck_default_chunk(P.n_t, P.num_sms));
       if (s != DS_OK) return s;

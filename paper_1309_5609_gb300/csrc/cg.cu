@@ -364,9 +364,12 @@ __device__ __forceinline__ void seg_sum_to_head(int key, float (&val)[NC]) {
   }
 }
 
-// u += R^T r (shared-memory sums per block, one flush per block) and
+// u += R^T r (float32 sums per block in shared memory, where the warps' segment
+// heads add with native float atomics; one float64 flush per block) and
 // r . D^-1 r; mode 1 (no coarse space): rz = r . D^-1 r.  One thread per
-// baseline: its outputs' residuals meet the slot's moments in registers.
+// baseline: its outputs' residuals meet the slot's moments in registers.  R and
+// the residual enter in float32 already, so the block's float32 sums lose nothing
+// the coarse correction keeps.
 template <int KS>
 __global__ void __launch_bounds__(kBlock) k_pc_restrict(const double* __restrict__ r,
                                                         const int32_t* __restrict__ nvalid,
@@ -379,8 +382,8 @@ __global__ void __launch_bounds__(kBlock) k_pc_restrict(const double* __restrict
   using K = KSet<KS>;
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
-  extern __shared__ double s_u[];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s_u[i] = 0.0;
+  extern __shared__ float s_u[];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_u[i] = 0.f;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -417,14 +420,14 @@ __global__ void __launch_bounds__(kBlock) k_pc_restrict(const double* __restrict
         const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
         if (key >= 0 && (lane == 0 || kprev != key)) {
 #pragma unroll
-          for (int c = 0; c < NC; ++c) atomicAdd(s_u + key * NC + c, f64_of_f32(v[c]));
+          for (int c = 0; c < NC; ++c) atomicAdd(s_u + key * NC + c, v[c]);
         }
       }
     }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x)
-    if (s_u[j] != 0.0) atomicAdd(u + j, s_u[j]);
+    if (s_u[j] != 0.f) atomicAdd(u + j, f64_of_f32(s_u[j]));
   double tot;
   if (finish_sum(acc, red, ticket, &tot)) {
     if (n > 0) {
@@ -599,7 +602,7 @@ void enqueue_precond_direction(const Plan& P, cudaStream_t st) {
   const int vg = vec_grid(P, P.n_b);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_pc_restrict<KS><<<vg, kBlock, sizeof(double) * n, st>>>(
+    k_pc_restrict<KS><<<vg, kBlock, sizeof(float) * n, st>>>(
         P.r, P.nvalid, P.pc_slot, P.n_b, P.kinds, n, P.pc_u, P.red, P.counters + 4, P.state);
     if (coarse)
       k_pc_coarse<<<stream_grid(P, (int64_t)n * 32, kBlock, 8), kBlock, 0, st>>>(
@@ -607,6 +610,21 @@ void enqueue_precond_direction(const Plan& P, cudaStream_t st) {
     k_pc_direction<KS><<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.nvalid, P.pc_slot, P.pc_c, P.n_b,
                                              P.kinds, n, P.state);
   });
+}
+
+// Shared memory of the restriction kernel for n coarse columns (above 48 KB it
+// needs the opt-in); false when n columns do not fit a block.
+bool pc_restrict_fits(const Plan& P, int n) {
+  const size_t bytes = sizeof(float) * (size_t)n;
+  if (bytes > kPcRestrictSmemMax) return false;
+  bool ok = true;
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int KS = decltype(ksc)::value;
+    if (cudaFuncSetAttribute(k_pc_restrict<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(bytes > 0 ? bytes : 1)) != cudaSuccess)
+      ok = false;
+  });
+  return ok;
 }
 
 // accurate: the iteration applies the operator in the accurate arithmetic

@@ -118,6 +118,7 @@ struct CgState {
 enum ErrBits { ERR_PIX = 1, ERR_NAN = 2 };
 
 constexpr int kPcSlots = 2;  // coarse cells kept per baseline by the two-level preconditioner
+constexpr size_t kPcRestrictSmemMax = 160 * 1024;  // float32 R^T r sums per block (40960 columns)
 
 struct Plan {
   ds_desc desc;
@@ -223,6 +224,7 @@ struct Plan {
   int64_t* tl2_chunk;       // [tiles + 1] first warp chunk of each long tile
   int64_t tl2_tiles, tl2_tb, tl2_chunks;
   int64_t tl_bin_samples;   // samples per long tile (tune key "bin_tile_samples")
+  int tl_pending;           // layout 3 chosen by the plan, records not built yet (tl_ensure)
   float4* tl_x4;            // [n_b] float32 baselines of every output, per baseline
   int rescan_samples;       // run-length plans: the rescans read the time-ordered samples (dense
                             // runs: a record per run costs more than 12 bytes per sample)
@@ -280,6 +282,7 @@ bool rl_ready(const Plan& P);
 ds_status tl_build(Plan& P);
 bool tl_ready(const Plan& P);
 void launch_pack_tl(const Plan& P, cudaStream_t st, const double* x, Gate g);
+ds_status tl_ensure(Plan& P);
 void launch_bin_tl(const Plan& P, cudaStream_t st, Gate g);
 void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g);
 void launch_bin_rl(const Plan& P, cudaStream_t st, Gate g);
@@ -351,6 +354,7 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm);
 // builds the coarse space, first making (and afterwards freeing) the run records
 // and their pixel-major copy when the plan's operator does not keep them
 ds_status pc_prepare(Plan& P);
+bool pc_restrict_fits(const Plan& P, int n);
 void pc_free(Plan& P, cudaStream_t st);
 bool pc_ready(const Plan& P);
 // cg.cu: the preconditioner's kernels of one CG step (restrict, coarse solve,

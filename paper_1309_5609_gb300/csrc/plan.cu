@@ -363,17 +363,13 @@ ds_status plan_build(Plan& P, const int32_t* d_pix, const uint8_t* d_valid) {
       const ds_status s = rl_fill(P, n_runs);
       if (s != DS_OK) return s;
       P.layout = 2;
-    } else if (P.n_t >= P.tl_bin_samples) {
-      ds_status s = rl_fill(P, n_runs);
-      if (s == DS_OK) s = tl_build(P);
-      if (s == DS_OK) {
-        P.layout = 3;
-      } else if (s == DS_ESTATE || s == DS_ENOMEM) {  // runs too long, or no room
-        cudaGetLastError();
-        rl_release(P, st);
-      } else {
-        return s;
-      }
+    } else if (P.n_t >= P.tl_bin_samples && P.shard_allreduce == nullptr) {
+      // built by the first single-problem solve or operator application (tl_ensure):
+      // batched problems run their own kernels and never pay for it
+      cudaFreeAsync(P.rl_tiles, st);
+      P.rl_tiles = nullptr;
+      P.layout = 3;
+      P.tl_pending = 1;
     } else {
       cudaFreeAsync(P.rl_tiles, st);
       P.rl_tiles = nullptr;

@@ -533,7 +533,8 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   // samples in kPcSlots cells; such a coarse space spans the slow modes badly
   // and costs more than it saves, so the plan keeps D^-1 alone.
   const bool spans = h_kept[1] > 0 && (double)h_kept[0] >= kPcKeptMin * (double)h_kept[1];
-  if (n == 0 || !spans) {
+  // the restriction sums a block's share of R^T r in shared memory
+  if (n == 0 || !spans || !pc_restrict_fits(P, n)) {
     void* tmp[] = {cell_of, used, cmap, kept};
     for (void* t : tmp) cudaFreeAsync(t, st);
     pc_free(P, st);

@@ -738,4 +738,22 @@ ds_status tl_build(Plan& P) {
   return DS_OK;
 }
 
+// Builds the records a plan chose at its creation (synchronises); where they cannot be
+// built (a run above 255 samples, too many runs, no room) the plan keeps the
+// time-ordered operator.
+ds_status tl_ensure(Plan& P) {
+  if (!P.tl_pending) return DS_OK;
+  P.tl_pending = 0;
+  ds_status s = P.rl_rec == nullptr ? rl_build(P) : DS_OK;
+  if (s == DS_OK) s = tl_build(P);
+  if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
+  if (s == DS_ESTATE || s == DS_ENOMEM) {
+    cudaGetLastError();
+    rl_release(P, P.stream);
+    P.layout = 0;
+    return DS_OK;
+  }
+  return s;
+}
+
 }  // namespace ds
