@@ -30,6 +30,7 @@
 // R^T D R (null modes of A, where E is rounding noise); the I null mode (a common
 // offset of the I-carrying outputs, which R reproduces) gets a rank-one term so
 // that it is swept like the rest.
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -44,6 +45,7 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kCand = 4;      // cells a baseline can hold while its samples are read
 constexpr int kWarpCells = 8; // cells of one pixel's baselines merged per warp
+constexpr int64_t kPcWarpRows = 256;  // baselines from this length get a warp each
 constexpr double kPcKeptMin = 0.8;  // share of valid samples the kept slots must hold
 constexpr double kPcPivotMin = 1e-6;  // share of diag(R^T D R) below which a pivot is skipped
 
@@ -200,6 +202,118 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
     valid_all += __shfl_down_sync(0xffffffffu, valid_all, d);
   }
   if ((threadIdx.x & 31) == 0) {
+    atomicAdd(kept_total, kept_all);
+    atomicAdd(kept_total + 1, valid_all);
+  }
+}
+
+// The same for long baselines, one warp per baseline: each lane takes every 32nd
+// sample into its own kCand candidate cells, then the warp merges the lanes'
+// candidates (smallest cell first, at most kWarpCells cells; sums in a fixed
+// shuffle order, so the result does not depend on timing) and keeps the two
+// cells with most samples.  A thread per baseline would walk L samples one
+// dependent load after another.
+__global__ void __launch_bounds__(kBlock) k_pc_rows_warp(const int32_t* __restrict__ pix,
+                                                         const float* __restrict__ cc,
+                                                         const float* __restrict__ ss,
+                                                         const int32_t* __restrict__ cell_of,
+                                                         const int32_t* __restrict__ nvalid,
+                                                         int64_t n_t, int64_t L, int64_t n_b,
+                                                         float4* __restrict__ slot,
+                                                         int32_t* __restrict__ used,
+                                                         unsigned long long* __restrict__ kept_total) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long kept_all = 0, valid_all = 0;
+  for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < n_b;
+       b += warps) {
+    int id[kCand];
+    int cnt[kCand];
+    float sc[kCand], sn[kCand];
+#pragma unroll
+    for (int j = 0; j < kCand; ++j) {
+      id[j] = -1;
+      cnt[j] = 0;
+      sc[j] = sn[j] = 0.f;
+    }
+    const int64_t t1 = (b + 1) * L < n_t ? (b + 1) * L : n_t;
+    for (int64_t t = b * L + lane; t < t1; t += 32) {
+      const int p = pix[t];
+      if (p < 0) continue;
+      const int k = __ldg(cell_of + p);
+      const float c = cc[t], s = ss[t];
+      bool placed = false;
+#pragma unroll
+      for (int j = 0; j < kCand; ++j) {
+        if (!placed && (id[j] == k || id[j] < 0)) {
+          id[j] = k;
+          cnt[j] += 1;
+          sc[j] += c;
+          sn[j] += s;
+          placed = true;
+        }
+      }
+    }
+    // merge: repeatedly the smallest candidate cell left in any lane
+    int best_id[kPcSlots], best_cnt[kPcSlots];
+    float best_c[kPcSlots], best_s[kPcSlots];
+#pragma unroll
+    for (int s = 0; s < kPcSlots; ++s) {
+      best_id[s] = -1;
+      best_cnt[s] = 0;
+      best_c[s] = best_s[s] = 0.f;
+    }
+    for (int round = 0; round < kWarpCells; ++round) {
+      int mine = INT_MAX;
+#pragma unroll
+      for (int j = 0; j < kCand; ++j)
+        if (id[j] >= 0 && id[j] < mine) mine = id[j];
+      const int cell = __reduce_min_sync(full, mine);
+      if (cell == INT_MAX) break;  // warp-uniform
+      int n = 0;
+      float c = 0.f, s = 0.f;
+#pragma unroll
+      for (int j = 0; j < kCand; ++j)
+        if (id[j] == cell) {
+          n = cnt[j];
+          c = sc[j];
+          s = sn[j];
+          id[j] = -1;
+        }
+      n = __reduce_add_sync(full, n);
+      for (int d = 16; d > 0; d >>= 1) {
+        c += __shfl_xor_sync(full, c, d);
+        s += __shfl_xor_sync(full, s, d);
+      }
+      // insert into the two best (more samples first; the smaller cell on a tie)
+      if (n > best_cnt[0]) {
+        best_id[1] = best_id[0]; best_cnt[1] = best_cnt[0]; best_c[1] = best_c[0]; best_s[1] = best_s[0];
+        best_id[0] = cell; best_cnt[0] = n; best_c[0] = c; best_s[0] = s;
+      } else if (n > best_cnt[1]) {
+        best_id[1] = cell; best_cnt[1] = n; best_c[1] = c; best_s[1] = s;
+      }
+    }
+    if (lane == 0) {
+      const int nv = nvalid[b];
+      const float inv = nv > 0 ? 1.f / (float)nv : 0.f;
+#pragma unroll
+      for (int s = 0; s < kPcSlots; ++s) {
+        kept_all += (unsigned long long)best_cnt[s];
+        slot[b * kPcSlots + s] =
+            best_id[s] >= 0 ? make_float4(__int_as_float(best_id[s]), (float)best_cnt[s] * inv,
+                                          best_c[s] * inv, best_s[s] * inv)
+                            : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+        if (best_id[s] >= 0) used[best_id[s]] = 1;
+      }
+      valid_all += (unsigned long long)(nv > 0 ? nv : 0);
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    kept_all += __shfl_down_sync(full, kept_all, d);
+    valid_all += __shfl_down_sync(full, valid_all, d);
+  }
+  if (lane == 0) {
     atomicAdd(kept_total, kept_all);
     atomicAdd(kept_total + 1, valid_all);
   }
@@ -512,8 +626,12 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   const int g_pix = stream_grid(P, P.npix, kBlock, 8);
   k_pc_cell_table<<<g_pix, kBlock, 0, st>>>(cell_of, P.npix, P.desc.nside, nc);
   const int g_b = stream_grid(P, P.n_b, kBlock, 8);
-  k_pc_rows<<<g_b, kBlock, 0, st>>>(P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b,
-                                    P.pc_slot, used, kept);
+  if (P.L >= kPcWarpRows)
+    k_pc_rows_warp<<<stream_grid(P, P.n_b * 32, kBlock, 8), kBlock, 0, st>>>(
+        P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b, P.pc_slot, used, kept);
+  else
+    k_pc_rows<<<g_b, kBlock, 0, st>>>(P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b,
+                                      P.pc_slot, used, kept);
   P.launches += 2;
   e = cudaGetLastError();
   // kept cells: numbered in cell order on the host

@@ -103,6 +103,26 @@ def test_preconditioned_warm_start_matches_oracle():
     assert np.abs(a - ref["a"]).max() < 1e-4
 
 
+def test_long_baselines_coarse_space_matches_oracle():
+    # 8 s baselines on a slowly spinning scan: each baseline stays within one or two
+    # cells, so the coarse space is built (one warp per baseline gathers its cells),
+    # and the two-level preconditioner needs fewer iterations than D^-1 alone
+    prob = make_problem(200_000, 16, ("I", "q", "u"), baseline_len=400, f_knee=0.1, alpha=1.7,
+                        seed=13, scan=ScanParams(spin_period=600.0, sidereal_day=7200.0),
+                        flag_frac=0.02, flag_mean_len=200,
+                        sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
+    op, ref = oracle_of(prob, "mixed")
+    iters = {}
+    for pc in (1, 2):
+        st, it, rel, a, m, info = solve_gpu(prob, "mixed", pc, coarse_nside=4)
+        assert st == ds.DS_OK and rel < 1e-9, (pc, st, it, rel)
+        assert rel_rms(a, ref["a"]) < 1e-5, pc
+        assert np.abs(a - ref["a"]).max() < 1e-4, pc
+        assert rel_rms(m.reshape(op.n_c, -1)[:, op.mask], ref["map"][:, op.mask]) < 1e-5
+        iters[pc] = it
+    assert iters[2] < iters[1], iters
+
+
 LATTE_SHAPED = dict(n_t=3 * 86400 * 5, nside=64, kinds=("iqu",), baseline_len=5, f_knee=0.05,
                     alpha=1.5, seed=1004, sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0},
                     flag_frac=0.02, flag_mean_len=50,
