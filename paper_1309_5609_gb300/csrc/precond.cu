@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
   }
 }
 
-// The same for long baselines, one warp per baseline: each lane takes every 32nd
+// The same for long baselines, one warp per baseline (every step-th baseline; step > 1
+// is a probe that only counts the kept samples): each lane takes every 32nd
 // sample into its own kCand candidate cells, then the warp merges the lanes'
 // candidates (smallest cell first, at most kWarpCells cells; sums in a fixed
 // shuffle order, so the result does not depend on timing) and keeps the two
@@ -219,15 +220,16 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows_warp(const int32_t* __restri
                                                          const int32_t* __restrict__ cell_of,
                                                          const int32_t* __restrict__ nvalid,
                                                          int64_t n_t, int64_t L, int64_t n_b,
-                                                         float4* __restrict__ slot,
+                                                         int64_t step, float4* __restrict__ slot,
                                                          int32_t* __restrict__ used,
                                                          unsigned long long* __restrict__ kept_total) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   unsigned long long kept_all = 0, valid_all = 0;
-  for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < n_b;
-       b += warps) {
+  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j * step < n_b;
+       j += warps) {
+    const int64_t b = j * step;
     int id[kCand];
     int cnt[kCand];
     float sc[kCand], sn[kCand];
@@ -300,6 +302,7 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows_warp(const int32_t* __restri
 #pragma unroll
       for (int s = 0; s < kPcSlots; ++s) {
         kept_all += (unsigned long long)best_cnt[s];
+        if (step > 1) continue;  // a probe of every step-th baseline counts only
         slot[b * kPcSlots + s] =
             best_id[s] >= 0 ? make_float4(__int_as_float(best_id[s]), (float)best_cnt[s] * inv,
                                           best_c[s] * inv, best_s[s] * inv)
@@ -626,10 +629,31 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   const int g_pix = stream_grid(P, P.npix, kBlock, 8);
   k_pc_cell_table<<<g_pix, kBlock, 0, st>>>(cell_of, P.npix, P.desc.nside, nc);
   const int g_b = stream_grid(P, P.n_b, kBlock, 8);
-  if (P.L >= kPcWarpRows)
+  if (P.L >= kPcWarpRows) {
+    // long baselines often sweep too many cells: a probe of about 4096 of them first
+    const int64_t step = P.n_b / 4096 > 1 ? P.n_b / 4096 : 1;
+    if (step > 1) {
+      unsigned long long h_probe[2] = {0, 0};
+      k_pc_rows_warp<<<stream_grid(P, (P.n_b / step + 1) * 32, kBlock, 8), kBlock, 0, st>>>(
+          P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b, step, P.pc_slot, used, kept);
+      P.launches += 1;
+      e = cudaMemcpyAsync(h_probe, kept, sizeof(h_probe), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return fail(e);
+      if (h_probe[1] > 0 && (double)h_probe[0] < (kPcKeptMin - 0.1) * (double)h_probe[1]) {
+        void* tmp[] = {cell_of, used, cmap, kept};
+        for (void* tp : tmp)
+          if (tp) cudaFreeAsync(tp, st);
+        pc_free(P, st);
+        P.pc_built = 1;
+        return DS_OK;
+      }
+      e = cudaMemsetAsync(kept, 0, sizeof(unsigned long long) * 2, st);
+      if (e != cudaSuccess) return fail(e);
+    }
     k_pc_rows_warp<<<stream_grid(P, P.n_b * 32, kBlock, 8), kBlock, 0, st>>>(
-        P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b, P.pc_slot, used, kept);
-  else
+        P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b, 1, P.pc_slot, used, kept);
+  } else
     k_pc_rows<<<g_b, kBlock, 0, st>>>(P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b,
                                       P.pc_slot, used, kept);
   P.launches += 2;
