@@ -323,7 +323,9 @@ ds_status ds::plan_create(const ds_desc* desc, const ds_exchange* ex, const int3
   P->rescan_rounds = 0;
   P->bin_order = 1;
   P->samples_per_thread = 4;
-  P->precond = 2;
+  // the coarse space costs a few ms to build (one sweep launch per coarse column):
+  // small problems keep D^-1
+  P->precond = desc->n_samples >= kPcMinSamples ? 2 : 1;
   P->pc_nside = 8;
   P->tl_bin_samples = int64_t(1) << 26;
   if (ex != nullptr) {

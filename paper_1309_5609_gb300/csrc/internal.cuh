@@ -119,6 +119,7 @@ enum ErrBits { ERR_PIX = 1, ERR_NAN = 2 };
 
 constexpr int kPcSlots = 2;  // coarse cells kept per baseline by the two-level preconditioner
 constexpr size_t kPcRestrictSmemMax = 160 * 1024;  // float32 R^T r sums per block (40960 columns)
+constexpr int64_t kPcMinSamples = int64_t(1) << 23;  // the two-level default from this many samples
 
 struct Plan {
   ds_desc desc;
