@@ -11,7 +11,10 @@ the kernels themselves against the oracle.
     kept across rounds, warp flushes only where a baseline ends;
   * run hand-off in the accurate binning (k_bin_df): a lane's last run carried
     into the next lane's first when they share a pixel;
-  * the two-level offsets of the pixel-major copy (k_pm_scan_up / k_pm_scan_down)."""
+  * the two-level offsets of the pixel-major copy (k_pm_scan_up / k_pm_scan_down);
+  * the lane-sequential binning over pixel-sorted records (k_tl_bin_lanes): a lane's
+    head, interior and tail pixels, the segmented scan of tails over the lanes, and
+    the pixel carried across rounds: every pixel reduced once per chunk."""
 import numpy as np
 import pytest
 
@@ -319,3 +322,104 @@ def test_pixel_major_offsets_are_the_exclusive_prefix_of_runs_per_pixel():
                 carry += tile.sum()
         off[npix] = cnt.sum()
         assert (off == np.concatenate([[0], np.cumsum(cnt)])).all()
+
+
+# ---- lane-sequential binning over pixel-sorted records (k_tl_bin_lanes) --------------
+
+LANE_RECS = 8
+ROUND = LANES * LANE_RECS
+
+
+def lanes_round_flushes(keys, vals, ckey, carry):
+    """One round of k_tl_bin_lanes: keys/vals of the round's ROUND records (key -1
+    past the chunk's end, only at the end), the pixel carried from the previous
+    round.  Returns (flushes [(key, value)], new ckey, new carry)."""
+    flushes = []
+    cur = [-1] * LANES
+    hkey = [-1] * LANES
+    head = [False] * LANES
+    acc = [0.0] * LANES
+    hacc = [0.0] * LANES
+    for l in range(LANES):  # each lane sums its LANE_RECS consecutive records
+        for k in range(LANE_RECS):
+            key, w = keys[l * LANE_RECS + k], vals[l * LANE_RECS + k]
+            if key < 0:
+                continue
+            if key != cur[l]:
+                if cur[l] >= 0:
+                    if not head[l]:
+                        head[l], hkey[l], hacc[l] = True, cur[l], acc[l]
+                    else:
+                        flushes.append((cur[l], acc[l]))  # interior pixel
+                cur[l], acc[l] = key, w
+            else:
+                acc[l] += w
+    first = [hkey[l] if head[l] else cur[l] for l in range(LANES)]
+    if ckey >= 0:  # the carried pixel joins lane 0's first pixel, or is complete
+        if first[0] == ckey:
+            if head[0]:
+                hacc[0] += carry
+            else:
+                acc[0] += carry
+        else:
+            flushes.append((ckey, carry))
+    prev = [cur[0]] + cur[:-1]  # shfl_up by one: lane 0 reads itself
+    f = [l == 0 or head[l] or prev[l] != cur[l] for l in range(LANES)]
+    s = list(acc)
+    d = 1
+    while d < LANES:  # Hillis-Steele segmented inclusive scan of the tails
+        s_up, f_up = list(s), list(f)
+        for l in range(LANES):
+            if l >= d and not f[l]:
+                s_up[l] = s[l] + s[l - d]
+                f_up[l] = f[l - d]
+            else:
+                s_up[l], f_up[l] = s[l], f[l]
+        s, f = s_up, f_up
+        d *= 2
+    for l in range(LANES):
+        if head[l]:
+            v = hacc[l] + (s[l - 1] if l > 0 and prev[l] == hkey[l] else 0.0)
+            flushes.append((hkey[l], v))
+    nxt = first[1:] + [first[-1]]
+    for l in range(LANES - 1):
+        if cur[l] >= 0 and nxt[l] != cur[l]:
+            flushes.append((cur[l], s[l]))
+    return flushes, cur[LANES - 1], s[LANES - 1]
+
+
+def lanes_chunk_flushes(keys, vals):
+    flushes, ckey, carry = [], -1, 0.0
+    for base in range(0, len(keys), ROUND):
+        k = list(keys[base:base + ROUND]) + [-1] * max(0, base + ROUND - len(keys))
+        v = list(vals[base:base + ROUND]) + [0.0] * max(0, base + ROUND - len(vals))
+        fl, ckey, carry = lanes_round_flushes(k, v, ckey, carry)
+        flushes += fl
+    if ckey >= 0:
+        flushes.append((ckey, carry))
+    return flushes
+
+
+@pytest.mark.parametrize("mean_run", [1.0, 1.5, 7.0, 40.0, 600.0])
+def test_lane_sequential_binning_sums_every_pixel_once_per_chunk(mean_run):
+    rng = np.random.default_rng(int(mean_run * 10))
+    for n in (1, 7, ROUND - 1, ROUND, ROUND + 1, 5 * ROUND + 123):
+        # pixel-sorted keys: segments of geometric length
+        keys = []
+        p = 0
+        while len(keys) < n:
+            p += int(rng.integers(1, 4))
+            keys += [p] * int(rng.geometric(1.0 / mean_run))
+        keys = keys[:n]
+        vals = rng.integers(-8, 9, size=n).astype(float)  # exact sums in any order
+        flushes = lanes_chunk_flushes(keys, vals)
+        got, seen = {}, {}
+        for k, v in flushes:
+            got[k] = got.get(k, 0.0) + v
+            seen[k] = seen.get(k, 0) + 1
+        want = {}
+        for k, v in zip(keys, vals):
+            want[k] = want.get(k, 0.0) + v
+        assert got == want
+        # one flush per pixel: a pixel's records are contiguous within the chunk
+        assert all(c == 1 for c in seen.values()), seen
