@@ -345,10 +345,10 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     (20 bytes per run); chosen when the records are requested above
  *                     0.6 runs per sample
  *   "precond"         preconditioner of the CG (no counterpart in the paper, which uses
- *                     unpreconditioned Krylov solvers): 0 = none; 1 = D^-1, the valid
- *                     samples of each baseline (default below 2^23 samples, where the
- *                     coarse space's build of a few ms does not pay); 2 = two-level
- *                     (default from 2^23 samples): D^-1 plus a
+ *                     unpreconditioned Krylov solvers): 0 = none (default below 2^23
+ *                     samples, where the coarse space's build of a few ms does not pay
+ *                     and D^-1 alone saves no iterations); 1 = D^-1, the valid samples of
+ *                     each baseline; 2 = two-level (default from 2^23 samples): D^-1 plus a
  *                     coarse correction R E^+ R^T on a space of large-scale sky modes
  *                     (cells of the sphere, "coarse_nside"), E = R^T A R built once per
  *                     plan at its first solve (from the pixel-major run records, made

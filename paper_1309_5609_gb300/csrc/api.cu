@@ -114,7 +114,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->tl_rec, P->tl_off, P->tl2_rec, P->tl2_off, P->tl2_chunk, P->tl_x4, P->pc_slot, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->tl_rec, P->tl_off, P->tl2_rec, P->tl2_off, P->tl2_chunk, P->tl2_end, P->tl_x4, P->pc_slot, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a
@@ -323,9 +323,10 @@ ds_status ds::plan_create(const ds_desc* desc, const ds_exchange* ex, const int3
   P->rescan_rounds = 0;
   P->bin_order = 1;
   P->samples_per_thread = 4;
-  // the coarse space costs a few ms to build (one sweep launch per coarse column):
-  // small problems keep D^-1
-  P->precond = desc->n_samples >= kPcMinSamples ? 2 : 1;
+  // the coarse space costs a few ms to build (one sweep launch per coarse column),
+  // and D^-1 alone (about a scalar where baselines hold equal counts) saves no
+  // iterations: small problems iterate plain CG, with one kernel less per iteration
+  P->precond = desc->n_samples >= kPcMinSamples ? 2 : 0;
   P->pc_nside = 8;
   P->tl_bin_samples = int64_t(1) << 26;
   if (ex != nullptr) {

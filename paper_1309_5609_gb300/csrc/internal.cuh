@@ -224,6 +224,8 @@ struct Plan {
   int64_t* tl2_off;         // [tiles + 1]
   int64_t* tl2_chunk;       // [tiles + 1] first warp chunk of each long tile
   int64_t tl2_tiles, tl2_tb, tl2_chunks;
+  uint32_t* tl2_end;        // [tiles][ranks] end of each pixel rank's records in a long tile
+  int64_t tl2_nkeys;        // pixel ranks (observed pixels)
   int64_t tl_bin_samples;   // samples per long tile (tune key "bin_tile_samples")
   int tl_pending;           // layout 3 chosen by the plan, records not built yet (tl_ensure)
   float4* tl_x4;            // [n_b] float32 baselines of every output, per baseline

@@ -373,34 +373,21 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_diag(const float4* __restrict__
   }
 }
 
-// E -= (K R)^T M^-1 (K R), one warp per pixel over its pixel-major runs.  A run
-// (count n, sum cos, sum sin, baseline b) is one entry of K: the row sums k_o of
-// each output on the pixel's components.  (K R)_p[c'][(cell, c)] =
-// sum over runs and outputs of k_o[c'] R[(o,b), (cell, c)].  Each lane sums its
-// runs for up to kCand cells in registers; the warp merges the lanes' cells in
-// shared memory and adds the pixel's term into E.
+// E -= (K R)^T M^-1 (K R), one warp per pixel over its runs.  A run (count n,
+// sum cos, sum sin, baseline b) is one entry of K: the row sums k_o of each output
+// on the pixel's components.  (K R)_p[c'][(cell, c)] = sum over runs and outputs of
+// k_o[c'] R[(o,b), (cell, c)].  Each lane sums its runs for up to kCand cells in
+// registers; the warp merges the lanes' cells in shared memory and adds the
+// pixel's term into E.  The runs come from the pixel-major copy (k_pc_E_pix) or
+// from the long tiles of the tiled operator, where a pixel's runs of each tile are
+// contiguous (k_pc_E_tiles).
 template <int KS>
-__global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict__ off,
-                                                     const float4* __restrict__ rec,
-                                                     const float4* __restrict__ slot,
-                                                     const double* __restrict__ minv,
-                                                     const uint8_t* __restrict__ mask,
-                                                     int64_t npix, int64_t n_b, KindsArg kk,
-                                                     int n, double* __restrict__ E) {
-  using K = KSet<KS>;
-  constexpr int NC = K::NC, NO = K::NO, NM = NC * (NC + 1) / 2;
-  const int n_o = K::n_o(kk);
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  __shared__ int s_id[kBlock / 32][kWarpCells];
-  __shared__ double s_kr[kBlock / 32][kWarpCells][NC][NC];
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; p < npix; p += warps) {
-    if (!mask[p]) continue;  // warp-uniform
-    const uint32_t beg = __ldg(off + p), end = __ldg(off + p + 1);
-    if (beg == end) continue;
-    int id[kCand];
-    double kr[kCand][NC][NC];
+struct PixTerm {
+  static constexpr int NC = KSet<KS>::NC, NO = KSet<KS>::NO;
+  int id[kCand];
+  double kr[kCand][NC][NC];
+
+  __device__ __forceinline__ void clear() {
 #pragma unroll
     for (int j = 0; j < kCand; ++j) {
       id[j] = -1;
@@ -409,72 +396,81 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict_
 #pragma unroll
         for (int c = 0; c < NC; ++c) kr[j][a][c] = 0.0;
     }
-    for (uint32_t i = beg + lane; i < end; i += 32) {
-      const float4 r = __ldg(rec + i);
-      const int64_t b = __float_as_int(r.w);
+  }
+
+  // one run: n samples, sums C and S, baseline b
+  __device__ __forceinline__ void add_run(float n, float C, float S, int64_t b,
+                                          const float4* __restrict__ slot, const KindsArg& kk) {
+    using K = KSet<KS>;
+    const int n_o = K::n_o(kk);
 #pragma unroll
-      for (int o = 0; o < NO; ++o) {
-        if (o >= n_o) continue;
-        float kv[NC];
+    for (int o = 0; o < NO; ++o) {
+      if (o >= n_o) continue;
+      float kv[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) kv[c] = 0.f;
-        // the output's row summed over the run (z = 1)
-        {
-          using F = Frame<NC>;
-          const int kind = K::kind(o, kk);
-          if (kind == DS_KIND_I) {
-            if constexpr (F::I >= 0) kv[F::I] = r.x;
-          } else if (kind == DS_KIND_Q) {
-            if constexpr (F::Q >= 0) { kv[F::Q] = r.y; kv[F::U] = r.z; }
-          } else if (kind == DS_KIND_U) {
-            if constexpr (F::Q >= 0) { kv[F::Q] = -r.z; kv[F::U] = r.y; }
-          } else {
-            if constexpr (F::I >= 0 && F::Q >= 0) { kv[F::I] = r.x; kv[F::Q] = r.y; kv[F::U] = r.z; }
-          }
+      for (int c = 0; c < NC; ++c) kv[c] = 0.f;
+      {  // the output's row summed over the run (z = 1)
+        using F = Frame<NC>;
+        const int kind = K::kind(o, kk);
+        if (kind == DS_KIND_I) {
+          if constexpr (F::I >= 0) kv[F::I] = n;
+        } else if (kind == DS_KIND_Q) {
+          if constexpr (F::Q >= 0) { kv[F::Q] = C; kv[F::U] = S; }
+        } else if (kind == DS_KIND_U) {
+          if constexpr (F::Q >= 0) { kv[F::Q] = -S; kv[F::U] = C; }
+        } else {
+          if constexpr (F::I >= 0 && F::Q >= 0) { kv[F::I] = n; kv[F::Q] = C; kv[F::U] = S; }
         }
+      }
 #pragma unroll
-        for (int s = 0; s < kPcSlots; ++s) {
-          const float4 m = __ldg(slot + b * kPcSlots + s);
-          const int cell = __float_as_int(m.x);
-          if (cell < 0) continue;
-          float rv[NC];
-          row_moments<NC>(K::kind(o, kk), m.y, m.z, m.w, rv);
-          bool placed = false;
+      for (int s = 0; s < kPcSlots; ++s) {
+        const float4 m = __ldg(slot + b * kPcSlots + s);
+        const int cell = __float_as_int(m.x);
+        if (cell < 0) continue;
+        float rv[NC];
+        row_moments<NC>(K::kind(o, kk), m.y, m.z, m.w, rv);
+        bool placed = false;
 #pragma unroll
-          for (int j = 0; j < kCand; ++j) {
-            if (!placed && (id[j] == cell || id[j] < 0)) {
-              id[j] = cell;
+        for (int j = 0; j < kCand; ++j) {
+          if (!placed && (id[j] == cell || id[j] < 0)) {
+            id[j] = cell;
 #pragma unroll
-              for (int a = 0; a < NC; ++a)
+            for (int a = 0; a < NC; ++a)
 #pragma unroll
-                for (int c = 0; c < NC; ++c) kr[j][a][c] = fma((double)kv[a], (double)rv[c], kr[j][a][c]);
-              placed = true;
-            }
+              for (int c = 0; c < NC; ++c) kr[j][a][c] = fma((double)kv[a], (double)rv[c], kr[j][a][c]);
+            placed = true;
           }
         }
       }
     }
-    // merge the lanes' cells: the warp's table of distinct cells
-    if (lane < kWarpCells) s_id[wib][lane] = -1;
+  }
+
+  // the warp's merged cells and E -= (K R)_p^T M_p^-1 (K R)_p
+  __device__ __forceinline__ void finish(int64_t p, const double* __restrict__ minv, int n,
+                                         double* __restrict__ E, int (&s_id)[kWarpCells],
+                                         double (&s_kr)[kWarpCells][NC][NC]) {
+    constexpr int NM = NC * (NC + 1) / 2;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (lane < kWarpCells) s_id[lane] = -1;
     __syncwarp();
-    int slot[kCand];
+    int slot_of[kCand];
 #pragma unroll
     for (int j = 0; j < kCand; ++j) {
-      slot[j] = -1;
+      slot_of[j] = -1;
       if (id[j] < 0) continue;
       for (int t = 0; t < kWarpCells; ++t) {
-        const int old = atomicCAS(&s_id[wib][t], -1, id[j]);
+        const int old = atomicCAS(&s_id[t], -1, id[j]);
         if (old == -1 || old == id[j]) {
-          slot[j] = t;
+          slot_of[j] = t;
           break;
         }
       }
     }
     __syncwarp();
     int ncell = 0;
-    while (ncell < kWarpCells && s_id[wib][ncell] >= 0) ++ncell;
-    // warp sums of every (cell, a, c) entry
-    for (int t = 0; t < ncell; ++t) {
+    while (ncell < kWarpCells && s_id[ncell] >= 0) ++ncell;
+    for (int t = 0; t < ncell; ++t) {  // warp sums of every (cell, a, c) entry
 #pragma unroll
       for (int a = 0; a < NC; ++a)
 #pragma unroll
@@ -482,14 +478,13 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict_
           double v = 0.0;
 #pragma unroll
           for (int j = 0; j < kCand; ++j)
-            if (slot[j] == t) v += kr[j][a][c];
+            if (slot_of[j] == t) v += kr[j][a][c];
           for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(full, v, d);
-          if (lane == 0) s_kr[wib][t][a][c] = v;
+          if (lane == 0) s_kr[t][a][c] = v;
         }
     }
     __syncwarp();
-    // the pixel's M^-1 (packed symmetric)
-    double mi[NC][NC];
+    double mi[NC][NC];  // the pixel's M^-1 (packed symmetric)
     {
       const double* mp = minv + p * NM;
       if constexpr (NC == 1) {
@@ -510,11 +505,72 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict_
       for (int a = 0; a < NC; ++a)
 #pragma unroll
         for (int a2 = 0; a2 < NC; ++a2)
-          v += s_kr[wib][t1][a][c1] * mi[a][a2] * s_kr[wib][t2][a2][c2];
+          v += s_kr[t1][a][c1] * mi[a][a2] * s_kr[t2][a2][c2];
       if (v != 0.0)
-        atomicAdd(E + (int64_t)(s_id[wib][t1] * NC + c1) * n + s_id[wib][t2] * NC + c2, -v);
+        atomicAdd(E + (int64_t)(s_id[t1] * NC + c1) * n + s_id[t2] * NC + c2, -v);
     }
     __syncwarp();
+  }
+};
+
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict__ off,
+                                                     const float4* __restrict__ rec,
+                                                     const float4* __restrict__ slot,
+                                                     const double* __restrict__ minv,
+                                                     const uint8_t* __restrict__ mask,
+                                                     int64_t npix, KindsArg kk, int n,
+                                                     double* __restrict__ E) {
+  constexpr int NC = KSet<KS>::NC;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  __shared__ int s_id[kBlock / 32][kWarpCells];
+  __shared__ double s_kr[kBlock / 32][kWarpCells][NC][NC];
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; p < npix; p += warps) {
+    if (!mask[p]) continue;  // warp-uniform
+    const uint32_t beg = __ldg(off + p), end = __ldg(off + p + 1);
+    if (beg == end) continue;
+    PixTerm<KS> pt;
+    pt.clear();
+    for (uint32_t i = beg + lane; i < end; i += 32) {
+      const float4 r = __ldg(rec + i);
+      pt.add_run(r.x, r.y, r.z, (int64_t)__float_as_int(r.w), slot, kk);
+    }
+    pt.finish(p, minv, n, E, s_id[wib], s_kr[wib]);
+  }
+}
+
+// The same over the long tiles: pixel rank r's runs of tile t are records
+// [end[t nkeys + r - 1], end[t nkeys + r]) (16-byte tiled records: pixel,
+// n << 24 | baseline in the tile, sum cos, sum sin).
+template <int KS>
+__global__ void __launch_bounds__(kBlock) k_pc_E_tiles(const int4* __restrict__ rec,
+                                                       const uint32_t* __restrict__ end,
+                                                       int64_t n_tiles, int64_t nkeys, int64_t Tb,
+                                                       const float4* __restrict__ slot,
+                                                       const double* __restrict__ minv,
+                                                       KindsArg kk, int n, double* __restrict__ E) {
+  constexpr int NC = KSet<KS>::NC;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  __shared__ int s_id[kBlock / 32][kWarpCells];
+  __shared__ double s_kr[kBlock / 32][kWarpCells][NC][NC];
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; r < nkeys; r += warps) {
+    PixTerm<KS> pt;
+    pt.clear();
+    int p = -1;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+      const int64_t k = t * nkeys + r;
+      const uint32_t b0 = k > 0 ? __ldg(end + k - 1) : 0u, b1 = __ldg(end + k);
+      if (b0 == b1) continue;  // warp-uniform
+      if (p < 0) p = __ldg(rec + b0).x;
+      for (uint32_t i = b0 + lane; i < b1; i += 32) {
+        const int4 v = __ldcs(rec + i);
+        pt.add_run((float)((unsigned)v.y >> 24), __int_as_float(v.z), __int_as_float(v.w),
+                   t * Tb + (int64_t)((unsigned)v.y & 0xFFFFFFu), slot, kk);
+      }
+    }
+    if (p >= 0) pt.finish(p, minv, n, E, s_id[wib], s_kr[wib]);
   }
 }
 
@@ -683,8 +739,10 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
     P.pc_built = 1;
     return DS_OK;
   }
-  // the pixel-major runs for the second term of E
-  if (P.pm_rec == nullptr) {
+  // the runs of each pixel for the second term of E: the tiled operator's long
+  // tiles, else the pixel-major copy (made for the purpose when the plan has none)
+  const bool tiles = P.layout == 3 && P.tl2_end != nullptr && P.tl2_rec != nullptr;
+  if (!tiles && P.pm_rec == nullptr) {
     ds_status sr = DS_OK;
     if (P.rl_rec == nullptr) {
       sr = rl_build(P);
@@ -724,11 +782,15 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   });
   // the scale of each coarse direction: diag(R^T D R), before the pixel term
   k_pc_diag<<<(n + 255) / 256, 256, 0, st>>>(E, diag0, n);
-  const int g_w = stream_grid(P, P.npix * 32, kBlock, 8);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
-    k_pc_E_pix<KS><<<g_w, kBlock, 0, st>>>(P.pm_off, P.pm_rec, P.pc_slot, P.minv,
-                                           P.mask, P.npix, P.n_b, P.kinds, n, E);
+    if (tiles)
+      k_pc_E_tiles<KS><<<stream_grid(P, P.tl2_nkeys * 32, kBlock, 8), kBlock, 0, st>>>(
+          P.tl2_rec, P.tl2_end, P.tl2_tiles, P.tl2_nkeys, P.tl2_tb, P.pc_slot, P.minv, P.kinds,
+          n, E);
+    else
+      k_pc_E_pix<KS><<<stream_grid(P, P.npix * 32, kBlock, 8), kBlock, 0, st>>>(
+          P.pm_off, P.pm_rec, P.pc_slot, P.minv, P.mask, P.npix, P.kinds, n, E);
   });
   P.launches += 3;
   e = cudaGetLastError();

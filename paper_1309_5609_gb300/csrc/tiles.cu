@@ -549,7 +549,7 @@ void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g) {
 // fit kSortCounts entries and its runs 32-bit cursors.  One host synchronisation
 // for the tile offsets; the rest is stream-ordered on the plan's stream.
 static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nkeys,
-                           int4** out_rec, int64_t** out_off) {
+                           int4** out_rec, int64_t** out_off, uint32_t** keep_ends = nullptr) {
   constexpr int64_t kSortCounts = int64_t(1) << 30;  // 4 GB of uint32 counts per batch
   cudaStream_t st = P.stream;
   const int64_t n_tiles = (P.n_b + Tb - 1) / Tb;
@@ -558,10 +558,12 @@ static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nke
   const int64_t per = kSortCounts / nkeys > 0 ? kSortCounts / nkeys : 1;  // tiles per batch
   const int64_t cap = (per < n_tiles ? per : n_tiles) * nkeys;
   const int64_t gmax = stream_grid(P, cap, kBlock, 8);
+  // one batch: after the scatter the cursors are the keys' ends, kept on request
+  const bool keep = keep_ends != nullptr && per >= n_tiles;
   cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(out_rec), sizeof(int4) * P.rl_n, true);
   if (e == cudaSuccess)
     e = plan_alloc(P, reinterpret_cast<void**>(out_off), sizeof(int64_t) * (n_tiles + 1), true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * cap, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * cap, keep);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * gmax, false);
   std::vector<int64_t> off(n_tiles + 1);
   if (e == cudaSuccess) {
@@ -589,6 +591,10 @@ static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nke
     P.launches += 5;
     e = cudaGetLastError();
     t0 = t1;
+  }
+  if (keep && e == cudaSuccess) {
+    *keep_ends = cnt;
+    cnt = nullptr;
   }
   for (void* t : {(void*)cnt, (void*)blk})
     if (t) cudaFreeAsync(t, st);
@@ -628,9 +634,10 @@ static cudaError_t tl_rank(Plan& P, int32_t** rank, int64_t* nkeys) {
 }
 
 static void tl_free(Plan& P) {
-  void* mine[] = {P.tl_rec, P.tl_off, P.tl2_rec, P.tl2_off, P.tl2_chunk, P.tl_x4};
+  void* mine[] = {P.tl_rec, P.tl_off, P.tl2_rec, P.tl2_off, P.tl2_chunk, P.tl_x4, P.tl2_end};
   for (void* t : mine)
     if (t) cudaFreeAsync(t, P.stream);
+  P.tl2_end = nullptr;
   P.tl_rec = nullptr;
   P.tl_off = nullptr;
   P.tl2_rec = nullptr;
@@ -690,7 +697,8 @@ ds_status tl_build(Plan& P) {
   if (e == cudaSuccess) e = tl_sort(P, Tb, nullptr, P.npix, &P.tl_rec, &P.tl_off);
   if (e != cudaSuccess) return release(e);
   // the long tiles and their chunk table (tile t's chunks start at chunk_first[t])
-  e = tl_sort(P, Tb2, rank, nkeys, &P.tl2_rec, &P.tl2_off);
+  e = tl_sort(P, Tb2, rank, nkeys, &P.tl2_rec, &P.tl2_off, &P.tl2_end);
+  P.tl2_nkeys = nkeys;
   if (e == cudaSuccess) {
     cudaFreeAsync(rank, st);
     rank = nullptr;
