@@ -254,8 +254,8 @@ constexpr int kRound = 32 * kLaneRecs;  // records per warp round
 constexpr int kBinWarps = 8;   // warps per block of the binning
 constexpr int64_t kChunk = kRound * 8;  // records per warp chunk of the binning
 
-// x32[o][b] = x[o][b] rounded to float32, and x4[b] = every output's baseline b
-// (one 16-byte gather per run record in the tiled passes).
+// x32[o][b] = x[o][b] rounded to float32, and (several outputs) x4[b] = every
+// output's baseline b (one 16-byte gather per run record in the tiled binning).
 __global__ void __launch_bounds__(kBlock) k_tl_pack(const double* __restrict__ x,
                                                     float* __restrict__ x32,
                                                     float4* __restrict__ x4, int64_t n_b, int n_o,
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) k_tl_pack(const double* __restrict__ x
         v[o] = (float)x[o * n_b + b];
         x32[o * n_b + b] = v[o];
       }
-    x4[b] = make_float4(v[0], v[1], v[2], v[3]);
+    if (x4 != nullptr) x4[b] = make_float4(v[0], v[1], v[2], v[3]);
   }
 }
 
@@ -506,9 +506,17 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
 
 }  // namespace
 
+// whether the plan's kind set gathers packed baselines (more than one output slot);
+// with one, the passes gather x32 directly
+static bool tl_packs(const Plan& P) {
+  int no = 0;
+  with_kindset(P.kindset, [&](auto ksc) { no = KSet<decltype(ksc)::value>::NO; });
+  return no > 1;
+}
+
 bool tl_ready(const Plan& P) {
   return P.layout == 3 && P.tl_rec != nullptr && P.tl2_rec != nullptr && P.x32 != nullptr &&
-         P.tl_x4 != nullptr;
+         (P.tl_x4 != nullptr || !tl_packs(P));
 }
 
 void launch_pack_tl(const Plan& P, cudaStream_t st, const double* x, Gate g) {
@@ -688,7 +696,7 @@ ds_status tl_build(Plan& P) {
     release(cudaSuccess);
     return DS_ESTATE;
   }
-  e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_x4), sizeof(float4) * P.n_b, true);
+  if (tl_packs(P)) e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_x4), sizeof(float4) * P.n_b, true);
   int64_t nkeys = 0;
   if (e == cudaSuccess) e = tl_rank(P, &rank, &nkeys);
   if (e == cudaSuccess && nkeys <= 0) e = cudaErrorInvalidValue;
