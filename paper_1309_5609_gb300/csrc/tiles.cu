@@ -256,21 +256,35 @@ constexpr int64_t kChunk = kRound * 8;  // records per warp chunk of the binning
 
 // x32[o][b] = x[o][b] rounded to float32, and (several outputs) x4[b] = every
 // output's baseline b (one 16-byte gather per run record in the tiled binning).
+// Two baselines per thread and iteration, so that two loads per output are in
+// flight.
+template <int NO>
 __global__ void __launch_bounds__(kBlock) k_tl_pack(const double* __restrict__ x,
                                                     float* __restrict__ x32,
                                                     float4* __restrict__ x4, int64_t n_b, int n_o,
                                                     Gate g) {
   if (gate_closed(g)) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += stride) {
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
+  const int64_t half = (n_b + 1) >> 1;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < half; h += stride) {
+    const int64_t b0 = h, b1 = h + half;  // two coalesced streams
+    float v0[4] = {0.f, 0.f, 0.f, 0.f}, v1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int o = 0; o < 4; ++o)
+    for (int o = 0; o < NO; ++o)
       if (o < n_o) {
-        v[o] = (float)x[o * n_b + b];
-        x32[o * n_b + b] = v[o];
+        v0[o] = (float)x[o * n_b + b0];
+        if (b1 < n_b) v1[o] = (float)x[o * n_b + b1];
       }
-    if (x4 != nullptr) x4[b] = make_float4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (o < n_o) {
+        x32[o * n_b + b0] = v0[o];
+        if (b1 < n_b) x32[o * n_b + b1] = v1[o];
+      }
+    if constexpr (NO > 1) {
+      x4[b0] = make_float4(v0[0], v0[1], v0[2], v0[3]);
+      if (b1 < n_b) x4[b1] = make_float4(v1[0], v1[1], v1[2], v1[3]);
+    }
   }
 }
 
@@ -520,8 +534,11 @@ bool tl_ready(const Plan& P) {
 }
 
 void launch_pack_tl(const Plan& P, cudaStream_t st, const double* x, Gate g) {
-  k_tl_pack<<<stream_grid(P, P.n_b, kBlock, 8), kBlock, 0, st>>>(x, P.x32, P.tl_x4, P.n_b, P.n_o,
-                                                                  g);
+  const int grid = stream_grid(P, (P.n_b + 1) / 2, kBlock, 8);
+  with_kindset(P.kindset, [&](auto ksc) {
+    constexpr int NO = KSet<decltype(ksc)::value>::NO;
+    k_tl_pack<NO><<<grid, kBlock, 0, st>>>(x, P.x32, P.tl_x4, P.n_b, P.n_o, g);
+  });
 }
 
 void launch_bin_tl(const Plan& P, cudaStream_t st, Gate g) {
