@@ -153,20 +153,31 @@ __global__ void __launch_bounds__(kBlock) k_pc_rows(const int32_t* __restrict__ 
       sc[j] = sn[j] = 0.f;
     }
     const int64_t t1 = (b + 1) * L < n_t ? (b + 1) * L : n_t;
-    for (int64_t t = b * L; t < t1; ++t) {
-      const int p = pix[t];
-      if (p < 0) continue;
-      const int k = __ldg(cell_of + p);
-      const float c = cc[t], s = ss[t];
-      bool placed = false;
+    for (int64_t t = b * L; t < t1; t += 4) {
+      // four samples' loads and cell lookups in flight, then summed in order
+      int p[4], k[4];
+      float c[4], s[4];
 #pragma unroll
-      for (int j = 0; j < kCand; ++j) {
-        if (!placed && (id[j] == k || id[j] < 0)) {
-          id[j] = k;
-          cnt[j] += 1;
-          sc[j] += c;
-          sn[j] += s;
-          placed = true;
+      for (int u = 0; u < 4; ++u) p[u] = t + u < t1 ? pix[t + u] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        k[u] = p[u] >= 0 ? __ldg(cell_of + p[u]) : -1;
+        c[u] = p[u] >= 0 ? cc[t + u] : 0.f;
+        s[u] = p[u] >= 0 ? ss[t + u] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (p[u] < 0) continue;
+        bool placed = false;
+#pragma unroll
+        for (int j = 0; j < kCand; ++j) {
+          if (!placed && (id[j] == k[u] || id[j] < 0)) {
+            id[j] = k[u];
+            cnt[j] += 1;
+            sc[j] += c[u];
+            sn[j] += s[u];
+            placed = true;
+          }
         }
       }
     }
@@ -381,6 +392,40 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_diag(const float4* __restrict__
 // pixel's term into E.  The runs come from the pixel-major copy (k_pc_E_pix) or
 // from the long tiles of the tiled operator, where a pixel's runs of each tile are
 // contiguous (k_pc_E_tiles).
+// A warp's sum of pixel terms over the cells its recent pixels touched (shared
+// memory): neighbouring pixels mostly touch the same few cells, so their terms are
+// added here and reach E (float64 atomics, contended by every pixel of a cell) once
+// per change of cells instead of once per pixel.
+template <int NC>
+struct EBuf {
+  int id[kWarpCells];  // the buffer's cells
+  int n;               // cells in use
+  int full;            // the current pixel's cells do not fit: flush first
+  int map[kWarpCells]; // the current pixel's cells in the buffer
+  double v[kWarpCells * NC][kWarpCells * NC];
+
+  __device__ __forceinline__ void clear() {
+    const int lane = threadIdx.x & 31;
+    for (int q = lane; q < kWarpCells * NC * kWarpCells * NC; q += 32)
+      v[q / (kWarpCells * NC)][q % (kWarpCells * NC)] = 0.0;
+    if (lane == 0) n = 0;
+    __syncwarp();
+  }
+
+  __device__ __forceinline__ void flush(double* __restrict__ E, int nE) {
+    const int lane = threadIdx.x & 31;
+    const int m = n * NC;
+    for (int q = lane; q < m * m; q += 32) {
+      const int e1 = q / m, e2 = q - (q / m) * m;
+      const double x = v[e1][e2];
+      if (x != 0.0)
+        atomicAdd(E + (int64_t)(id[e1 / NC] * NC + e1 % NC) * nE + id[e2 / NC] * NC + e2 % NC, x);
+    }
+    __syncwarp();
+    clear();
+  }
+};
+
 template <int KS>
 struct PixTerm {
   static constexpr int NC = KSet<KS>::NC, NO = KSet<KS>::NO;
@@ -398,9 +443,17 @@ struct PixTerm {
     }
   }
 
-  // one run: n samples, sums C and S, baseline b
-  __device__ __forceinline__ void add_run(float n, float C, float S, int64_t b,
-                                          const float4* __restrict__ slot, const KindsArg& kk) {
+  template <int J>
+  __device__ __forceinline__ void update(const float (&kv)[NC], const float (&rv)[NC]) {
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) kr[J][a][c] = fma((double)kv[a], (double)rv[c], kr[J][a][c]);
+  }
+
+  // one run: n samples, sums C and S, the slots of its baseline
+  __device__ __forceinline__ void add_run(float n, float C, float S,
+                                          const float4 (&ms)[kPcSlots], const KindsArg& kk) {
     using K = KSet<KS>;
     const int n_o = K::n_o(kk);
 #pragma unroll
@@ -424,22 +477,29 @@ struct PixTerm {
       }
 #pragma unroll
       for (int s = 0; s < kPcSlots; ++s) {
-        const float4 m = __ldg(slot + b * kPcSlots + s);
+        const float4 m = ms[s];
         const int cell = __float_as_int(m.x);
         if (cell < 0) continue;
         float rv[NC];
         row_moments<NC>(K::kind(o, kk), m.y, m.z, m.w, rv);
-        bool placed = false;
+        // the candidate first, then one block of updates under a branch that is
+        // nearly always warp-uniform (a pixel's runs mostly fall in its first
+        // cell): GB300's float64 pipe is narrow, and predicated updates of every
+        // candidate cost it kCand times over
+        int jsel = -1;
 #pragma unroll
-        for (int j = 0; j < kCand; ++j) {
-          if (!placed && (id[j] == cell || id[j] < 0)) {
-            id[j] = cell;
+        for (int j = 0; j < kCand; ++j)
+          if (jsel < 0 && (id[j] == cell || id[j] < 0)) jsel = j;
 #pragma unroll
-            for (int a = 0; a < NC; ++a)
-#pragma unroll
-              for (int c = 0; c < NC; ++c) kr[j][a][c] = fma((double)kv[a], (double)rv[c], kr[j][a][c]);
-            placed = true;
-          }
+        for (int j = 0; j < kCand; ++j)
+          if (j == jsel) id[j] = cell;
+        static_assert(kCand == 4, "one case per candidate");
+        switch (jsel) {
+          case 0: update<0>(kv, rv); break;
+          case 1: update<1>(kv, rv); break;
+          case 2: update<2>(kv, rv); break;
+          case 3: update<3>(kv, rv); break;
+          default: break;
         }
       }
     }
@@ -448,7 +508,7 @@ struct PixTerm {
   // the warp's merged cells and E -= (K R)_p^T M_p^-1 (K R)_p
   __device__ __forceinline__ void finish(int64_t p, const double* __restrict__ minv, int n,
                                          double* __restrict__ E, int (&s_id)[kWarpCells],
-                                         double (&s_kr)[kWarpCells][NC][NC]) {
+                                         double (&s_kr)[kWarpCells][NC][NC], EBuf<NC>& buf) {
     constexpr int NM = NC * (NC + 1) / 2;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -496,6 +556,40 @@ struct PixTerm {
         mi[1][1] = mp[3]; mi[1][2] = mi[2][1] = mp[4]; mi[2][2] = mp[5];
       }
     }
+    // the pixel's cells in the warp's buffer: new ones appended while there is
+    // room, else the buffer goes to E and starts over with this pixel's cells
+    if (lane == 0) {
+      const int n0 = buf.n;
+      int nb = n0;
+      bool fits = true;
+      for (int t = 0; t < ncell; ++t) {
+        int idx = -1;
+        for (int u = 0; u < n0; ++u)  // the buffer's cells (the pixel's are distinct)
+          if (buf.id[u] == s_id[t]) idx = u;
+        if (idx < 0) {
+          if (nb < kWarpCells) idx = nb++;
+          else fits = false;
+        }
+        buf.map[t] = idx;
+      }
+      if (fits) {
+        for (int t = 0; t < ncell; ++t) buf.id[buf.map[t]] = s_id[t];
+        buf.n = nb;
+      }
+      buf.full = fits ? 0 : 1;
+    }
+    __syncwarp();
+    if (buf.full) {
+      buf.flush(E, n);
+      if (lane == 0) {
+        for (int t = 0; t < ncell; ++t) {
+          buf.id[t] = s_id[t];
+          buf.map[t] = t;
+        }
+        buf.n = ncell;
+      }
+      __syncwarp();
+    }
     const int m = ncell * NC;
     for (int q = lane; q < m * m; q += 32) {
       const int e1 = q / m, e2 = q - (q / m) * m;
@@ -506,8 +600,7 @@ struct PixTerm {
 #pragma unroll
         for (int a2 = 0; a2 < NC; ++a2)
           v += s_kr[t1][a][c1] * mi[a][a2] * s_kr[t2][a2][c2];
-      if (v != 0.0)
-        atomicAdd(E + (int64_t)(s_id[t1] * NC + c1) * n + s_id[t2] * NC + c2, -v);
+      buf.v[buf.map[t1] * NC + c1][buf.map[t2] * NC + c2] -= v;
     }
     __syncwarp();
   }
@@ -525,19 +618,37 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_pix(const uint32_t* __restrict_
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   __shared__ int s_id[kBlock / 32][kWarpCells];
   __shared__ double s_kr[kBlock / 32][kWarpCells][NC][NC];
+  __shared__ EBuf<NC> s_buf[kBlock / 32];
+  s_buf[wib].clear();
+  // each warp a contiguous range of pixels (neighbours share cells)
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; p < npix; p += warps) {
+  const int64_t per = (npix + warps - 1) / warps;
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int64_t p1 = (w + 1) * per < npix ? (w + 1) * per : npix;
+  for (int64_t p = w * per; p < p1; ++p) {
     if (!mask[p]) continue;  // warp-uniform
     const uint32_t beg = __ldg(off + p), end = __ldg(off + p + 1);
     if (beg == end) continue;
     PixTerm<KS> pt;
     pt.clear();
-    for (uint32_t i = beg + lane; i < end; i += 32) {
-      const float4 r = __ldg(rec + i);
-      pt.add_run(r.x, r.y, r.z, (int64_t)__float_as_int(r.w), slot, kk);
+    for (uint32_t i = beg + lane; i < end; i += 64) {
+      // two runs per lane: their records, then their slots, in flight together
+      const bool two = i + 32 < end;
+      const float4 r0 = __ldg(rec + i);
+      const float4 r1 = two ? __ldg(rec + i + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 m0[kPcSlots], m1[kPcSlots];
+#pragma unroll
+      for (int s = 0; s < kPcSlots; ++s) {
+        m0[s] = __ldg(slot + (int64_t)__float_as_int(r0.w) * kPcSlots + s);
+        m1[s] = two ? __ldg(slot + (int64_t)__float_as_int(r1.w) * kPcSlots + s)
+                    : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+      }
+      pt.add_run(r0.x, r0.y, r0.z, m0, kk);
+      if (two) pt.add_run(r1.x, r1.y, r1.z, m1, kk);
     }
-    pt.finish(p, minv, n, E, s_id[wib], s_kr[wib]);
+    pt.finish(p, minv, n, E, s_id[wib], s_kr[wib], s_buf[wib]);
   }
+  s_buf[wib].flush(E, n);
 }
 
 // The same over the long tiles: pixel rank r's runs of tile t are records
@@ -554,8 +665,14 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_tiles(const int4* __restrict__ 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   __shared__ int s_id[kBlock / 32][kWarpCells];
   __shared__ double s_kr[kBlock / 32][kWarpCells][NC][NC];
+  __shared__ EBuf<NC> s_buf[kBlock / 32];
+  s_buf[wib].clear();
+  // each warp a contiguous range of ranks (neighbours along the scan share cells)
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; r < nkeys; r += warps) {
+  const int64_t per = (nkeys + warps - 1) / warps;
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int64_t r1 = (w + 1) * per < nkeys ? (w + 1) * per : nkeys;
+  for (int64_t r = w * per; r < r1; ++r) {
     PixTerm<KS> pt;
     pt.clear();
     int p = -1;
@@ -564,14 +681,29 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_tiles(const int4* __restrict__ 
       const uint32_t b0 = k > 0 ? __ldg(end + k - 1) : 0u, b1 = __ldg(end + k);
       if (b0 == b1) continue;  // warp-uniform
       if (p < 0) p = __ldg(rec + b0).x;
-      for (uint32_t i = b0 + lane; i < b1; i += 32) {
-        const int4 v = __ldcs(rec + i);
-        pt.add_run((float)((unsigned)v.y >> 24), __int_as_float(v.z), __int_as_float(v.w),
-                   t * Tb + (int64_t)((unsigned)v.y & 0xFFFFFFu), slot, kk);
+      for (uint32_t i = b0 + lane; i < b1; i += 64) {
+        // two runs per lane: their records, then their slots, in flight together
+        const bool two = i + 32 < b1;
+        const int4 v0 = __ldcs(rec + i);
+        const int4 v1 = two ? __ldcs(rec + i + 32) : make_int4(0, 0, 0, 0);
+        const int64_t bb0 = t * Tb + (int64_t)((unsigned)v0.y & 0xFFFFFFu);
+        const int64_t bb1 = t * Tb + (int64_t)((unsigned)v1.y & 0xFFFFFFu);
+        float4 m0[kPcSlots], m1[kPcSlots];
+#pragma unroll
+        for (int s = 0; s < kPcSlots; ++s) {
+          m0[s] = __ldg(slot + bb0 * kPcSlots + s);
+          m1[s] = two ? __ldg(slot + bb1 * kPcSlots + s)
+                      : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+        }
+        pt.add_run((float)((unsigned)v0.y >> 24), __int_as_float(v0.z), __int_as_float(v0.w), m0, kk);
+        if (two)
+          pt.add_run((float)((unsigned)v1.y >> 24), __int_as_float(v1.z), __int_as_float(v1.w), m1,
+                     kk);
       }
     }
-    if (p >= 0) pt.finish(p, minv, n, E, s_id[wib], s_kr[wib]);
+    if (p >= 0) pt.finish(p, minv, n, E, s_id[wib], s_kr[wib], s_buf[wib]);
   }
+  s_buf[wib].flush(E, n);
 }
 
 // Rank-one term mu/m on every pair of the m I-component columns.

@@ -128,6 +128,14 @@ __global__ void __launch_bounds__(kBlock) k_tl_rank_write(const RunRec* __restri
   }
 }
 
+// seen[p] = 1 for the pixels some run visits (scanned into their numbering)
+__global__ void __launch_bounds__(kBlock) k_tl_seen(const uint32_t* __restrict__ first,
+                                                    int64_t npix, uint32_t* __restrict__ seen) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+       p += (int64_t)gridDim.x * blockDim.x)
+    seen[p] = first[p] != 0xFFFFFFFFu ? 1u : 0u;
+}
+
 // Sort key of run i within a batch of tiles [t0, ..): (tile - t0) x nkeys + the
 // pixel's rank (rank == nullptr: the pixel)
 __device__ __forceinline__ int64_t tl_key(const RunRec& r, int32_t b, const int32_t* rank,
@@ -225,8 +233,8 @@ __global__ void __launch_bounds__(kBlock) k_tl_scan_down(uint32_t* __restrict__ 
   }
 }
 
-// Each run of tiles [t0, t1) to its key's next slot (cursors relative to the
-// batch's first run), as a 16-byte record with the baseline relative to its tile.
+// Each run of tiles [t0, t1) to its key's next slot (absolute cursors), as a
+// 16-byte record with the baseline relative to its tile.
 __global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict__ rec,
                                                        const int32_t* __restrict__ rb,
                                                        const int32_t* __restrict__ rank,
@@ -240,7 +248,7 @@ __global__ void __launch_bounds__(kBlock) k_tl_scatter(const RunRec* __restrict_
     const RunRec r = rec[i];
     const int32_t b = rb[i];
     const unsigned bl = (unsigned)((int64_t)b % Tb);
-    const int64_t slot = r0 + atomicAdd(cursor + tl_key(r, b, rank, Tb, t0, nkeys), 1u);
+    const int64_t slot = atomicAdd(cursor + tl_key(r, b, rank, Tb, t0, nkeys), 1u);
     out[slot] = make_int4(r.pix, (int)(((unsigned)r.n << 24) | bl), __float_as_int(r.c),
                           __float_as_int(r.s));
   }
@@ -567,15 +575,17 @@ void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g) {
   });
 }
 
-// Sorts the time-ordered runs by pixel rank (first-visit order, nkeys ranks; or,
-// with rank == nullptr, by pixel over nkeys = n_pix) within tiles of Tb baselines
-// into *out_rec (16-byte records), with the tiles' first records in *out_off.  One
-// counting sort per batch of tiles over the keys (tile, rank): the batch's counts
-// fit kSortCounts entries and its runs 32-bit cursors.  One host synchronisation
-// for the tile offsets; the rest is stream-ordered on the plan's stream.
+// Sorts the time-ordered runs by a key per pixel (rank[p], nkeys keys; or, with
+// rank == nullptr, the pixel over nkeys = n_pix) within tiles of Tb baselines into
+// *out_rec (16-byte records), with the tiles' first records in *out_off.  One
+// counting sort per batch of tiles over the keys (tile, key).  One host
+// synchronisation for the tile offsets; the rest is stream-ordered on the plan's
+// stream.  keep_ends: every key's end (absolute) per tile, [n_tiles][nkeys].
 static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nkeys,
                            int4** out_rec, int64_t** out_off, uint32_t** keep_ends = nullptr) {
-  constexpr int64_t kSortCounts = int64_t(1) << 30;  // 4 GB of uint32 counts per batch
+  // counters per batch: kept within L2, where the histogram's and the scatter's
+  // atomic updates stay (a batch of a few tiles; at least one)
+  constexpr int64_t kSortCounts = int64_t(1) << 24;
   cudaStream_t st = P.stream;
   const int64_t n_tiles = (P.n_b + Tb - 1) / Tb;
   uint32_t* cnt = nullptr;
@@ -583,12 +593,14 @@ static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nke
   const int64_t per = kSortCounts / nkeys > 0 ? kSortCounts / nkeys : 1;  // tiles per batch
   const int64_t cap = (per < n_tiles ? per : n_tiles) * nkeys;
   const int64_t gmax = stream_grid(P, cap, kBlock, 8);
-  // one batch: after the scatter the cursors are the keys' ends, kept on request
-  const bool keep = keep_ends != nullptr && per >= n_tiles;
+  // kept ends: the counters of every batch side by side (after the scatter each
+  // cursor holds its key's end), 4 bytes per key and tile
+  const bool keep = keep_ends != nullptr;
+  const int64_t n_cnt = keep ? n_tiles * nkeys : cap;
   cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(out_rec), sizeof(int4) * P.rl_n, true);
   if (e == cudaSuccess)
     e = plan_alloc(P, reinterpret_cast<void**>(out_off), sizeof(int64_t) * (n_tiles + 1), true);
-  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * cap, keep);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&cnt), sizeof(uint32_t) * n_cnt, keep);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * gmax, false);
   std::vector<int64_t> off(n_tiles + 1);
   if (e == cudaSuccess) {
@@ -599,19 +611,20 @@ static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nke
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
   for (int64_t t0 = 0; t0 < n_tiles && e == cudaSuccess;) {
-    int64_t t1 = t0 + 1;  // the batch: at most `per` tiles and fewer than 2^32 runs
-    while (t1 < n_tiles && t1 - t0 < per && off[t1 + 1] - off[t0] < (int64_t)0xFFFFFFFF) ++t1;
+    const int64_t t1 = t0 + per < n_tiles ? t0 + per : n_tiles;
     const int64_t n = (t1 - t0) * nkeys;
     const int64_t g = stream_grid(P, n, kBlock, 8);
     const int64_t S = (n + g - 1) / g, G = (n + S - 1) / S;
-    const int rg = stream_grid(P, off[t1] - off[t0], kBlock, 8);
-    e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n, st);
+    const int rg = stream_grid(P, off[t1] - off[t0] > 0 ? off[t1] - off[t0] : 1, kBlock, 8);
+    uint32_t* c = keep ? cnt + t0 * nkeys : cnt;
+    e = cudaMemsetAsync(c, 0, sizeof(uint32_t) * n, st);
     if (e != cudaSuccess) break;
-    k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, rank, *out_off, t0, t1, Tb, nkeys, cnt);
-    k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(cnt, n, S, blk);
-    k_tl_scan_top<<<1, kScanTop, 0, st>>>(blk, G, nullptr, 0);
-    k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(cnt, n, S, blk);
-    k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, rank, *out_off, t0, t1, Tb, nkeys, cnt,
+    // positions are absolute (runs are fewer than 2^32)
+    k_tl_hist<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, rank, *out_off, t0, t1, Tb, nkeys, c);
+    k_tl_scan_up<<<(unsigned)G, kBlock, 0, st>>>(c, n, S, blk);
+    k_tl_scan_top<<<1, kScanTop, 0, st>>>(blk, G, *out_off, t0);
+    k_tl_scan_down<<<(unsigned)G, kBlock, 0, st>>>(c, n, S, blk);
+    k_tl_scatter<<<rg, kBlock, 0, st>>>(P.rl_rec, P.rl_b, rank, *out_off, t0, t1, Tb, nkeys, c,
                                         *out_rec);
     P.launches += 5;
     e = cudaGetLastError();
@@ -629,15 +642,22 @@ static cudaError_t tl_sort(Plan& P, int64_t Tb, const int32_t* rank, int64_t nke
 
 // rank[p] = first-visit order of the observed pixels (*nkeys of them); stream-
 // ordered, one host synchronisation for the count.
-static cudaError_t tl_rank(Plan& P, int32_t** rank, int64_t* nkeys) {
+// and cidx[p] = the number of observed pixels below p (the observed pixels
+// numbered in pixel order: keys of the rescan's tiles over observed pixels only)
+static cudaError_t tl_rank(Plan& P, int32_t** rank, int32_t** cidx, int64_t* nkeys) {
   cudaStream_t st = P.stream;
   const int64_t g = stream_grid(P, P.rl_n, kBlock, 8);
   const int64_t S = (P.rl_n + g - 1) / g, G = (P.rl_n + S - 1) / S;
+  const int64_t gp = stream_grid(P, P.npix, kBlock, 8);
+  const int64_t Sp = (P.npix + gp - 1) / gp, Gp = (P.npix + Sp - 1) / Sp;
   uint32_t* first = nullptr;
   int64_t* blk = nullptr;
+  int64_t* blkp = nullptr;
   cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(&first), sizeof(uint32_t) * P.npix, false);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(rank), sizeof(int32_t) * P.npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(cidx), sizeof(int32_t) * P.npix, false);
   if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blk), sizeof(int64_t) * (G + 1), false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&blkp), sizeof(int64_t) * Gp, false);
   if (e == cudaSuccess) e = cudaMemsetAsync(first, 0xFF, sizeof(uint32_t) * P.npix, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(blk + G, 0, sizeof(int64_t), st);
   int64_t h_total = 0;
@@ -646,13 +666,18 @@ static cudaError_t tl_rank(Plan& P, int32_t** rank, int64_t* nkeys) {
     k_tl_rank_count<<<(unsigned)G, kBlock, 0, st>>>(P.rl_rec, P.rl_n, first, S, blk);
     k_tl_scan_top<<<1, kScanTop, 0, st>>>(blk, G + 1, nullptr, 0);  // blk[G] = the total
     k_tl_rank_write<<<(unsigned)G, kBlock, 0, st>>>(P.rl_rec, P.rl_n, first, S, blk, *rank);
-    P.launches += 4;
+    uint32_t* seen = reinterpret_cast<uint32_t*>(*cidx);
+    k_tl_seen<<<(unsigned)gp, kBlock, 0, st>>>(first, P.npix, seen);
+    k_tl_scan_up<<<(unsigned)Gp, kBlock, 0, st>>>(seen, P.npix, Sp, blkp);
+    k_tl_scan_top<<<1, kScanTop, 0, st>>>(blkp, Gp, nullptr, 0);
+    k_tl_scan_down<<<(unsigned)Gp, kBlock, 0, st>>>(seen, P.npix, Sp, blkp);
+    P.launches += 8;
     e = cudaGetLastError();
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(&h_total, blk + G, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
-  for (void* t : {(void*)first, (void*)blk})
+  for (void* t : {(void*)first, (void*)blk, (void*)blkp})
     if (t) cudaFreeAsync(t, st);
   *nkeys = h_total;
   return e;
@@ -690,11 +715,12 @@ ds_status tl_build(Plan& P) {
   if (Tb2 > P.n_b) Tb2 = P.n_b;
   const int64_t n_tiles = (P.n_b + Tb - 1) / Tb, n_tiles2 = (P.n_b + Tb2 - 1) / Tb2;
   int* longest = nullptr;
-  int32_t* rank = nullptr;
+  int32_t *rank = nullptr, *cidx = nullptr;
   const int64_t held_before = P.device_bytes;
   auto release = [&](cudaError_t e) {
     if (longest) cudaFreeAsync(longest, st);
     if (rank) cudaFreeAsync(rank, st);
+    if (cidx) cudaFreeAsync(cidx, st);
     tl_free(P);
     P.device_bytes = held_before;
     return e == cudaErrorMemoryAllocation ? DS_ENOMEM : DS_ECUDA;
@@ -715,11 +741,16 @@ ds_status tl_build(Plan& P) {
   }
   if (tl_packs(P)) e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_x4), sizeof(float4) * P.n_b, true);
   int64_t nkeys = 0;
-  if (e == cudaSuccess) e = tl_rank(P, &rank, &nkeys);
+  if (e == cudaSuccess) e = tl_rank(P, &rank, &cidx, &nkeys);
   if (e == cudaSuccess && nkeys <= 0) e = cudaErrorInvalidValue;
-  // the rescan's tiles in pixel order: the runs of neighbouring pixels along the
-  // scan share baselines, and would collide on the tile's shared baseline sums
-  if (e == cudaSuccess) e = tl_sort(P, Tb, nullptr, P.npix, &P.tl_rec, &P.tl_off);
+  // the rescan's tiles in pixel order (keys: the observed pixels numbered in pixel
+  // order): the runs of neighbouring pixels along the scan share baselines, and
+  // would collide on the tile's shared baseline sums
+  if (e == cudaSuccess) e = tl_sort(P, Tb, cidx, nkeys, &P.tl_rec, &P.tl_off);
+  if (e == cudaSuccess) {
+    cudaFreeAsync(cidx, st);
+    cidx = nullptr;
+  }
   if (e != cudaSuccess) return release(e);
   // the long tiles and their chunk table (tile t's chunks start at chunk_first[t])
   e = tl_sort(P, Tb2, rank, nkeys, &P.tl2_rec, &P.tl2_off, &P.tl2_end);

@@ -188,3 +188,64 @@ def test_segmented_sum_reaches_each_segment_head(seed):
             e += 1
         assert abs(got[l] - vals[l:e + 1].sum()) < 1e-12
         l = e + 1
+
+
+def warp_buffered_terms(pixels, nE, nc, max_cells=8):
+    """Host restatement of the coarse matrix's per-warp buffer (k_pc_E_*): each
+    pixel's term over its cells is added into a buffer over at most max_cells
+    cells; new cells are appended while there is room, else the buffer is added
+    into E and restarts with the pixel's cells.  pixels: [(cells, term)] with
+    term an (len(cells) nc) x (len(cells) nc) block."""
+    E = np.zeros((nE, nE))
+    ids, buf = [], np.zeros((max_cells * nc, max_cells * nc))
+    stale = list(range(1000, 1000 + max_cells))  # ids of slots not in use
+
+    def flush():
+        m = len(ids) * nc
+        for e1 in range(m):
+            for e2 in range(m):
+                E[ids[e1 // nc] * nc + e1 % nc, ids[e2 // nc] * nc + e2 % nc] += buf[e1, e2]
+        buf[:] = 0.0
+
+    for cells, term in pixels:
+        slots, n0, nb = [], len(ids), len(ids)
+        for c in cells:  # search the buffer's cells only, never the stale slots
+            idx = ids.index(c) if c in ids[:n0] else -1
+            if idx < 0:
+                idx = nb if nb < max_cells else -1
+                nb += 1
+            slots.append(idx)
+        if nb > max_cells:
+            flush()
+            ids, slots = list(cells), list(range(len(cells)))
+        else:
+            for c, s in zip(cells, slots):
+                if s >= len(ids):
+                    ids.append(c)
+        for i, s1 in enumerate(slots):
+            for j, s2 in enumerate(slots):
+                buf[s1 * nc:(s1 + 1) * nc, s2 * nc:(s2 + 1) * nc] += term[i * nc:(i + 1) * nc,
+                                                                           j * nc:(j + 1) * nc]
+    flush()
+    return E
+
+
+def test_warp_buffer_of_pixel_terms_equals_direct_sum():
+    rng = np.random.default_rng(7)
+    ncell, nc = 40, 3
+    pixels, cur = [], [0]
+    for _ in range(2000):  # neighbouring pixels mostly share cells
+        if rng.random() < 0.3:
+            cur = sorted(set(int(c) for c in rng.integers(0, ncell, size=rng.integers(1, 5))))
+        cells = list(cur)
+        rng.shuffle(cells)
+        k = len(cells) * nc
+        pixels.append((cells, rng.standard_normal((k, k))))
+    direct = np.zeros((ncell * nc, ncell * nc))
+    for cells, term in pixels:
+        for i, c1 in enumerate(cells):
+            for j, c2 in enumerate(cells):
+                direct[c1 * nc:(c1 + 1) * nc, c2 * nc:(c2 + 1) * nc] += term[i * nc:(i + 1) * nc,
+                                                                           j * nc:(j + 1) * nc]
+    got = warp_buffered_terms(pixels, ncell * nc, nc)
+    assert np.allclose(got, direct, rtol=0, atol=1e-9)
