@@ -35,6 +35,7 @@
 #include <cstring>
 #include <vector>
 
+#include "df.cuh"
 #include "internal.cuh"
 #include "rows.cuh"
 
@@ -443,12 +444,17 @@ struct PixTerm {
     }
   }
 
+  // float32 operands widened by bit re-encoding (f64_of_f32: integer pipes), so
+  // that GB300's narrow float64 pipe does only the multiply-adds
   template <int J>
-  __device__ __forceinline__ void update(const float (&kv)[NC], const float (&rv)[NC]) {
+  __device__ __forceinline__ void update(const double (&kv)[NC], const float (&rv)[NC]) {
+    double r[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) r[c] = f64_of_f32(rv[c]);
 #pragma unroll
     for (int a = 0; a < NC; ++a)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) kr[J][a][c] = fma((double)kv[a], (double)rv[c], kr[J][a][c]);
+      for (int c = 0; c < NC; ++c) kr[J][a][c] = fma(kv[a], r[c], kr[J][a][c]);
   }
 
   // one run: n samples, sums C and S, the slots of its baseline
@@ -475,6 +481,9 @@ struct PixTerm {
           if constexpr (F::I >= 0 && F::Q >= 0) { kv[F::I] = n; kv[F::Q] = C; kv[F::U] = S; }
         }
       }
+      double dkv[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) dkv[c] = f64_of_f32(kv[c]);
 #pragma unroll
       for (int s = 0; s < kPcSlots; ++s) {
         const float4 m = ms[s];
@@ -495,10 +504,10 @@ struct PixTerm {
           if (j == jsel) id[j] = cell;
         static_assert(kCand == 4, "one case per candidate");
         switch (jsel) {
-          case 0: update<0>(kv, rv); break;
-          case 1: update<1>(kv, rv); break;
-          case 2: update<2>(kv, rv); break;
-          case 3: update<3>(kv, rv); break;
+          case 0: update<0>(dkv, rv); break;
+          case 1: update<1>(dkv, rv); break;
+          case 2: update<2>(dkv, rv); break;
+          case 3: update<3>(dkv, rv); break;
           default: break;
         }
       }
@@ -672,33 +681,51 @@ __global__ void __launch_bounds__(kBlock) k_pc_E_tiles(const int4* __restrict__ 
   const int64_t per = (nkeys + warps - 1) / warps;
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t r1 = (w + 1) * per < nkeys ? (w + 1) * per : nkeys;
+  const unsigned full = 0xffffffffu;
   for (int64_t r = w * per; r < r1; ++r) {
     PixTerm<KS> pt;
     pt.clear();
     int p = -1;
-    for (int64_t t = 0; t < n_tiles; ++t) {
-      const int64_t k = t * nkeys + r;
-      const uint32_t b0 = k > 0 ? __ldg(end + k - 1) : 0u, b1 = __ldg(end + k);
-      if (b0 == b1) continue;  // warp-uniform
-      if (p < 0) p = __ldg(rec + b0).x;
-      for (uint32_t i = b0 + lane; i < b1; i += 64) {
-        // two runs per lane: their records, then their slots, in flight together
-        const bool two = i + 32 < b1;
-        const int4 v0 = __ldcs(rec + i);
-        const int4 v1 = two ? __ldcs(rec + i + 32) : make_int4(0, 0, 0, 0);
-        const int64_t bb0 = t * Tb + (int64_t)((unsigned)v0.y & 0xFFFFFFu);
-        const int64_t bb1 = t * Tb + (int64_t)((unsigned)v1.y & 0xFFFFFFu);
-        float4 m0[kPcSlots], m1[kPcSlots];
+    // the rank's runs of 32 tiles at a time, numbered through so that every lane
+    // has one (a pixel holds a dozen or two runs per tile)
+    for (int64_t tg = 0; tg < n_tiles; tg += 32) {
+      const int64_t t = tg + lane;
+      uint32_t b0 = 0, len = 0;
+      if (t < n_tiles) {
+        const int64_t k = t * nkeys + r;
+        b0 = k > 0 ? __ldg(end + k - 1) : 0u;
+        len = __ldg(end + k) - b0;
+      }
+      uint32_t pre = len;  // inclusive prefix over the lanes' tiles
 #pragma unroll
-        for (int s = 0; s < kPcSlots; ++s) {
-          m0[s] = __ldg(slot + bb0 * kPcSlots + s);
-          m1[s] = two ? __ldg(slot + bb1 * kPcSlots + s)
-                      : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(full, pre, d);
+        if (lane >= d) pre += u;
+      }
+      const uint32_t total = __shfl_sync(full, pre, 31);
+      pre -= len;  // exclusive
+      if (p < 0 && total > 0) {  // the pixel, from the first record of the group
+        const unsigned nz = __ballot_sync(full, len > 0);
+        const uint32_t bf = __shfl_sync(full, b0, __ffs(nz) - 1);
+        p = __ldg(rec + bf).x;
+      }
+      for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t f = base + lane;
+        // the lane whose tile holds run f: the last with pre <= f
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t pc = __shfl_sync(full, pre, lo + step);
+          if (lo + step < 32 && pc <= f) lo += step;
         }
-        pt.add_run((float)((unsigned)v0.y >> 24), __int_as_float(v0.z), __int_as_float(v0.w), m0, kk);
-        if (two)
-          pt.add_run((float)((unsigned)v1.y >> 24), __int_as_float(v1.z), __int_as_float(v1.w), m1,
-                     kk);
+        const uint32_t b0l = __shfl_sync(full, b0, lo), prel = __shfl_sync(full, pre, lo);
+        if (f >= total) continue;
+        const int4 v = __ldcs(rec + b0l + (f - prel));
+        const int64_t bb = (tg + lo) * Tb + (int64_t)((unsigned)v.y & 0xFFFFFFu);
+        float4 m[kPcSlots];
+#pragma unroll
+        for (int s = 0; s < kPcSlots; ++s) m[s] = __ldg(slot + bb * kPcSlots + s);
+        pt.add_run((float)((unsigned)v.y >> 24), __int_as_float(v.z), __int_as_float(v.w), m, kk);
       }
     }
     if (p >= 0) pt.finish(p, minv, n, E, s_id[wib], s_kr[wib], s_buf[wib]);
