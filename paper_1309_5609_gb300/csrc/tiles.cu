@@ -3,24 +3,26 @@
 // the time-ordered samples nor the pixel-major copy pays.
 //
 // The runs of consecutive samples on one pixel within a baseline (runs_build.cu)
-// are cut into tiles of consecutive baselines, and within each tile sorted by
-// pixel (one counting sort per tile at plan time).  A record is 16 bytes:
+// are cut into tiles of consecutive baselines, and within each tile sorted by a
+// key per pixel (counting sorts over batches of tiles at plan time).  A record is
+// 16 bytes:
 //     (pixel, n << 24 | baseline - first baseline of the tile, sum cos 2psi, sum sin 2psi)
 // with n <= 255 samples (plans with longer runs keep the other forms).  Two
 // copies are kept, sorted within tiles of two lengths (Sect. 3 operator, exact
 // reformulation: only the float32 rounding order changes):
-//  * binning (P~^T R^T F~ x) reads long tiles (about two weeks of data): a pixel
-//    is revisited every sidereal day, so its runs of a tile are many and
-//    contiguous.  Each lane sums consecutive records of one pixel in registers,
-//    gathering each run's baselines as one 16-byte vector (all outputs packed per
-//    baseline), and about one vector reduction per pixel and tile reaches L2,
-//    instead of one per run as in time order;
+//  * binning (P~^T R^T F~ x) reads long tiles (about two weeks of data), pixels in
+//    the order of their first visit: a pixel is revisited every sidereal day, so
+//    its runs of a tile are many and contiguous, and its neighbours along the scan
+//    follow it, their runs sharing baselines.  Each lane sums consecutive records
+//    of one pixel in registers, gathering each run's baselines (one float32, or a
+//    16-byte vector of all outputs), and about one vector reduction per pixel and
+//    tile reaches L2, instead of one per run as in time order;
 //  * rescan and per-baseline sums (F~^T (z - R P~ m)) read short tiles (a few
-//    hours): each block keeps its tile's map-term sums per baseline in shared
-//    memory (float32 atomics; the runs of one pixel lie in different baselines, so
-//    lanes rarely collide), gathers the map row of each run, and stores each
-//    baseline's valid samples times its baseline minus that sum once (each
-//    baseline belongs to one tile: no atomics in global memory).
+//    hours), pixels in pixel order: each block keeps its tile's map-term sums per
+//    baseline in shared memory (float32 atomics; the runs of one pixel lie in
+//    different baselines, so lanes rarely collide), gathers the map row of each
+//    run, and stores each baseline's valid samples times its baseline minus that
+//    sum once (each baseline belongs to one tile: no atomics in global memory).
 #include <vector>
 
 #include "internal.cuh"
