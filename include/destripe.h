@@ -354,8 +354,8 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     plan at its first solve (from the pixel-major run records, made
  *                     for the purpose when the plan has none; synchronises).  Where
  *                     baselines sweep more than two cells for over a fifth of the valid
- *                     samples (long baselines) the coarse space is not built and D^-1
- *                     alone applies.  A solve that breaks down or stalls with the
+ *                     samples (long baselines) the coarse space is not built and the
+ *                     plan iterates plain CG (D^-1 alone is nearly a scalar there).  A solve that breaks down or stalls with the
  *                     coarse correction (a nearly singular system whose slow modes
  *                     the iteration's arithmetic cannot resolve) continues from its
  *                     best iterate with D^-1 alone, which the plan keeps afterwards.

@@ -506,7 +506,7 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
     if (s != DS_OK) return s;
   }
   enqueue_cg_setup(P, st, tol, max_iter, P.reliable_delta, warm_start ? 1 : 0, true);
-  P.launches += 3 + 3 + (warm_start ? 3 : 0) + (P.precond ? 3 : 0);
+  P.launches += 3 + 3 + (warm_start ? 3 : 0) + (pc_mode(P) ? 3 : 0);
   s = launch_status();
   if (s != DS_OK) return s;
   s = build_graph(P);

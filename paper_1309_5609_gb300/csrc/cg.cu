@@ -629,7 +629,7 @@ bool pc_restrict_fits(const Plan& P, int n) {
 
 // accurate: the iteration applies the operator in the accurate arithmetic
 int kernels_per_iteration(const Plan& P, bool accurate) {
-  const int pc = P.precond ? (pc_ready(P) ? 2 : 1) : 0;  // extra kernels of the direction
+  const int pc = pc_mode(P);  // extra kernels of the direction
   if (P.desc.precision != DS_PREC_MIXED) return 6 + pc;
   const bool df = P.accurate_df && P.maplo != nullptr;  // + the baseline split kernel
   const bool f32 = P.x32 != nullptr && !accurate && P.layout != 1;
@@ -661,7 +661,7 @@ void enqueue_iteration(const Plan& P, cudaStream_t st, cudaEvent_t* ev, bool acc
     k_cg_reliable<<<vg, kBlock, 0, st>>>(P.r, P.b, P.t, P.n_u, P.red, P.counters, P.state);
     k_cg_keep_best<<<vg, kBlock, 0, st>>>(P.x, P.x_best, P.n_u, P.state);
   }
-  if (P.precond)
+  if (pc_mode(P))
     enqueue_precond_direction(P, st);
   else
     k_cg_direction<<<vg, kBlock, 0, st>>>(P.p, P.r, P.q, P.n_u, P.state);
@@ -675,14 +675,14 @@ void enqueue_cg_setup(const Plan& P, cudaStream_t st, double tol, int max_iter, 
   enqueue_dot(P, st, P.b, P.b, P.n_u, &P.state->bb);
   k_set_state<<<1, 1, 0, st>>>(P.state, tol, max_iter, mixed ? 1 : 0, delta, P.refresh_max,
                                P.drift_ratio, P.accurate_start, P.stall_iters,
-                               precond && P.precond ? 1 : 0);
+                               precond && pc_mode(P) ? 1 : 0);
   if (warm) {
     cudaMemsetAsync(P.t, 0, sizeof(double) * P.n_u, st);
     enqueue_apply(P, st, true, P.x, P.t, Gate{nullptr, nullptr});
   }
   k_cg_start<<<vec_grid(P, P.n_u), kBlock, 0, st>>>(P.x, P.r, P.p, P.q, P.b, P.t, warm, P.n_u,
                                                      P.red, P.counters, P.state, P.x_best);
-  if (precond && P.precond) enqueue_precond_direction(P, st);  // the first direction z_0
+  if (precond && pc_mode(P)) enqueue_precond_direction(P, st);  // the first direction z_0
 }
 
 }  // namespace ds

@@ -358,6 +358,7 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm);
 // and their pixel-major copy when the plan's operator does not keep them
 ds_status pc_prepare(Plan& P);
 bool pc_restrict_fits(const Plan& P, int n);
+int pc_mode(const Plan& P);
 void pc_free(Plan& P, cudaStream_t st);
 bool pc_ready(const Plan& P);
 // cg.cu: the preconditioner's kernels of one CG step (restrict, coarse solve,

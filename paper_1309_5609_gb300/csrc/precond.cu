@@ -812,6 +812,17 @@ bool pc_ready(const Plan& P) {
   return P.precond == 2 && P.pc_built && P.pc_n > 0 && !P.pc_fallback;
 }
 
+// The preconditioner the iteration applies: 0 none, 1 D^-1, 2 two-level.  A
+// two-level plan whose coarse space was not built (it would not span the slow
+// modes, or has no room) iterates plain CG: D^-1 alone is nearly a scalar where
+// baselines hold equal counts, and costs a kernel per iteration; after a breakdown
+// with the coarse correction it keeps D^-1.
+int pc_mode(const Plan& P) {
+  if (P.precond != 2) return P.precond;
+  if (pc_ready(P)) return 2;
+  return P.pc_built && !P.pc_fallback ? 0 : 1;
+}
+
 // Builds the coarse space and E^+ on the plan's stream (synchronises it).  The
 // second term of E reads the pixel-major copy of the run records; a plan whose
 // operator does not keep one gets it for the purpose (made_runs / made_pm) and
