@@ -105,7 +105,7 @@ typedef struct {
   int32_t layout;        /* form of the float32 operator in use (tune key "layout") */
   int32_t bin_order;     /* run-length operator: 1 = binning over the pixel-major copy
                             (built by the first solve or operator application) */
-  int64_t n_runs;        /* run-length records held (0 if none) */
+  int64_t n_runs;        /* run-length records held, time-ordered or tiled (0 if none) */
 } ds_info;
 
 /* Build a plan: hits, per-pixel normal matrices M_p, their inverses and the

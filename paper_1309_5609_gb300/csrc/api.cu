@@ -49,9 +49,9 @@ namespace {
 
 // Plan memory comes from one stream-ordered pool per device, owned by the library:
 // freeing a plan needs no device-wide synchronisation (cudaFree has one), and a
-// plan built after another reuses its memory without a trip to the driver.  Up
-// to kPoolKeep bytes of freed memory stay in the pool.
-constexpr uint64_t kPoolKeep = uint64_t(8) << 30;
+// plan built after another reuses its memory without a trip to the driver (mapping
+// a tiled plan's 80 GB anew costs about 0.1 s).  Up to half of the device's memory
+// of freed plan memory stays in the pool.
 constexpr int kMaxDevices = 64;
 std::mutex g_pool_mutex;
 cudaMemPool_t g_pools[kMaxDevices] = {};
@@ -67,7 +67,12 @@ cudaError_t plan_pool(int device, cudaMemPool_t* out) {
     cudaMemPool_t pool = nullptr;
     cudaError_t e = cudaMemPoolCreate(&pool, &props);
     if (e != cudaSuccess) return e;
-    uint64_t keep = kPoolKeep;
+    size_t free_b = 0, total_b = 0;
+    int cur = 0;
+    uint64_t keep = uint64_t(8) << 30;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur == device &&
+        cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+      keep = (uint64_t)total_b / 2;
     e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     if (e != cudaSuccess) {
       cudaMemPoolDestroy(pool);
@@ -410,7 +415,7 @@ ds_status destripe_plan_info(ds_plan_t plan, ds_info* info) {
   info->device_bytes = P.device_bytes;
   info->layout = P.layout;
   info->bin_order = (P.layout == 2 && P.bin_order == 1 && P.rl_rec != nullptr) ? 1 : 0;
-  info->n_runs = P.rl_rec != nullptr ? P.rl_n : 0;
+  info->n_runs = P.rl_rec != nullptr ? P.rl_n : (P.tl_rec != nullptr ? P.tl_runs : 0);
   return DS_OK;
 }
 
@@ -637,6 +642,10 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
       const ds_status s = chunk_index(P, ck_default_chunk(P.n_t, P.num_sms));
       if (s != DS_OK) return s;
     }
+    if (value == 2.0 && P.rl_rec != nullptr && P.rl_df == nullptr) {
+      cudaStreamSynchronize(P.stream);
+      rl_release(P, P.stream);  // runs kept for tiles lack the accurate passes' sums
+    }
     if (value == 2.0 && P.rl_rec == nullptr) {
       clear_stale_error();
       const ds_status s = rl_build(P);
@@ -777,6 +786,14 @@ ds_status destripe_run_host(const ds_desc* desc, const int32_t* h_pix, const flo
   if (e == cudaSuccess) e = cudaEventRecord(ev_y, st_y);
   if (e != cudaSuccess) s = (e == cudaErrorMemoryAllocation) ? DS_ENOMEM : DS_ECUDA;
   if (s == DS_OK) s = destripe_plan(desc, d_pix, d_c, d_s, d_valid, &plan);
+  // the work of the first solve that reads only the pointing (the tiled records, a
+  // coarse space that needs no pixel-major copy) also runs while the timelines travel
+  if (s == DS_OK) {
+    Plan& P = *reinterpret_cast<Plan*>(plan);
+    s = tl_ensure(P);
+    if (s == DS_OK && P.precond == 2 && !P.pc_built && P.layout == 3 && P.tl2_end != nullptr)
+      s = pc_prepare(P);
+  }
   if (ev_y != nullptr && cudaStreamWaitEvent(st, ev_y, 0) != cudaSuccess && s == DS_OK) s = DS_ECUDA;
   ds_status solve_s = DS_OK;
   if (s == DS_OK) {

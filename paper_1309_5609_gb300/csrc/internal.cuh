@@ -228,6 +228,7 @@ struct Plan {
   int64_t tl2_nkeys;        // pixel ranks (observed pixels)
   int64_t tl_bin_samples;   // samples per long tile (tune key "bin_tile_samples")
   int tl_pending;           // layout 3 chosen by the plan, records not built yet (tl_ensure)
+  int64_t tl_runs;          // records of each tiled copy
   float4* tl_x4;            // [n_b] float32 baselines of every output, per baseline
   int rescan_samples;       // run-length plans: the rescans read the time-ordered samples (dense
                             // runs: a record per run costs more than 12 bytes per sample)
@@ -263,8 +264,10 @@ cudaError_t plan_alloc_on(Plan& P, cudaStream_t st, void** ptr, size_t bytes, bo
 
 // runs.cu
 ds_status rl_count(Plan& P, int64_t* d_total);
-ds_status rl_fill(Plan& P, int64_t n_runs);
-ds_status rl_build(Plan& P);
+// with_df: also the double-float run sums of the accurate run passes and the
+// pixel-major copy (the tiled records do without them)
+ds_status rl_fill(Plan& P, int64_t n_runs, bool with_df = true);
+ds_status rl_build(Plan& P, bool with_df = true);
 ds_status pm_build(Plan& P, cudaStream_t st);
 // builds the pixel-major copy on the plan's stream before its first use if the
 // plan bins from it

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kBlock) k_rl_fill(const int32_t* __restrict__ 
       if (member && !cont) {
         rec[r] = RunRec{p, n, C.hi, S.hi};
         rb[r] = (int32_t)bl;
-        rdf[r] = make_float4(C.hi, C.lo, S.hi, S.lo);
+        if (rdf != nullptr) rdf[r] = make_float4(C.hi, C.lo, S.hi, S.lo);
       }
       // carry lane 31's open run into the next round
       const bool carry = __shfl_sync(full, member && cont, 31);
@@ -376,7 +376,7 @@ ds_status rl_count(Plan& P, int64_t* d_total) {
   return DS_OK;
 }
 
-ds_status rl_fill(Plan& P, int64_t n_runs) {
+ds_status rl_fill(Plan& P, int64_t n_runs, bool with_df) {
   const int64_t n_sub = (P.n_t + kSub - 1) / kSub;
   P.rl_n = n_runs;
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_rec),
@@ -384,8 +384,9 @@ ds_status rl_fill(Plan& P, int64_t n_runs) {
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_b),
                          sizeof(int32_t) * (n_runs > 0 ? n_runs : 1), true));
   const int grid = stream_grid(P, n_sub * 32, kBlock, 8);
-  DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_df),
-                         sizeof(float4) * (n_runs > 0 ? n_runs : 1), true));
+  if (with_df)
+    DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&P.rl_df),
+                           sizeof(float4) * (n_runs > 0 ? n_runs : 1), true));
   int64_t S, G;
   count_split(P, n_sub, S, G);
   k_rl_fill<<<grid, kBlock, 0, P.stream>>>(P.pix, P.c, P.s, P.n_t, P.L, n_sub, S, P.rl_tiles,
@@ -404,7 +405,10 @@ ds_status rl_fill(Plan& P, int64_t n_runs) {
 // problems bin with their own kernels and never need it).
 ds_status pm_build(Plan& P, cudaStream_t st) {
   // run offsets are 32-bit, with room for the binning loop's stride past the end
-  if (P.rl_rec == nullptr || P.rl_n <= 0 || P.rl_n > (int64_t)UINT32_MAX - 256) return DS_OK;
+  // (and the runs' double-float sums, whose low parts it keeps)
+  if (P.rl_rec == nullptr || P.rl_df == nullptr || P.rl_n <= 0 ||
+      P.rl_n > (int64_t)UINT32_MAX - 256)
+    return DS_OK;
   const int64_t npix = P.npix;
   const int64_t g = stream_grid(P, npix, kBlock, 8);
   const int64_t S = (npix + g - 1) / g, G = (npix + S - 1) / S;
@@ -530,7 +534,7 @@ void rl_release(Plan& P, cudaStream_t st) {
   P.rl_n = 0;
 }
 
-ds_status rl_build(Plan& P) {
+ds_status rl_build(Plan& P, bool with_df) {
   int64_t* total = nullptr;
   DS_CUDA_TRY(plan_alloc(P, reinterpret_cast<void**>(&total), sizeof(int64_t), false));
   ds_status s = rl_count(P, total);
@@ -540,7 +544,7 @@ ds_status rl_build(Plan& P) {
     s = DS_ECUDA;
   if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
   cudaFreeAsync(total, P.stream);
-  if (s == DS_OK) s = rl_fill(P, n_runs);
+  if (s == DS_OK) s = rl_fill(P, n_runs, with_df);
   if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
   return s;
 }

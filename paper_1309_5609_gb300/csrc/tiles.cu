@@ -778,6 +778,7 @@ ds_status tl_build(Plan& P) {
   if (e != cudaSuccess) return release(e);
   P.tl2_tiles = n_tiles2;
   P.tl2_tb = Tb2;
+  P.tl_runs = P.rl_n;
   P.tl2_chunks = first[n_tiles2];
   P.tl_tiles = n_tiles;
   P.tl_tb = Tb;
@@ -810,7 +811,8 @@ ds_status tl_build(Plan& P) {
 ds_status tl_ensure(Plan& P) {
   if (!P.tl_pending) return DS_OK;
   P.tl_pending = 0;
-  ds_status s = P.rl_rec == nullptr ? rl_build(P) : DS_OK;
+  const bool made = P.rl_rec == nullptr;
+  ds_status s = made ? rl_build(P, false) : DS_OK;
   if (s == DS_OK) s = tl_build(P);
   if (s == DS_OK && cudaStreamSynchronize(P.stream) != cudaSuccess) s = DS_ECUDA;
   if (s == DS_ESTATE || s == DS_ENOMEM) {
@@ -819,6 +821,9 @@ ds_status tl_ensure(Plan& P) {
     P.layout = 0;
     return DS_OK;
   }
+  // the tiled records hold everything the passes read: the runs they came from go
+  // (a later switch to the run-length layout builds them again)
+  if (s == DS_OK && made) rl_release(P, P.stream);
   return s;
 }
 
