@@ -302,7 +302,9 @@ ds_status destripe_profile(ds_plan_t plan, int32_t enable, ds_profile* out);
  *                     system has reached its floor (default 2000; 0 = never)
  *   "bin_mode"        MIXED plans: 1 = float32 pixel sums with one vector atomic per run
  *                     (default), 0 = float64 pixel sums with scalar atomics
- *   "graph_iters"     1..64 CG iterations per captured graph replay (default 16)
+ *   "graph_iters"     1..64 CG iterations per captured graph replay; 0 (default) = 16,
+ *                     halved down to 4 while a replay would hold more than about 4 ms
+ *                     of work (estimated at 2 ns per sample and output)
  *   "accurate_df"     MIXED plans: 1 = the accurate passes (right-hand side, maps,
  *                     float64 residual refreshes) use double-float operands and
  *                     compensated float32 sums on the float32 pipes with float64

@@ -176,8 +176,21 @@ ds_status capture_iterations(Plan& P, bool accurate, cudaEvent_t* ev, cudaGraphE
   return DS_OK;
 }
 
+// CG iterations per graph replay: 16, halved (down to 4) while a replay would hold
+// more than about 4 ms of work, estimated at 2 ns per sample and output.  Long
+// replays hide the host's wait between them; short ones instantiate faster and
+// run fewer gated iterations after convergence.
+int graph_iters_for(const Plan& P) {
+  if (P.graph_iters_cfg > 0) return P.graph_iters_cfg;
+  const double est_ms = 2e-9 * (double)P.n_t * (double)P.desc.n_outputs;
+  int gi = 16;
+  while (gi > 4 && gi * est_ms > 4.0) gi /= 2;
+  return gi;
+}
+
 ds_status build_graph(Plan& P) {
-  if (P.graph_exec && P.graph_profiled == P.profiling) return DS_OK;
+  const int gi = graph_iters_for(P);
+  if (P.graph_exec && P.graph_profiled == P.profiling && P.graph_iters == gi) return DS_OK;
   if (P.graph_exec) {
     cudaGraphExecDestroy(P.graph_exec);
     P.graph_exec = nullptr;
@@ -191,7 +204,7 @@ ds_status build_graph(Plan& P) {
     if (P.ev == nullptr) return DS_ENOMEM;
     for (int i = 0; i < kGraphItersMax * 5; ++i) DS_CUDA_TRY(cudaEventCreate(&P.ev[i]));
   }
-  P.graph_iters = P.graph_iters_cfg;
+  P.graph_iters = gi;
   // the accurate-operator graph is captured when a problem first needs it
   ds_status s = capture_iterations(P, false, P.profiling ? P.ev : nullptr, &P.graph_exec);
   if (s != DS_OK) return s;
@@ -316,7 +329,7 @@ ds_status ds::plan_create(const ds_desc* desc, const ds_exchange* ex, const int3
   P->red_len = 2 * P->num_sms * 8 + 64;
   P->reliable_delta = 1e-5;
   P->bin_mode = P->desc.precision == DS_PREC_MIXED ? 1 : 0;
-  P->graph_iters_cfg = 16;
+  P->graph_iters_cfg = 0;  // from the problem's size
   P->blocks_per_sm = 16;
   P->accurate_df = 1;
   P->refresh_max = 50;
@@ -499,10 +512,23 @@ ds_status destripe_solve(ds_plan_t plan, const void* d_y, double* d_a, double to
   // beside its right-hand side
   const ds_status stl = tl_ensure(P);
   if (stl != DS_OK) return stl;
+  // the probe of long baselines waits for its result, so it comes before the
+  // right-hand side is queued
+  const ds_status spr = pc_probe(P);
+  if (spr != DS_OK) return spr;
   bool pm_started = false;
   const ds_status sp = pm_begin(P, &pm_started);
   if (sp != DS_OK) return sp;
   enqueue_rhs(P, st, d_y, P.b, Gate{nullptr, nullptr});
+  // b lies in the range of A up to rounding: its component along A's null vector
+  // (one offset on every I-carrying baseline) is rounding alone, which CG cannot
+  // reduce and which would grow the iterate along that vector.  Removed here, so
+  // that a right-hand side of rounding size (a noiseless sky) is solved like any
+  // other.
+  if (P.has_I_outputs) {
+    enqueue_gauge(P, st, P.b);
+    P.launches += 2;
+  }
   ds_status s = pm_join(P, pm_started);
   if (s != DS_OK) return s;
   // the two-level preconditioner's coarse space, built once per plan
@@ -625,7 +651,7 @@ ds_status destripe_tune(ds_plan_t plan, const char* key, double value) {
     if (value == 1.0 && P.bins32 == nullptr) return DS_ESTATE;
     P.bin_mode = (int)value;
   } else if (k == "graph_iters") {
-    if (!(value >= 1.0 && value <= kGraphItersMax)) return DS_EINVAL;
+    if (!(value >= 0.0 && value <= kGraphItersMax) || value != std::floor(value)) return DS_EINVAL;
     P.graph_iters_cfg = (int)value;
   } else if (k == "accurate_df") {
     if (value != 0.0 && value != 1.0) return DS_EINVAL;
@@ -791,6 +817,7 @@ ds_status destripe_run_host(const ds_desc* desc, const int32_t* h_pix, const flo
   if (s == DS_OK) {
     Plan& P = *reinterpret_cast<Plan*>(plan);
     s = tl_ensure(P);
+    if (s == DS_OK) s = pc_probe(P);
     if (s == DS_OK && P.precond == 2 && !P.pc_built && P.layout == 3 && P.tl2_end != nullptr)
       s = pc_prepare(P);
   }

@@ -238,6 +238,7 @@ struct Plan {
   int pc_nside;             // the coarse space has 12 pc_nside^2 cells
   int pc_built;             // coarse space and E^+ built for this plan
   int pc_fallback;          // a solve broke down with the coarse correction: D^-1 alone
+  int pc_probed;            // the probe of long baselines ran (and found enough kept samples)
   int pc_n;                 // coarse columns (kept cells x n_c)
   int pc_cells;             // kept cells
   float4* pc_slot;          // [n_b][kPcSlots] per slot: x = kept-cell number (int bits, -1 =
@@ -360,6 +361,7 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm);
 // builds the coarse space, first making (and afterwards freeing) the run records
 // and their pixel-major copy when the plan's operator does not keep them
 ds_status pc_prepare(Plan& P);
+ds_status pc_probe(Plan& P);
 bool pc_restrict_fits(const Plan& P, int n);
 int pc_mode(const Plan& P);
 void pc_free(Plan& P, cudaStream_t st);

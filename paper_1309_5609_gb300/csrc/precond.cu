@@ -806,6 +806,7 @@ void pc_free(Plan& P, cudaStream_t st) {
   P.pc_cells = 0;
   P.pc_built = 0;
   P.pc_fallback = 0;
+  P.pc_probed = 0;
 }
 
 bool pc_ready(const Plan& P) {
@@ -823,6 +824,52 @@ int pc_mode(const Plan& P) {
   return P.pc_built && !P.pc_fallback ? 0 : 1;
 }
 
+// Long baselines often sweep too many cells for their two slots to hold most of
+// their samples.  A probe of about 4096 of them (counting only) decides first:
+// where the slots would keep too few samples the plan gets no coarse space and
+// iterates plain CG.  The host waits for the count, so a solve probes before it
+// queues its right-hand side.
+ds_status pc_probe(Plan& P) {
+  if (P.precond != 2 || P.pc_built || P.pc_probed) return DS_OK;
+  const int64_t step = P.n_b / 4096 > 1 ? P.n_b / 4096 : 1;
+  if (P.L < kPcWarpRows || step <= 1) {
+    P.pc_probed = 1;
+    return DS_OK;
+  }
+  cudaStream_t st = P.stream;
+  const int64_t nc = P.pc_nside < P.desc.nside ? P.pc_nside : P.desc.nside;
+  int32_t* cell_of = nullptr;
+  unsigned long long* kept = nullptr;  // samples in kept slots, valid samples
+  unsigned long long h_probe[2] = {0, 0};
+  cudaError_t e = plan_alloc(P, reinterpret_cast<void**>(&cell_of), sizeof(int32_t) * P.npix, false);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&kept), sizeof(h_probe), false);
+  if (e == cudaSuccess) e = cudaMemsetAsync(kept, 0, sizeof(h_probe), st);
+  if (e == cudaSuccess) {
+    k_pc_cell_table<<<stream_grid(P, P.npix, kBlock, 8), kBlock, 0, st>>>(cell_of, P.npix,
+                                                                        P.desc.nside, nc);
+    // with step > 1 the kernel writes neither slots nor the used-cell flags
+    k_pc_rows_warp<<<stream_grid(P, (P.n_b / step + 1) * 32, kBlock, 8), kBlock, 0, st>>>(
+        P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b, step, nullptr, nullptr, kept);
+    P.launches += 2;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_probe, kept, sizeof(h_probe), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (cell_of) cudaFreeAsync(cell_of, st);
+  if (kept) cudaFreeAsync(kept, st);
+  if (e == cudaErrorMemoryAllocation) {  // the coarse-space build reports it
+    (void)cudaGetLastError();
+    return DS_OK;
+  }
+  if (e != cudaSuccess) return DS_ECUDA;
+  P.pc_probed = 1;
+  if (h_probe[1] > 0 && (double)h_probe[0] < (kPcKeptMin - 0.1) * (double)h_probe[1]) {
+    pc_free(P, st);
+    P.pc_built = 1;
+  }
+  return DS_OK;
+}
+
 // Builds the coarse space and E^+ on the plan's stream (synchronises it).  The
 // second term of E reads the pixel-major copy of the run records; a plan whose
 // operator does not keep one gets it for the purpose (made_runs / made_pm) and
@@ -830,6 +877,8 @@ int pc_mode(const Plan& P) {
 ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   *made_runs = *made_pm = false;
   if (P.pc_built) return DS_OK;
+  const ds_status sp = pc_probe(P);
+  if (sp != DS_OK || P.pc_built) return sp;
   cudaStream_t st = P.stream;
   const int64_t nc = P.pc_nside < P.desc.nside ? P.pc_nside : P.desc.nside;
   const int64_t ncell = 12 * nc * nc;
@@ -856,27 +905,6 @@ ds_status pc_build(Plan& P, bool* made_runs, bool* made_pm) {
   k_pc_cell_table<<<g_pix, kBlock, 0, st>>>(cell_of, P.npix, P.desc.nside, nc);
   const int g_b = stream_grid(P, P.n_b, kBlock, 8);
   if (P.L >= kPcWarpRows) {
-    // long baselines often sweep too many cells: a probe of about 4096 of them first
-    const int64_t step = P.n_b / 4096 > 1 ? P.n_b / 4096 : 1;
-    if (step > 1) {
-      unsigned long long h_probe[2] = {0, 0};
-      k_pc_rows_warp<<<stream_grid(P, (P.n_b / step + 1) * 32, kBlock, 8), kBlock, 0, st>>>(
-          P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b, step, P.pc_slot, used, kept);
-      P.launches += 1;
-      e = cudaMemcpyAsync(h_probe, kept, sizeof(h_probe), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return fail(e);
-      if (h_probe[1] > 0 && (double)h_probe[0] < (kPcKeptMin - 0.1) * (double)h_probe[1]) {
-        void* tmp[] = {cell_of, used, cmap, kept};
-        for (void* tp : tmp)
-          if (tp) cudaFreeAsync(tp, st);
-        pc_free(P, st);
-        P.pc_built = 1;
-        return DS_OK;
-      }
-      e = cudaMemsetAsync(kept, 0, sizeof(unsigned long long) * 2, st);
-      if (e != cudaSuccess) return fail(e);
-    }
     k_pc_rows_warp<<<stream_grid(P, P.n_b * 32, kBlock, 8), kBlock, 0, st>>>(
         P.pix, P.c, P.s, cell_of, P.nvalid, P.n_t, P.L, P.n_b, 1, P.pc_slot, used, kept);
   } else

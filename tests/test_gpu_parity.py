@@ -179,8 +179,10 @@ def test_max_iter_reports_noconv_with_best_iterate():
 
 def test_signal_only_gives_null_baselines():
     # Sect. 5: a noiseless sky gives null baselines.  The right-hand side vanishes to
-    # rounding; a CG run relative to that rounding only amplifies it through the
-    # near-null modes, so the baselines are held to the parity bar (1e-4 sigma).
+    # rounding; the solve removes its component along the I offset (rounding that
+    # CG cannot reduce), and a CG run relative to the rest only amplifies it
+    # through the near-null modes, so the baselines are held to the parity bar
+    # (1e-4 sigma).
     prob = make_problem(400_000, 64, ("I", "q", "u"), baseline_len=500, noise=False, seed=3,
                         sky_sigma={"I": 10.0, "Q": 1.0, "U": 1.0})
     for precision in ("fp64", "mixed"):
