@@ -119,7 +119,7 @@ void plan_free(Plan* P) {
     for (int i = 0; i < kGraphItersMax * 5; ++i) cudaEventDestroy(P->ev[i]);
     delete[] P->ev;
   }
-  void* dev[] = {P->tl_rec, P->tl_off, P->tl2_rec, P->tl2_off, P->tl2_chunk, P->tl2_end, P->tl_x4, P->pc_slot, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
+  void* dev[] = {P->tl_rec, P->tl_off, P->tl2_rec, P->tl2_off, P->tl2_chunk, P->tl2_end, P->tl_x4, P->tl_mmax, P->pc_slot, P->pc_einv, P->pc_u, P->pc_c, P->pm_off, P->pm_rec, P->pm_lo, P->x4, P->xd4, P->rl_df, P->rl_tiles, P->rl_rec, P->rl_b, P->x32, P->xdf, P->lid, P->upix, P->ucnt, P->pix, P->hits, P->mask, P->minv, P->bins, P->bins32, P->map32, P->maplo, P->map64, P->nvalid,
                  P->x,   P->r,    P->p,    P->q,    P->b,    P->t,     P->x_best, P->red,   P->counters,
                  P->state, P->err, P->scal};
   // the plan's own stream is the last user of its memory (batches retire a

@@ -281,10 +281,11 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve(BT* __restrict__ bins,
                                                         const uint8_t* __restrict__ mask,
                                                         T* __restrict__ map,
                                                         double* __restrict__ out_map, int64_t npix,
-                                                        Gate g) {
+                                                        unsigned* __restrict__ mmax, Gate g) {
   if (gate_closed(g)) return;
   constexpr int NM = NC * (NC + 1) / 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float big = 0.f;  // largest |m| of this thread's pixels (mmax: the grid's, as float bits)
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
     double s[NC], m[NC];
     if constexpr (std::is_same<BT, float>::value) {
@@ -316,6 +317,11 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve(BT* __restrict__ bins,
       if constexpr (NC > 1) o4.y = (float)m[1];
       if constexpr (NC > 2) o4.z = (float)m[2];
       reinterpret_cast<float4*>(map)[p] = o4;
+      // the largest |m| by the bits of non-negative floats, which order as the values
+      // do and keep a NaN (above +inf; fmaxf would drop it)
+      big = __uint_as_float(max(__float_as_uint(big),
+                                max(__float_as_uint(fabsf(o4.x)),
+                                    max(__float_as_uint(fabsf(o4.y)), __float_as_uint(fabsf(o4.z))))));
     } else {
       reinterpret_cast<double2*>(map)[2 * p] = make_double2(m[0], NC > 1 ? m[NC > 1 ? 1 : 0] : 0.0);
       if constexpr (NC > 2) map[4 * p + 2] = m[2];
@@ -324,6 +330,10 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve(BT* __restrict__ bins,
 #pragma unroll
       for (int j = 0; j < NC; ++j) out_map[(int64_t)j * npix + p] = m[j];
     }
+  }
+  if (mmax != nullptr) {
+    const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(big));
+    if ((threadIdx.x & 31) == 0) atomicMax(mmax, w);
   }
 }
 
@@ -480,13 +490,14 @@ void launch_pixel_solve(const Plan& P, cudaStream_t st, bool fp64, double* out_m
     constexpr int NC = decltype(ncc)::value;
     if (fp64)
       k_pixel_solve<NC, double, double><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map64,
-                                                                  out_map, P.npix, g);
+                                                                  out_map, P.npix, nullptr, g);
     else if (f32_bins(P, fp64))
-      k_pixel_solve<NC, float, float><<<grid, kBlock, 0, st>>>(P.bins32, P.minv, P.mask, P.map32,
-                                                                out_map, P.npix, g);
+      k_pixel_solve<NC, float, float><<<grid, kBlock, 0, st>>>(
+          P.bins32, P.minv, P.mask, P.map32, out_map, P.npix, tl_ready(P) ? P.tl_mmax : nullptr,
+          g);
     else
       k_pixel_solve<NC, float, double><<<grid, kBlock, 0, st>>>(P.bins, P.minv, P.mask, P.map32,
-                                                                 out_map, P.npix, g);
+                                                                 out_map, P.npix, nullptr, g);
   };
   if (P.n_c == 1) go(std::integral_constant<int, 1>{});
   else if (P.n_c == 2) go(std::integral_constant<int, 2>{});

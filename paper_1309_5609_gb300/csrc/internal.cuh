@@ -230,6 +230,7 @@ struct Plan {
   int tl_pending;           // layout 3 chosen by the plan, records not built yet (tl_ensure)
   int64_t tl_runs;          // records of each tiled copy
   float4* tl_x4;            // [n_b] float32 baselines of every output, per baseline
+  unsigned* tl_mmax;        // largest |m| of the operator's map (float bits): the rescan's scale
   int rescan_samples;       // run-length plans: the rescans read the time-ordered samples (dense
                             // runs: a record per run costs more than 12 bytes per sample)
   // preconditioner of the CG (precond.cu): 0 none, 1 D^-1 (valid samples per

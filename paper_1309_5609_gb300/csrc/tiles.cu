@@ -19,8 +19,8 @@
 //    tile reaches L2, instead of one per run as in time order;
 //  * rescan and per-baseline sums (F~^T (z - R P~ m)) read short tiles (a few
 //    hours), pixels in pixel order: each block keeps its tile's map-term sums per
-//    baseline in shared memory (float32 atomics; the runs of one pixel lie in
-//    different baselines, so lanes rarely collide), gathers the map row of each
+//    baseline in shared memory (fixed-point integer atomics; the runs of one pixel
+//    lie in different baselines, so lanes rarely collide), gathers the map row of each
 //    run, and stores each baseline's valid samples times its baseline minus that
 //    sum once (each baseline belongs to one tile: no atomics in global memory).
 #include <vector>
@@ -267,13 +267,15 @@ constexpr int64_t kChunk = kRound * 8;  // records per warp chunk of the binning
 // x32[o][b] = x[o][b] rounded to float32, and (several outputs) x4[b] = every
 // output's baseline b (one 16-byte gather per run record in the tiled binning).
 // Two baselines per thread and iteration, so that two loads per output are in
-// flight.
+// flight.  The first kernel of an operator application: it also clears the map
+// maximum that the pixel solve raises for the rescan.
 template <int NO>
 __global__ void __launch_bounds__(kBlock) k_tl_pack(const double* __restrict__ x,
                                                     float* __restrict__ x32,
                                                     float4* __restrict__ x4, int64_t n_b, int n_o,
-                                                    Gate g) {
+                                                    unsigned* __restrict__ mmax, Gate g) {
   if (gate_closed(g)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *mmax = 0u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t half = (n_b + 1) >> 1;
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < half; h += stride) {
@@ -473,9 +475,16 @@ __global__ void __launch_bounds__(32 * kBinWarps, 3) k_tl_bin_lanes(
 
 // out[o][b] = nvalid[b] x[o][b] - sum over the tile's runs in baseline b of
 // (row sums) . m_p: the baseline term of every run of b adds up to the valid
-// samples of b times x, so only the map term is summed per run (float32 sums in
-// shared memory, one float64 store per baseline).  Each thread issues the loads
-// of kUnroll records, then their map rows, before any sum.
+// samples of b times x, so only the map term is summed per run, in shared memory,
+// and each baseline is stored once.  The shared sums are fixed-point integers
+// (integer atomics on random addresses run about 4.5x faster than float ones):
+// a run's term times 2^e, e set so that L x 3 x max|m| x 2^e <= 2^30 (a run's
+// term is at most n x 3 max|m|, a baseline holds at most L samples), split into
+// its rounded integer (hi) and the rest times 2^f (lo, f = 16 while L < 2^14,
+// fewer beyond), so that no partial sum overflows and the result is exact to far
+// below float32 rounding.  A map with a
+// non-finite value gives NaN baselines.  Each thread issues the loads of kUnroll
+// records, then their map rows, before any sum.
 template <int KS>
 __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restrict__ rec,
                                                             const int64_t* __restrict__ tile_off,
@@ -483,17 +492,33 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
                                                             const float* __restrict__ x32,
                                                             const int32_t* __restrict__ nvalid,
                                                             const float* __restrict__ map,
-                                                            double* __restrict__ out, int64_t n_b,
-                                                            KindsArg kk, Gate g) {
+                                                            const unsigned* __restrict__ mmax,
+                                                            int64_t L, double* __restrict__ out,
+                                                            int64_t n_b, KindsArg kk, Gate g) {
   if (gate_closed(g)) return;
   using K = KSet<KS>;
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
-  extern __shared__ float sums[];  // [n_o][Tb]
+  extern __shared__ int hi[];  // [n_o][Tb] integer parts, then [n_o][Tb] fractions x 2^16
+  int* lo = hi + (int64_t)n_o * Tb;
+  const float big = __uint_as_float(*mmax);
+  const bool finite = big <= 3.0e38f;  // false for +inf and NaN
+  int e = 0;
+  if (finite && big > 0.f) {
+    int ex = 0;
+    frexp((double)L * 3.0 * (double)big, &ex);  // the bound is below 2^ex
+    e = 30 - ex;
+    e = e < -126 ? -126 : (e > 126 ? 126 : e);
+  }
+  // lo: at most L terms of at most 2^(f - 1) each stay below 2^29
+  int f = 30 - (64 - __clzll((unsigned long long)L));
+  f = f < 0 ? 0 : (f > 16 ? 16 : f);
+  const float scale = ldexpf(1.f, e), inv = ldexpf(1.f, -e), frac = ldexpf(1.f, f),
+              inv_lo = ldexpf(1.f, -e - f);
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t b0 = t * Tb;
     const int64_t nb = b0 + Tb < n_b ? Tb : n_b - b0;
-    for (int64_t j = threadIdx.x; j < (int64_t)n_o * Tb; j += blockDim.x) sums[j] = 0.f;
+    for (int64_t j = threadIdx.x; j < 2 * (int64_t)n_o * Tb; j += blockDim.x) hi[j] = 0;
     __syncthreads();
     const int64_t r0 = tile_off[t], r1 = tile_off[t + 1];
     for (int64_t base = r0 + threadIdx.x; base < r1; base += (int64_t)kUnroll * blockDim.x) {
@@ -515,14 +540,21 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
         const float c = __int_as_float(v[u].z), sn = __int_as_float(v[u].w);
 #pragma unroll
         for (int o = 0; o < NO; ++o)
-          if (o < n_o) atomicAdd(sums + o * Tb + bl, -run_dot<NC>(K::kind(o, kk), n, c, sn, m[u]));
+          if (o < n_o) {
+            // |v| <= 2^30 / L: its integer part is exact, and so is the rest below 2^24
+            const float v = -run_dot<NC>(K::kind(o, kk), n, c, sn, m[u]) * scale;
+            const float h = rintf(v);
+            atomicAdd(hi + o * Tb + bl, (int)h);
+            atomicAdd(lo + o * Tb + bl, __float2int_rn((v - h) * frac));
+          }
       }
     }
     __syncthreads();
     for (int o = 0; o < n_o; ++o)
       for (int64_t j = threadIdx.x; j < nb; j += blockDim.x) {
         const int64_t i = o * n_b + b0 + j;
-        out[i] = to_f64(fmaf((float)nvalid[b0 + j], x32[i], sums[o * Tb + j]));
+        const float s = __int2float_rn(hi[o * Tb + j]) * inv + __int2float_rn(lo[o * Tb + j]) * inv_lo;
+        out[i] = finite ? to_f64(fmaf((float)nvalid[b0 + j], x32[i], s)) : __longlong_as_double(0x7ff8000000000000LL);
       }
     __syncthreads();
   }
@@ -540,6 +572,7 @@ static bool tl_packs(const Plan& P) {
 
 bool tl_ready(const Plan& P) {
   return P.layout == 3 && P.tl_rec != nullptr && P.tl2_rec != nullptr && P.x32 != nullptr &&
+         P.tl_mmax != nullptr &&
          (P.tl_x4 != nullptr || !tl_packs(P));
 }
 
@@ -547,7 +580,7 @@ void launch_pack_tl(const Plan& P, cudaStream_t st, const double* x, Gate g) {
   const int grid = stream_grid(P, (P.n_b + 1) / 2, kBlock, 8);
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int NO = KSet<decltype(ksc)::value>::NO;
-    k_tl_pack<NO><<<grid, kBlock, 0, st>>>(x, P.x32, P.tl_x4, P.n_b, P.n_o, g);
+    k_tl_pack<NO><<<grid, kBlock, 0, st>>>(x, P.x32, P.tl_x4, P.n_b, P.n_o, P.tl_mmax, g);
   });
 }
 
@@ -568,12 +601,12 @@ void launch_rescan_tl(const Plan& P, cudaStream_t st, double* out, Gate g) {
   const int64_t per_sm = P.tl_rescan_blocks > 0 ? P.tl_rescan_blocks : 1;
   const int64_t cap = (int64_t)P.num_sms * per_sm;
   const int grid = (int)(P.tl_tiles < cap ? P.tl_tiles : cap);
-  const size_t smem = sizeof(float) * (size_t)P.n_o * P.tl_tb;
+  const size_t smem = 2 * sizeof(int) * (size_t)P.n_o * P.tl_tb;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     k_tl_rescan<KS><<<grid, kTileThreads, smem, st>>>(P.tl_rec, P.tl_off, P.tl_tiles, P.tl_tb,
-                                                      P.x32, P.nvalid, P.map32, out, P.n_b,
-                                                      P.kinds, g);
+                                                      P.x32, P.nvalid, P.map32, P.tl_mmax, P.L,
+                                                      out, P.n_b, P.kinds, g);
   });
 }
 
@@ -686,9 +719,11 @@ static cudaError_t tl_rank(Plan& P, int32_t** rank, int32_t** cidx, int64_t* nke
 }
 
 static void tl_free(Plan& P) {
-  void* mine[] = {P.tl_rec, P.tl_off, P.tl2_rec, P.tl2_off, P.tl2_chunk, P.tl_x4, P.tl2_end};
+  void* mine[] = {P.tl_rec, P.tl_off, P.tl2_rec, P.tl2_off, P.tl2_chunk, P.tl_x4, P.tl2_end,
+                  P.tl_mmax};
   for (void* t : mine)
     if (t) cudaFreeAsync(t, P.stream);
+  P.tl_mmax = nullptr;
   P.tl2_end = nullptr;
   P.tl_rec = nullptr;
   P.tl_off = nullptr;
@@ -742,6 +777,8 @@ ds_status tl_build(Plan& P) {
     return DS_ESTATE;
   }
   if (tl_packs(P)) e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_x4), sizeof(float4) * P.n_b, true);
+  if (e == cudaSuccess) e = plan_alloc(P, reinterpret_cast<void**>(&P.tl_mmax), sizeof(unsigned), true);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.tl_mmax, 0, sizeof(unsigned), st);
   int64_t nkeys = 0;
   if (e == cudaSuccess) e = tl_rank(P, &rank, &cidx, &nkeys);
   if (e == cudaSuccess && nkeys <= 0) e = cudaErrorInvalidValue;
@@ -782,9 +819,9 @@ ds_status tl_build(Plan& P) {
   P.tl2_chunks = first[n_tiles2];
   P.tl_tiles = n_tiles;
   P.tl_tb = Tb;
-  // the rescan's shared array above 48 KB needs the kernel's opt-in; resident
+  // the rescan's shared arrays above 48 KB need the kernel's opt-in; resident
   // blocks per SM of both passes
-  const size_t smem = sizeof(float) * (size_t)P.n_o * Tb;
+  const size_t smem = 2 * sizeof(int) * (size_t)P.n_o * Tb;
   with_kindset(P.kindset, [&](auto ksc) {
     constexpr int KS = decltype(ksc)::value;
     if (e == cudaSuccess)

@@ -14,7 +14,12 @@ the kernels themselves against the oracle.
   * the two-level offsets of the pixel-major copy (k_pm_scan_up / k_pm_scan_down);
   * the lane-sequential binning over pixel-sorted records (k_tl_bin_lanes): a lane's
     head, interior and tail pixels, the segmented scan of tails over the lanes, and
-    the pixel carried across rounds: every pixel reduced once per chunk."""
+    the pixel carried across rounds: every pixel reduced once per chunk;
+  * the fixed-point baseline sums of the tiled rescan (k_tl_rescan): the scale from
+    the map maximum, the split into integer and fraction parts, no partial sum
+    outside int32, and the sum recovered to half a unit per term."""
+import math
+
 import numpy as np
 import pytest
 
@@ -423,3 +428,43 @@ def test_lane_sequential_binning_sums_every_pixel_once_per_chunk(mean_run):
         assert got == want
         # one flush per pixel: a pixel's records are contiguous within the chunk
         assert all(c == 1 for c in seen.values()), seen
+
+
+# ---- fixed-point baseline sums of the tiled rescan (k_tl_rescan) ---------------------
+
+def fixed_point_scale(L, big):
+    """The rescan's exponents: e with L x 3 x big x 2^e <= 2^30, f fraction bits."""
+    e = 0
+    if big > 0.0:
+        _, ex = math.frexp(L * 3.0 * big)
+        e = min(126, max(-126, 30 - ex))
+    f = min(16, max(0, 30 - int(L).bit_length()))
+    return e, f
+
+
+@pytest.mark.parametrize("L,big", [(1, 1.0), (50, 37.5), (50, 1e-20), (3000, 2.5e6), (30000, 0.3),
+                                   (200000, 5.0)])
+def test_fixed_point_baseline_sums_match_float64(L, big):
+    rng = np.random.default_rng(L)
+    e, f = fixed_point_scale(L, big)
+    scale, frac = np.float32(2.0 ** e), np.float32(2.0 ** f)
+    for trial in range(20):
+        # one baseline: runs of n samples (sum n <= L), terms up to n x 3 x big
+        n = []
+        while sum(n) < L:
+            n.append(int(min(L - sum(n), rng.integers(1, 256))))
+        n = np.array(n)
+        terms = (rng.uniform(-1.0, 1.0, size=len(n)) * n * 3.0 * big).astype(np.float32)
+        if trial == 0:
+            terms = (n * 3.0 * big * np.sign(rng.uniform(-1, 1))).astype(np.float32)  # the bound
+        v = terms * scale  # exact: a power of two
+        h = np.rint(v)
+        lo = np.rint((v - h) * frac)
+        assert np.all((v - h) == (v.astype(np.float64) - h.astype(np.float64)))  # exact rest
+        hi_sum = np.cumsum(h.astype(np.int64))
+        lo_sum = np.cumsum(lo.astype(np.int64))
+        assert np.abs(hi_sum).max() < 2 ** 31 and np.abs(lo_sum).max() < 2 ** 31
+        got = float(hi_sum[-1]) * 2.0 ** -e + float(lo_sum[-1]) * 2.0 ** (-e - f)
+        want = float(np.sum(terms.astype(np.float64)))
+        # each term is kept to half a unit of 2^-(e + f); the float32 terms are the input
+        assert abs(got - want) <= len(n) * 0.5 * 2.0 ** (-e - f) * (1 + 1e-9) + 1e-300
