@@ -331,9 +331,16 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve(BT* __restrict__ bins,
       for (int j = 0; j < NC; ++j) out_map[(int64_t)j * npix + p] = m[j];
     }
   }
-  if (mmax != nullptr) {
+  if (mmax != nullptr) {  // one atomic per block: a warp's each would queue on one address
+    __shared__ unsigned s_big[kBlock / 32];
     const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(big));
-    if ((threadIdx.x & 31) == 0) atomicMax(mmax, w);
+    if ((threadIdx.x & 31) == 0) s_big[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned m = 0u;
+      for (int q = 0; q < kBlock / 32; ++q) m = max(m, s_big[q]);
+      atomicMax(mmax, m);
+    }
   }
 }
 
