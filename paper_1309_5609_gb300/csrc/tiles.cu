@@ -482,9 +482,9 @@ __global__ void __launch_bounds__(32 * kBinWarps, 3) k_tl_bin_lanes(
 // term is at most n x 3 max|m|, a baseline holds at most L samples), split into
 // its rounded integer (hi) and the rest times 2^f (lo, f = 16 while L < 2^14,
 // fewer beyond), so that no partial sum overflows and the result is exact to far
-// below float32 rounding.  A map with a
-// non-finite value gives NaN baselines.  Each thread issues the loads of kUnroll
-// records, then their map rows, before any sum.
+// below float32 rounding.  A map with a non-finite value gives NaN baselines.
+// Each thread issues the loads of kUnroll records, then their map rows, before
+// any sum.
 template <int KS>
 __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restrict__ rec,
                                                             const int64_t* __restrict__ tile_off,
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
   using K = KSet<KS>;
   constexpr int NC = K::NC, NO = K::NO;
   const int n_o = K::n_o(kk);
-  extern __shared__ int hi[];  // [n_o][Tb] integer parts, then [n_o][Tb] fractions x 2^16
+  extern __shared__ int hi[];  // [n_o][Tb] integer parts, then [n_o][Tb] fractions x 2^f
   int* lo = hi + (int64_t)n_o * Tb;
   const float big = __uint_as_float(*mmax);
   const bool finite = big <= 3.0e38f;  // false for +inf and NaN
@@ -541,11 +541,11 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
 #pragma unroll
         for (int o = 0; o < NO; ++o)
           if (o < n_o) {
-            // |v| <= 2^30 / L: its integer part is exact, and so is the rest below 2^24
-            const float v = -run_dot<NC>(K::kind(o, kk), n, c, sn, m[u]) * scale;
-            const float h = rintf(v);
+            // |q| <= 2^30 n / L; q - h is exact (q is a whole number from 2^23 up)
+            const float q = -run_dot<NC>(K::kind(o, kk), n, c, sn, m[u]) * scale;
+            const float h = rintf(q);
             atomicAdd(hi + o * Tb + bl, (int)h);
-            atomicAdd(lo + o * Tb + bl, __float2int_rn((v - h) * frac));
+            atomicAdd(lo + o * Tb + bl, __float2int_rn((q - h) * frac));
           }
       }
     }
@@ -553,8 +553,10 @@ __global__ void __launch_bounds__(kTileThreads) k_tl_rescan(const int4* __restri
     for (int o = 0; o < n_o; ++o)
       for (int64_t j = threadIdx.x; j < nb; j += blockDim.x) {
         const int64_t i = o * n_b + b0 + j;
-        const float s = __int2float_rn(hi[o * Tb + j]) * inv + __int2float_rn(lo[o * Tb + j]) * inv_lo;
-        out[i] = finite ? to_f64(fmaf((float)nvalid[b0 + j], x32[i], s)) : __longlong_as_double(0x7ff8000000000000LL);
+        const float s =
+            __int2float_rn(hi[o * Tb + j]) * inv + __int2float_rn(lo[o * Tb + j]) * inv_lo;
+        out[i] = finite ? to_f64(fmaf((float)nvalid[b0 + j], x32[i], s))
+                        : __longlong_as_double(0x7ff8000000000000LL);
       }
     __syncthreads();
   }
