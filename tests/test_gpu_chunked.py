@@ -300,3 +300,32 @@ def test_tiled_operator_on_random_pixels():
     prob = random_pixel_problem(200_003, 64, ("q", "u"), 25, seed=5)
     check_apply(prob, None, layout=3)
     check_apply(prob, None, layout=3, before={"bin_tile_samples": 25 * 3})
+
+
+def test_tiled_rescan_fixed_point_scale_follows_the_map():
+    # The rescan's fixed-point sums take their scale from the map's largest value in
+    # each application: baselines scaled by 2^-100 or 2^100 (map values near 1e-30
+    # and 1e30) give the operator scaled by the same factor, at the operator bar
+    # against the oracle; a non-finite baseline gives non-finite output.
+    kinds, nside, n_t, L, ff, scan = CASES[2]
+    prob = make_problem(n_t, nside, kinds, baseline_len=L, seed=26, scan=scan, flag_frac=ff,
+                        flag_mean_len=200, y_dtype=torch.float64)
+    d = prob.numpy()
+    op = oracle.make_plan(d["pix"], d["c"], d["s"], d["valid"], prob.nside, prob.kinds,
+                          prob.baseline_len)
+    gp = prob.to(DEV)
+    plan = ds.destripe_plan(gp.pix, gp.c32, gp.s32, gp.valid, nside=prob.nside,
+                            kinds=prob.kinds, baseline_len=prob.baseline_len, precision="mixed")
+    ds.destripe_tune(plan, "layout", 3)
+    x = np.random.default_rng(18).standard_normal(plan.n_u)
+    ref = oracle.apply_A(op, x)
+    Ax = torch.empty(plan.n_u, dtype=torch.float64, device=DEV)
+    for s in (2.0 ** -100, 1.0, 2.0 ** 100):
+        ds.destripe_apply_A(plan, torch.from_numpy(x * s).to(DEV), Ax)
+        got = Ax.cpu().numpy() / s
+        assert rel_err(got, ref) < 1e-5, (s, rel_err(got, ref))
+    xn = x.copy()
+    xn[plan.n_u // 2] = np.nan
+    ds.destripe_apply_A(plan, torch.from_numpy(xn).to(DEV), Ax)
+    assert not np.isfinite(Ax.cpu().numpy()).all()
+    plan.close()
