@@ -718,6 +718,8 @@ def run_batch(args):
     rank, world, local, dev, dist = _dist_setup()
     ds.load_library()
     cfgs = batch_configs(64, seed=1003)
+    if args.n_samples:  # each problem cut to its first n_samples (small profiling runs)
+        cfgs = [dict(c, n_t=min(c["n_t"], args.n_samples)) for c in cfgs]
     probs = [make_problem(device=dev, y_dtype=torch.float32, keep_f64_trig=False, **c) for c in cfgs]
 
     shape, tuning = {}, None
@@ -806,7 +808,8 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (64 seeded scans), resident in HBM",
-            "config": {"workload": "batch64-qu-nside64-256-1e6-3e7-L50-3000",
+            "config": {"workload": "batch64-qu-nside64-256-1e6-3e7-L50-3000"
+                       + (f"-cap{args.n_samples}" if args.n_samples else ""),
                        "problems": len(probs), "n_samples_total": int(sum(p.n_t for p in probs)),
                        "precision": "mixed", "tol": args.tol,
                        "step": "64 plans + batched RHS/CG (one graph per 8 iterations) + retire"},

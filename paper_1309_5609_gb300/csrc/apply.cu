@@ -288,6 +288,40 @@ __global__ void __launch_bounds__(kBlock) k_pixel_solve(BT* __restrict__ bins,
   float big = 0.f;  // largest |m| of this thread's pixels (mmax: the grid's, as float bits)
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += stride) {
     double s[NC], m[NC];
+    if constexpr (std::is_same<BT, float>::value && std::is_same<T, float>::value) {
+      // The float32 operator's pass.  A pixel no run touched has zero sums, and a cut
+      // pixel's map entry is zero from the plan's creation on (every pass leaves it
+      // so): both cost two loads here and no float64 work, which is narrow on this
+      // GPU.  The sums of a kept pixel widen on the integer pipes.
+      const float4 v = reinterpret_cast<const float4*>(bins)[p];
+      if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+        reinterpret_cast<float4*>(bins)[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!mask[p]) {
+        if (out_map != nullptr)
+#pragma unroll
+          for (int j = 0; j < NC; ++j) out_map[(int64_t)j * npix + p] = 0.0;
+        continue;
+      }
+      s[0] = f64_of_f32(v.x);
+      if constexpr (NC > 1) s[1] = f64_of_f32(v.y);
+      if constexpr (NC > 2) s[2] = f64_of_f32(v.z);
+      double mi[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
+      sym_mul<NC>(mi, s, m);
+      float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      o4.x = (float)m[0];
+      if constexpr (NC > 1) o4.y = (float)m[1];
+      if constexpr (NC > 2) o4.z = (float)m[2];
+      reinterpret_cast<float4*>(map)[p] = o4;
+      big = __uint_as_float(max(__float_as_uint(big),
+                                max(__float_as_uint(fabsf(o4.x)),
+                                    max(__float_as_uint(fabsf(o4.y)), __float_as_uint(fabsf(o4.z))))));
+      if (out_map != nullptr)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) out_map[(int64_t)j * npix + p] = m[j];
+      continue;
+    }
     if constexpr (std::is_same<BT, float>::value) {
       const float4 v = reinterpret_cast<const float4*>(bins)[p];
       s[0] = v.x;

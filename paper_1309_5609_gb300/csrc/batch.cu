@@ -242,21 +242,20 @@ __global__ void __launch_bounds__(kBlock) k_bb_pixel_solve(const SlotDesc* __res
     const uint8_t* __restrict__ mask = slots[T.slot].mask;
     const double* __restrict__ minv = slots[T.slot].minv;
     for (int64_t p = T.begin + threadIdx.x; p < T.end; p += blockDim.x) {
+      // a pixel no run touched has zero sums, and a cut pixel's map entry is zero
+      // from its plan's creation on: both cost two loads and no float64 work
       const float4 v = bins[p];
-      bins[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-      const double sv[4] = {v.x, v.y, v.z, v.w};
+      if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+        bins[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!mask[p]) continue;
+      const float sv[4] = {v.x, v.y, v.z, v.w};
       double s[NC], m[NC];
 #pragma unroll
-      for (int j = 0; j < NC; ++j) s[j] = sv[j];
-      if (mask[p]) {
-        double mi[NM];
+      for (int j = 0; j < NC; ++j) s[j] = f64_of_f32(sv[j]);
+      double mi[NM];
 #pragma unroll
-        for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
-        sym_mul<NC>(mi, s, m);
-      } else {
-#pragma unroll
-        for (int j = 0; j < NC; ++j) m[j] = 0.0;
-      }
+      for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
+      sym_mul<NC>(mi, s, m);
       float o4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < NC; ++j) o4[j] = (float)m[j];
