@@ -397,6 +397,8 @@ ds_status ds::plan_create(const ds_desc* desc, const ds_exchange* ex, const int3
   if (e == cudaSuccess) e = cudaMemsetAsync(P->x, 0, sizeof(double) * P->n_u, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->map32, 0, sizeof(float) * P->npix * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->map64, 0, sizeof(double) * P->npix * 4, st);
+  // cut pixels keep a zero map from here on (the batched pixel solves skip them)
+  if (e == cudaSuccess && P->maplo) e = cudaMemsetAsync(P->maplo, 0, sizeof(float) * P->npix * 4, st);
   if (e != cudaSuccess) {
     plan_free(P);
     return DS_ECUDA;

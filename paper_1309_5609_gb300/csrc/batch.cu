@@ -433,21 +433,23 @@ __global__ void __launch_bounds__(kBlock) k_bb_pixel_solve_df(const SlotDesc* __
     const uint8_t* __restrict__ mask = slots[T.slot].mask;
     const double* __restrict__ minv = slots[T.slot].minv;
     for (int64_t p = T.begin + threadIdx.x; p < T.end; p += blockDim.x) {
+      // as in the float32 pass: untouched pixels (zero sums) and cut ones (a zero map
+      // from the plan's creation on) cost loads only
       double s[NC], m[NC];
+      bool touched = false;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         s[j] = bins[4 * p + j];
-        bins[4 * p + j] = 0.0;
+        touched |= s[j] != 0.0;
       }
-      if (mask[p]) {
-        double mi[NM];
+      if (touched)
 #pragma unroll
-        for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
-        sym_mul<NC>(mi, s, m);
-      } else {
+        for (int j = 0; j < NC; ++j) bins[4 * p + j] = 0.0;
+      if (!mask[p]) continue;
+      double mi[NM];
 #pragma unroll
-        for (int j = 0; j < NC; ++j) m[j] = 0.0;
-      }
+      for (int j = 0; j < NM; ++j) mi[j] = minv[p * NM + j];
+      sym_mul<NC>(mi, s, m);
       float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
