@@ -331,7 +331,9 @@ def run_reference(args):
         cfg.update(workload=f"{cfg['workload']}-prefix{n}", n_samples=n,
                    unknowns=len(prob.kinds) * (-(-n // prob.baseline_len)),
                    full_workload=config_dict(args)["workload"],
-                   full_n_samples=config_dict(args)["n_samples"])
+                   full_n_samples=config_dict(args)["n_samples"],
+                   l2=f"host run: the oracle on a {n}-sample prefix ({12 * n / 1e6:.0f} MB "
+                      "of pointing) on the host cores; the GPU's L2 does not apply")
     else:
         cfg = {"workload": name, "n_samples": n}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
