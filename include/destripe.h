@@ -157,7 +157,10 @@ ds_status destripe_rhs(ds_plan_t plan, const void* d_y, double* d_b);
  *              gauge-fixed (outputs carrying I get zero mean over baselines with data;
  *              baselines without data are 0)
  *   tol        stop when ||b - A a|| / ||b|| < tol (recursive residual, confirmed by a
- *              float64 residual in MIXED mode)
+ *              float64 residual in MIXED mode).  For outputs carrying I, b's component
+ *              along the null mode (rounding only, b lying in the range of A) is
+ *              removed first, so that a right-hand side of rounding size (a noiseless
+ *              sky) converges to null baselines
  *   max_iter   iteration cap (<= 0 means 10000)
  *   iters, rel_resid  host outputs (may be NULL): iterations run and the float64
  *              relative residual at exit
